@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 chaotic video cipher (arXiv 2302.07411), one JSON line.
+
+Workload (default): the 240-frame 768 x 768 x 3 uint8 smooth synthetic clip
+(gradients + 8 moving Gaussian blobs + N(0, 4^2) noise), n = 4096 subframes,
+r = 5 rounds, PLCM key from a seed.  One step = encrypt the whole clip through
+the C ABI (keystream + confusion + diffusion of all frames, inputs resident in
+HBM); the stream state carries from step to step as it would in a long video.
+The 240 input frames (425 MB) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): every rank encrypts its own stream
+(its own key) on its own GPU -- replicas with no collective on the data path;
+value = total pixels of all ranks / max step time ("scaling": "weak").
+--impl reference times the CPU oracle (the plain single-threaded C
+implementation) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "5-round enc Mpixel/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--map", choices=["plcm", "2dlasm"], default="plcm")
+    ap.add_argument("--frames", type=int, default=240)
+    ap.add_argument("--size", type=int, default=768)
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--rounds", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return f"{a.frames}-frame {a.size}x{a.size}x3 smooth clip, n={a.n}, r={a.rounds}, {a.map.upper()}"
+
+
+def config(a, world: int) -> dict:
+    return {"workload": workload_name(a), "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
+            "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
+            "l2": "inputs 425 MB > 129 MB L2, no flush"}
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid: str | None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_uuid:
+            cmd += ["-i", gpu_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.tmp.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle timing
+
+def time_oracle(a, budget_s: float, seed_frames):
+    """The oracle as it stands, single thread, on consecutive frames of the
+    workload until the time budget is used (at least one frame)."""
+    import oracle
+    import synth
+
+    kind = 0 if a.map == "plcm" else 1
+    c = oracle.OracleCipher(kind, synth.key_for_seed(kind, 100), a.size, a.size, 3, a.n, a.rounds)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        c.encrypt(seed_frames[done % len(seed_frames)])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= a.frames:
+            break
+    return done, el
+
+
+def run_reference(a) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+
+    frames = synth.smooth_clip(4, a.size, a.size, 3, seed=3)
+    px = a.size * a.size
+    # each step: a bounded sample (enough consecutive frames for ~budget/steps seconds)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        time_oracle(a, per_step / 4, frames)
+    tot_frames, tot_s = 0, 0.0
+    for _ in range(a.steps):
+        n, s = time_oracle(a, per_step, frames)
+        tot_frames += n
+        tot_s += s
+    value = tot_frames * px / tot_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * tot_s / a.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u8",
+            "data": "synthetic", "config": config(a, 1),
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{tot_frames} consecutive frames of the workload ({per_step:.0f} s per step)"},
+            "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(a) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import synth
+    from paper_2302_07411_gb300 import binding as B
+    from paper_2302_07411_gb300 import build as cuda_build
+
+    cuda_build.build()
+    kind = B.VC_PLCM if a.map == "plcm" else B.VC_2DLASM
+    F, H, W, Cc = a.frames, a.size, a.size, 3
+    N = H * W * Cc
+    X = synth.smooth_clip(F, H, W, Cc, seed=3)
+    d_in = torch.from_numpy(X).cuda()
+    d_out = torch.empty_like(d_in)
+    key = synth.key_for_seed(kind, 100 + rank)
+    ciph = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
+    ciph.set_chunk(F)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ciph.encrypt(d_in, d_out, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ciph.sync()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    B.enc_profile_enable(ciph.ctx, True)
+    B.enc_profile_read(ciph.ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / a.steps
+    prof = B.enc_profile_read(ciph.ctx)
+    B.enc_profile_enable(ciph.ctx, False)
+    clk = clocks.stop()
+    ciph.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    px_step = F * H * W
+    value = world * px_step / (ms * 1e-3) / 1e6
+
+    # ---- end to end: host buffers through crypt_frames_host, copies inside
+    e2e = None
+    if not a.no_e2e:
+        h_in = torch.from_numpy(X).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        ce = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
+        ce.set_chunk(max(1, F // 4))
+        for _ in range(max(1, a.warmup - 1)):
+            ce.crypt_host(0, h_in, h_out, stream=stream)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        k2 = max(1, a.steps)
+        for _ in range(k2):
+            ce.crypt_host(0, h_in, h_out, stream=stream)
+        el = (time.perf_counter() - t0) / k2
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": round(world * px_step / el / 1e6, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": F * N,
+               "d2h_bytes_per_step": F * N, "ms_per_step": round(el * 1e3, 3)}
+        ce.close()
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel (keystream) and the split
+    peaks = load_peaks()
+    ks_ms = prof["keystream"]["ms"] / max(1, prof["keystream"]["launches"])
+    rd_ms = prof["rounds"]["ms"] / max(1, a.steps)
+    sc_ms = prof["schedule"]["ms"] / max(1, a.steps)
+    iters_per_launch = F * a.n * 0  # filled below
+    step_bytes = a.rounds * N  # keystream bytes per frame
+    if a.map == "plcm":
+        iters = F * (a.rounds * N) / 6.0 * 2  # two PLCM iterations per 6 bytes
+    else:
+        iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 bytes
+    iters_per_launch = iters
+    achieved_iter = iters_per_launch / (ks_ms * 1e-3)
+    # FP64 ceiling: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz = 629e9 FP64 instr/s;
+    # binary64 instructions per map iteration (branch-free PLCM: 2 compares,
+    # 2 subtractions, one IEEE division of ~8 FP64 instructions) ~ 12.
+    fp64_per_iter = 12.0 if a.map == "plcm" else 60.0
+    peak_fp64 = 152 * 2 * 2.07e9
+    peak_iter = peak_fp64 / fp64_per_iter
+    roofline = {"bound": "alu", "kernel": "k_keystream", "unit": "Giter/s",
+                "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
+                "frac": round(achieved_iter / peak_iter, 4), "traffic": None,
+                "peak_basis": f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration",
+                "launch_ms": round(ks_ms, 3)}
+    hbm = peaks.get("hbm_gbs")
+    alg_bytes = 2 * N * F  # plaintext read once + ciphertext written once
+    split = {"keystream_ms": round(ks_ms, 3), "rounds_ms": round(rd_ms, 3), "schedule_ms": round(sc_ms, 3),
+             "hbm_bound_ms": round(alg_bytes / (hbm * 1e9) * 1e3, 4) if hbm else None}
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        n_fr, s = time_oracle(a, a.cpu_seconds, X[:8])
+        cpu = {"value": round(n_fr * H * W / s / 1e6, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_fr} consecutive frames of the workload, single thread, {s:.1f} s"}
+
+    launches = sum(v["launches"] for v in prof.values())
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+u8", "data": "synthetic", "config": config(a, world),
+            "roofline": roofline, "split": split, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    ciph.close()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

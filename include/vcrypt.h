@@ -1,0 +1,143 @@
+/*
+ * vcrypt.h -- C ABI of the GB300 (sm_103a) implementation of the chaotic video
+ * cipher of "Real-time chaotic video encryption based on multithreaded
+ * parallel confusion and diffusion" (arXiv 2302.07411).
+ *
+ * The cipher (Sec. 2, Alg. 1, Alg. 2): a key K seeds a main chaotic PRBG_m
+ * whose output gives every subframe i its own PRBG_a^i (two PLCMs, Eq. 5, or
+ * two 2DLASMs, Eq. 6; Sec. 3) and gives every frame a confusion seed s_c.  Each
+ * frame then goes through r rounds of whole-frame confusion (Eq. 1) followed by
+ * per-subframe diffusion with ciphertext feedback (Eq. 3); decryption applies
+ * Eq. 4 and Eq. 2 in reverse round order.
+ *
+ * Conventions for every entry point:
+ *  - Frames are H x W x C uint8 in HWC order (row-major, channel fastest),
+ *    N = H*W*C bytes per frame, consecutive frames N bytes apart.
+ *  - Device pointers are CUDA device memory of the current device; the caller
+ *    owns them.  Host pointers are ordinary (preferably pinned) host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is stream-ordered; a call returns once its work is enqueued,
+ *    except where stated.
+ *  - Every function returns VC_OK (0) or a VC_ERR_* code; none throws, none
+ *    aborts.  On error nothing of the call's frames has been consumed from the
+ *    keystream unless stated.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef VCRYPT_H
+#define VCRYPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define VC_OK 0
+#define VC_ERR_ARG 1        /* null pointer, negative count, bad enum */
+#define VC_ERR_KEY_RANGE 2  /* key outside the valid ranges of Eq. 5 / Eq. 6 */
+#define VC_ERR_LAYOUT 3     /* H, W < 1; C not in {1,3,4}; n < 1; a subframe below 2 bytes; sizes too large */
+#define VC_ERR_CUDA 4       /* a CUDA runtime call failed (message: vc_last_error) */
+#define VC_ERR_OOM 5        /* device or host allocation failed */
+#define VC_ERR_TIMEOUT 6    /* a bounded device-side wait gave up */
+#define VC_ERR_SEQUENCE 7   /* frame submitted out of the stream's order */
+#define VC_ERR_STATE 8      /* malformed checkpoint blob */
+#define VC_ERR_UNSUPPORTED 9
+
+/* ---- chaotic map of the PRBGs (Sec. 3) ---- */
+#define VC_PLCM 0   /* key k = {x0^1, p^1, x0^2, p^2}: x0 in (0,1), p in (0, 1/2)        (Eq. 5) */
+#define VC_2DLASM 1 /* key k = {x0, mu, y0, unused}: x0, y0 in (0,1),
+                       mu in [.37,.38] u [.4,.42] u [.44,.93] u {1}                       (Eq. 6) */
+
+typedef struct {
+  int32_t kind;  /* VC_PLCM or VC_2DLASM */
+  double k[4];   /* the key K of Alg. 1 (Sec. 5.1: four or three doubles) */
+} vc_key;
+
+typedef struct {
+  int32_t height;      /* H, rows (the paper's frames are square, w x w) */
+  int32_t width;       /* W, columns */
+  int32_t channels;    /* C: 1, 3 (RGB, the paper's case) or 4 */
+  int32_t n_subframes; /* n of Alg. 1 / Alg. 2: subframe i is pixels [floor(iP/n), floor((i+1)P/n)) */
+  int32_t rounds;      /* r of Alg. 1, 1..16 (the paper uses 5, Sec. 6) */
+} vc_layout;
+
+typedef struct vc_ctx vc_ctx;
+
+/* Create a cipher context for one video stream on the current CUDA device.
+ * Validates the key (Eq. 5 / Eq. 6 ranges) and the layout, allocates the
+ * device-resident chaotic state, and runs the key schedule of Alg. 1 (PRBG_m
+ * keyed by K -> the parameters P_m of every PRBG_a^i) on the device
+ * (synchronously).  Limits: H, W <= 16384, N = H*W*C < 2^31, n <= H*W, every
+ * subframe >= 2 bytes.  *out receives the context (owned by the caller; free
+ * with enc_destroy).  Errors: VC_ERR_ARG, VC_ERR_KEY_RANGE, VC_ERR_LAYOUT,
+ * VC_ERR_OOM, VC_ERR_CUDA. */
+int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out);
+
+/* Encrypt nframes >= 0 consecutive frames of the stream (Alg. 1: per frame
+ * s_c from PRBG_m; Alg. 2: r rounds of Eq. 1 then Eq. 3).  d_in and d_out are
+ * device buffers of nframes*N bytes; d_in == d_out (in place) is allowed,
+ * other overlap is not.  Advances the stream by nframes frames.  Errors:
+ * VC_ERR_ARG, VC_ERR_CUDA. */
+int encrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
+
+/* Decrypt nframes consecutive frames (Eq. 4 then Eq. 2, rounds r-1..0), same
+ * buffers, ordering and errors as encrypt_frames.  A decrypting context made
+ * from the same key and layout reproduces the encrypting context's keystream
+ * frame for frame. */
+int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
+
+/* encrypt_frames / decrypt_frames on HOST buffers: copies h_in to the device,
+ * runs the cipher, copies the result to h_out, in chunks that overlap copies
+ * with compute; returns after the result is in h_out (synchronous).  direction
+ * 0 = encrypt, 1 = decrypt.  Errors as above plus VC_ERR_OOM. */
+int crypt_frames_host(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
+                      void* stream);
+
+/* Size in bytes of a checkpoint of the context's stream state (chaotic map
+ * values, pending keystream bytes, PRBG_m, frame counter). */
+size_t enc_state_size(const vc_ctx* ctx);
+
+/* Write the checkpoint into buf (host, *len >= enc_state_size); synchronises
+ * the context's last stream.  *len receives the size.  Errors: VC_ERR_ARG,
+ * VC_ERR_CUDA. */
+int enc_save_state(vc_ctx* ctx, void* buf, size_t* len);
+
+/* Restore a checkpoint taken from a context with the same key kind and layout.
+ * Errors: VC_ERR_ARG, VC_ERR_STATE (size/layout mismatch), VC_ERR_CUDA. */
+int enc_load_state(vc_ctx* ctx, const void* buf, size_t len);
+
+/* Frames consumed so far by this context. */
+int64_t enc_frame_index(const vc_ctx* ctx);
+
+/* Synchronise the context's last stream and return the first error recorded
+ * by its device code or its asynchronous CUDA work (VC_OK if none); clears it. */
+int enc_sync_status(vc_ctx* ctx);
+
+/* Upper bound on frames processed per internal pass (scratch memory grows with
+ * it: about (r + 2) * N bytes per frame).  Default 32. */
+int enc_set_chunk(vc_ctx* ctx, int32_t frames_per_pass);
+
+/* Stage timing for profiling.  While enabled, every pass brackets its stages
+ * with CUDA events recorded on the pass's stream: 0 = frame schedule (s_c and
+ * the Eq. 1 shift table), 1 = keystream kernel, 2 = round kernels (all r rounds
+ * and the diffusion fix-up).  Errors: VC_ERR_ARG. */
+int enc_profile_enable(vc_ctx* ctx, int32_t enable);
+
+/* Device milliseconds and kernel launches per stage accumulated since the last
+ * read (ms3[3], launches3[3]); synchronises the recorded events and resets
+ * the counters.  Errors: VC_ERR_ARG, VC_ERR_CUDA. */
+int enc_profile_read(vc_ctx* ctx, double* ms3, int64_t* launches3);
+
+/* Release the context and its device memory (synchronises its stream). */
+void enc_destroy(vc_ctx* ctx);
+
+/* Human-readable text of a status code; last CUDA error text of this thread. */
+const char* vc_strerror(int code);
+const char* vc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCRYPT_H */

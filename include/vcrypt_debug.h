@@ -1,0 +1,41 @@
+/*
+ * vcrypt_debug.h -- diagnostic entry points of the CUDA library, used by the
+ * tests to compare single stages with an independent CPU implementation.
+ * Same conventions as vcrypt.h (device pointers, stream-ordered, status codes).
+ */
+#ifndef VCRYPT_DEBUG_H
+#define VCRYPT_DEBUG_H
+
+#include <stdint.h>
+
+#include "vcrypt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* out[i] = the cipher's sine of t[i] (the reading of "sin" in Eq. 1 / Eq. 6:
+ * Cody-Waite reduction by pi/2, Taylor polynomials by Horner), n doubles each. */
+int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream);
+
+/* out[i] = one PLCM step F(x[i], p[i]) (Eq. 5). */
+int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, void* stream);
+
+/* One 2DLASM step (Eq. 6): in = n triples (x, y, mu), out = n pairs (x', y'). */
+int vc_dbg_lasm(const double* d_xymu, double* d_out, int64_t n, void* stream);
+
+/* The keystream the next nframes frames of the stream would use, advancing the
+ * stream exactly as encrypt_frames would: d_ks receives nframes*rounds*N bytes
+ * laid out [frame][round][frame byte q] (the byte diffused into position q in
+ * that round, Eq. 3), d_sc the frames' confusion seeds s_c (Alg. 1). */
+int vc_dbg_keystream(vc_ctx* ctx, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, void* stream);
+
+/* Internal geometry, for tests: {rows per tile, tiles per frame, padded frame
+ * stride, N, P, scratch frames allocated, frames per pass, round-kernel shared
+ * memory bytes}. */
+int vc_dbg_layout(const vc_ctx* ctx, int32_t* out8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCRYPT_DEBUG_H */

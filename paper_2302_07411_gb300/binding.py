@@ -1,0 +1,264 @@
+"""Thin Python binding of the C ABI in include/vcrypt.h (ctypes).
+
+Argument marshalling only: every step of the cipher runs in libvcrypt.so's
+CUDA kernels.  PyTorch supplies device memory (tensors) and the current CUDA
+stream.  The functions carry the C names; ``Cipher`` wraps a context.
+If the library is not built this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvcrypt.so")
+_lib = None
+
+VC_OK = 0
+VC_PLCM, VC_2DLASM = 0, 1
+ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
+          6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
+
+
+class VcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().vc_last_error().decode(errors="replace") if _lib is not None else ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class vc_key(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("k", C.c_double * 4)]
+
+
+class vc_layout(C.Structure):
+    _fields_ = [("height", C.c_int32), ("width", C.c_int32), ("channels", C.c_int32),
+                ("n_subframes", C.c_int32), ("rounds", C.c_int32)]
+
+
+def lib():
+    """Load libvcrypt.so (built by paper_2302_07411_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        p, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        sig = {
+            "enc_init": (C.c_int, [p, p, p]),
+            "encrypt_frames": (C.c_int, [p, p, p, i32, p]),
+            "decrypt_frames": (C.c_int, [p, p, p, i32, p]),
+            "crypt_frames_host": (C.c_int, [p, i32, p, p, i32, p]),
+            "enc_state_size": (sz, [p]),
+            "enc_save_state": (C.c_int, [p, p, C.POINTER(C.c_size_t)]),
+            "enc_load_state": (C.c_int, [p, p, sz]),
+            "enc_frame_index": (i64, [p]),
+            "enc_sync_status": (C.c_int, [p]),
+            "enc_set_chunk": (C.c_int, [p, i32]),
+            "enc_destroy": (None, [p]),
+            "enc_profile_enable": (C.c_int, [p, i32]),
+            "enc_profile_read": (C.c_int, [p, p, p]),
+            "vc_strerror": (C.c_char_p, [C.c_int]),
+            "vc_last_error": (C.c_char_p, []),
+            "vc_dbg_csin": (C.c_int, [p, p, i64, p]),
+            "vc_dbg_plcm": (C.c_int, [p, p, p, i64, p]),
+            "vc_dbg_lasm": (C.c_int, [p, p, i64, p]),
+            "vc_dbg_keystream": (C.c_int, [p, p, p, i32, p]),
+            "vc_dbg_layout": (C.c_int, [p, p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != VC_OK:
+        raise VcError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    if t.device.type != "cuda":
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a contiguous array")
+        return C.c_void_p(a.ctypes.data)
+    if a.device.type != "cpu" or not a.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    return C.c_void_p(a.data_ptr())
+
+
+# ---- C names ---------------------------------------------------------------
+
+def enc_init(kind: int, key, height: int, width: int, channels: int = 3, n_subframes: int = 4,
+             rounds: int = 5) -> C.c_void_p:
+    k = vc_key(kind, (C.c_double * 4)(*([float(v) for v in key] + [0.0] * (4 - len(key)))))
+    lay = vc_layout(height, width, channels, n_subframes, rounds)
+    ctx = C.c_void_p()
+    _check(lib().enc_init(C.byref(k), C.byref(lay), C.byref(ctx)), "enc_init")
+    return ctx
+
+
+def encrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
+    _check(lib().encrypt_frames(ctx, _dptr(d_in), _dptr(d_out), nframes, _stream(stream)), "encrypt_frames")
+
+
+def decrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
+    _check(lib().decrypt_frames(ctx, _dptr(d_in), _dptr(d_out), nframes, _stream(stream)), "decrypt_frames")
+
+
+def crypt_frames_host(ctx, direction: int, h_in, h_out, nframes: int, stream=None) -> None:
+    _check(lib().crypt_frames_host(ctx, direction, _hptr(h_in), _hptr(h_out), nframes, _stream(stream)),
+           "crypt_frames_host")
+
+
+def enc_save_state(ctx) -> bytes:
+    n = lib().enc_state_size(ctx)
+    buf = (C.c_uint8 * n)()
+    ln = C.c_size_t(n)
+    _check(lib().enc_save_state(ctx, buf, C.byref(ln)), "enc_save_state")
+    return bytes(buf)
+
+
+def enc_load_state(ctx, state: bytes) -> None:
+    buf = (C.c_uint8 * len(state)).from_buffer_copy(state)
+    _check(lib().enc_load_state(ctx, buf, len(state)), "enc_load_state")
+
+
+def enc_frame_index(ctx) -> int:
+    return lib().enc_frame_index(ctx)
+
+
+def enc_sync_status(ctx) -> None:
+    _check(lib().enc_sync_status(ctx), "enc_sync_status")
+
+
+def enc_set_chunk(ctx, frames: int) -> None:
+    _check(lib().enc_set_chunk(ctx, frames), "enc_set_chunk")
+
+
+def enc_profile_enable(ctx, enable: bool) -> None:
+    _check(lib().enc_profile_enable(ctx, 1 if enable else 0), "enc_profile_enable")
+
+
+def enc_profile_read(ctx) -> dict:
+    ms = (C.c_double * 3)()
+    ln = (C.c_int64 * 3)()
+    _check(lib().enc_profile_read(ctx, ms, ln), "enc_profile_read")
+    names = ("schedule", "keystream", "rounds")
+    return {nm: {"ms": ms[i], "launches": ln[i]} for i, nm in enumerate(names)}
+
+
+def enc_destroy(ctx) -> None:
+    lib().enc_destroy(ctx)
+
+
+def vc_dbg_csin(d_t, d_out, stream=None) -> None:
+    _check(lib().vc_dbg_csin(_dptr(d_t), _dptr(d_out), d_t.numel(), _stream(stream)), "vc_dbg_csin")
+
+
+def vc_dbg_plcm(d_x, d_p, d_out, stream=None) -> None:
+    _check(lib().vc_dbg_plcm(_dptr(d_x), _dptr(d_p), _dptr(d_out), d_x.numel(), _stream(stream)), "vc_dbg_plcm")
+
+
+def vc_dbg_lasm(d_xymu, d_out, stream=None) -> None:
+    _check(lib().vc_dbg_lasm(_dptr(d_xymu), _dptr(d_out), d_xymu.numel() // 3, _stream(stream)), "vc_dbg_lasm")
+
+
+def vc_dbg_keystream(ctx, d_ks, d_sc, nframes: int, stream=None) -> None:
+    _check(lib().vc_dbg_keystream(ctx, _dptr(d_ks), _dptr(d_sc), nframes, _stream(stream)), "vc_dbg_keystream")
+
+
+def vc_dbg_layout(ctx) -> dict:
+    out = (C.c_int32 * 8)()
+    _check(lib().vc_dbg_layout(ctx, out), "vc_dbg_layout")
+    return dict(zip(["T", "NT", "Npad", "N", "P", "cap", "chunk", "smem"], list(out)))
+
+
+# ---- convenience wrapper -----------------------------------------------------
+
+class Cipher:
+    """One video stream: key, layout and device-resident chaotic state."""
+
+    def __init__(self, kind: int, key, height: int, width: int, channels: int = 3, n_subframes: int = 4,
+                 rounds: int = 5):
+        self.kind, self.H, self.W, self.C = kind, height, width, channels
+        self.n, self.rounds = n_subframes, rounds
+        self.N = height * width * channels
+        self.ctx = enc_init(kind, key, height, width, channels, n_subframes, rounds)
+
+    def encrypt(self, d_in, d_out=None, stream=None):
+        """Encrypt a (F, H, W, C) uint8 CUDA tensor; returns the ciphertext tensor."""
+        import torch
+
+        if d_out is None:
+            d_out = torch.empty_like(d_in)
+        nframes = d_in.numel() // self.N
+        assert d_in.numel() == nframes * self.N and d_in.dtype == torch.uint8
+        encrypt_frames(self.ctx, d_in, d_out, nframes, stream)
+        return d_out
+
+    def decrypt(self, d_in, d_out=None, stream=None):
+        import torch
+
+        if d_out is None:
+            d_out = torch.empty_like(d_in)
+        nframes = d_in.numel() // self.N
+        assert d_in.numel() == nframes * self.N and d_in.dtype == torch.uint8
+        decrypt_frames(self.ctx, d_in, d_out, nframes, stream)
+        return d_out
+
+    def crypt_host(self, direction: int, h_in, h_out, stream=None) -> None:
+        nframes = (h_in.size if isinstance(h_in, np.ndarray) else h_in.numel()) // self.N
+        crypt_frames_host(self.ctx, direction, h_in, h_out, nframes, stream)
+
+    def save_state(self) -> bytes:
+        return enc_save_state(self.ctx)
+
+    def load_state(self, state: bytes) -> None:
+        enc_load_state(self.ctx, state)
+
+    @property
+    def frame_index(self) -> int:
+        return enc_frame_index(self.ctx)
+
+    def sync(self) -> None:
+        enc_sync_status(self.ctx)
+
+    def set_chunk(self, frames: int) -> None:
+        enc_set_chunk(self.ctx, frames)
+
+    def layout_info(self) -> dict:
+        return vc_dbg_layout(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            enc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

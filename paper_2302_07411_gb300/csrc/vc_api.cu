@@ -1,0 +1,606 @@
+// vc_api.cu -- the C ABI of include/vcrypt.h and include/vcrypt_debug.h:
+// argument checks, device memory of a stream context, and the order of the
+// kernel launches of one pass (Alg. 1 / Alg. 2 on the GPU).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vc_internal.h"
+#include "vcrypt.h"
+#include "vcrypt_debug.h"
+
+using vc::Layout;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define VC_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return VC_ERR_CUDA;                                                                  \
+    }                                                                                      \
+  } while (0)
+
+constexpr size_t kTileBudget = 96 * 1024;  // bytes of one row-band tile in shared memory
+constexpr uint32_t kStateMagic = 0x56435354u;  // "VCST"
+constexpr uint32_t kStateVersion = 1;
+
+bool key_valid(const vc_key& k) {
+  if (k.kind == VC_PLCM) {
+    for (int i = 0; i < 4; i += 2)
+      if (!(k.k[i] > 0.0 && k.k[i] < 1.0 && k.k[i + 1] > 0.0 && k.k[i + 1] < 0.5)) return false;
+    return true;
+  }
+  if (k.kind == VC_2DLASM) {
+    const double mu = k.k[1];
+    const bool mu_ok = (mu >= 0.37 && mu <= 0.38) || (mu >= 0.4 && mu <= 0.42) || (mu >= 0.44 && mu <= 0.93) ||
+                       mu == 1.0;
+    return k.k[0] > 0.0 && k.k[0] < 1.0 && k.k[2] > 0.0 && k.k[2] < 1.0 && mu_ok;
+  }
+  return false;
+}
+
+// Geometry checks and the tile shape of the round kernels.
+int make_layout(const vc_layout& l, Layout* L) {
+  if (l.height < 1 || l.width < 1 || l.height > 16384 || l.width > 16384) return VC_ERR_LAYOUT;
+  if (!(l.channels == 1 || l.channels == 3 || l.channels == 4)) return VC_ERR_LAYOUT;
+  if (l.rounds < 1 || l.rounds > 16 || l.n_subframes < 1) return VC_ERR_LAYOUT;
+  const long long P = (long long)l.height * l.width;
+  const long long N = P * l.channels;
+  if (N >= (1LL << 31) - 4096) return VC_ERR_LAYOUT;
+  if (l.n_subframes > P) return VC_ERR_LAYOUT;
+  if ((long long)l.channels * (P / l.n_subframes) < 2) return VC_ERR_LAYOUT;  // every subframe >= 2 bytes
+  const long long rowb = (long long)l.width * l.channels;
+  if (rowb > vc::kMaxRowBytes) return VC_ERR_LAYOUT;
+  int T = 32;
+  while (T > 1 && (size_t)T * rowb > kTileBudget) T >>= 1;
+  const int NT = (l.height + T - 1) / T;
+  if (NT > vc::kMaxTiles) return VC_ERR_LAYOUT;
+  L->H = l.height;
+  L->W = l.width;
+  L->C = l.channels;
+  L->n = l.n_subframes;
+  L->rounds = l.rounds;
+  L->P = (int)P;
+  L->N = (int)N;
+  L->Npad = (N + 255) & ~255LL;
+  L->T = T;
+  L->NT = NT;
+  return VC_OK;
+}
+
+}  // namespace
+
+struct vc_ctx {
+  int kind = 0;
+  Layout L{};
+  int dev = 0;
+  // partition tables
+  int* d_pi = nullptr;
+  uint32_t* d_sbits = nullptr;
+  int* d_srank = nullptr;
+  int* d_fixlim = nullptr;
+  // stream state
+  vc::MainPrbg* d_main = nullptr;
+  double* d_st = nullptr;
+  double* d_par = nullptr;
+  uint64_t* d_carry = nullptr;
+  int* d_carry_len = nullptr;
+  // per-pass scratch, sized for `cap` frames
+  int chunk = 32;
+  int cap = 0;
+  uint8_t* d_ks = nullptr;
+  uint8_t* d_buf[2] = {nullptr, nullptr};
+  uint8_t* d_agg[2] = {nullptr, nullptr};
+  long long* d_sc = nullptr;
+  int* d_kmod = nullptr;
+  // staging for host-buffer calls
+  uint8_t* d_io[2] = {nullptr, nullptr};
+  int io_cap = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev[6] = {};
+  int64_t frame = 0;
+  cudaStream_t last = nullptr;
+  // stage profiling: recorded (stage, start, end) event pairs and a free pool
+  bool prof = false;
+  struct Mark {
+    int stage, launches;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+
+  vc::Tables tables() const { return vc::Tables{d_pi, d_sbits, d_srank, d_fixlim}; }
+  vc::Chains chains() const { return vc::Chains{d_st, d_par, d_carry, d_carry_len}; }
+  int state_words() const { return kind == VC_PLCM ? 2 : 4; }
+  int par_words() const { return kind == VC_PLCM ? 4 : 2; }
+};
+
+namespace {
+
+void free_scratch(vc_ctx* c) {
+  cudaFree(c->d_ks);
+  cudaFree(c->d_buf[0]);
+  cudaFree(c->d_buf[1]);
+  cudaFree(c->d_agg[0]);
+  cudaFree(c->d_agg[1]);
+  cudaFree(c->d_sc);
+  cudaFree(c->d_kmod);
+  c->d_ks = c->d_buf[0] = c->d_buf[1] = c->d_agg[0] = c->d_agg[1] = nullptr;
+  c->d_sc = nullptr;
+  c->d_kmod = nullptr;
+  c->cap = 0;
+}
+
+int ensure_scratch(vc_ctx* c, int frames) {
+  if (frames <= c->cap) return VC_OK;
+  if (c->last) cudaStreamSynchronize(c->last);
+  free_scratch(c);
+  const Layout& L = c->L;
+  const size_t F = (size_t)frames;
+  if (cudaMalloc(&c->d_ks, F * L.rounds * L.Npad) != cudaSuccess ||
+      cudaMalloc(&c->d_buf[0], F * L.Npad) != cudaSuccess || cudaMalloc(&c->d_buf[1], F * L.Npad) != cudaSuccess ||
+      cudaMalloc(&c->d_agg[0], F * L.NT + 16) != cudaSuccess ||
+      cudaMalloc(&c->d_agg[1], F * L.NT + 16) != cudaSuccess || cudaMalloc(&c->d_sc, F * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&c->d_kmod, F * L.H * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    free_scratch(c);
+    set_err("cudaMalloc of %d frames of scratch failed", frames);
+    return VC_ERR_OOM;
+  }
+  c->cap = frames;
+  return VC_OK;
+}
+
+cudaEvent_t pool_event(vc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one stage of a pass with events when profiling is on.
+struct StageMark {
+  vc_ctx* c;
+  cudaStream_t st;
+  int stage, launches;
+  cudaEvent_t a = nullptr;
+  StageMark(vc_ctx* c_, cudaStream_t st_, int stage_, int launches_) : c(c_), st(st_), stage(stage_), launches(launches_) {
+    if (c->prof) {
+      a = pool_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~StageMark() {
+    if (a) {
+      cudaEvent_t b = pool_event(c);
+      cudaEventRecord(b, st);
+      c->marks.push_back(vc_ctx::Mark{stage, launches, a, b});
+    }
+  }
+};
+
+// One pass over nf <= cap frames (encrypt when dir == 0).  in/out strides in bytes.
+int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride, int nf,
+             cudaStream_t st) {
+  const Layout& L = c->L;
+  const vc::Tables tb = c->tables();
+  const long long ks_stride = (long long)L.rounds * L.Npad;
+  {
+    StageMark m(c, st, 0, 2);
+    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
+  }
+  {
+    StageMark m(c, st, 1, 1);
+    VC_CUDA(vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, st));
+  }
+  const int r = L.rounds;
+  StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
+  // with one round and in == out, the round cannot write its own input: go through a buffer
+  const bool bounce = (r == 1) && (in == out);
+  uint8_t* final_out = bounce ? c->d_buf[0] : out;
+  const long long final_stride = bounce ? L.Npad : out_stride;
+  for (int step = 0; step < r; step++) {
+    const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
+    const long long ss = step == 0 ? in_stride : L.Npad;
+    uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
+    const long long ds = step == r - 1 ? final_stride : L.Npad;
+    if (dir == 0) {
+      const int j = step;
+      VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, c->d_ks + (long long)j * L.Npad, ks_stride, c->d_kmod,
+                                   step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
+    } else {
+      const int j = r - 1 - step;
+      VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, c->d_ks + (long long)j * L.Npad, ks_stride, c->d_kmod,
+                                   nf, st));
+    }
+  }
+  if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
+  if (bounce)
+    VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
+                              cudaMemcpyDeviceToDevice, st));
+  return VC_OK;
+}
+
+int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nframes, void* stream) {
+  if (!c || nframes < 0 || (nframes > 0 && (!d_in || !d_out))) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  if (nframes == 0) return VC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last = st;
+  const int F = nframes < c->chunk ? nframes : c->chunk;
+  int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  const long long N = c->L.N;
+  for (int f0 = 0; f0 < nframes; f0 += F) {
+    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+    rc = run_pass(c, dir, d_in + f0 * N, N, d_out + f0 * N, N, nf, st);
+    if (rc) return rc;
+  }
+  c->frame += nframes;
+  return VC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vc_strerror(int code) {
+  switch (code) {
+    case VC_OK: return "ok";
+    case VC_ERR_ARG: return "invalid argument";
+    case VC_ERR_KEY_RANGE: return "key outside the valid ranges of the chaotic map";
+    case VC_ERR_LAYOUT: return "invalid frame layout or subframe count";
+    case VC_ERR_CUDA: return "CUDA error";
+    case VC_ERR_OOM: return "out of memory";
+    case VC_ERR_TIMEOUT: return "device wait timed out";
+    case VC_ERR_SEQUENCE: return "frame out of sequence";
+    case VC_ERR_STATE: return "malformed state checkpoint";
+    case VC_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* vc_last_error(void) { return g_err; }
+
+int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
+  if (!key || !layout || !out) {
+    set_err("null argument");
+    return VC_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!key_valid(*key)) {
+    set_err("key outside the valid ranges");
+    return VC_ERR_KEY_RANGE;
+  }
+  Layout L{};
+  int rc = make_layout(*layout, &L);
+  if (rc) {
+    set_err("invalid layout");
+    return rc;
+  }
+  vc_ctx* c = new (std::nothrow) vc_ctx();
+  if (!c) return VC_ERR_OOM;
+  c->kind = key->kind;
+  c->L = L;
+  cudaGetDevice(&c->dev);
+  const int n = L.n;
+  const int nwords = L.P / 32 + 2;
+  bool ok = cudaMalloc(&c->d_pi, sizeof(int) * (n + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_sbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
+            cudaMalloc(&c->d_srank, sizeof(int) * nwords) == cudaSuccess &&
+            cudaMalloc(&c->d_fixlim, sizeof(int) * L.NT) == cudaSuccess &&
+            cudaMalloc(&c->d_main, sizeof(vc::MainPrbg)) == cudaSuccess &&
+            cudaMalloc(&c->d_st, sizeof(double) * c->state_words() * n) == cudaSuccess &&
+            cudaMalloc(&c->d_par, sizeof(double) * c->par_words() * n) == cudaSuccess &&
+            cudaMalloc(&c->d_carry, sizeof(uint64_t) * 2 * n) == cudaSuccess &&
+            cudaMalloc(&c->d_carry_len, sizeof(int) * n) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    enc_destroy(c);
+    set_err("device allocation failed");
+    return VC_ERR_OOM;
+  }
+  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    enc_destroy(c);
+    set_err("stream creation failed");
+    return VC_ERR_CUDA;
+  }
+  for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  vc::MainPrbg m{};
+  m.kind = key->kind;
+  if (key->kind == VC_PLCM) {
+    for (int i = 0; i < 4; i++) m.s[i] = key->k[i];
+  } else {  // K = (x0, mu, y0) -> state (x, y, mu)
+    m.s[0] = key->k[0];
+    m.s[1] = key->k[2];
+    m.s[2] = key->k[1];
+  }
+  cudaStream_t st = c->copy_stream;
+  cudaError_t e = cudaMemcpyAsync(c->d_main, &m, sizeof(m), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = vc::launch_build_tables(L, c->d_pi, c->d_sbits, c->d_srank, c->d_fixlim, st);
+  if (e == cudaSuccess) e = vc::launch_key_schedule(c->kind, c->d_main, c->chains(), n, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_err("key schedule failed: %s", cudaGetErrorString(e));
+    enc_destroy(c);
+    return VC_ERR_CUDA;
+  }
+  *out = c;
+  return VC_OK;
+}
+
+int encrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream) {
+  return crypt_device(ctx, 0, d_in, d_out, nframes, stream);
+}
+
+int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream) {
+  return crypt_device(ctx, 1, d_in, d_out, nframes, stream);
+}
+
+int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
+                      void* stream) {
+  if (!c || nframes < 0 || (direction != 0 && direction != 1) || (nframes > 0 && (!h_in || !h_out))) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  if (nframes == 0) return VC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last = st;
+  const int F = nframes < c->chunk ? nframes : c->chunk;
+  int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  const size_t N = (size_t)c->L.N;
+  if (c->io_cap < F) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaFree(c->d_io[0]);
+    cudaFree(c->d_io[1]);
+    c->d_io[0] = c->d_io[1] = nullptr;
+    c->io_cap = 0;
+    if (cudaMalloc(&c->d_io[0], F * N) != cudaSuccess || cudaMalloc(&c->d_io[1], F * N) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("staging allocation failed");
+      return VC_ERR_OOM;
+    }
+    c->io_cap = F;
+  }
+  // copy stream: H2D(k) ... D2H(k); compute stream st: pass(k).  Buffers alternate.
+  cudaEvent_t* h2d = c->ev;      // [2]
+  cudaEvent_t* done = c->ev + 2; // [2]
+  int k = 0;
+  for (int f0 = 0; f0 < nframes; f0 += F, k++) {
+    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+    uint8_t* buf = c->d_io[k & 1];
+    VC_CUDA(cudaMemcpyAsync(buf, h_in + (size_t)f0 * N, nf * N, cudaMemcpyHostToDevice, c->copy_stream));
+    VC_CUDA(cudaEventRecord(h2d[k & 1], c->copy_stream));
+    VC_CUDA(cudaStreamWaitEvent(st, h2d[k & 1], 0));
+    rc = run_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st);
+    if (rc) return rc;
+    VC_CUDA(cudaEventRecord(done[k & 1], st));
+    VC_CUDA(cudaStreamWaitEvent(c->copy_stream, done[k & 1], 0));
+    VC_CUDA(cudaMemcpyAsync(h_out + (size_t)f0 * N, buf, nf * N, cudaMemcpyDeviceToHost, c->copy_stream));
+  }
+  VC_CUDA(cudaStreamSynchronize(c->copy_stream));
+  VC_CUDA(cudaStreamSynchronize(st));
+  c->frame += nframes;
+  return VC_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t kind, H, W, C, n, rounds;
+  int64_t frame;
+};
+}  // namespace
+
+size_t enc_state_size(const vc_ctx* c) {
+  if (!c) return 0;
+  const size_t n = (size_t)c->L.n;
+  return sizeof(StateHeader) + sizeof(vc::MainPrbg) + n * sizeof(double) * (c->state_words() + c->par_words()) +
+         n * 2 * sizeof(uint64_t) + n * sizeof(int);
+}
+
+int enc_save_state(vc_ctx* c, void* buf, size_t* len) {
+  if (!c || !buf || !len || *len < enc_state_size(c)) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  if (c->last) VC_CUDA(cudaStreamSynchronize(c->last));
+  VC_CUDA(cudaDeviceSynchronize());
+  const size_t n = (size_t)c->L.n;
+  uint8_t* p = static_cast<uint8_t*>(buf);
+  StateHeader h{kStateMagic, kStateVersion, c->kind, c->L.H, c->L.W, c->L.C, c->L.n, c->L.rounds, c->frame};
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  VC_CUDA(cudaMemcpy(p, c->d_main, sizeof(vc::MainPrbg), cudaMemcpyDeviceToHost));
+  p += sizeof(vc::MainPrbg);
+  VC_CUDA(cudaMemcpy(p, c->d_st, n * sizeof(double) * c->state_words(), cudaMemcpyDeviceToHost));
+  p += n * sizeof(double) * c->state_words();
+  VC_CUDA(cudaMemcpy(p, c->d_par, n * sizeof(double) * c->par_words(), cudaMemcpyDeviceToHost));
+  p += n * sizeof(double) * c->par_words();
+  VC_CUDA(cudaMemcpy(p, c->d_carry, n * 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  p += n * 2 * sizeof(uint64_t);
+  VC_CUDA(cudaMemcpy(p, c->d_carry_len, n * sizeof(int), cudaMemcpyDeviceToHost));
+  *len = enc_state_size(c);
+  return VC_OK;
+}
+
+int enc_load_state(vc_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  if (len != enc_state_size(c)) {
+    set_err("checkpoint size %zu does not match %zu", len, enc_state_size(c));
+    return VC_ERR_STATE;
+  }
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.version != kStateVersion || h.kind != c->kind || h.H != c->L.H ||
+      h.W != c->L.W || h.C != c->L.C || h.n != c->L.n || h.rounds != c->L.rounds || h.frame < 0) {
+    set_err("checkpoint header does not match this context");
+    return VC_ERR_STATE;
+  }
+  if (c->last) VC_CUDA(cudaStreamSynchronize(c->last));
+  const size_t n = (size_t)c->L.n;
+  const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof(h);
+  VC_CUDA(cudaMemcpy(c->d_main, p, sizeof(vc::MainPrbg), cudaMemcpyHostToDevice));
+  p += sizeof(vc::MainPrbg);
+  VC_CUDA(cudaMemcpy(c->d_st, p, n * sizeof(double) * c->state_words(), cudaMemcpyHostToDevice));
+  p += n * sizeof(double) * c->state_words();
+  VC_CUDA(cudaMemcpy(c->d_par, p, n * sizeof(double) * c->par_words(), cudaMemcpyHostToDevice));
+  p += n * sizeof(double) * c->par_words();
+  VC_CUDA(cudaMemcpy(c->d_carry, p, n * 2 * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  p += n * 2 * sizeof(uint64_t);
+  VC_CUDA(cudaMemcpy(c->d_carry_len, p, n * sizeof(int), cudaMemcpyHostToDevice));
+  c->frame = h.frame;
+  return VC_OK;
+}
+
+int64_t enc_frame_index(const vc_ctx* c) { return c ? c->frame : -1; }
+
+int enc_sync_status(vc_ctx* c) {
+  if (!c) return VC_ERR_ARG;
+  cudaError_t e = c->last ? cudaStreamSynchronize(c->last) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_err("asynchronous CUDA error: %s", cudaGetErrorString(e));
+    return VC_ERR_CUDA;
+  }
+  return VC_OK;
+}
+
+int enc_set_chunk(vc_ctx* c, int32_t frames_per_pass) {
+  if (!c || frames_per_pass < 1 || frames_per_pass > 65535) return VC_ERR_ARG;
+  c->chunk = frames_per_pass;
+  return VC_OK;
+}
+
+int enc_profile_enable(vc_ctx* c, int32_t enable) {
+  if (!c) return VC_ERR_ARG;
+  c->prof = enable != 0;
+  return VC_OK;
+}
+
+int enc_profile_read(vc_ctx* c, double* ms3, int64_t* launches3) {
+  if (!c || !ms3 || !launches3) return VC_ERR_ARG;
+  for (int i = 0; i < 3; i++) {
+    ms3[i] = 0.0;
+    launches3[i] = 0;
+  }
+  for (auto& m : c->marks) {
+    VC_CUDA(cudaEventSynchronize(m.b));
+    float ms = 0.f;
+    VC_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
+    ms3[m.stage] += ms;
+    launches3[m.stage] += m.launches;
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->marks.clear();
+  return VC_OK;
+}
+
+void enc_destroy(vc_ctx* c) {
+  if (!c) return;
+  if (c->last) cudaStreamSynchronize(c->last);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  free_scratch(c);
+  cudaFree(c->d_io[0]);
+  cudaFree(c->d_io[1]);
+  cudaFree(c->d_pi);
+  cudaFree(c->d_sbits);
+  cudaFree(c->d_srank);
+  cudaFree(c->d_fixlim);
+  cudaFree(c->d_main);
+  cudaFree(c->d_st);
+  cudaFree(c->d_par);
+  cudaFree(c->d_carry);
+  cudaFree(c->d_carry_len);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  delete c;
+}
+
+// ---- diagnostics (include/vcrypt_debug.h) ----
+
+int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_t || !d_out))) return VC_ERR_ARG;
+  VC_CUDA(vc::launch_dbg_csin(d_t, d_out, n, (cudaStream_t)stream));
+  return VC_OK;
+}
+
+int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_p || !d_out))) return VC_ERR_ARG;
+  VC_CUDA(vc::launch_dbg_plcm(d_x, d_p, d_out, n, (cudaStream_t)stream));
+  return VC_OK;
+}
+
+int vc_dbg_lasm(const double* d_xymu, double* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_xymu || !d_out))) return VC_ERR_ARG;
+  VC_CUDA(vc::launch_dbg_lasm(d_xymu, d_out, n, (cudaStream_t)stream));
+  return VC_OK;
+}
+
+int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, void* stream) {
+  if (!c || nframes < 0 || (nframes > 0 && (!d_ks || !d_sc))) return VC_ERR_ARG;
+  if (nframes == 0) return VC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last = st;
+  const Layout& L = c->L;
+  const int F = nframes < c->chunk ? nframes : c->chunk;
+  int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  for (int f0 = 0; f0 < nframes; f0 += F) {
+    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
+    VC_CUDA(vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, st));
+    VC_CUDA(cudaMemcpy2DAsync(d_ks + (size_t)f0 * L.rounds * L.N, (size_t)L.N, c->d_ks, (size_t)L.Npad, (size_t)L.N,
+                              (size_t)nf * L.rounds, cudaMemcpyDeviceToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(d_sc + f0, c->d_sc, nf * sizeof(long long), cudaMemcpyDeviceToDevice, st));
+  }
+  c->frame += nframes;
+  return VC_OK;
+}
+
+int vc_dbg_layout(const vc_ctx* c, int32_t* out8) {
+  if (!c || !out8) return VC_ERR_ARG;
+  out8[0] = c->L.T;
+  out8[1] = c->L.NT;
+  out8[2] = (int32_t)c->L.Npad;
+  out8[3] = c->L.N;
+  out8[4] = c->L.P;
+  out8[5] = c->cap;
+  out8[6] = c->chunk;
+  out8[7] = (int32_t)vc::round_smem_bytes(c->L);
+  return VC_OK;
+}
+
+}  // extern "C"

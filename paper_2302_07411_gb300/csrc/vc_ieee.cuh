@@ -1,0 +1,165 @@
+// vc_ieee.cuh -- IEEE-754 binary64 round-to-nearest-even subtraction and
+// division evaluated on the integer pipes.
+//
+// GB300 executes binary64 at 2 lanes per clock per SM with ~63-cycle latency,
+// while 32-bit integer multiply-adds run at 64 lanes per clock.  The PLCM
+// (Eq. 5) needs one binary64 division per iteration by one of two constants
+// of its chain (p or 1/2 - p).  These routines return exactly the correctly
+// rounded binary64 result (the value __ddiv_rn / __dsub_rn return) from
+// integer arithmetic:
+//  * division by a constant divisor b = mb 2^e: a precomputed reciprocal
+//    inv = floor(2^115 / mb) gives a quotient estimate within one unit
+//    (Granlund & Montgomery, "Division by invariant integers using
+//    multiplication", PLDI 1994), one correction step makes it exact, and the
+//    remainder decides round-to-nearest-even;
+//  * subtraction a - b, a >= b > 0: alignment with 10 guard bits and a sticky
+//    bit, then rounding of the dropped bits (the classical guard/round/sticky
+//    scheme of IEEE adders).
+// Operands or results outside the normal range are reported through `ok`
+// (false) and the caller falls back to the hardware operation, so the result
+// is correctly rounded for every input.
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+namespace vc {
+
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ uint64_t ieee_bits(double v) { return (uint64_t)__double_as_longlong(v); }
+__device__ __forceinline__ double ieee_double(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ uint64_t ieee_mulhi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+__device__ __forceinline__ int ieee_clz64(uint64_t v) { return __clzll((long long)v); }
+#else
+inline uint64_t ieee_bits(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  return b;
+}
+inline double ieee_double(uint64_t b) {
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+}
+inline uint64_t ieee_mulhi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+inline int ieee_clz64(uint64_t v) { return v ? __builtin_clzll(v) : 64; }
+#endif
+
+constexpr uint64_t kMant52 = (1ull << 52) - 1;
+
+// A positive normal binary64 divisor: mantissa with the hidden bit, biased
+// exponent and inv = floor(2^115 / mb) (in (2^62, 2^63]).
+struct Divisor {
+  uint64_t mb;
+  uint64_t inv;
+  int eb;
+};
+
+// floor(2^115 / m) for m in [2^52, 2^53): restoring long division, 63
+// quotient bits (used once per chain, off the hot loop).
+__host__ __device__ inline uint64_t recip115(uint64_t m) {
+  // 2^115 / m = 2^62 * (2^53 / m); start from the remainder of 2^53 / m.
+  uint64_t q = 1;           // 2^53 / m >= 1 (m < 2^53), first quotient bit
+  uint64_t r = (1ull << 53) - m;
+  for (int i = 0; i < 62; i++) {
+    r <<= 1;
+    q <<= 1;
+    if (r >= m) {
+      r -= m;
+      q |= 1;
+    }
+  }
+  return q;
+}
+
+__host__ __device__ inline Divisor make_divisor(double b) {
+  const uint64_t bb = ieee_bits(b);
+  Divisor d;
+  d.eb = (int)(bb >> 52);
+  d.mb = (bb & kMant52) | (1ull << 52);
+  d.inv = recip115(d.mb);
+  return d;
+}
+
+// RN(a / b) for a > 0 normal and b = d (positive normal).  ok = false when a is
+// zero/subnormal or the quotient is not a normal number.
+__host__ __device__ __forceinline__ double div_rn_int(double a, const Divisor& d, bool& ok) {
+  const uint64_t ab = ieee_bits(a);
+  const int ea = (int)(ab >> 52);
+  const uint64_t ma = (ab & kMant52) | (1ull << 52);
+  const bool lt = ma < d.mb;
+  const int s = lt ? 53 : 52;
+  // q = floor(ma * inv / 2^(115 - s)), within one of floor(ma 2^s / mb)
+  const uint64_t lo = ma * d.inv;
+  const uint64_t hi = ieee_mulhi(ma, d.inv);
+  const int sh = 115 - s;  // 62 or 63
+  uint64_t q = (hi << (64 - sh)) | (lo >> sh);
+  uint64_t rem = (ma << s) - q * d.mb;  // exact: the true value lies in [0, 2 mb)
+  if (rem >= d.mb) {
+    q++;
+    rem -= d.mb;
+  }
+  const uint64_t twice = rem << 1;
+  q += (twice > d.mb || (twice == d.mb && (q & 1))) ? 1 : 0;
+  int e = ea - d.eb + 1023 - (lt ? 1 : 0);
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    e++;
+  }
+  ok = (ea >= 1) && (e >= 1) && (e <= 2046);
+  return ieee_double(((uint64_t)(e & 0x7FF) << 52) | (q & kMant52));
+}
+
+// RN(a - b) for a >= b > 0, both normal.  ok = false when the result is
+// zero/subnormal (a == b, or a tiny difference) or an operand is not normal.
+__host__ __device__ __forceinline__ double sub_rn_int(double a, double b, bool& ok) {
+  const uint64_t ab = ieee_bits(a), bb = ieee_bits(b);
+  const int ea = (int)(ab >> 52), eb = (int)(bb >> 52);
+  const uint64_t A = ((ab & kMant52) | (1ull << 52)) << 10;  // 63 bits
+  const uint64_t Bf = ((bb & kMant52) | (1ull << 52)) << 10;
+  const int shift = ea - eb;  // >= 0
+  uint64_t B, sticky;
+  if (shift >= 64) {
+    B = 0;
+    sticky = 1;
+  } else if (shift == 0) {
+    B = Bf;
+    sticky = 0;
+  } else {
+    B = Bf >> shift;
+    sticky = (Bf << (64 - shift)) != 0 ? 1 : 0;
+  }
+  // D = floor(true difference) in units of 2^(ea - 1085); sticky: a fraction remains
+  const uint64_t D = A - B - sticky;
+  const int L = 64 - ieee_clz64(D);  // bit length (0 if D == 0)
+  const int k = L - 53;              // bits to drop (> 8 whenever sticky is set)
+  uint64_t q;
+  if (k > 0) {
+    q = D >> k;
+    const uint64_t R = D & ((1ull << k) - 1);
+    const uint64_t half = 1ull << (k - 1);
+    q += (R > half || (R == half && (sticky || (q & 1)))) ? 1 : 0;
+  } else {
+    q = D << (-k);  // exact (no sticky possible here)
+  }
+  int e = k + ea - 10;
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    e++;
+  }
+  ok = (ea >= 1) && (eb >= 1) && (ab >= bb) && (L > 0) && (e >= 1);
+  return ieee_double(((uint64_t)(e & 0x7FF) << 52) | (q & kMant52));
+}
+
+// 1 - x for x in (1/2, 1): exact; x = mx 2^-53 with mx in (2^52, 2^53).
+__host__ __device__ __forceinline__ double one_minus_int(double x, bool& ok) {
+  const uint64_t xb = ieee_bits(x);
+  const int ex = (int)(xb >> 52);
+  const uint64_t y = (1ull << 53) - ((xb & kMant52) | (1ull << 52));  // in (0, 2^52)
+  const int L = 64 - ieee_clz64(y);
+  const uint64_t m = y << (53 - L);
+  const int e = 1022 - (53 - L);
+  ok = (ex == 1022) && (y != 0);
+  return ieee_double(((uint64_t)e << 52) | (m & kMant52));
+}
+
+}  // namespace vc

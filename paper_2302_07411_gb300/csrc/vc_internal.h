@@ -1,0 +1,69 @@
+// vc_internal.h -- types shared by the kernels (vc_kernels.cu) and the C-ABI
+// layer (vc_api.cu).  Not part of the public interface.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vc {
+
+constexpr int kMaxTiles = 4096;   // tiles (row bands of the round kernels) per frame
+constexpr int kMaxRowBytes = 96 * 1024;
+constexpr int kRoundThreads = 256;
+
+// Frame geometry and the subframe partition (pi_i = floor(i P / n) pixels).
+struct Layout {
+  int H, W, C, n, rounds;
+  int P;              // pixels per frame
+  int N;              // bytes per frame (< 2^31)
+  long long Npad;     // stride of internal per-frame buffers (multiple of 256)
+  int T;              // rows per tile of the round kernels (power of two <= 32)
+  int NT;             // tiles per frame = ceil(H / T)
+};
+
+// Read-only per-layout tables built on the device at init.
+struct Tables {
+  const int* pi;          // [n+1] first pixel of each subframe, pi[n] = P
+  const uint32_t* sbits;  // [P/32 + 1] bit p set <=> pixel p starts a subframe
+  const int* srank;       // [P/32 + 1] number of subframe starts before bit-word w
+  const int* fixlim;      // [NT] first subframe-start byte at or after the tile's first byte (or the tile end)
+};
+
+// Device-resident chaotic state of the n assistant PRBGs (Alg. 2).
+struct Chains {
+  double* st;         // PLCM: {x1, x2} per chain; 2DLASM: {x1, y1, x2, y2}
+  double* par;        // PLCM: {p1, q1, p2, q2} with q = RN(1/2 - p); 2DLASM: {pm1, pm2} with pm = RN(pi mu)
+  uint64_t* carry;    // [2] per chain: unconsumed bytes of the last iterate, first byte lowest
+  int* carry_len;     // per chain, 0..11
+};
+
+// PRBG_m of Alg. 1 (one per stream).
+struct MainPrbg {
+  double s[4];        // PLCM pair {x1, p1, x2, p2}; 2DLASM single {x, y, mu, 0}
+  uint64_t carry[2];  // unconsumed bytes, first byte lowest
+  int carry_len;
+  int kind;
+};
+
+// Launchers (vc_kernels.cu).  All enqueue on `st` and return the launch error.
+cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* srank, int* fixlim, cudaStream_t st);
+cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cudaStream_t st);
+cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
+                                  cudaStream_t st);
+cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+                             cudaStream_t st);
+cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
+                             long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
+                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st);
+cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
+                             int nframes, cudaStream_t st);
+cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
+                             long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
+                             int nframes, cudaStream_t st);
+size_t round_smem_bytes(const Layout& L);
+
+// Diagnostics: the chaotic primitives applied elementwise.
+cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st);
+cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, cudaStream_t st);
+cudaError_t launch_dbg_lasm(const double* xymu, double* out, long long n, cudaStream_t st);
+
+}  // namespace vc

@@ -1,0 +1,835 @@
+// vc_kernels.cu -- sm_103a kernels of the chaotic video cipher.
+//
+//   k_tables_*        subframe partition tables (pi_i, start bitmap, ranks, tile limits)
+//   k_key_schedule    Alg. 1: PRBG_m keyed by K -> parameters P_m of every PRBG_a^i
+//   k_frame_sc        Alg. 1: one confusion seed s_c per frame from PRBG_m
+//   k_kmod            Eq. 1: shift table k(alpha) = floor(s_c sin(2 pi alpha / H)), reduced mod W
+//   k_keystream       Sec. 3 + Alg. 2: r * S_i bytes per frame from every PRBG_a^i (Eq. 5 / Eq. 6)
+//   k_enc_round       Eq. 1 (confusion) fused with Eq. 3 (diffusion) for one round
+//   k_enc_fixup       completes the diffusion chains that cross row-band tiles
+//   k_dec_round       Eq. 4 (inverse diffusion) fused with Eq. 2 (inverse confusion)
+//
+// Layout of a frame: H x W x C bytes, HWC.  Byte q of a frame belongs to pixel
+// q / C; subframe i owns bytes [C pi_i, C pi_{i+1}), pi_i = floor(i P / n).
+#include <cstdint>
+
+#include "vc_internal.h"
+#include "vc_maps.cuh"
+
+namespace vc {
+
+// =============================================================================
+// Partition tables
+// =============================================================================
+
+__global__ void k_tables_pi(Layout L, int* pi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= L.n) pi[i] = (int)(((long long)i * L.P) / L.n);
+}
+
+__global__ void k_tables_bits(Layout L, const int* pi, uint32_t* sbits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.n) {
+    const int p = pi[i];
+    atomicOr(&sbits[p >> 5], 1u << (p & 31));
+  }
+}
+
+// srank[w] = #{i < n : pi_i < 32 w} = min(n, ceil(32 w n / P)).
+__global__ void k_tables_rank(Layout L, int* srank, int nwords) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < nwords) {
+    const long long x = 32LL * w;
+    const long long r = (x * L.n + L.P - 1) / L.P;
+    srank[w] = (int)(r < L.n ? r : L.n);
+  }
+}
+
+// fixlim[t] = first subframe-start byte >= the tile's first byte, capped at the
+// tile's end: the smallest i with pi_i >= x0 is ceil(x0 n / P).
+__global__ void k_tables_fixlim(Layout L, int* fixlim) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L.NT) {
+    const long long x0 = (long long)t * L.T * L.W;
+    const long long istar = (x0 * L.n + L.P - 1) / L.P;
+    const int rows_end = min(L.H, (t + 1) * L.T);
+    long long fl = (long long)rows_end * L.W * L.C;
+    if (istar < L.n) {
+      const long long ps = (istar * L.P) / L.n;
+      if (ps * L.C < fl) fl = ps * L.C;
+    }
+    fixlim[t] = (int)fl;
+  }
+}
+
+cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* srank, int* fixlim, cudaStream_t st) {
+  const int nwords = L.P / 32 + 2;
+  cudaError_t e = cudaMemsetAsync(sbits, 0, sizeof(uint32_t) * nwords, st);
+  if (e != cudaSuccess) return e;
+  k_tables_pi<<<(L.n + 1 + 255) / 256, 256, 0, st>>>(L, pi);
+  k_tables_bits<<<(L.n + 255) / 256, 256, 0, st>>>(L, pi, sbits);
+  k_tables_rank<<<(nwords + 255) / 256, 256, 0, st>>>(L, srank, nwords);
+  k_tables_fixlim<<<(L.NT + 255) / 256, 256, 0, st>>>(L, fixlim);
+  return cudaGetLastError();
+}
+
+// =============================================================================
+// PRBG_m (Alg. 1): key schedule and per-frame confusion seeds
+// =============================================================================
+
+// Next 6-byte group U of PRBG_m's byte stream (first byte least significant).
+__device__ uint64_t main_next_group(MainPrbg& m) {
+  if (m.carry_len == 0) {
+    if (m.kind == 0) {  // PLCM pair, 6 bytes per iterate
+      m.s[0] = plcm_step(m.s[0], m.s[1], __dsub_rn(0.5, m.s[1]));
+      m.s[2] = plcm_step(m.s[2], m.s[3], __dsub_rn(0.5, m.s[3]));
+      m.carry[0] = mant48(m.s[0]) ^ mant48(m.s[2]);
+      m.carry[1] = 0;
+      m.carry_len = 6;
+    } else {  // single 2DLASM, x bytes then y bytes
+      lasm_step(m.s[0], m.s[1], __dmul_rn(kPi, m.s[2]));
+      const uint64_t vx = mant48(m.s[0]), vy = mant48(m.s[1]);
+      m.carry[0] = vx | (vy << 48);
+      m.carry[1] = vy >> 16;
+      m.carry_len = 12;
+    }
+  }
+  const uint64_t U = m.carry[0] & 0xFFFFFFFFFFFFull;
+  m.carry[0] = (m.carry[0] >> 48) | (m.carry[1] << 16);
+  m.carry[1] >>= 48;
+  m.carry_len -= 6;
+  return U;
+}
+
+// u = (U + 1/2) 2^-48, exact.
+__device__ __forceinline__ double unit_of(uint64_t U) { return __dmul_rn(__ull2double_rn(2 * U + 1), 0x1p-49); }
+
+__global__ void k_key_schedule(int kind, MainPrbg* mp, Chains ch, int n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  MainPrbg m = *mp;
+  for (int i = 0; i < n; i++) {
+    if (kind == 0) {
+      const double u1 = unit_of(main_next_group(m));
+      const double u2 = unit_of(main_next_group(m));
+      const double u3 = unit_of(main_next_group(m));
+      const double u4 = unit_of(main_next_group(m));
+      const double p1 = __dadd_rn(0.05, __dmul_rn(0.4, u2));
+      const double p2 = __dadd_rn(0.05, __dmul_rn(0.4, u4));
+      ch.st[2 * i] = u1;
+      ch.st[2 * i + 1] = u3;
+      ch.par[4 * i] = p1;
+      ch.par[4 * i + 1] = __dsub_rn(0.5, p1);
+      ch.par[4 * i + 2] = p2;
+      ch.par[4 * i + 3] = __dsub_rn(0.5, p2);
+    } else {
+      const double u1 = unit_of(main_next_group(m));
+      const double u2 = unit_of(main_next_group(m));
+      const double u3 = unit_of(main_next_group(m));
+      const double u4 = unit_of(main_next_group(m));
+      const double u5 = unit_of(main_next_group(m));
+      const double u6 = unit_of(main_next_group(m));
+      const double mu1 = __dadd_rn(0.44, __dmul_rn(0.49, u3));
+      const double mu2 = __dadd_rn(0.44, __dmul_rn(0.49, u6));
+      ch.st[4 * i] = u1;
+      ch.st[4 * i + 1] = u2;
+      ch.st[4 * i + 2] = u4;
+      ch.st[4 * i + 3] = u5;
+      ch.par[2 * i] = __dmul_rn(kPi, mu1);
+      ch.par[2 * i + 1] = __dmul_rn(kPi, mu2);
+    }
+    ch.carry[2 * i] = 0;
+    ch.carry[2 * i + 1] = 0;
+    ch.carry_len[i] = 0;
+  }
+  *mp = m;
+}
+
+cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cudaStream_t st) {
+  k_key_schedule<<<1, 32, 0, st>>>(kind, main, ch, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_frame_sc(MainPrbg* mp, int nframes, long long* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  MainPrbg m = *mp;
+  for (int f = 0; f < nframes; f++) sc[f] = 1 + (long long)(main_next_group(m) & 0xFFFFull);
+  *mp = m;
+}
+
+// kmod[f][alpha] = floor(s_c * csin((2 pi alpha) / H)) mod W, in [0, W).
+__global__ void k_kmod(Layout L, const long long* sc, int nframes, int* kmod) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nframes * L.H) return;
+  const int f = (int)(idx / L.H);
+  const int a = (int)(idx - (long long)f * L.H);
+  const double t = __ddiv_rn(__dmul_rn(kTwoPi, (double)a), (double)L.H);
+  const double v = __dmul_rn((double)sc[f], csin(t));
+  long long k = (long long)floor(v) % L.W;
+  if (k < 0) k += L.W;
+  kmod[idx] = (int)k;
+}
+
+cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
+                                  cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  k_frame_sc<<<1, 32, 0, st>>>(main, nframes, sc);
+  const long long tot = (long long)nframes * L.H;
+  k_kmod<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, sc, nframes, kmod);
+  return cudaGetLastError();
+}
+
+// =============================================================================
+// Keystream (Sec. 3): one thread per subframe chain, both maps of the pair in
+// the same thread (two independent dependency chains).
+// =============================================================================
+
+// Writes a chain's byte stream into KS[f][j][q], q in [qstart, qend), round j
+// after round j-1, merging bytes into aligned 8-byte words.  The first and
+// last word of a range may be shared with the neighbouring subframe's chain:
+// those are written byte by byte.
+struct KsWriter {
+  uint8_t* fbase;
+  long long Npad;
+  int rounds, j, q, qstart, qend;
+  uint8_t* waddr;
+  uint64_t acc;
+  uint32_t mask;
+
+  __device__ __forceinline__ void begin_round() {
+    waddr = fbase + (long long)j * Npad + (q & ~7);
+    acc = 0;
+    mask = 0;
+  }
+  __device__ __forceinline__ void flush() {
+    if (mask == 0xFFu) {
+      *reinterpret_cast<uint64_t*>(waddr) = acc;
+    } else if (mask) {
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (mask & (1u << k)) waddr[k] = (uint8_t)(acc >> (8 * k));
+    }
+    acc = 0;
+    mask = 0;
+  }
+  // Append the low `cnt` (1..8) bytes of v, lowest byte first.
+  __device__ __forceinline__ void put(uint64_t v, int cnt) {
+    while (cnt > 0) {
+      const int room = qend - q;
+      const int take = cnt < room ? cnt : room;
+      const int s = q & 7;
+      const int n1 = take < 8 - s ? take : 8 - s;
+      const uint64_t m1 = (n1 == 8) ? ~0ull : ((1ull << (8 * n1)) - 1);
+      acc |= (v & m1) << (8 * s);
+      mask |= ((1u << n1) - 1u) << s;
+      if (s + n1 == 8) {
+        flush();
+        waddr += 8;
+      }
+      if (take > n1) {  // remainder starts the next word (n1 < 8, n2 <= 7)
+        const int n2 = take - n1;
+        acc = (v >> (8 * n1)) & ((1ull << (8 * n2)) - 1);
+        mask = (1u << n2) - 1u;
+      }
+      q += take;
+      v = (take == 8) ? 0 : (v >> (8 * take));
+      cnt -= take;
+      if (q == qend) {
+        flush();
+        j++;
+        q = qstart;
+        if (j < rounds) begin_round();
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ void shr128(uint64_t& lo, uint64_t& hi, int bits) {
+  if (bits == 0) return;
+  if (bits >= 64) {
+    lo = (bits >= 128) ? 0 : (hi >> (bits - 64));
+    hi = 0;
+  } else {
+    lo = (lo >> bits) | (hi << (64 - bits));
+    hi >>= bits;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  constexpr int STEP = KIND == 0 ? 6 : 12;  // bytes per iterate of the pair
+  const int qstart = L.C * tb.pi[i];
+  const int qend = L.C * tb.pi[i + 1];
+  double x1, x2, y1 = 0, y2 = 0, p1 = 0, q1 = 0, p2 = 0, q2 = 0, pm1 = 0, pm2 = 0;
+  if (KIND == 0) {
+    x1 = ch.st[2 * i];
+    x2 = ch.st[2 * i + 1];
+    p1 = ch.par[4 * i];
+    q1 = ch.par[4 * i + 1];
+    p2 = ch.par[4 * i + 2];
+    q2 = ch.par[4 * i + 3];
+  } else {
+    x1 = ch.st[4 * i];
+    y1 = ch.st[4 * i + 1];
+    x2 = ch.st[4 * i + 2];
+    y2 = ch.st[4 * i + 3];
+    pm1 = ch.par[2 * i];
+    pm2 = ch.par[2 * i + 1];
+  }
+  uint64_t c0 = ch.carry[2 * i], c1 = ch.carry[2 * i + 1];
+  int clen = ch.carry_len[i];
+  const long long per_frame = (long long)L.rounds * (qend - qstart);
+
+  for (int f = 0; f < nframes; f++) {
+    KsWriter w;
+    w.fbase = ks + (long long)f * L.rounds * L.Npad;
+    w.Npad = L.Npad;
+    w.rounds = L.rounds;
+    w.j = 0;
+    w.q = qstart;
+    w.qstart = qstart;
+    w.qend = qend;
+    w.begin_round();
+    long long rem = per_frame;
+    // 1. bytes left over from the previous frame's last iterate (R7)
+    while (clen > 0 && rem > 0) {
+      int take = clen < 8 ? clen : 8;
+      if (take > rem) take = (int)rem;
+      w.put(c0, take);
+      shr128(c0, c1, 8 * take);
+      clen -= take;
+      rem -= take;
+    }
+    // 2. whole iterates
+    while (rem >= STEP) {
+      if (KIND == 0) {
+        x1 = plcm_step(x1, p1, q1);
+        x2 = plcm_step(x2, p2, q2);
+        w.put(mant48(x1) ^ mant48(x2), 6);
+      } else {
+        lasm_step(x1, y1, pm1);
+        lasm_step(x2, y2, pm2);
+        w.put(mant48(x1) ^ mant48(x2), 6);
+        w.put(mant48(y1) ^ mant48(y2), 6);
+      }
+      rem -= STEP;
+    }
+    // 3. a last, partly used iterate; its other bytes carry over
+    if (rem > 0) {
+      uint64_t lo, hi;
+      if (KIND == 0) {
+        x1 = plcm_step(x1, p1, q1);
+        x2 = plcm_step(x2, p2, q2);
+        lo = mant48(x1) ^ mant48(x2);
+        hi = 0;
+      } else {
+        lasm_step(x1, y1, pm1);
+        lasm_step(x2, y2, pm2);
+        const uint64_t vx = mant48(x1) ^ mant48(x2), vy = mant48(y1) ^ mant48(y2);
+        lo = vx | (vy << 48);
+        hi = vy >> 16;
+      }
+      const int r = (int)rem;
+      w.put(lo, r < 8 ? r : 8);
+      if (r > 8) w.put(hi, r - 8);
+      shr128(lo, hi, 8 * r);
+      c0 = lo;
+      c1 = hi;
+      clen = STEP - r;
+      rem = 0;
+    }
+  }
+  if (KIND == 0) {
+    ch.st[2 * i] = x1;
+    ch.st[2 * i + 1] = x2;
+  } else {
+    ch.st[4 * i] = x1;
+    ch.st[4 * i + 1] = y1;
+    ch.st[4 * i + 2] = x2;
+    ch.st[4 * i + 3] = y2;
+  }
+  ch.carry[2 * i] = c0;
+  ch.carry[2 * i + 1] = c1;
+  ch.carry_len[i] = clen;
+}
+
+cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+                             cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  const int blocks = (L.n + 31) / 32;
+  if (kind == 0)
+    k_keystream<0><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  else
+    k_keystream<1><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  return cudaGetLastError();
+}
+
+// =============================================================================
+// Rounds
+// =============================================================================
+//
+// Encryption round (Eq. 1 then Eq. 3), one CTA per (row-band tile of the
+// OUTPUT frame, frame).  Output rows alpha in [a0, a0+T) of the confused frame
+// Y need Z[alpha][o] = X[(alpha - o) mod H][o] (the column shear) followed by
+// the row rotation Y[alpha][beta] = Z[alpha][(beta - k(alpha)) mod W].  Source
+// row a contributes the contiguous columns o = (alpha - a) mod H (+ m H), one
+// per output row, so the gather reads T consecutive pixels per source row into
+// shared memory.  The tile's bytes are then diffused in raster order as a
+// segmented XOR scan: c_q = c_{q-1} xor d_q with d_q = b xor (y_q + b), reset to
+// s_d xor d_q at every subframe start (Eq. 3 with the seed of Alg. 2).
+//
+// Chains that enter the tile from the previous tile are left relative to the
+// tile's first byte: bytes q < fixlim[t] hold c_q xor c(end of tile t-1).  The
+// tile's value at its last byte is written to agg_out; the next round (or
+// k_enc_fixup after the last round) scans these per-tile values and applies
+// the missing prefix while reading.  No CTA waits on another.
+
+// Segmented-scan element: bit 8 = "a subframe start lies in the span",
+// bits 0..7 = XOR value (relative to the span's start if no start).
+__device__ __forceinline__ uint32_t seg_combine(uint32_t a, uint32_t b) {
+  return (b & 0x100u) ? b : ((a & 0x100u) | ((a ^ b) & 0xFFu));
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x = seg_combine(o, x);
+  }
+  return x;
+}
+
+// s_carry[t] = true ciphertext byte at the last byte of tile t-1 (warp 0).
+__device__ void tile_carries(const Layout& L, const Tables& tb, const uint8_t* agg, uint8_t* s_carry) {
+  const int lane = threadIdx.x & 31;
+  uint32_t run = 0;
+  const int rowb = L.W * L.C;
+  for (int base = 0; base < L.NT; base += 32) {
+    const int t = base + lane;
+    uint32_t x = 0;
+    if (t < L.NT) {
+      const int tend = min(L.H, (t + 1) * L.T) * rowb;
+      const bool flag = __ldg(&tb.fixlim[t]) < tend;
+      x = (flag ? 0x100u : 0u) | (uint32_t)agg[t];
+    }
+    x = seg_combine(run, warp_incl_scan(x));
+    if (t + 1 < L.NT) s_carry[t + 1] = (uint8_t)x;
+    run = __shfl_sync(0xFFFFFFFFu, x, 31);
+  }
+  if (lane == 0) s_carry[0] = 0;
+}
+
+// Exclusive block-wide segmented scan; *total = inclusive total of the block.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t inc = warp_incl_scan(x);
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? s_warp[lane] : 0u;
+    v = warp_incl_scan(v);
+    if (lane < nw) s_warp[lane] = v;
+  }
+  __syncthreads();
+  const uint32_t wpre = warp > 0 ? s_warp[warp - 1] : 0u;
+  uint32_t lex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+  if (lane == 0) lex = 0;
+  *total = s_warp[nw - 1];
+  __syncthreads();
+  return seg_combine(wpre, lex);
+}
+
+__device__ __forceinline__ int mod_h(int v, int H) {
+  v %= H;
+  return v < 0 ? v + H : v;
+}
+
+struct RoundArgs {
+  Layout L;
+  Tables tb;
+  const uint8_t* in;
+  long long in_stride;
+  uint8_t* out;
+  long long out_stride;
+  const uint8_t* ks;
+  long long ks_stride;
+  const int* kmod;
+  const uint8_t* agg_in;
+  uint8_t* agg_out;
+};
+
+// Byte qb of the current round's confused frame Y, read through Eq. 1 from
+// the previous round's output X (with the pending tile prefixes applied).
+template <int C>
+__device__ __forceinline__ uint8_t enc_y_at(const Layout& L, const Tables& tb, const uint8_t* X, const int* kmod,
+                                            const uint8_t* s_carry, bool fix, int qb) {
+  const int pp = qb / C, ch = qb - pp * C;
+  const int alpha = pp / L.W, beta = pp - alpha * L.W;
+  int o = beta - __ldg(&kmod[alpha]);
+  if (o < 0) o += L.W;
+  const int a = mod_h(alpha - o, L.H);
+  const int qx = (a * L.W + o) * C + ch;
+  uint8_t x = X[qx];
+  if (fix) {
+    const int ta = a / L.T;
+    if (qx < __ldg(&tb.fixlim[ta])) x ^= s_carry[ta];
+  }
+  return x;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Layout& L = A.L;
+  const int f = blockIdx.y, t = blockIdx.x;
+  const int rowb = L.W * C;
+  const int a0 = t * L.T;
+  const int Te = min(L.T, L.H - a0);
+  uint8_t* Z = smem;
+  uint8_t* s_carry = smem + (((size_t)L.T * rowb + 15) & ~(size_t)15);
+  int* s_kmod = reinterpret_cast<int*>(s_carry + ((L.NT + 15) & ~15));
+  uint32_t* s_warp = reinterpret_cast<uint32_t*>(s_kmod + 32);
+
+  const uint8_t* X = A.in + f * A.in_stride;
+  uint8_t* Out = A.out + f * A.out_stride;
+  const uint8_t* KS = A.ks + f * A.ks_stride;
+  const int* kmod = A.kmod + (long long)f * L.H;
+  const bool fix = A.agg_in != nullptr;
+
+  if (fix && threadIdx.x < 32) tile_carries(L, A.tb, A.agg_in + (long long)f * L.NT, s_carry);
+  if (threadIdx.x < Te) s_kmod[threadIdx.x] = kmod[a0 + threadIdx.x];
+  __syncthreads();
+
+  // ---- gather: Z[tt][o] = X[(a0 + tt - o) mod H][o] -------------------------
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rpw = 32 / L.T;  // source rows per warp pass
+    const int tt = lane & (L.T - 1);
+    const int sub = lane / L.T;
+    for (int a = warp * rpw + sub; a < L.H; a += nw * rpw) {
+      if (tt >= Te) continue;
+      int o = a0 + tt - a;
+      if (o < 0) o += L.H;
+      const int ta = a / L.T;
+      const int lim = fix ? __ldg(&A.tb.fixlim[ta]) : 0;
+      const uint8_t cy = fix ? s_carry[ta] : 0;
+      for (; o < L.W; o += L.H) {
+        const int qx = (a * L.W + o) * C;
+        const uint8_t m = (qx < lim) ? cy : 0;  // subframe starts are pixel-aligned
+#pragma unroll
+        for (int c = 0; c < C; c++) Z[tt * rowb + o * C + c] = X[qx + c] ^ m;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- diffusion over the tile's bytes, 16-byte chunks per thread ----------
+  const int tstart = a0 * rowb;
+  const int tend = tstart + Te * rowb;
+  const int base16 = tstart & ~15;
+  const int nchunks = (tend - base16 + 15) >> 4;
+  const bool out_vec = ((reinterpret_cast<uintptr_t>(Out)) & 15) == 0;
+  uint32_t run = 0;
+  for (int cb = 0; cb < nchunks; cb += blockDim.x) {
+    const int c = cb + threadIdx.x;
+    int cs = base16 + 16 * c, ce = cs + 16;
+    if (cs < tstart) cs = tstart;
+    if (ce > tend) ce = tend;
+    const int len = (c < nchunks && ce > cs) ? ce - cs : 0;
+    uint32_t pre[4] = {0u, 0u, 0u, 0u};
+    int fse = 16;
+    uint32_t agg = 0;
+    if (len > 0) {
+      uint8_t kb[16];
+      if (len == 16 && (cs & 15) == 0) {
+        const uint4 v = *reinterpret_cast<const uint4*>(KS + cs);
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 16; k++) kb[k] = (uint8_t)(wv[k >> 2] >> (8 * (k & 3)));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) kb[k] = k < len ? KS[cs + k] : 0;
+      }
+      const int off = cs - tstart;
+      int tt = off / rowb;
+      int e = off - tt * rowb;
+      int beta = e / C;
+      int ch = e - beta * C;
+      int zo = beta - s_kmod[tt];
+      if (zo < 0) zo += L.W;
+      const int pix0 = cs / C;
+      const int w0 = pix0 >> 5;
+      const uint64_t win = (uint64_t)__ldg(&A.tb.sbits[w0]) | ((uint64_t)__ldg(&A.tb.sbits[w0 + 1]) << 32);
+      uint32_t v = 0;
+      bool has = false;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        if (k < len) {
+          const uint8_t y = Z[tt * rowb + zo * C + ch];
+          const uint8_t b = kb[k];
+          const uint8_t d = b ^ (uint8_t)(y + b);
+          bool st = false;
+          int pix = 0;
+          if (ch == 0) {
+            pix = (cs + k) / C;
+            st = (win >> (pix - (w0 << 5))) & 1ull;
+          }
+          if (st) {
+            const int wq = pix >> 5;
+            const int s = __ldg(&A.tb.srank[wq]) + __popc(__ldg(&A.tb.sbits[wq]) & ((1u << (pix & 31)) - 1u));
+            const int nx = (s + 1 == L.n) ? 0 : s + 1;
+            const int sb = C * __ldg(&A.tb.pi[nx + 1]) - 1;
+            const uint8_t sd = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, sb);
+            v = (uint32_t)(sd ^ d);
+            if (!has) {
+              has = true;
+              fse = k;
+            }
+          } else {
+            v ^= d;
+          }
+          pre[k >> 2] |= (v & 0xFFu) << (8 * (k & 3));
+          if (++ch == C) {
+            ch = 0;
+            if (++zo == L.W) zo = 0;
+          }
+          if (++e == rowb) {
+            e = 0;
+            ch = 0;
+            tt++;
+            if (tt < Te) {
+              zo = L.W - s_kmod[tt];
+              if (zo == L.W) zo = 0;
+            }
+          }
+        }
+      }
+      agg = (has ? 0x100u : 0u) | (v & 0xFFu);
+    }
+    uint32_t total;
+    const uint32_t excl = block_excl_scan(agg, &total, s_warp);
+    const uint32_t E = seg_combine(run, excl);
+    run = seg_combine(run, total);
+    if (len > 0) {
+      const uint32_t ev = E & 0xFFu;
+      const uint32_t evx4 = ev * 0x01010101u;
+#pragma unroll
+      for (int w4 = 0; w4 < 4; w4++) {
+        // bytes k < fse of the chunk still miss the prefix E
+        const int k0 = w4 * 4;
+        uint32_t msk = 0;
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (k0 + b < fse) msk |= 0xFFu << (8 * b);
+        pre[w4] ^= evx4 & msk;
+      }
+      if (len == 16 && (cs & 15) == 0 && out_vec) {
+        *reinterpret_cast<uint4*>(Out + cs) = make_uint4(pre[0], pre[1], pre[2], pre[3]);
+      } else {
+        for (int k = 0; k < len; k++) Out[cs + k] = (uint8_t)(pre[k >> 2] >> (8 * (k & 3)));
+      }
+    }
+  }
+  if (threadIdx.x == 0) A.agg_out[(long long)f * L.NT + t] = (uint8_t)run;
+}
+
+// [Z tile, 16-aligned][tile carries, NT bytes rounded to 16][row shifts, 32 ints][scan, 32 words]
+size_t round_smem_bytes(const Layout& L) {
+  return (((size_t)L.T * L.W * L.C + 15) & ~(size_t)15) + ((L.NT + 15) & ~15) + 32 * sizeof(int) +
+         32 * sizeof(uint32_t);
+}
+
+template <int C>
+static cudaError_t enc_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
+  const size_t smem = round_smem_bytes(A.L);
+  cudaError_t e = cudaFuncSetAttribute(k_enc_round<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(A.L.NT, nframes);
+  k_enc_round<C><<<grid, kRoundThreads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
+                             long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
+                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  RoundArgs A{L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, agg_in, agg_out};
+  switch (L.C) {
+    case 1: return enc_round_c<1>(A, nframes, st);
+    case 3: return enc_round_c<3>(A, nframes, st);
+    case 4: return enc_round_c<4>(A, nframes, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// After the last round: apply each tile's missing prefix in place.
+__global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb, uint8_t* out, long long out_stride,
+                                                             const uint8_t* agg) {
+  __shared__ uint8_t s_carry[kMaxTiles];
+  const int f = blockIdx.y, t = blockIdx.x;
+  if (threadIdx.x < 32) tile_carries(L, tb, agg + (long long)f * L.NT, s_carry);
+  __syncthreads();
+  if (t == 0) return;
+  const int rowb = L.W * L.C;
+  const int tstart = t * L.T * rowb;
+  const int lim = __ldg(&tb.fixlim[t]);
+  if (lim <= tstart) return;
+  uint8_t* O = out + f * out_stride;
+  const uint8_t cy = s_carry[t];
+  const uint32_t c4 = cy * 0x01010101u;
+  // head bytes up to 16-byte alignment, aligned body, tail bytes
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(O + tstart);
+  int head = (int)((16 - (addr & 15)) & 15);
+  if (head > lim - tstart) head = lim - tstart;
+  for (int k = threadIdx.x; k < head; k += blockDim.x) O[tstart + k] ^= cy;
+  const int body0 = tstart + head;
+  const int nvec = (lim - body0) >> 4;
+  uint4* V = reinterpret_cast<uint4*>(O + body0);
+  for (int k = threadIdx.x; k < nvec; k += blockDim.x) {
+    uint4 v = V[k];
+    v.x ^= c4; v.y ^= c4; v.z ^= c4; v.w ^= c4;
+    V[k] = v;
+  }
+  for (int k = body0 + nvec * 16 + threadIdx.x; k < lim; k += blockDim.x) O[k] ^= cy;
+}
+
+cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
+                             int nframes, cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  dim3 grid(L.NT, nframes);
+  k_enc_fixup<<<grid, kRoundThreads, 0, st>>>(L, tb, out, out_stride, agg);
+  return cudaGetLastError();
+}
+
+// Decryption round (Eq. 4 then Eq. 2), one CTA per (row-band tile of the
+// OUTPUT frame X, frame).  X[a][o] = Y[(a + o) mod H][(o + k(alpha)) mod W], and
+// Y is elementwise in the ciphertext C of the round: y_q = (b xor c_q xor c_{q-1}) - b,
+// with c_{q-1} replaced at a subframe start by the seed y of the last byte of
+// the next subframe (itself a non-first byte, so computable the same way).
+template <int C>
+__global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Layout& L = A.L;
+  const int f = blockIdx.y, t = blockIdx.x;
+  const int rowb = L.W * C;
+  const int a0 = t * L.T;
+  const int Te = min(L.T, L.H - a0);
+  uint8_t* Xt = smem;
+  const uint8_t* Cin = A.in + f * A.in_stride;
+  uint8_t* Out = A.out + f * A.out_stride;
+  const uint8_t* KS = A.ks + f * A.ks_stride;
+  const int* kmod = A.kmod + (long long)f * L.H;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rpw = 32 / L.T;
+  const int tt = lane & (L.T - 1);
+  const int sub = lane / L.T;
+  for (int alpha = warp * rpw + sub; alpha < L.H; alpha += nw * rpw) {
+    if (tt >= Te) continue;
+    int o = alpha - (a0 + tt);
+    if (o < 0) o += L.H;
+    const int km = __ldg(&kmod[alpha]);
+    for (; o < L.W; o += L.H) {
+      int beta = o + km;
+      if (beta >= L.W) beta -= L.W;
+      const int pix = alpha * L.W + beta;
+      const int qb = pix * C;
+      uint8_t prev;
+      if ((__ldg(&A.tb.sbits[pix >> 5]) >> (pix & 31)) & 1u) {
+        const int wq = pix >> 5;
+        const int s = __ldg(&A.tb.srank[wq]) + __popc(__ldg(&A.tb.sbits[wq]) & ((1u << (pix & 31)) - 1u));
+        const int nx = (s + 1 == L.n) ? 0 : s + 1;
+        const int sb = C * __ldg(&A.tb.pi[nx + 1]) - 1;
+        const uint8_t bs = KS[sb];
+        prev = (uint8_t)((uint8_t)(bs ^ Cin[sb] ^ Cin[sb - 1]) - bs);
+      } else {
+        prev = Cin[qb - 1];
+      }
+#pragma unroll
+      for (int c = 0; c < C; c++) {
+        const uint8_t cq = Cin[qb + c];
+        const uint8_t b = KS[qb + c];
+        Xt[tt * rowb + o * C + c] = (uint8_t)((uint8_t)(b ^ cq ^ prev) - b);
+        prev = cq;
+      }
+    }
+  }
+  __syncthreads();
+  // write the tile's rows (contiguous bytes)
+  const int tstart = a0 * rowb;
+  const int nb = Te * rowb;
+  uint8_t* dst = Out + tstart;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    const int nvec = nb >> 4;
+    for (int k = threadIdx.x; k < nvec; k += blockDim.x)
+      reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(Xt)[k];
+    for (int k = nvec * 16 + threadIdx.x; k < nb; k += blockDim.x) dst[k] = Xt[k];
+  } else {
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) dst[k] = Xt[k];
+  }
+}
+
+template <int C>
+static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
+  const size_t smem = round_smem_bytes(A.L);
+  cudaError_t e = cudaFuncSetAttribute(k_dec_round<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(A.L.NT, nframes);
+  k_dec_round<C><<<grid, kRoundThreads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
+                             long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
+                             int nframes, cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  RoundArgs A{L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nullptr, nullptr};
+  switch (L.C) {
+    case 1: return dec_round_c<1>(A, nframes, st);
+    case 3: return dec_round_c<3>(A, nframes, st);
+    case 4: return dec_round_c<4>(A, nframes, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// =============================================================================
+// Diagnostics
+// =============================================================================
+
+__global__ void k_dbg_csin(const double* t, double* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = csin(t[i]);
+}
+__global__ void k_dbg_plcm(const double* x, const double* p, double* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = plcm_step(x[i], p[i], __dsub_rn(0.5, p[i]));
+}
+__global__ void k_dbg_lasm(const double* xymu, double* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double x = xymu[3 * i], y = xymu[3 * i + 1];
+    lasm_step(x, y, __dmul_rn(kPi, xymu[3 * i + 2]));
+    out[2 * i] = x;
+    out[2 * i + 1] = y;
+  }
+}
+
+cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_dbg_csin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_dbg_plcm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, p, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dbg_lasm(const double* xymu, double* out, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_dbg_lasm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xymu, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace vc

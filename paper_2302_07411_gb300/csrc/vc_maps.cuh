@@ -1,0 +1,95 @@
+// vc_maps.cuh -- device arithmetic of the cipher's chaotic generators.
+//
+// Every floating-point operation is an explicit IEEE-754 binary64
+// round-to-nearest intrinsic (__dadd_rn, __dmul_rn, __ddiv_rn, ...), so the
+// compiler can neither contract a multiply-add into an FMA nor reorder
+// anything: the results are bit-identical to any other binary64 evaluation in
+// the same operation order.
+#pragma once
+#include <cstdint>
+
+namespace vc {
+
+// ---- the cipher's sine (reading of "sin" in Eq. 1 and Eq. 6) ----------------
+// k = floor(t * 2/pi + 1/2); r = (t - k*PIO2_HI) - k*PIO2_LO (Cody-Waite, 33-bit
+// head so k*PIO2_HI is exact); quadrant k mod 4 selects +-sin(r) / +-cos(r);
+// Taylor polynomials in r^2 by Horner, sin to degree 17, cos to degree 16.
+static constexpr double kPi = 0x1.921fb54442d18p+1;       // nearest double to pi
+static constexpr double kTwoPi = 0x1.921fb54442d18p+2;    // nearest double to 2 pi
+static constexpr double kTwoOverPi = 0x1.45f306dc9c883p-1; // nearest double to 2/pi
+static constexpr double kPio2Hi = 0x1.921fb544p+0;
+static constexpr double kPio2Lo = 0x1.0b4611a626331p-34;
+
+// (-1)^k / (2k+1)!  and  (-1)^k / (2k)!, k = 1..8: each a quotient of exactly
+// representable integers, rounded once by the compiler's constant folding.
+#define VC_S(k, f) ((((k) & 1) ? -1.0 : 1.0) / (f))
+static constexpr double kSin1 = VC_S(1, 6.0);
+static constexpr double kSin2 = VC_S(2, 120.0);
+static constexpr double kSin3 = VC_S(3, 5040.0);
+static constexpr double kSin4 = VC_S(4, 362880.0);
+static constexpr double kSin5 = VC_S(5, 39916800.0);
+static constexpr double kSin6 = VC_S(6, 6227020800.0);
+static constexpr double kSin7 = VC_S(7, 1307674368000.0);
+static constexpr double kSin8 = VC_S(8, 355687428096000.0);
+static constexpr double kCos1 = VC_S(1, 2.0);
+static constexpr double kCos2 = VC_S(2, 24.0);
+static constexpr double kCos3 = VC_S(3, 720.0);
+static constexpr double kCos4 = VC_S(4, 40320.0);
+static constexpr double kCos5 = VC_S(5, 3628800.0);
+static constexpr double kCos6 = VC_S(6, 479001600.0);
+static constexpr double kCos7 = VC_S(7, 87178291200.0);
+static constexpr double kCos8 = VC_S(8, 20922789888000.0);
+#undef VC_S
+
+// sin(r) = r + (r*r^2) * S(r^2) and cos(r) = 1 + (1*r^2) * C(r^2), both as
+// A + (m*r^2) * Horner(coefficients; r^2): the lanes of a warp pick their
+// coefficient set by quadrant instead of branching, so a warp whose lanes sit
+// in different quadrants still evaluates one polynomial.  (1*r^2 == r^2
+// exactly, so the cosine is the same binary64 value as 1 + r^2*C(r^2).)
+__device__ __forceinline__ double csin(double t) {
+  const double kd = floor(__dadd_rn(__dmul_rn(t, kTwoOverPi), 0.5));
+  const double r = __dsub_rn(__dsub_rn(t, __dmul_rn(kd, kPio2Hi)), __dmul_rn(kd, kPio2Lo));
+  const long long k = __double2ll_rz(kd);
+  const int quad = (int)(k & 3);  // two's complement: the mathematical k mod 4
+  const bool c = (quad & 1) != 0;
+  const double r2 = __dmul_rn(r, r);
+  double s = c ? kCos8 : kSin8;
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos7 : kSin7);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos6 : kSin6);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos5 : kSin5);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos4 : kSin4);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos3 : kSin3);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos2 : kSin2);
+  s = __dadd_rn(__dmul_rn(s, r2), c ? kCos1 : kSin1);
+  const double a = c ? 1.0 : r;
+  const double v = __dadd_rn(a, __dmul_rn(__dmul_rn(a, r2), s));
+  return (quad & 2) ? -v : v;
+}
+
+// ---- PLCM, Eq. 5 ------------------------------------------------------------
+// x in [0,1]; p in (0,1/2); q = RN(1/2 - p) (the same value the map computes
+// each step).  Reflect above 1/2 (exact), then one correctly rounded division.
+// Branch-free so a warp never executes both divisions.
+__device__ __forceinline__ double plcm_step(double x, double p, double q) {
+  const double xr = (x > 0.5) ? __dsub_rn(1.0, x) : x;
+  const bool lo = xr < p;
+  const double num = lo ? xr : __dsub_rn(xr, p);
+  const double den = lo ? p : q;
+  return __ddiv_rn(num, den);
+}
+
+// ---- 2DLASM, Eq. 6 ----------------------------------------------------------
+// pm = RN(pi * mu).  x' = csin(((pm*(y+3))*x)*(1-x)); y' uses the new x'.
+__device__ __forceinline__ void lasm_step(double& x, double& y, double pm) {
+  const double xn = csin(__dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(y, 3.0)), x), __dsub_rn(1.0, x)));
+  const double yn = csin(__dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(xn, 3.0)), y), __dsub_rn(1.0, y)));
+  x = xn;
+  y = yn;
+}
+
+// ---- Sec. 3: six mantissa bytes = low 48 bits of the pattern, LSB first -----
+__device__ __forceinline__ uint64_t mant48(double v) {
+  return (uint64_t)__double_as_longlong(v) & 0xFFFFFFFFFFFFull;
+}
+
+}  // namespace vc

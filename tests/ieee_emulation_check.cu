@@ -1,0 +1,85 @@
+// Host-side check of the integer-pipe binary64 routines of the CUDA library
+// (csrc/vc_ieee.cuh) against the host CPU's IEEE-754 arithmetic, which rounds
+// every operation to nearest even.  Compiled by nvcc as host code and run by
+// tests/test_ieee_emulation.py.  Prints "mismatches <n>" per routine.
+#include <cinttypes>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+
+#include "vc_ieee.cuh"
+
+static double from_bits(uint64_t b) { double v; std::memcpy(&v, &b, 8); return v; }
+static uint64_t to_bits(double v) { uint64_t b; std::memcpy(&b, &v, 8); return b; }
+
+int main(int argc, char** argv) {
+  const long long n = argc > 1 ? atoll(argv[1]) : 10000000LL;
+  std::mt19937_64 g(12345);
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  long long bad_div = 0, bad_sub = 0, bad_om = 0, fb_div = 0, fb_sub = 0, checked_div = 0, checked_sub = 0;
+  for (long long i = 0; i < n; i++) {
+    // divisor: PLCM-like p in (0, 1/2) or an arbitrary positive normal
+    double b;
+    switch (i & 3) {
+      case 0: b = 0.01 + 0.48 * U(g); break;
+      case 1: b = 0.5 - (0.01 + 0.48 * U(g)); break;
+      case 2: b = from_bits((g() & ((1ull << 52) - 1)) | ((uint64_t)(900 + g() % 200) << 52)); break;
+      default: b = from_bits((g() & ((1ull << 52) - 1)) | (1022ull << 52)); break;
+    }
+    double a;
+    switch ((i >> 2) & 3) {
+      case 0: a = U(g) * b; break;                       // x < p branch
+      case 1: a = from_bits(g() & 0x3FEFFFFFFFFFFFFFull); break;  // any value below 1
+      case 2: a = from_bits((g() & ((1ull << 52) - 1)) | ((uint64_t)(1 + g() % 1022) << 52)); break;
+      default: a = b * (1.0 + 1e-12 * (U(g) - 0.5)); break;  // quotient near 1
+    }
+    if (a > 0) {
+      const vc::Divisor d = vc::make_divisor(b);
+      bool ok = false;
+      const double q = vc::div_rn_int(a, d, ok);
+      if (ok) {
+        checked_div++;
+        if (to_bits(q) != to_bits(a / b)) {
+          if (bad_div < 5) printf("div a=%a b=%a got %a want %a\n", a, b, q, a / b);
+          bad_div++;
+        }
+      } else {
+        fb_div++;
+      }
+    }
+    // subtraction a >= b > 0 with nearby exponents
+    double x = from_bits(to_bits(0.5 * U(g) + 1e-300));
+    double y;
+    switch ((i >> 4) & 3) {
+      case 0: y = U(g) * x; break;
+      case 1: y = x * (1.0 - std::ldexp(U(g), -(int)(g() % 60))); break;
+      case 2: y = std::ldexp(x, -(int)(g() % 70)) * (0.5 + 0.5 * U(g)); break;
+      default: y = from_bits(to_bits(x) - (g() % 4)); break;
+    }
+    if (y > 0 && y <= x) {
+      bool ok = false;
+      const double s = vc::sub_rn_int(x, y, ok);
+      if (ok) {
+        checked_sub++;
+        if (to_bits(s) != to_bits(x - y)) {
+          if (bad_sub < 5) printf("sub a=%a b=%a got %a want %a\n", x, y, s, x - y);
+          bad_sub++;
+        }
+      } else {
+        fb_sub++;
+      }
+    }
+    // 1 - x on (1/2, 1)
+    double z = from_bits((g() & ((1ull << 52) - 1)) | (1022ull << 52));
+    if (z > 0.5) {
+      bool ok = false;
+      const double o = vc::one_minus_int(z, ok);
+      if (!ok || to_bits(o) != to_bits(1.0 - z)) bad_om++;
+    }
+  }
+  printf("div checked %lld fallback %lld mismatches %lld\n", checked_div, fb_div, bad_div);
+  printf("sub checked %lld fallback %lld mismatches %lld\n", checked_sub, fb_sub, bad_sub);
+  printf("one_minus mismatches %lld\n", bad_om);
+  return (bad_div || bad_sub || bad_om) ? 1 : 0;
+}

@@ -1,0 +1,237 @@
+"""GPU path == CPU oracle, byte for byte (integer/byte work: the bar is exact
+equality), through the C ABI.  Stages first (sine, maps, keystream), then whole
+frames over the paper's configurations and odd shapes."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_07411_gb300 import binding, build
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# --------------------------------------------------------------------- stages
+
+def test_csin_bitwise(B, orc):
+    rng = np.random.default_rng(100)
+    t = np.concatenate([rng.uniform(0, 2 * np.pi, 200000), rng.uniform(0, np.pi, 100000),
+                        np.array([0.0, 1e-300, np.pi / 4, np.pi / 2, np.pi, 2 * np.pi, 6.283185307179586])])
+    out = torch.empty(t.size, dtype=torch.float64, device="cuda")
+    B.vc_dbg_csin(dev(t), out)
+    got = host(out)
+    idx = rng.choice(t.size, 20000, replace=False)
+    exp = np.array([orc.csin(float(v)) for v in t[idx]])
+    assert np.array_equal(got[idx].view(np.uint64), exp.view(np.uint64))
+
+
+def test_plcm_step_bitwise(B, orc):
+    rng = np.random.default_rng(101)
+    x = np.concatenate([rng.uniform(0, 1, 50000), rng.uniform(0, 1e-6, 1000), np.array([0.0, 0.5, 1.0, 0.25])])
+    p = rng.uniform(0.01, 0.49, x.size)
+    p[-4:] = [0.3, 0.3, 0.3, 0.25]
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    B.vc_dbg_plcm(dev(x), dev(p), out)
+    got = host(out)
+    exp = np.array([orc.plcm_step(float(a), float(b)) for a, b in zip(x, p)])
+    assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def test_lasm_step_bitwise(B, orc):
+    rng = np.random.default_rng(102)
+    n = 20000
+    xymu = np.stack([rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.uniform(0.44, 0.93, n)], axis=1)
+    out = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    B.vc_dbg_lasm(dev(xymu.ravel()), out)
+    got = host(out).reshape(n, 2)
+    exp = np.array([orc.lasm_step(*map(float, r)) for r in xymu])
+    assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
+    """oracle keystream (subframe-major, r*S_i each) -> [round][frame byte q]."""
+    out = np.zeros((rounds, N), np.uint8)
+    off = 0
+    for i in range(len(bounds) - 1):
+        S = bounds[i + 1] - bounds[i]
+        for j in range(rounds):
+            out[j, bounds[i]:bounds[i + 1]] = ks_cat[off + j * S: off + (j + 1) * S]
+        off += rounds * S
+    return out
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
+                                               (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6)])
+def test_keystream_and_confusion_seeds(B, orc, kind, H, W, C, n, r, frames):
+    """Sec. 3 byte streams and Alg. 1's s_c per frame, across frames (the left
+    over bytes of an iterate carry over, R7)."""
+    key = synth.key_for_seed(kind, 200 + n)
+    ref = orc.OracleCipher(kind, key, H, W, C, n, r)
+    g = B.Cipher(kind, key, H, W, C, n, r)
+    N = H * W * C
+    d_ks = torch.empty(frames * r * N, dtype=torch.uint8, device="cuda")
+    d_sc = torch.empty(frames, dtype=torch.int64, device="cuda")
+    B.vc_dbg_keystream(g.ctx, d_ks, d_sc, frames)
+    ks = host(d_ks).reshape(frames, r, N)
+    sc = host(d_sc)
+    bounds = orc.subframe_bounds(H, W, C, n)
+    for f in range(frames):
+        cat, s = ref.frame_keystream()
+        assert sc[f] == s
+        assert np.array_equal(ks[f], _oracle_ks_to_frame_layout(cat, bounds, r, N)), f"frame {f}"
+    g.close()
+
+
+# --------------------------------------------------------------------- whole frames
+
+def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False):
+    F, H, W, C = X.shape
+    ref_e = orc.OracleCipher(kind, key, H, W, C, n, r)
+    ref_d = orc.OracleCipher(kind, key, H, W, C, n, r)
+    Y_ref = ref_e.encrypt(X)
+    g_e = B.Cipher(kind, key, H, W, C, n, r)
+    g_d = B.Cipher(kind, key, H, W, C, n, r)
+    if chunk:
+        g_e.set_chunk(chunk)
+        g_d.set_chunk(chunk)
+    d = dev(X)
+    Yg = g_e.encrypt(d, d if inplace else None)
+    g_e.sync()
+    Y = host(Yg)
+    assert np.array_equal(Y, Y_ref), f"ciphertext differs in {(Y != Y_ref).sum()} bytes"
+    Xg = g_d.decrypt(Yg, Yg if inplace else None)
+    g_d.sync()
+    assert np.array_equal(host(Xg), X)
+    assert np.array_equal(ref_d.decrypt(Y_ref), X)
+    g_e.close()
+    g_d.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_config_single_480_frame(B, orc, kind):
+    """480 x 480 x 3, uniform random bytes (seed 1), key from seed 1, n = 4, r = 5:
+    encrypt and decrypt bit-exact against the oracle."""
+    X = synth.uniform_frames(1, 480, 480, 3, seed=1)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 1), X, 4, 5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("n", [4, 8, 12])
+def test_config_smooth_576_clip(B, orc, kind, n):
+    """576 x 576 x 3 smooth synthetic video, n in {4, 8, 12}: 3 consecutive frames
+    of the clip (state carried across frames), encrypt + decrypt."""
+    X = synth.smooth_clip(3, 576, 576, 3, seed=2)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 2 + n), X, n, 5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("H,W,C,n,r", [
+    (17, 23, 3, 5, 5),     # odd sizes, one tile
+    (100, 37, 3, 91, 2),   # several tiles, ragged last tile, tiny subframes
+    (45, 200, 3, 300, 5),  # W > H: source rows wrap several times
+    (200, 45, 1, 12, 5),   # C = 1, tall
+    (31, 31, 4, 1, 5),     # n = 1: the subframe seeds from its own last byte
+    (64, 64, 1, 2048, 3),  # 2-byte subframes (the minimum)
+    (33, 65, 3, 7, 1),     # one round
+    (70, 70, 3, 4900, 5),  # one pixel per subframe
+])
+def test_odd_shapes(B, orc, kind, H, W, C, n, r):
+    X = synth.uniform_frames(2, H, W, C, seed=H + W)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 300 + n), X, n, r)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_chunked_and_in_place(B, orc, kind):
+    """Frames processed in passes of 2 and in place give the same stream."""
+    X = synth.uniform_frames(5, 40, 56, 3, seed=9)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 9), X, 6, 5, chunk=2, inplace=True)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 9), X, 6, 1, chunk=3, inplace=True)
+
+
+def test_state_checkpoint_resume(B):
+    """10 frames in one call == 5 + save + load into a fresh context + 5."""
+    X = synth.uniform_frames(10, 32, 48, 3, seed=10)
+    key = synth.key_for_seed(0, 10)
+    a = B.Cipher(0, key, 32, 48, 3, 6, 5)
+    full = host(a.encrypt(dev(X)))
+    b = B.Cipher(0, key, 32, 48, 3, 6, 5)
+    first = host(b.encrypt(dev(X[:5])))
+    st = b.save_state()
+    assert b.frame_index == 5
+    c = B.Cipher(0, key, 32, 48, 3, 6, 5)
+    c.load_state(st)
+    assert c.frame_index == 5
+    second = host(c.encrypt(dev(X[5:])))
+    assert np.array_equal(np.concatenate([first, second]), full)
+    with pytest.raises(B.VcError):
+        B.Cipher(0, key, 32, 48, 3, 7, 5).load_state(st)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_host_buffer_entry_point(B, direction):
+    """crypt_frames_host (host buffers, copies inside) == the device entry point."""
+    X = synth.uniform_frames(7, 48, 64, 3, seed=11)
+    key = synth.key_for_seed(1, 11)
+    a = B.Cipher(1, key, 48, 64, 3, 8, 5)
+    a.set_chunk(3)
+    out = np.empty_like(X)
+    a.crypt_host(direction, X, out)
+    b = B.Cipher(1, key, 48, 64, 3, 8, 5)
+    ref = host(b.encrypt(dev(X)) if direction == 0 else b.decrypt(dev(X)))
+    assert np.array_equal(out, ref)
+
+
+def test_invalid_arguments_are_errors(B):
+    with pytest.raises(B.VcError) as e:
+        B.Cipher(0, [0.3, 0.6, 0.5, 0.2], 16, 16)
+    assert e.value.code == 2
+    with pytest.raises(B.VcError) as e:
+        B.Cipher(0, [0.3, 0.2, 0.5, 0.2], 4, 4, 1, 16)
+    assert e.value.code == 3
+    with pytest.raises(B.VcError) as e:
+        B.Cipher(1, [0.3, 0.39, 0.5], 16, 16)
+    assert e.value.code == 2
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_full_size_768_n4096_sampled(B, orc, kind):
+    """The benchmark's launch configuration (768 x 768 x 3, n = 4096, r = 5, many
+    frames per pass): all 24 frames round-trip; the first 3 equal the oracle
+    byte for byte."""
+    F = 24
+    X = synth.smooth_clip(F, 768, 768, 3, seed=12)
+    key = synth.key_for_seed(kind, 12)
+    g = B.Cipher(kind, key, 768, 768, 3, 4096, 5)
+    g.set_chunk(F)
+    d = dev(X)
+    Y = g.encrypt(d)
+    g.sync()
+    Yh = host(Y)
+    ref = orc.OracleCipher(kind, key, 768, 768, 3, 4096, 5)
+    assert np.array_equal(Yh[:3], ref.encrypt(X[:3]))
+    dd = B.Cipher(kind, key, 768, 768, 3, 4096, 5)
+    dd.set_chunk(F)
+    assert np.array_equal(host(dd.decrypt(Y)), X)
