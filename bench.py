@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--size", type=int, default=768)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--rounds", type=int, default=5)
+    ap.add_argument("--plcm-fp64", action="store_true", help="PLCM division on the binary64 pipe (A/B)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -55,7 +56,8 @@ def workload_name(a) -> str:
 
 
 def config(a, world: int) -> dict:
-    return {"workload": workload_name(a), "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
+    return {"workload": workload_name(a), "plcm_division": "binary64 pipe" if a.plcm_fp64 else "integer pipes",
+            "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
             "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
             "l2": "inputs 425 MB > 129 MB L2, no flush"}
 
@@ -194,6 +196,7 @@ def run_ours(a) -> None:
     key = synth.key_for_seed(kind, 100 + rank)
     ciph = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
     ciph.set_chunk(F)
+    ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -244,6 +247,7 @@ def run_ours(a) -> None:
         h_out = torch.empty_like(h_in).pin_memory()
         ce = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
         ce.set_chunk(max(1, F // 4))
+        ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
         for _ in range(max(1, a.warmup - 1)):
             ce.crypt_host(0, h_in, h_out, stream=stream)
         if world > 1:

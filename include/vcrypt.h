@@ -115,6 +115,19 @@ int64_t enc_frame_index(const vc_ctx* ctx);
  * by its device code or its asynchronous CUDA work (VC_OK if none); clears it. */
 int enc_sync_status(vc_ctx* ctx);
 
+/* ---- tuning options (enc_set_option / enc_get_option) ----
+ * VC_OPT_CHUNK:    frames per internal pass (same as enc_set_chunk), 1..65535.
+ * VC_OPT_PLCM_INT: 1 (default) evaluates the PLCM division and subtraction of
+ *                  Eq. 5 exactly on the integer pipes, 0 uses the binary64
+ *                  pipe; both give identical bits (IEEE-754 round to nearest). */
+#define VC_OPT_CHUNK 1
+#define VC_OPT_PLCM_INT 2
+
+/* Set / read a tuning option.  Options never change the ciphertext.
+ * Errors: VC_ERR_ARG (unknown option or value out of range). */
+int enc_set_option(vc_ctx* ctx, int32_t option, int64_t value);
+int enc_get_option(const vc_ctx* ctx, int32_t option, int64_t* value);
+
 /* Upper bound on frames processed per internal pass (scratch memory grows with
  * it: about (r + 2) * N bytes per frame).  Default 32. */
 int enc_set_chunk(vc_ctx* ctx, int32_t frames_per_pass);

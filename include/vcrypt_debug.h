@@ -18,8 +18,9 @@ extern "C" {
  * Cody-Waite reduction by pi/2, Taylor polynomials by Horner), n doubles each. */
 int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream);
 
-/* out[i] = one PLCM step F(x[i], p[i]) (Eq. 5). */
-int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, void* stream);
+/* out[i] = one PLCM step F(x[i], p[i]) (Eq. 5); variant 0 = binary64 pipe,
+ * 1 = integer-pipe evaluation (must give the same bits). */
+int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, int32_t variant, void* stream);
 
 /* One 2DLASM step (Eq. 6): in = n triples (x, y, mu), out = n pairs (x', y'). */
 int vc_dbg_lasm(const double* d_xymu, double* d_out, int64_t n, void* stream);

@@ -18,6 +18,7 @@ _lib = None
 
 VC_OK = 0
 VC_PLCM, VC_2DLASM = 0, 1
+VC_OPT_CHUNK, VC_OPT_PLCM_INT = 1, 2
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
 
@@ -63,7 +64,9 @@ def lib():
             "vc_strerror": (C.c_char_p, [C.c_int]),
             "vc_last_error": (C.c_char_p, []),
             "vc_dbg_csin": (C.c_int, [p, p, i64, p]),
-            "vc_dbg_plcm": (C.c_int, [p, p, p, i64, p]),
+            "vc_dbg_plcm": (C.c_int, [p, p, p, i64, i32, p]),
+            "enc_set_option": (C.c_int, [p, i32, i64]),
+            "enc_get_option": (C.c_int, [p, i32, C.POINTER(C.c_int64)]),
             "vc_dbg_lasm": (C.c_int, [p, p, i64, p]),
             "vc_dbg_keystream": (C.c_int, [p, p, p, i32, p]),
             "vc_dbg_layout": (C.c_int, [p, p]),
@@ -178,8 +181,19 @@ def vc_dbg_csin(d_t, d_out, stream=None) -> None:
     _check(lib().vc_dbg_csin(_dptr(d_t), _dptr(d_out), d_t.numel(), _stream(stream)), "vc_dbg_csin")
 
 
-def vc_dbg_plcm(d_x, d_p, d_out, stream=None) -> None:
-    _check(lib().vc_dbg_plcm(_dptr(d_x), _dptr(d_p), _dptr(d_out), d_x.numel(), _stream(stream)), "vc_dbg_plcm")
+def vc_dbg_plcm(d_x, d_p, d_out, variant: int = 0, stream=None) -> None:
+    _check(lib().vc_dbg_plcm(_dptr(d_x), _dptr(d_p), _dptr(d_out), d_x.numel(), variant, _stream(stream)),
+           "vc_dbg_plcm")
+
+
+def enc_set_option(ctx, option: int, value: int) -> None:
+    _check(lib().enc_set_option(ctx, option, value), "enc_set_option")
+
+
+def enc_get_option(ctx, option: int) -> int:
+    v = C.c_int64()
+    _check(lib().enc_get_option(ctx, option, C.byref(v)), "enc_get_option")
+    return v.value
 
 
 def vc_dbg_lasm(d_xymu, d_out, stream=None) -> None:
@@ -248,6 +262,12 @@ class Cipher:
 
     def set_chunk(self, frames: int) -> None:
         enc_set_chunk(self.ctx, frames)
+
+    def set_option(self, option: int, value: int) -> None:
+        enc_set_option(self.ctx, option, value)
+
+    def get_option(self, option: int) -> int:
+        return enc_get_option(self.ctx, option)
 
     def layout_info(self) -> dict:
         return vc_dbg_layout(self.ctx)

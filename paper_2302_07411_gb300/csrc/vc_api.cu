@@ -114,6 +114,7 @@ struct vc_ctx {
   cudaEvent_t ev[6] = {};
   int64_t frame = 0;
   cudaStream_t last = nullptr;
+  bool plcm_int = true;
   // stage profiling: recorded (stage, start, end) event pairs and a free pool
   bool prof = false;
   struct Mark {
@@ -209,7 +210,7 @@ int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t
   }
   {
     StageMark m(c, st, 1, 1);
-    VC_CUDA(vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, st));
+    VC_CUDA(vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st));
   }
   const int r = L.rounds;
   StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
@@ -522,6 +523,29 @@ int enc_profile_read(vc_ctx* c, double* ms3, int64_t* launches3) {
   return VC_OK;
 }
 
+int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
+  if (!c) return VC_ERR_ARG;
+  switch (option) {
+    case VC_OPT_CHUNK:
+      return enc_set_chunk(c, value < 1 || value > 65535 ? 0 : (int32_t)value);
+    case VC_OPT_PLCM_INT:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      c->plcm_int = value != 0;
+      return VC_OK;
+  }
+  set_err("unknown option %d", option);
+  return VC_ERR_ARG;
+}
+
+int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
+  if (!c || !value) return VC_ERR_ARG;
+  switch (option) {
+    case VC_OPT_CHUNK: *value = c->chunk; return VC_OK;
+    case VC_OPT_PLCM_INT: *value = c->plcm_int ? 1 : 0; return VC_OK;
+  }
+  return VC_ERR_ARG;
+}
+
 void enc_destroy(vc_ctx* c) {
   if (!c) return;
   if (c->last) cudaStreamSynchronize(c->last);
@@ -557,9 +581,9 @@ int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream) {
   return VC_OK;
 }
 
-int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, void* stream) {
-  if (n < 0 || (n > 0 && (!d_x || !d_p || !d_out))) return VC_ERR_ARG;
-  VC_CUDA(vc::launch_dbg_plcm(d_x, d_p, d_out, n, (cudaStream_t)stream));
+int vc_dbg_plcm(const double* d_x, const double* d_p, double* d_out, int64_t n, int32_t variant, void* stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_p || !d_out)) || variant < 0 || variant > 1) return VC_ERR_ARG;
+  VC_CUDA(vc::launch_dbg_plcm(d_x, d_p, d_out, n, variant, (cudaStream_t)stream));
   return VC_OK;
 }
 
@@ -581,7 +605,7 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
   for (int f0 = 0; f0 < nframes; f0 += F) {
     const int nf = (nframes - f0) < F ? (nframes - f0) : F;
     VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
-    VC_CUDA(vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, st));
+    VC_CUDA(vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st));
     VC_CUDA(cudaMemcpy2DAsync(d_ks + (size_t)f0 * L.rounds * L.N, (size_t)L.N, c->d_ks, (size_t)L.Npad, (size_t)L.N,
                               (size_t)nf * L.rounds, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaMemcpyAsync(d_sc + f0, c->d_sc, nf * sizeof(long long), cudaMemcpyDeviceToDevice, st));

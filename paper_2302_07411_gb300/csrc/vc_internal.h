@@ -50,7 +50,7 @@ cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cuda
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
                                   cudaStream_t st);
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             cudaStream_t st);
+                             bool plcm_int, cudaStream_t st);
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
                              const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st);
@@ -63,7 +63,8 @@ size_t round_smem_bytes(const Layout& L);
 
 // Diagnostics: the chaotic primitives applied elementwise.
 cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st);
-cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, cudaStream_t st);
+cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant,
+                            cudaStream_t st);
 cudaError_t launch_dbg_lasm(const double* xymu, double* out, long long n, cudaStream_t st);
 
 }  // namespace vc

@@ -254,7 +254,7 @@ __device__ __forceinline__ void shr128(uint64_t& lo, uint64_t& hi, int bits) {
   }
 }
 
-template <int KIND>
+template <int KIND, bool INTDIV>
 __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
@@ -276,6 +276,11 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
     y2 = ch.st[4 * i + 3];
     pm1 = ch.par[2 * i];
     pm2 = ch.par[2 * i + 1];
+  }
+  PlcmMap m1{}, m2{};
+  if (KIND == 0 && INTDIV) {
+    m1 = make_plcm(p1, q1);
+    m2 = make_plcm(p2, q2);
   }
   uint64_t c0 = ch.carry[2 * i], c1 = ch.carry[2 * i + 1];
   int clen = ch.carry_len[i];
@@ -304,8 +309,13 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
     // 2. whole iterates
     while (rem >= STEP) {
       if (KIND == 0) {
-        x1 = plcm_step(x1, p1, q1);
-        x2 = plcm_step(x2, p2, q2);
+        if (INTDIV) {
+          x1 = plcm_step_int(x1, m1);
+          x2 = plcm_step_int(x2, m2);
+        } else {
+          x1 = plcm_step(x1, p1, q1);
+          x2 = plcm_step(x2, p2, q2);
+        }
         w.put(mant48(x1) ^ mant48(x2), 6);
       } else {
         lasm_step(x1, y1, pm1);
@@ -319,8 +329,13 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
     if (rem > 0) {
       uint64_t lo, hi;
       if (KIND == 0) {
-        x1 = plcm_step(x1, p1, q1);
-        x2 = plcm_step(x2, p2, q2);
+        if (INTDIV) {
+          x1 = plcm_step_int(x1, m1);
+          x2 = plcm_step_int(x2, m2);
+        } else {
+          x1 = plcm_step(x1, p1, q1);
+          x2 = plcm_step(x2, p2, q2);
+        }
         lo = mant48(x1) ^ mant48(x2);
         hi = 0;
       } else {
@@ -355,13 +370,15 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
 }
 
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             cudaStream_t st) {
+                             bool plcm_int, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
   const int blocks = (L.n + 31) / 32;
-  if (kind == 0)
-    k_keystream<0><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  if (kind == 0 && plcm_int)
+    k_keystream<0, true><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  else if (kind == 0)
+    k_keystream<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   else
-    k_keystream<1><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+    k_keystream<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   return cudaGetLastError();
 }
 
@@ -802,9 +819,12 @@ __global__ void k_dbg_csin(const double* t, double* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = csin(t[i]);
 }
-__global__ void k_dbg_plcm(const double* x, const double* p, double* out, long long n) {
+__global__ void k_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = plcm_step(x[i], p[i], __dsub_rn(0.5, p[i]));
+  if (i < n) {
+    const double q = __dsub_rn(0.5, p[i]);
+    out[i] = variant ? plcm_step_int(x[i], make_plcm(p[i], q)) : plcm_step(x[i], p[i], q);
+  }
 }
 __global__ void k_dbg_lasm(const double* xymu, double* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -821,9 +841,10 @@ cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStrea
   k_dbg_csin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, out, n);
   return cudaGetLastError();
 }
-cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, cudaStream_t st) {
+cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant,
+                            cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_dbg_plcm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, p, out, n);
+  k_dbg_plcm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, p, out, n, variant);
   return cudaGetLastError();
 }
 cudaError_t launch_dbg_lasm(const double* xymu, double* out, long long n, cudaStream_t st) {

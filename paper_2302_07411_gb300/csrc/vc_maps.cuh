@@ -8,6 +8,8 @@
 #pragma once
 #include <cstdint>
 
+#include "vc_ieee.cuh"
+
 namespace vc {
 
 // ---- the cipher's sine (reading of "sin" in Eq. 1 and Eq. 6) ----------------
@@ -76,6 +78,41 @@ __device__ __forceinline__ double plcm_step(double x, double p, double q) {
   const double num = lo ? xr : __dsub_rn(xr, p);
   const double den = lo ? p : q;
   return __ddiv_rn(num, den);
+}
+
+// The same PLCM step evaluated on the integer pipes (vc_ieee.cuh): identical
+// binary64 results; the rare operands outside the normal range (x = 0 or 1,
+// x = p, subnormal quotients) take the hardware path above.
+struct PlcmMap {
+  double p, q;    // p and RN(1/2 - p)
+  Divisor dp, dq;
+};
+
+__device__ __forceinline__ PlcmMap make_plcm(double p, double q) {
+  PlcmMap m;
+  m.p = p;
+  m.q = q;
+  m.dp = make_divisor(p);
+  m.dq = make_divisor(q);
+  return m;
+}
+
+__device__ __forceinline__ double plcm_step_int(double x, const PlcmMap& m) {
+  const uint64_t xb = ieee_bits(x);
+  const bool refl = xb > 0x3FE0000000000000ull;  // x > 1/2 (positive doubles order like their bits)
+  bool ok1 = true, ok2 = true, ok3 = true;
+  const double om = one_minus_int(x, ok1);
+  const double xr = refl ? om : x;
+  const bool lo = ieee_bits(xr) < ieee_bits(m.p);
+  const double sb = sub_rn_int(xr, m.p, ok2);
+  const double a = lo ? xr : sb;
+  Divisor d;
+  d.mb = lo ? m.dp.mb : m.dq.mb;
+  d.inv = lo ? m.dp.inv : m.dq.inv;
+  d.eb = lo ? m.dp.eb : m.dq.eb;
+  double r = div_rn_int(a, d, ok3);
+  if ((refl && !ok1) || (!lo && !ok2) || !ok3) r = plcm_step(x, m.p, m.q);
+  return r;
 }
 
 // ---- 2DLASM, Eq. 6 ----------------------------------------------------------

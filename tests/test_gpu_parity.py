@@ -47,16 +47,41 @@ def test_csin_bitwise(B, orc):
     assert np.array_equal(got[idx].view(np.uint64), exp.view(np.uint64))
 
 
-def test_plcm_step_bitwise(B, orc):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_plcm_step_bitwise(B, orc, variant):
+    """Eq. 5 on the binary64 pipe (0) and on the integer pipes (1) == oracle,
+    including the edge operands 0, 1/2, 1, x = p and tiny x."""
     rng = np.random.default_rng(101)
-    x = np.concatenate([rng.uniform(0, 1, 50000), rng.uniform(0, 1e-6, 1000), np.array([0.0, 0.5, 1.0, 0.25])])
+    x = np.concatenate([rng.uniform(0, 1, 50000), rng.uniform(0, 1e-6, 1000), 2.0 ** -rng.uniform(30, 1074, 500),
+                        np.array([0.0, 0.5, 1.0, 0.25, 0.3, 0.7, 1 - 2 ** -53])])
     p = rng.uniform(0.01, 0.49, x.size)
-    p[-4:] = [0.3, 0.3, 0.3, 0.25]
+    p[-7:] = [0.3, 0.3, 0.3, 0.25, 0.3, 0.3, 0.3]
     out = torch.empty(x.size, dtype=torch.float64, device="cuda")
-    B.vc_dbg_plcm(dev(x), dev(p), out)
+    B.vc_dbg_plcm(dev(x), dev(p), out, variant)
     got = host(out)
     exp = np.array([orc.plcm_step(float(a), float(b)) for a, b in zip(x, p)])
     assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def test_plcm_integer_pipe_equals_binary64_pipe_at_scale(B):
+    """2^26 random operands per batch, 4 batches: the integer-pipe step returns
+    the same bits as the device's binary64 division (which is IEEE-correct)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    n = 1 << 26
+    for batch in range(4):
+        x = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+        if batch == 1:
+            x = x * 1e-3
+        if batch == 2:
+            x = 1.0 - x * 1e-9
+        p = 0.01 + 0.48 * torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+        a = torch.empty_like(x)
+        b = torch.empty_like(x)
+        B.vc_dbg_plcm(x, p, a, 0)
+        B.vc_dbg_plcm(x, p, b, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(a.view(torch.int64), b.view(torch.int64))
 
 
 def test_lasm_step_bitwise(B, orc):
@@ -82,15 +107,16 @@ def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
     return out
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind,plcm_int", [(0, 1), (0, 0), (1, 1)])
 @pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
                                                (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6)])
-def test_keystream_and_confusion_seeds(B, orc, kind, H, W, C, n, r, frames):
+def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, H, W, C, n, r, frames):
     """Sec. 3 byte streams and Alg. 1's s_c per frame, across frames (the left
     over bytes of an iterate carry over, R7)."""
     key = synth.key_for_seed(kind, 200 + n)
     ref = orc.OracleCipher(kind, key, H, W, C, n, r)
     g = B.Cipher(kind, key, H, W, C, n, r)
+    g.set_option(B.VC_OPT_PLCM_INT, plcm_int)
     N = H * W * C
     d_ks = torch.empty(frames * r * N, dtype=torch.uint8, device="cuda")
     d_sc = torch.empty(frames, dtype=torch.int64, device="cuda")
