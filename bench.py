@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--rounds", type=int, default=5)
     ap.add_argument("--plcm-fp64", action="store_true", help="PLCM division on the binary64 pipe (A/B)")
+    ap.add_argument("--ks-lanes", type=int, default=2, choices=[1, 2], help="lanes per subframe in the keystream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -197,6 +198,7 @@ def run_ours(a) -> None:
     ciph = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
     ciph.set_chunk(F)
     ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
+    ciph.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -248,6 +250,7 @@ def run_ours(a) -> None:
         ce = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
         ce.set_chunk(max(1, F // 4))
         ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
+        ce.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
         for _ in range(max(1, a.warmup - 1)):
             ce.crypt_host(0, h_in, h_out, stream=stream)
         if world > 1:

@@ -119,9 +119,13 @@ int enc_sync_status(vc_ctx* ctx);
  * VC_OPT_CHUNK:    frames per internal pass (same as enc_set_chunk), 1..65535.
  * VC_OPT_PLCM_INT: 1 (default) evaluates the PLCM division and subtraction of
  *                  Eq. 5 exactly on the integer pipes, 0 uses the binary64
- *                  pipe; both give identical bits (IEEE-754 round to nearest). */
+ *                  pipe; both give identical bits (IEEE-754 round to nearest).
+ * VC_OPT_KS_LANES: lanes per subframe chain pair in the keystream kernel:
+ *                  2 (default, one lane per chaotic map) or 1 (one thread runs
+ *                  both maps of the pair). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
+#define VC_OPT_KS_LANES 3
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */

@@ -115,6 +115,7 @@ struct vc_ctx {
   int64_t frame = 0;
   cudaStream_t last = nullptr;
   bool plcm_int = true;
+  int ks_lanes = 2;
   // stage profiling: recorded (stage, start, end) event pairs and a free pool
   bool prof = false;
   struct Mark {
@@ -210,7 +211,8 @@ int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t
   }
   {
     StageMark m(c, st, 1, 1);
-    VC_CUDA(vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st));
+    VC_CUDA(c->ks_lanes == 2 ? vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st)
+                             : vc::launch_keystream_thread(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st));
   }
   const int r = L.rounds;
   StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
@@ -532,6 +534,10 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return VC_ERR_ARG;
       c->plcm_int = value != 0;
       return VC_OK;
+    case VC_OPT_KS_LANES:
+      if (value != 1 && value != 2) return VC_ERR_ARG;
+      c->ks_lanes = (int)value;
+      return VC_OK;
   }
   set_err("unknown option %d", option);
   return VC_ERR_ARG;
@@ -542,6 +548,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
   switch (option) {
     case VC_OPT_CHUNK: *value = c->chunk; return VC_OK;
     case VC_OPT_PLCM_INT: *value = c->plcm_int ? 1 : 0; return VC_OK;
+    case VC_OPT_KS_LANES: *value = c->ks_lanes; return VC_OK;
   }
   return VC_ERR_ARG;
 }
@@ -605,7 +612,9 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
   for (int f0 = 0; f0 < nframes; f0 += F) {
     const int nf = (nframes - f0) < F ? (nframes - f0) : F;
     VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
-    VC_CUDA(vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st));
+    VC_CUDA(c->ks_lanes == 2
+                ? vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st)
+                : vc::launch_keystream_thread(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st));
     VC_CUDA(cudaMemcpy2DAsync(d_ks + (size_t)f0 * L.rounds * L.N, (size_t)L.N, c->d_ks, (size_t)L.Npad, (size_t)L.N,
                               (size_t)nf * L.rounds, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaMemcpyAsync(d_sc + f0, c->d_sc, nf * sizeof(long long), cudaMemcpyDeviceToDevice, st));

@@ -150,6 +150,81 @@ __host__ __device__ __forceinline__ double sub_rn_int(double a, double b, bool& 
   return ieee_double(((uint64_t)(e & 0x7FF) << 52) | (q & kMant52));
 }
 
+// PLCM (Eq. 5) step on the integer pipes in Q0.64 fixed point, for a chain
+// whose p and q = RN(1/2 - p) are both >= 2^-11 (true of every derived
+// parameter, p in [0.05, 0.45]).  Every double in [2^-12, 1) is an exact Q0.64
+// number, so the reflection 1 - x and the difference x - p are exact integer
+// operations; RN(x - p) is the 53-bit rounding of that integer, and the
+// quotient uses the reciprocal division above.  Operates on the bit pattern
+// of x; returns the bit pattern of F(x) with ok = false for the few operands
+// it does not cover (x = 0, x = 1, x = p, tiny quotients).
+struct PlcmFx {
+  uint64_t P;      // p 2^64
+  Divisor dp, dq;  // p and q as divisors
+};
+
+__host__ __device__ inline bool make_plcm_fx(double p, double q, PlcmFx& F) {
+  const uint64_t pb = ieee_bits(p), qb = ieee_bits(q);
+  const int ep = (int)(pb >> 52), eq = (int)(qb >> 52);
+  F.dp = make_divisor(p);
+  F.dq = make_divisor(q);
+  if (ep < 1012 || ep > 1021 || eq < 1012 || eq > 1021) {  // need 2^-11 <= p, q < 1/2
+    F.P = 0;
+    return false;
+  }
+  F.P = F.dp.mb << (ep - 1011);
+  return true;
+}
+
+__host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const PlcmFx& F, bool& ok) {
+  const int ex = (int)(xb >> 52);
+  const uint64_t m = (xb & kMant52) | (1ull << 52);
+  const int sx = ex - 1011;                 // x = m 2^(sx - 64) in Q0.64 when 0 <= sx <= 11
+  const bool small = sx < 0;                // x < 2^-12 < p: always the x/p branch
+  const uint64_t X = m << (sx & 15);
+  const bool refl = xb > 0x3FE0000000000000ull;  // x > 1/2
+  const uint64_t XR = refl ? (0ull - X) : X;      // 1 - x, exact
+  const bool lo = small || XR < F.P;
+  const uint64_t A = lo ? XR : XR - F.P;          // x (or 1 - x), or the exact x - p
+  const int lz = ieee_clz64(A);
+  const uint64_t An = A << (lz & 63);
+  uint64_t ma = An >> 11;                         // 53 significant bits
+  const uint32_t R = (uint32_t)An & 0x7FFu;       // dropped bits (zero unless x - p needs rounding)
+  ma += (R > 0x400u || (R == 0x400u && (ma & 1))) ? 1 : 0;
+  int ea = 1022 - lz;
+  if (ma == (1ull << 53)) {
+    ma = 1ull << 52;
+    ea++;
+  }
+  if (small) {
+    ma = m;
+    ea = ex;
+  }
+  // RN(a / b), b = p on the x/p branch, q on the (x - p)/q branch
+  const uint64_t mb = lo ? F.dp.mb : F.dq.mb;
+  const uint64_t inv = lo ? F.dp.inv : F.dq.inv;
+  const int eb = lo ? F.dp.eb : F.dq.eb;
+  const bool lt = ma < mb;
+  const int s = lt ? 53 : 52;
+  const uint64_t lo64 = ma * inv;
+  const uint64_t hi64 = ieee_mulhi(ma, inv);
+  // floor(ma inv / 2^(115 - s)): shift by 62 (s = 53) or 63 (s = 52)
+  uint64_t q = lt ? ((hi64 << 2) | (lo64 >> 62)) : ((hi64 << 1) | (lo64 >> 63));
+  uint64_t rem = (ma << s) - q * mb;
+  if (rem >= mb) {
+    q++;
+    rem -= mb;
+  }
+  q += ((rem << 1) > mb) ? 1 : 0;  // a quotient of two 53-bit numbers is never a tie
+  int e = ea - eb + 1023 - (lt ? 1 : 0);
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    e++;
+  }
+  ok = (ex >= 1) && (ex <= 1022) && (small || A != 0) && (e >= 1);
+  return ((uint64_t)(e & 0x7FF) << 52) | (q & kMant52);
+}
+
 // 1 - x for x in (1/2, 1): exact; x = mx 2^-53 with mx in (2^52, 2^53).
 __host__ __device__ __forceinline__ double one_minus_int(double x, bool& ok) {
   const uint64_t xb = ieee_bits(x);

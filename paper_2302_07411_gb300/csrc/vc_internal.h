@@ -51,6 +51,8 @@ cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, 
                                   cudaStream_t st);
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                              bool plcm_int, cudaStream_t st);
+cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+                                    bool plcm_int, cudaStream_t st);
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
                              const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st);

@@ -369,8 +369,222 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
   ch.carry_len[i] = clen;
 }
 
+// -----------------------------------------------------------------------------
+// Keystream, lane-pair form: the two maps of subframe i run on lanes 2i and
+// 2i+1 of a warp (one dependency chain per lane) and exchange their 6-byte
+// groups with one shuffle.  Both lanes then hold the same byte stream and
+// write it as aligned 8-byte words: 24 bytes (4 PLCM or 2 2DLASM iterates)
+// advance the write position by 3 whole words, so the phase q mod 8 is the
+// same at every group boundary and a group is three funnel shifts and three
+// 8-byte stores.  Range heads and tails (shared words with the neighbouring
+// subframes) go byte by byte.
+
+__device__ __forceinline__ uint64_t fsh(uint64_t a, uint64_t b, int sh) {
+  // (b:a) shifted left by sh bits, high word: b << sh | a >> (64 - sh); sh in [0, 56]
+  return (b << sh) | ((a >> (63 - sh)) >> 1);
+}
+
+struct PairWriter {
+  uint8_t* fb;     // keystream base of the current frame (round 0)
+  long long Npad;
+  int j, q, qs, qe, side;
+  uint64_t acc;    // bytes [0, q mod 8) of the word containing q
+  uint32_t own;    // which of them belong to this subframe's range
+
+  __device__ __forceinline__ uint8_t* word_ptr(int qq) const { return fb + (long long)j * Npad + (qq & ~7); }
+  __device__ __forceinline__ void flush(int qq) {
+    if (side == 0 && own) {
+      uint8_t* a = word_ptr(qq);
+      if (own == 0xFFu) {
+        *reinterpret_cast<uint64_t*>(a) = acc;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+          if (own & (1u << k)) a[k] = (uint8_t)(acc >> (8 * k));
+      }
+    }
+    acc = 0;
+    own = 0;
+  }
+  __device__ __forceinline__ void end_of_range_check() {
+    if (q == qe) {
+      flush(q - 1);
+      j++;
+      q = qs;
+    }
+  }
+  // Append the low cnt (0..8) bytes of v, one at a time.
+  __device__ __forceinline__ void put_slow(uint64_t v, int cnt) {
+    for (int k = 0; k < cnt; k++) {
+      const int ph = q & 7;
+      acc |= ((v >> (8 * k)) & 0xFFull) << (8 * ph);
+      own |= 1u << ph;
+      q++;
+      if (q == qe) {
+        flush(q - 1);
+        j++;
+        q = qs;
+      } else if ((q & 7) == 0) {
+        flush(q - 1);
+      }
+    }
+  }
+  __device__ __forceinline__ bool fast_ok() const { return q + 24 <= qe && own == ((1u << (q & 7)) - 1u); }
+  // Append 24 bytes c0 | c1 | c2 (little-endian order).
+  __device__ __forceinline__ void put24(uint64_t c0, uint64_t c1, uint64_t c2) {
+    const int sh = 8 * (q & 7);
+    const uint64_t w0 = acc | (c0 << sh);
+    const uint64_t w1 = fsh(c0, c1, sh);
+    const uint64_t w2 = fsh(c1, c2, sh);
+    acc = (c2 >> (63 - sh)) >> 1;
+    uint64_t* a = reinterpret_cast<uint64_t*>(word_ptr(q));
+    if (side == 0) {
+      a[0] = w0;
+      a[2] = w2;
+    } else {
+      a[1] = w1;
+    }
+    q += 24;
+    end_of_range_check();
+  }
+};
+
+template <int KIND, bool FX>
+__global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt >> 1;
+  const int side = gt & 1;
+  if (i >= L.n) return;  // both lanes of a pair leave together
+  const unsigned pmask = 3u << (threadIdx.x & 30);
+  constexpr int STEP = KIND == 0 ? 6 : 12;
+
+  double x = 0, y = 0, p = 0, qd = 0, pm = 0;
+  uint64_t xb = 0;
+  PlcmFx F{};
+  bool fx_ok = false;
+  if (KIND == 0) {
+    x = ch.st[2 * i + side];
+    p = ch.par[4 * i + 2 * side];
+    qd = ch.par[4 * i + 2 * side + 1];
+    xb = (uint64_t)__double_as_longlong(x);
+    if (FX) fx_ok = make_plcm_fx(p, qd, F);
+  } else {
+    x = ch.st[4 * i + 2 * side];
+    y = ch.st[4 * i + 2 * side + 1];
+    pm = ch.par[2 * i + side];
+  }
+  uint64_t c0 = ch.carry[2 * i], c1 = ch.carry[2 * i + 1];
+  int clen = ch.carry_len[i];
+
+  PairWriter w;
+  w.Npad = L.Npad;
+  w.qs = L.C * tb.pi[i];
+  w.qe = L.C * tb.pi[i + 1];
+  w.side = side;
+  const long long per_frame = (long long)L.rounds * (w.qe - w.qs);
+
+  // one PLCM iterate of this lane's map; the pair's XORed 6-byte group
+  auto plcm_next = [&]() -> uint64_t {
+    if (FX) {
+      bool ok = true;
+      uint64_t nb = fx_ok ? plcm_fx_step(xb, F, ok) : 0;
+      if (!fx_ok || !ok) nb = (uint64_t)__double_as_longlong(plcm_step(__longlong_as_double((long long)xb), p, qd));
+      xb = nb;
+    } else {
+      xb = (uint64_t)__double_as_longlong(plcm_step(__longlong_as_double((long long)xb), p, qd));
+    }
+    const uint64_t own48 = xb & 0xFFFFFFFFFFFFull;
+    return own48 ^ __shfl_xor_sync(pmask, own48, 1);
+  };
+  auto lasm_next = [&](uint64_t& vx, uint64_t& vy) {
+    lasm_step(x, y, pm);
+    const uint64_t ox = mant48(x), oy = mant48(y);
+    vx = ox ^ __shfl_xor_sync(pmask, ox, 1);
+    vy = oy ^ __shfl_xor_sync(pmask, oy, 1);
+  };
+
+  for (int f = 0; f < nframes; f++) {
+    w.fb = ks + (long long)f * L.rounds * L.Npad;
+    w.j = 0;
+    w.q = w.qs;
+    w.acc = 0;
+    w.own = 0;
+    long long rem = per_frame;
+    while (clen > 0 && rem > 0) {  // bytes left over from the last iterate (R7)
+      int take = clen < 8 ? clen : 8;
+      if (take > rem) take = (int)rem;
+      w.put_slow(c0, take);
+      shr128(c0, c1, 8 * take);
+      clen -= take;
+      rem -= take;
+    }
+    while (rem > 0) {
+      if (rem >= 24 && w.fast_ok()) {
+        uint64_t a0, a1, a2, a3;
+        if (KIND == 0) {
+          a0 = plcm_next();
+          a1 = plcm_next();
+          a2 = plcm_next();
+          a3 = plcm_next();
+        } else {
+          lasm_next(a0, a1);
+          lasm_next(a2, a3);
+        }
+        w.put24(a0 | (a1 << 48), (a1 >> 16) | (a2 << 32), (a2 >> 32) | (a3 << 16));
+        rem -= 24;
+      } else {
+        uint64_t lo, hi = 0;
+        if (KIND == 0) {
+          lo = plcm_next();
+        } else {
+          uint64_t vx, vy;
+          lasm_next(vx, vy);
+          lo = vx | (vy << 48);
+          hi = vy >> 16;
+        }
+        const int take = rem < STEP ? (int)rem : STEP;
+        w.put_slow(lo, take < 8 ? take : 8);
+        if (take > 8) w.put_slow(hi, take - 8);
+        if (take < STEP) {  // keep the rest of the iterate for the next frame
+          shr128(lo, hi, 8 * take);
+          c0 = lo;
+          c1 = hi;
+          clen = STEP - take;
+        }
+        rem -= take;
+      }
+    }
+  }
+  if (KIND == 0) {
+    ch.st[2 * i + side] = __longlong_as_double((long long)xb);
+  } else {
+    ch.st[4 * i + 2 * side] = x;
+    ch.st[4 * i + 2 * side + 1] = y;
+  }
+  if (side == 0) {
+    ch.carry[2 * i] = c0;
+    ch.carry[2 * i + 1] = c1;
+    ch.carry_len[i] = clen;
+  }
+}
+
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                              bool plcm_int, cudaStream_t st) {
+  if (nframes <= 0) return cudaSuccess;
+  const int blocks = (2 * L.n + 31) / 32;
+  if (kind == 0 && plcm_int)
+    k_ks_pair<0, true><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  else if (kind == 0)
+    k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  else
+    k_ks_pair<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  return cudaGetLastError();
+}
+
+// The earlier one-thread-per-subframe form (both maps in one thread), kept for
+// comparison measurements.
+cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+                                    bool plcm_int, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
   const int blocks = (L.n + 31) / 32;
   if (kind == 0 && plcm_int)
@@ -463,6 +677,13 @@ __device__ __forceinline__ int mod_h(int v, int H) {
   return v < 0 ? v + H : v;
 }
 
+// Byte-wise a + b mod 256 in each of the four bytes of a word.
+__device__ __forceinline__ uint32_t vadd4(uint32_t a, uint32_t b) {
+  return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
+}
+// Byte 3 of w in all four bytes.
+__device__ __forceinline__ uint32_t bcast3(uint32_t w) { return __byte_perm(w, 0u, 0x3333u); }
+
 struct RoundArgs {
   Layout L;
   Tables tb;
@@ -525,18 +746,50 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
     const int rpw = 32 / L.T;  // source rows per warp pass
     const int tt = lane & (L.T - 1);
     const int sub = lane / L.T;
-    for (int a = warp * rpw + sub; a < L.H; a += nw * rpw) {
-      if (tt >= Te) continue;
-      int o = a0 + tt - a;
-      if (o < 0) o += L.H;
-      const int ta = a / L.T;
-      const int lim = fix ? __ldg(&A.tb.fixlim[ta]) : 0;
-      const uint8_t cy = fix ? s_carry[ta] : 0;
-      for (; o < L.W; o += L.H) {
-        const int qx = (a * L.W + o) * C;
-        const uint8_t m = (qx < lim) ? cy : 0;  // subframe starts are pixel-aligned
+    const int astep = nw * rpw;
+    if (L.W <= L.H && tt < Te) {
+      // one column per source row: 4 rows per iteration keep 4C loads in flight
+      for (int a = warp * rpw + sub; a < L.H; a += 4 * astep) {
+        uint8_t v[4][C];
+        int zo[4];
 #pragma unroll
-        for (int c = 0; c < C; c++) Z[tt * rowb + o * C + c] = X[qx + c] ^ m;
+        for (int u = 0; u < 4; u++) {
+          const int au = a + u * astep;
+          int o = a0 + tt - au;
+          if (o < 0) o += L.H;
+          zo[u] = (au < L.H && o < L.W) ? o : -1;
+          if (zo[u] >= 0) {
+            const int qx = (au * L.W + o) * C;
+#pragma unroll
+            for (int c = 0; c < C; c++) v[u][c] = X[qx + c];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (zo[u] < 0) continue;
+          const int au = a + u * astep;
+          uint8_t m = 0;
+          if (fix) {
+            const int ta = au / L.T;
+            if ((au * L.W + zo[u]) * C < __ldg(&A.tb.fixlim[ta])) m = s_carry[ta];  // starts are pixel-aligned
+          }
+#pragma unroll
+          for (int c = 0; c < C; c++) Z[tt * rowb + zo[u] * C + c] = v[u][c] ^ m;
+        }
+      }
+    } else if (tt < Te) {
+      for (int a = warp * rpw + sub; a < L.H; a += astep) {
+        int o = a0 + tt - a;
+        if (o < 0) o += L.H;
+        const int ta = a / L.T;
+        const int lim = fix ? __ldg(&A.tb.fixlim[ta]) : 0;
+        const uint8_t cy = fix ? s_carry[ta] : 0;
+        for (; o < L.W; o += L.H) {
+          const int qx = (a * L.W + o) * C;
+          const uint8_t m = (qx < lim) ? cy : 0;  // subframe starts are pixel-aligned
+#pragma unroll
+          for (int c = 0; c < C; c++) Z[tt * rowb + o * C + c] = X[qx + c] ^ m;
+        }
       }
     }
   }
@@ -558,7 +811,52 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
     uint32_t pre[4] = {0u, 0u, 0u, 0u};
     int fse = 16;
     uint32_t agg = 0;
-    if (len > 0) {
+    bool fast = false;
+    if (len == 16 && (cs & 15) == 0) {
+      // fast path: the chunk lies in one row, its rotated source bytes do not
+      // wrap, and no subframe starts inside it
+      const int off = cs - tstart;
+      const int tt0 = off / rowb;
+      const int e0 = off - tt0 * rowb;
+      int zs = e0 - s_kmod[tt0] * C;
+      if (zs < 0) zs += rowb;
+      if (e0 + 16 <= rowb && zs + 16 <= rowb) {
+        const int pfirst = (cs + C - 1) / C, plast = (cs + 15) / C;
+        const int wq = pfirst >> 5;
+        const uint64_t win = (uint64_t)__ldg(&A.tb.sbits[wq]) | ((uint64_t)__ldg(&A.tb.sbits[wq + 1]) << 32);
+        const int lb = pfirst - (wq << 5), hb = plast - (wq << 5);
+        const uint64_t msk = ((2ull << hb) - 1ull) & ~((1ull << lb) - 1ull);
+        if ((win & msk) == 0) {
+          fast = true;
+          const uint4 kv = *reinterpret_cast<const uint4*>(KS + cs);
+          const int za = tt0 * rowb + zs;
+          const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
+          const uint32_t sh = (uint32_t)(za & 3) * 8u;
+          const uint32_t z0 = zw[0], z1 = zw[1], z2 = zw[2], z3 = zw[3], z4 = zw[4];
+          const uint32_t y0 = __funnelshift_r(z0, z1, sh), y1 = __funnelshift_r(z1, z2, sh);
+          const uint32_t y2 = __funnelshift_r(z2, z3, sh), y3 = __funnelshift_r(z3, z4, sh);
+          uint32_t d0 = kv.x ^ vadd4(y0, kv.x), d1 = kv.y ^ vadd4(y1, kv.y);
+          uint32_t d2 = kv.z ^ vadd4(y2, kv.z), d3 = kv.w ^ vadd4(y3, kv.w);
+          d0 ^= d0 << 8;
+          d0 ^= d0 << 16;
+          d1 ^= d1 << 8;
+          d1 ^= d1 << 16;
+          d2 ^= d2 << 8;
+          d2 ^= d2 << 16;
+          d3 ^= d3 << 8;
+          d3 ^= d3 << 16;
+          d1 ^= bcast3(d0);
+          d2 ^= bcast3(d1);
+          d3 ^= bcast3(d2);
+          pre[0] = d0;
+          pre[1] = d1;
+          pre[2] = d2;
+          pre[3] = d3;
+          agg = d3 >> 24;
+        }
+      }
+    }
+    if (len > 0 && !fast) {
       uint8_t kb[16];
       if (len == 16 && (cs & 15) == 0) {
         const uint4 v = *reinterpret_cast<const uint4*>(KS + cs);

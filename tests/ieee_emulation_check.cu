@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <cmath>
 #include <random>
 
 #include "vc_ieee.cuh"
@@ -78,8 +79,39 @@ int main(int argc, char** argv) {
       if (!ok || to_bits(o) != to_bits(1.0 - z)) bad_om++;
     }
   }
+  // PLCM step in Q0.64 (derived parameter range p in [0.05, 0.45]) against the
+  // map of Eq. 5 evaluated in the host's binary64 arithmetic
+  long long bad_plcm = 0, fb_plcm = 0, checked_plcm = 0;
+  for (long long i = 0; i < n; i++) {
+    const double p = 0.05 + 0.4 * U(g);
+    const double q = 0.5 - p;
+    vc::PlcmFx F;
+    if (!vc::make_plcm_fx(p, q, F)) { bad_plcm++; continue; }
+    double x;
+    switch (i & 7) {
+      case 0: x = U(g); break;
+      case 1: x = U(g) * 1e-3; break;
+      case 2: x = 1.0 - U(g) * 1e-9; break;
+      case 3: x = p * (1.0 + 1e-13 * (U(g) - 0.5)); break;
+      case 4: x = std::ldexp(U(g), -(int)(g() % 1000)); break;
+      case 5: x = 0.5 + 1e-12 * (U(g) - 0.5); break;
+      case 6: x = (1.0 - p) * (1.0 + 1e-13 * (U(g) - 0.5)); break;
+      default: x = from_bits(g() & 0x3FEFFFFFFFFFFFFFull); break;
+    }
+    double xr = x > 0.5 ? 1.0 - x : x;
+    const double want = xr < p ? xr / p : (xr - p) / q;
+    bool ok = false;
+    const uint64_t got = vc::plcm_fx_step(to_bits(x), F, ok);
+    if (!ok) { fb_plcm++; continue; }
+    checked_plcm++;
+    if (got != to_bits(want)) {
+      if (bad_plcm < 5) printf("plcm x=%a p=%a got %a want %a\n", x, p, from_bits(got), want);
+      bad_plcm++;
+    }
+  }
+  printf("plcm_fx checked %lld fallback %lld mismatches %lld\n", checked_plcm, fb_plcm, bad_plcm);
   printf("div checked %lld fallback %lld mismatches %lld\n", checked_div, fb_div, bad_div);
   printf("sub checked %lld fallback %lld mismatches %lld\n", checked_sub, fb_sub, bad_sub);
   printf("one_minus mismatches %lld\n", bad_om);
-  return (bad_div || bad_sub || bad_om) ? 1 : 0;
+  return (bad_div || bad_sub || bad_om || bad_plcm) ? 1 : 0;
 }

@@ -107,16 +107,17 @@ def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
     return out
 
 
-@pytest.mark.parametrize("kind,plcm_int", [(0, 1), (0, 0), (1, 1)])
+@pytest.mark.parametrize("kind,plcm_int,lanes", [(0, 1, 2), (0, 0, 2), (1, 1, 2), (0, 1, 1), (0, 0, 1), (1, 1, 1)])
 @pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
-                                               (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6)])
-def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, H, W, C, n, r, frames):
+                                               (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6), (33, 47, 3, 61, 5, 3)])
+def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n, r, frames):
     """Sec. 3 byte streams and Alg. 1's s_c per frame, across frames (the left
-    over bytes of an iterate carry over, R7)."""
+    over bytes of an iterate carry over, R7), for every keystream kernel form."""
     key = synth.key_for_seed(kind, 200 + n)
     ref = orc.OracleCipher(kind, key, H, W, C, n, r)
     g = B.Cipher(kind, key, H, W, C, n, r)
     g.set_option(B.VC_OPT_PLCM_INT, plcm_int)
+    g.set_option(B.VC_OPT_KS_LANES, lanes)
     N = H * W * C
     d_ks = torch.empty(frames * r * N, dtype=torch.uint8, device="cuda")
     d_sc = torch.empty(frames, dtype=torch.int64, device="cuda")
