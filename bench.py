@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--rounds", type=int, default=5)
     ap.add_argument("--plcm-fp64", action="store_true", help="PLCM division on the binary64 pipe (A/B)")
     ap.add_argument("--ks-lanes", type=int, default=2, choices=[1, 2], help="lanes per subframe in the keystream")
+    ap.add_argument("--chunk", type=int, default=0, help="frames per pass (0 = automatic)")
+    ap.add_argument("--no-overlap", action="store_true", help="keystream and rounds on one stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -60,6 +62,7 @@ def config(a, world: int) -> dict:
     return {"workload": workload_name(a), "plcm_division": "binary64 pipe" if a.plcm_fp64 else "integer pipes",
             "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
             "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
+            "keystream_overlap": not a.no_overlap, "frames_per_pass": a.chunk or "auto",
             "l2": "inputs 425 MB > 129 MB L2, no flush"}
 
 
@@ -161,6 +164,30 @@ def run_reference(a) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- replicas (N > 1)
+
+def stream_seed(rank: int) -> int:
+    """Key seed of the video stream a rank encrypts: every rank its own stream."""
+    return 100 + rank
+
+
+def reduce_max(x: float, device) -> float:
+    """Max over ranks (the slowest replica sets the step time); identity at N = 1."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(pixels_per_rank: int, world: int, seconds_per_step: float) -> float:
+    """Mpixel/s of all ranks together: every rank processed pixels_per_rank."""
+    return world * pixels_per_rank / seconds_per_step / 1e6
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def load_peaks() -> dict:
@@ -194,9 +221,10 @@ def run_ours(a) -> None:
     X = synth.smooth_clip(F, H, W, Cc, seed=3)
     d_in = torch.from_numpy(X).cuda()
     d_out = torch.empty_like(d_in)
-    key = synth.key_for_seed(kind, 100 + rank)
+    key = synth.key_for_seed(kind, stream_seed(rank))
     ciph = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
-    ciph.set_chunk(F)
+    ciph.set_option(B.VC_OPT_CHUNK, a.chunk)
+    ciph.set_option(B.VC_OPT_OVERLAP, 0 if a.no_overlap else 1)
     ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
     ciph.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
     stream = torch.cuda.current_stream()
@@ -234,13 +262,10 @@ def run_ours(a) -> None:
     B.enc_profile_enable(ciph.ctx, False)
     clk = clocks.stop()
     ciph.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, "cuda")
 
     px_step = F * H * W
-    value = world * px_step / (ms * 1e-3) / 1e6
+    value = whole_job_rate(px_step, world, ms * 1e-3)
 
     # ---- end to end: host buffers through crypt_frames_host, copies inside
     e2e = None
@@ -248,7 +273,8 @@ def run_ours(a) -> None:
         h_in = torch.from_numpy(X).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         ce = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
-        ce.set_chunk(max(1, F // 4))
+        ce.set_option(B.VC_OPT_CHUNK, a.chunk)
+        ce.set_option(B.VC_OPT_OVERLAP, 0 if a.no_overlap else 1)
         ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
         ce.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
         for _ in range(max(1, a.warmup - 1)):
@@ -259,12 +285,8 @@ def run_ours(a) -> None:
         k2 = max(1, a.steps)
         for _ in range(k2):
             ce.crypt_host(0, h_in, h_out, stream=stream)
-        el = (time.perf_counter() - t0) / k2
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": round(world * px_step / el / 1e6, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": F * N,
+        el = reduce_max((time.perf_counter() - t0) / k2, "cuda")
+        e2e = {"value": round(whole_job_rate(px_step, world, el), 3), "unit": "Mpixel/s", "h2d_bytes_per_step": F * N,
                "d2h_bytes_per_step": F * N, "ms_per_step": round(el * 1e3, 3)}
         ce.close()
 
@@ -273,17 +295,16 @@ def run_ours(a) -> None:
 
     # ---- roofline of the dominant kernel (keystream) and the split
     peaks = load_peaks()
-    ks_ms = prof["keystream"]["ms"] / max(1, prof["keystream"]["launches"])
+    ks_launches = max(1, prof["keystream"]["launches"])
+    ks_ms_step = prof["keystream"]["ms"] / max(1, a.steps)  # summed keystream launch time per step
+    ks_ms = prof["keystream"]["ms"] / ks_launches            # per launch
     rd_ms = prof["rounds"]["ms"] / max(1, a.steps)
     sc_ms = prof["schedule"]["ms"] / max(1, a.steps)
-    iters_per_launch = F * a.n * 0  # filled below
-    step_bytes = a.rounds * N  # keystream bytes per frame
     if a.map == "plcm":
-        iters = F * (a.rounds * N) / 6.0 * 2  # two PLCM iterations per 6 bytes
+        iters = F * (a.rounds * N) / 6.0 * 2  # two PLCM iterations per 6 keystream bytes
     else:
-        iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 bytes
-    iters_per_launch = iters
-    achieved_iter = iters_per_launch / (ks_ms * 1e-3)
+        iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 keystream bytes
+    achieved_iter = iters / (ks_ms_step * 1e-3)
     # FP64 ceiling: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz = 629e9 FP64 instr/s;
     # binary64 instructions per map iteration (branch-free PLCM: 2 compares,
     # 2 subtractions, one IEEE division of ~8 FP64 instructions) ~ 12.
@@ -294,10 +315,11 @@ def run_ours(a) -> None:
                 "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
                 "frac": round(achieved_iter / peak_iter, 4), "traffic": None,
                 "peak_basis": f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration",
-                "launch_ms": round(ks_ms, 3)}
+                "launch_ms": round(ks_ms, 3), "launches_per_step": ks_launches // max(1, a.steps)}
     hbm = peaks.get("hbm_gbs")
     alg_bytes = 2 * N * F  # plaintext read once + ciphertext written once
-    split = {"keystream_ms": round(ks_ms, 3), "rounds_ms": round(rd_ms, 3), "schedule_ms": round(sc_ms, 3),
+    split = {"keystream_ms": round(ks_ms_step, 3), "rounds_ms": round(rd_ms, 3), "schedule_ms": round(sc_ms, 3),
+             "overlapped": not a.no_overlap,
              "hbm_bound_ms": round(alg_bytes / (hbm * 1e9) * 1e3, 4) if hbm else None}
 
     cpu = None

@@ -122,10 +122,16 @@ int enc_sync_status(vc_ctx* ctx);
  *                  pipe; both give identical bits (IEEE-754 round to nearest).
  * VC_OPT_KS_LANES: lanes per subframe chain pair in the keystream kernel:
  *                  2 (default, one lane per chaotic map) or 1 (one thread runs
- *                  both maps of the pair). */
+ *                  both maps of the pair).
+ * VC_OPT_OVERLAP:  1 (default) generates the keystream of the next pass on an
+ *                  internal stream while the rounds of the current pass run on
+ *                  the caller's stream (the keystream does not depend on the
+ *                  frames); 0 runs everything on the caller's stream.
+ * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
 #define VC_OPT_KS_LANES 3
+#define VC_OPT_OVERLAP 4
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */
@@ -133,7 +139,8 @@ int enc_set_option(vc_ctx* ctx, int32_t option, int64_t value);
 int enc_get_option(const vc_ctx* ctx, int32_t option, int64_t* value);
 
 /* Upper bound on frames processed per internal pass (scratch memory grows with
- * it: about (r + 2) * N bytes per frame).  Default 32. */
+ * it: about 2 (r + 2) N bytes per frame).  Default: automatic (about a sixth of
+ * the call's frames, at most 64). */
 int enc_set_chunk(vc_ctx* ctx, int32_t frames_per_pass);
 
 /* Stage timing for profiling.  While enabled, every pass brackets its stages

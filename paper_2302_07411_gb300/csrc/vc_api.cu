@@ -99,14 +99,22 @@ struct vc_ctx {
   double* d_par = nullptr;
   uint64_t* d_carry = nullptr;
   int* d_carry_len = nullptr;
-  // per-pass scratch, sized for `cap` frames
-  int chunk = 32;
+  // per-pass scratch, sized for `cap` frames.  The keystream side (keystream,
+  // s_c, shift tables) is double-buffered so that pass k+1's keystream can be
+  // generated on ks_stream while pass k's rounds run on the caller's stream.
+  int chunk = 0;  // frames per pass; 0 = automatic
   int cap = 0;
-  uint8_t* d_ks = nullptr;
+  uint8_t* d_ks[2] = {nullptr, nullptr};
+  long long* d_sc[2] = {nullptr, nullptr};
+  int* d_kmod[2] = {nullptr, nullptr};
   uint8_t* d_buf[2] = {nullptr, nullptr};
   uint8_t* d_agg[2] = {nullptr, nullptr};
-  long long* d_sc = nullptr;
-  int* d_kmod = nullptr;
+  bool overlap = true;
+  cudaStream_t ks_stream = nullptr;
+  cudaEvent_t ev_ks[2] = {};   // keystream buffer b written
+  cudaEvent_t ev_rd[2] = {};   // rounds reading buffer b done
+  cudaEvent_t ev_entry = nullptr;
+  int64_t passes = 0;
   // staging for host-buffer calls
   uint8_t* d_io[2] = {nullptr, nullptr};
   int io_cap = 0;
@@ -133,31 +141,40 @@ struct vc_ctx {
 
 namespace {
 
+void sync_all(vc_ctx* c) {
+  if (c->last) cudaStreamSynchronize(c->last);
+  if (c->ks_stream) cudaStreamSynchronize(c->ks_stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+}
+
 void free_scratch(vc_ctx* c) {
-  cudaFree(c->d_ks);
-  cudaFree(c->d_buf[0]);
-  cudaFree(c->d_buf[1]);
-  cudaFree(c->d_agg[0]);
-  cudaFree(c->d_agg[1]);
-  cudaFree(c->d_sc);
-  cudaFree(c->d_kmod);
-  c->d_ks = c->d_buf[0] = c->d_buf[1] = c->d_agg[0] = c->d_agg[1] = nullptr;
-  c->d_sc = nullptr;
-  c->d_kmod = nullptr;
+  for (int b = 0; b < 2; b++) {
+    cudaFree(c->d_ks[b]);
+    cudaFree(c->d_sc[b]);
+    cudaFree(c->d_kmod[b]);
+    cudaFree(c->d_buf[b]);
+    cudaFree(c->d_agg[b]);
+    c->d_ks[b] = c->d_buf[b] = c->d_agg[b] = nullptr;
+    c->d_sc[b] = nullptr;
+    c->d_kmod[b] = nullptr;
+  }
   c->cap = 0;
 }
 
 int ensure_scratch(vc_ctx* c, int frames) {
   if (frames <= c->cap) return VC_OK;
-  if (c->last) cudaStreamSynchronize(c->last);
+  sync_all(c);
   free_scratch(c);
   const Layout& L = c->L;
   const size_t F = (size_t)frames;
-  if (cudaMalloc(&c->d_ks, F * L.rounds * L.Npad) != cudaSuccess ||
-      cudaMalloc(&c->d_buf[0], F * L.Npad) != cudaSuccess || cudaMalloc(&c->d_buf[1], F * L.Npad) != cudaSuccess ||
-      cudaMalloc(&c->d_agg[0], F * L.NT + 16) != cudaSuccess ||
-      cudaMalloc(&c->d_agg[1], F * L.NT + 16) != cudaSuccess || cudaMalloc(&c->d_sc, F * sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&c->d_kmod, F * L.H * sizeof(int)) != cudaSuccess) {
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; b++) {
+    ok = cudaMalloc(&c->d_ks[b], F * L.rounds * L.Npad) == cudaSuccess &&
+         cudaMalloc(&c->d_sc[b], F * sizeof(long long)) == cudaSuccess &&
+         cudaMalloc(&c->d_kmod[b], F * L.H * sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && cudaMalloc(&c->d_agg[b], F * L.NT + 16) == cudaSuccess;
+  }
+  if (!ok) {
     cudaGetLastError();
     free_scratch(c);
     set_err("cudaMalloc of %d frames of scratch failed", frames);
@@ -165,6 +182,15 @@ int ensure_scratch(vc_ctx* c, int frames) {
   }
   c->cap = frames;
   return VC_OK;
+}
+
+// Frames per pass for a call of nframes frames.
+int pass_frames(const vc_ctx* c, int nframes) {
+  if (c->chunk > 0) return nframes < c->chunk ? nframes : c->chunk;
+  int f = c->overlap ? (nframes + 5) / 6 : nframes;  // about six passes, so keystream and rounds overlap
+  if (f > 64) f = 64;
+  if (f < 1) f = 1;
+  return nframes < f ? nframes : f;
 }
 
 cudaEvent_t pool_event(vc_ctx* c) {
@@ -199,46 +225,100 @@ struct StageMark {
   }
 };
 
+// Keystream side of a pass into buffer b: s_c and shift tables (Alg. 1), then
+// r * S_i bytes per subframe and frame (Sec. 3).
+int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
+  const Layout& L = c->L;
+  {
+    StageMark m(c, ks, 0, 2);
+    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc[b], c->d_kmod[b], ks));
+  }
+  {
+    StageMark m(c, ks, 1, 1);
+    VC_CUDA(c->ks_lanes == 2
+                ? vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks)
+                : vc::launch_keystream_thread(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks));
+  }
+  return VC_OK;
+}
+
+// Issues the keystream of the next pass (on ks_stream when overlapping) and
+// makes `st` wait for it; returns the buffer index.
+int begin_pass(vc_ctx* c, int nf, cudaStream_t st, int* rc) {
+  const int b = (int)(c->passes & 1);
+  c->passes++;
+  if (c->overlap) {
+    cudaStream_t ks = c->ks_stream;
+    *rc = VC_OK;
+    if (cudaStreamWaitEvent(ks, c->ev_rd[b], 0) != cudaSuccess) {
+      set_err("cudaStreamWaitEvent failed");
+      *rc = VC_ERR_CUDA;
+      return b;
+    }
+    *rc = keystream_stage(c, b, nf, ks);
+    if (*rc) return b;
+    if (cudaEventRecord(c->ev_ks[b], ks) != cudaSuccess || cudaStreamWaitEvent(st, c->ev_ks[b], 0) != cudaSuccess) {
+      set_err("event record/wait failed");
+      *rc = VC_ERR_CUDA;
+    }
+  } else {
+    *rc = keystream_stage(c, b, nf, st);
+  }
+  return b;
+}
+
+int end_pass(vc_ctx* c, int b, cudaStream_t st) {
+  if (c->overlap) VC_CUDA(cudaEventRecord(c->ev_rd[b], st));
+  return VC_OK;
+}
+
 // One pass over nf <= cap frames (encrypt when dir == 0).  in/out strides in bytes.
 int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride, int nf,
              cudaStream_t st) {
   const Layout& L = c->L;
   const vc::Tables tb = c->tables();
   const long long ks_stride = (long long)L.rounds * L.Npad;
-  {
-    StageMark m(c, st, 0, 2);
-    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
-  }
-  {
-    StageMark m(c, st, 1, 1);
-    VC_CUDA(c->ks_lanes == 2 ? vc::launch_keystream(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st)
-                             : vc::launch_keystream_thread(c->kind, L, tb, c->chains(), nf, c->d_ks, c->plcm_int, st));
-  }
+  int rc = VC_OK;
+  const int b = begin_pass(c, nf, st, &rc);
+  if (rc) return rc;
+  const uint8_t* ksb = c->d_ks[b];
+  const int* kmod = c->d_kmod[b];
   const int r = L.rounds;
-  StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
-  // with one round and in == out, the round cannot write its own input: go through a buffer
-  const bool bounce = (r == 1) && (in == out);
-  uint8_t* final_out = bounce ? c->d_buf[0] : out;
-  const long long final_stride = bounce ? L.Npad : out_stride;
-  for (int step = 0; step < r; step++) {
-    const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
-    const long long ss = step == 0 ? in_stride : L.Npad;
-    uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
-    const long long ds = step == r - 1 ? final_stride : L.Npad;
-    if (dir == 0) {
-      const int j = step;
-      VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, c->d_ks + (long long)j * L.Npad, ks_stride, c->d_kmod,
-                                   step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
-    } else {
-      const int j = r - 1 - step;
-      VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, c->d_ks + (long long)j * L.Npad, ks_stride, c->d_kmod,
-                                   nf, st));
+  {
+    StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
+    // with one round and in == out, the round cannot write its own input: go through a buffer
+    const bool bounce = (r == 1) && (in == out);
+    uint8_t* final_out = bounce ? c->d_buf[0] : out;
+    const long long final_stride = bounce ? L.Npad : out_stride;
+    for (int step = 0; step < r; step++) {
+      const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
+      const long long ss = step == 0 ? in_stride : L.Npad;
+      uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
+      const long long ds = step == r - 1 ? final_stride : L.Npad;
+      if (dir == 0) {
+        const int j = step;
+        VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
+                                     step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
+      } else {
+        const int j = r - 1 - step;
+        VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod, nf, st));
+      }
     }
+    if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
+    if (bounce)
+      VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
+                                cudaMemcpyDeviceToDevice, st));
   }
-  if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
-  if (bounce)
-    VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
-                              cudaMemcpyDeviceToDevice, st));
+  return end_pass(c, b, st);
+}
+
+int enter(vc_ctx* c, cudaStream_t st) {
+  c->last = st;
+  if (c->overlap) {
+    // the keystream side starts after what the caller enqueued before this call
+    VC_CUDA(cudaEventRecord(c->ev_entry, st));
+    VC_CUDA(cudaStreamWaitEvent(c->ks_stream, c->ev_entry, 0));
+  }
   return VC_OK;
 }
 
@@ -249,9 +329,10 @@ int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nf
   }
   if (nframes == 0) return VC_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  c->last = st;
-  const int F = nframes < c->chunk ? nframes : c->chunk;
+  const int F = pass_frames(c, nframes);
   int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  rc = enter(c, st);
   if (rc) return rc;
   const long long N = c->L.N;
   for (int f0 = 0; f0 < nframes; f0 += F) {
@@ -329,6 +410,16 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
     return VC_ERR_CUDA;
   }
   for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  if (cudaStreamCreateWithFlags(&c->ks_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_ks[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_ks[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_rd[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_rd[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming) != cudaSuccess) {
+    enc_destroy(c);
+    set_err("stream/event creation failed");
+    return VC_ERR_CUDA;
+  }
   vc::MainPrbg m{};
   m.kind = key->kind;
   if (key->kind == VC_PLCM) {
@@ -368,9 +459,10 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   }
   if (nframes == 0) return VC_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  c->last = st;
-  const int F = nframes < c->chunk ? nframes : c->chunk;
+  const int F = pass_frames(c, nframes);
   int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  rc = enter(c, st);
   if (rc) return rc;
   const size_t N = (size_t)c->L.N;
   if (c->io_cap < F) {
@@ -428,8 +520,8 @@ int enc_save_state(vc_ctx* c, void* buf, size_t* len) {
     set_err("invalid argument");
     return VC_ERR_ARG;
   }
-  if (c->last) VC_CUDA(cudaStreamSynchronize(c->last));
-  VC_CUDA(cudaDeviceSynchronize());
+  sync_all(c);
+  VC_CUDA(cudaGetLastError());
   const size_t n = (size_t)c->L.n;
   uint8_t* p = static_cast<uint8_t*>(buf);
   StateHeader h{kStateMagic, kStateVersion, c->kind, c->L.H, c->L.W, c->L.C, c->L.n, c->L.rounds, c->frame};
@@ -464,7 +556,7 @@ int enc_load_state(vc_ctx* c, const void* buf, size_t len) {
     set_err("checkpoint header does not match this context");
     return VC_ERR_STATE;
   }
-  if (c->last) VC_CUDA(cudaStreamSynchronize(c->last));
+  sync_all(c);
   const size_t n = (size_t)c->L.n;
   const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof(h);
   VC_CUDA(cudaMemcpy(c->d_main, p, sizeof(vc::MainPrbg), cudaMemcpyHostToDevice));
@@ -486,6 +578,7 @@ int enc_sync_status(vc_ctx* c) {
   if (!c) return VC_ERR_ARG;
   cudaError_t e = c->last ? cudaStreamSynchronize(c->last) : cudaSuccess;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  if (e == cudaSuccess && c->ks_stream) e = cudaStreamSynchronize(c->ks_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_err("asynchronous CUDA error: %s", cudaGetErrorString(e));
@@ -529,7 +622,11 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
   if (!c) return VC_ERR_ARG;
   switch (option) {
     case VC_OPT_CHUNK:
-      return enc_set_chunk(c, value < 1 || value > 65535 ? 0 : (int32_t)value);
+      if (value == 0) {
+        c->chunk = 0;
+        return VC_OK;
+      }
+      return enc_set_chunk(c, value < 1 || value > 65535 ? -1 : (int32_t)value);
     case VC_OPT_PLCM_INT:
       if (value != 0 && value != 1) return VC_ERR_ARG;
       c->plcm_int = value != 0;
@@ -537,6 +634,11 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
     case VC_OPT_KS_LANES:
       if (value != 1 && value != 2) return VC_ERR_ARG;
       c->ks_lanes = (int)value;
+      return VC_OK;
+    case VC_OPT_OVERLAP:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      sync_all(c);
+      c->overlap = value != 0;
       return VC_OK;
   }
   set_err("unknown option %d", option);
@@ -549,14 +651,14 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
     case VC_OPT_CHUNK: *value = c->chunk; return VC_OK;
     case VC_OPT_PLCM_INT: *value = c->plcm_int ? 1 : 0; return VC_OK;
     case VC_OPT_KS_LANES: *value = c->ks_lanes; return VC_OK;
+    case VC_OPT_OVERLAP: *value = c->overlap ? 1 : 0; return VC_OK;
   }
   return VC_ERR_ARG;
 }
 
 void enc_destroy(vc_ctx* c) {
   if (!c) return;
-  if (c->last) cudaStreamSynchronize(c->last);
-  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  sync_all(c);
   free_scratch(c);
   cudaFree(c->d_io[0]);
   cudaFree(c->d_io[1]);
@@ -577,6 +679,12 @@ void enc_destroy(vc_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->ks_stream) cudaStreamDestroy(c->ks_stream);
+  for (int b = 0; b < 2; b++) {
+    if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
+    if (c->ev_rd[b]) cudaEventDestroy(c->ev_rd[b]);
+  }
+  if (c->ev_entry) cudaEventDestroy(c->ev_entry);
   delete c;
 }
 
@@ -604,20 +712,21 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
   if (!c || nframes < 0 || (nframes > 0 && (!d_ks || !d_sc))) return VC_ERR_ARG;
   if (nframes == 0) return VC_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  c->last = st;
   const Layout& L = c->L;
-  const int F = nframes < c->chunk ? nframes : c->chunk;
+  const int F = pass_frames(c, nframes);
   int rc = ensure_scratch(c, F);
+  if (rc) return rc;
+  rc = enter(c, st);
   if (rc) return rc;
   for (int f0 = 0; f0 < nframes; f0 += F) {
     const int nf = (nframes - f0) < F ? (nframes - f0) : F;
-    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc, c->d_kmod, st));
-    VC_CUDA(c->ks_lanes == 2
-                ? vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st)
-                : vc::launch_keystream_thread(c->kind, L, c->tables(), c->chains(), nf, c->d_ks, c->plcm_int, st));
-    VC_CUDA(cudaMemcpy2DAsync(d_ks + (size_t)f0 * L.rounds * L.N, (size_t)L.N, c->d_ks, (size_t)L.Npad, (size_t)L.N,
-                              (size_t)nf * L.rounds, cudaMemcpyDeviceToDevice, st));
-    VC_CUDA(cudaMemcpyAsync(d_sc + f0, c->d_sc, nf * sizeof(long long), cudaMemcpyDeviceToDevice, st));
+    const int b = begin_pass(c, nf, st, &rc);
+    if (rc) return rc;
+    VC_CUDA(cudaMemcpy2DAsync(d_ks + (size_t)f0 * L.rounds * L.N, (size_t)L.N, c->d_ks[b], (size_t)L.Npad,
+                              (size_t)L.N, (size_t)nf * L.rounds, cudaMemcpyDeviceToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(d_sc + f0, c->d_sc[b], nf * sizeof(long long), cudaMemcpyDeviceToDevice, st));
+    rc = end_pass(c, b, st);
+    if (rc) return rc;
   }
   c->frame += nframes;
   return VC_OK;
@@ -631,7 +740,7 @@ int vc_dbg_layout(const vc_ctx* c, int32_t* out8) {
   out8[3] = c->L.N;
   out8[4] = c->L.P;
   out8[5] = c->cap;
-  out8[6] = c->chunk;
+  out8[6] = c->chunk > 0 ? c->chunk : pass_frames(c, 1 << 20);
   out8[7] = (int32_t)vc::round_smem_bytes(c->L);
   return VC_OK;
 }

@@ -200,23 +200,25 @@ __host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const Plc
     ma = m;
     ea = ex;
   }
-  // RN(a / b), b = p on the x/p branch, q on the (x - p)/q branch
+  // RN(a / b), b = p on the x/p branch, q on the (x - p)/q branch.
+  // q53 = floor(ma 2^53 / mb) in [2^52, 2^54) (estimate within one, then one
+  // correction).  ma >= mb: the result is q53 / 2 rounded (its fraction is
+  // bit 0 of q53 plus less than a half unit, and a quotient of two 53-bit
+  // numbers is never exactly halfway); ma < mb: q53 rounded by the remainder.
   const uint64_t mb = lo ? F.dp.mb : F.dq.mb;
   const uint64_t inv = lo ? F.dp.inv : F.dq.inv;
   const int eb = lo ? F.dp.eb : F.dq.eb;
-  const bool lt = ma < mb;
-  const int s = lt ? 53 : 52;
   const uint64_t lo64 = ma * inv;
   const uint64_t hi64 = ieee_mulhi(ma, inv);
-  // floor(ma inv / 2^(115 - s)): shift by 62 (s = 53) or 63 (s = 52)
-  uint64_t q = lt ? ((hi64 << 2) | (lo64 >> 62)) : ((hi64 << 1) | (lo64 >> 63));
-  uint64_t rem = (ma << s) - q * mb;
+  uint64_t q = (hi64 << 2) | (lo64 >> 62);
+  uint64_t rem = (ma << 53) - q * mb;  // exact: the true value lies in [0, 2 mb)
   if (rem >= mb) {
     q++;
     rem -= mb;
   }
-  q += ((rem << 1) > mb) ? 1 : 0;  // a quotient of two 53-bit numbers is never a tie
-  int e = ea - eb + 1023 - (lt ? 1 : 0);
+  const bool big = q >= (1ull << 53);  // ma >= mb
+  int e = ea - eb + (big ? 1023 : 1022);
+  q = big ? ((q + 1) >> 1) : (q + (((rem << 1) > mb) ? 1 : 0));
   if (q == (1ull << 53)) {
     q >>= 1;
     e++;

@@ -430,6 +430,20 @@ struct PairWriter {
     }
   }
   __device__ __forceinline__ bool fast_ok() const { return q + 24 <= qe && own == ((1u << (q & 7)) - 1u); }
+  // Append 24 bytes without the end-of-range test (the caller knows q + 24 < qe
+  // or tests afterwards).
+  __device__ __forceinline__ void put24_raw(uint64_t c0, uint64_t c1, uint64_t c2) {
+    const int sh = 8 * (q & 7);
+    const uint64_t w0 = acc | (c0 << sh);
+    const uint64_t w1 = fsh(c0, c1, sh);
+    const uint64_t w2 = fsh(c1, c2, sh);
+    acc = (c2 >> (63 - sh)) >> 1;
+    uint64_t* a = reinterpret_cast<uint64_t*>(word_ptr(q));
+    // even lane: words 0 and 2; odd lane: word 1 (one predicated second store)
+    a[side] = side ? w1 : w0;
+    if (side == 0) a[2] = w2;
+    q += 24;
+  }
   // Append 24 bytes c0 | c1 | c2 (little-endian order).
   __device__ __forceinline__ void put24(uint64_t c0, uint64_t c1, uint64_t c2) {
     const int sh = 8 * (q & 7);
@@ -568,12 +582,142 @@ __global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, 
   }
 }
 
+// PLCM keystream on the integer pipes, lane-pair form with the writes of a
+// 24-byte group overlapped with the iterates of the next group: in the steady
+// loop a lane issues two iterates, stores the previous group (whose partner
+// bytes were exchanged a whole group earlier, so the shuffle latency is
+// hidden), then two more iterates.  The fallback for operands outside the
+// fixed-point range is checked once per group: the rare group that needs it
+// is recomputed step by step with the hardware division.
+__global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt >> 1;
+  const int side = gt & 1;
+  if (i >= L.n) return;
+  const unsigned pmask = 3u << (threadIdx.x & 30);
+  constexpr uint64_t M48 = 0xFFFFFFFFFFFFull;
+
+  const double p = ch.par[4 * i + 2 * side];
+  const double qd = ch.par[4 * i + 2 * side + 1];
+  uint64_t xb = (uint64_t)__double_as_longlong(ch.st[2 * i + side]);
+  PlcmFx F;
+  const bool fx_ok = make_plcm_fx(p, qd, F);
+  uint64_t c0 = ch.carry[2 * i], c1 = ch.carry[2 * i + 1];
+  int clen = ch.carry_len[i];
+
+  PairWriter w;
+  w.Npad = L.Npad;
+  w.qs = L.C * tb.pi[i];
+  w.qe = L.C * tb.pi[i + 1];
+  w.side = side;
+  const long long per_frame = (long long)L.rounds * (w.qe - w.qs);
+
+  auto safe_step = [&](uint64_t b) -> uint64_t {
+    bool ok = false;
+    uint64_t r = fx_ok ? plcm_fx_step(b, F, ok) : 0;
+    if (!ok) r = (uint64_t)__double_as_longlong(plcm_step(__longlong_as_double((long long)b), p, qd));
+    return r;
+  };
+  // own map's 24 bytes of 4 iterates as 3 words; the fix-up path recomputes
+  auto fix_group = [&](uint64_t x0, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+    a = safe_step(x0);
+    b = safe_step(a);
+    c = safe_step(b);
+    d = safe_step(c);
+  };
+  auto pack = [&](uint64_t a, uint64_t b, uint64_t c, uint64_t d, uint64_t& o0, uint64_t& o1, uint64_t& o2) {
+    a &= M48;
+    b &= M48;
+    c &= M48;
+    d &= M48;
+    o0 = a | (b << 48);
+    o1 = (b >> 16) | (c << 32);
+    o2 = (c >> 32) | (d << 16);
+  };
+
+  for (int f = 0; f < nframes; f++) {
+    w.fb = ks + (long long)f * L.rounds * L.Npad;
+    w.j = 0;
+    w.q = w.qs;
+    w.acc = 0;
+    w.own = 0;
+    long long rem = per_frame;
+    while (clen > 0 && rem > 0) {  // bytes left over from the last iterate (R7)
+      int take = clen < 8 ? clen : 8;
+      if (take > rem) take = (int)rem;
+      w.put_slow(c0, take);
+      shr128(c0, c1, 8 * take);
+      clen -= take;
+      rem -= take;
+    }
+    while (rem > 0) {
+      if (rem >= 24 && w.fast_ok()) {
+        long long G = (w.qe - w.q) / 24;
+        if (G > rem / 24) G = rem / 24;
+        // first group
+        uint64_t o0, o1, o2, s0, s1, s2;
+        {
+          const uint64_t x0 = xb;
+          bool k0, k1, k2, k3;
+          uint64_t a = plcm_fx_step(x0, F, k0);
+          uint64_t b = plcm_fx_step(a, F, k1);
+          uint64_t c = plcm_fx_step(b, F, k2);
+          uint64_t d = plcm_fx_step(c, F, k3);
+          if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
+          xb = d;
+          pack(a, b, c, d, o0, o1, o2);
+          s0 = __shfl_xor_sync(pmask, o0, 1);
+          s1 = __shfl_xor_sync(pmask, o1, 1);
+          s2 = __shfl_xor_sync(pmask, o2, 1);
+        }
+        for (long long g = 1; g < G; g++) {
+          const uint64_t x0 = xb;
+          bool k0, k1, k2, k3;
+          uint64_t a = plcm_fx_step(x0, F, k0);
+          uint64_t b = plcm_fx_step(a, F, k1);
+          w.put24_raw(o0 ^ s0, o1 ^ s1, o2 ^ s2);  // previous group, off the chain
+          uint64_t c = plcm_fx_step(b, F, k2);
+          uint64_t d = plcm_fx_step(c, F, k3);
+          if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
+          xb = d;
+          pack(a, b, c, d, o0, o1, o2);
+          s0 = __shfl_xor_sync(pmask, o0, 1);
+          s1 = __shfl_xor_sync(pmask, o1, 1);
+          s2 = __shfl_xor_sync(pmask, o2, 1);
+        }
+        w.put24_raw(o0 ^ s0, o1 ^ s1, o2 ^ s2);
+        w.end_of_range_check();
+        rem -= 24 * G;
+      } else {
+        const uint64_t nb = safe_step(xb);
+        xb = nb;
+        const uint64_t own48 = nb & M48;
+        const uint64_t v = own48 ^ __shfl_xor_sync(pmask, own48, 1);
+        const int take = rem < 6 ? (int)rem : 6;
+        w.put_slow(v, take);
+        if (take < 6) {  // keep the rest of the iterate for the next frame
+          c0 = v >> (8 * take);
+          c1 = 0;
+          clen = 6 - take;
+        }
+        rem -= take;
+      }
+    }
+  }
+  ch.st[2 * i + side] = __longlong_as_double((long long)xb);
+  if (side == 0) {
+    ch.carry[2 * i] = c0;
+    ch.carry[2 * i + 1] = c1;
+    ch.carry_len[i] = clen;
+  }
+}
+
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                              bool plcm_int, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
   const int blocks = (2 * L.n + 31) / 32;
   if (kind == 0 && plcm_int)
-    k_ks_pair<0, true><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+    k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   else if (kind == 0)
     k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   else
