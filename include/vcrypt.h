@@ -95,6 +95,34 @@ int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nfr
 int crypt_frames_host(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
                       void* stream);
 
+/* ---- encryption without allocation ----
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * must not allocate device memory while they work: programs whose GPU memory
+ * is handed out by a framework's own pool or by a fixed budget reserved at
+ * start-up, and latency-critical threads for which cudaMalloc, which may
+ * synchronise the whole device, would stall the video pipeline.
+ *
+ * encrypt_frames_static does what encrypt_frames does (same arguments, same
+ * ciphertext, same stream order, advances the stream the same way) but calls
+ * no allocator: its scratch is one static device array of 16 MiB that the
+ * library holds on every GPU that loads it, until the process exits.  The
+ * caller still passes the input and output buffers and a context from
+ * enc_init.
+ *  - Limit: one frame needs about (r + 2) * N bytes of scratch plus small
+ *    tables; a layout whose single frame does not fit in 16 MiB (768x768x3
+ *    with r = 5 fits, 1280x720x3 does not) gets VC_ERR_UNSUPPORTED before any
+ *    GPU work.  Frames that fit are processed several per pass.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents: calls whose GPU work overlaps in time (other host threads, or
+ *    other streams without ordering between them) race on it.  Keep them on
+ *    one stream or synchronise between them.  No byte of the array needs to
+ *    start at zero: a call writes everything it reads.
+ * Errors: VC_ERR_ARG, VC_ERR_UNSUPPORTED (frame too large), VC_ERR_CUDA. */
+int encrypt_frames_static(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
+
 /* Size in bytes of a checkpoint of the context's stream state (chaotic map
  * values, pending keystream bytes, PRBG_m, frame counter). */
 size_t enc_state_size(const vc_ctx* ctx);

@@ -52,6 +52,7 @@ def lib():
             "encrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "decrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "crypt_frames_host": (C.c_int, [p, i32, p, p, i32, p]),
+            "encrypt_frames_static": (C.c_int, [p, p, p, i32, p]),
             "enc_state_size": (sz, [p]),
             "enc_save_state": (C.c_int, [p, p, C.POINTER(C.c_size_t)]),
             "enc_load_state": (C.c_int, [p, p, sz]),
@@ -129,6 +130,12 @@ def encrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
 
 def decrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
     _check(lib().decrypt_frames(ctx, _dptr(d_in), _dptr(d_out), nframes, _stream(stream)), "decrypt_frames")
+
+
+def encrypt_frames_static(ctx, d_in, d_out, nframes: int, stream=None) -> None:
+    """encrypt_frames without any device allocation (scratch in a static device array)."""
+    _check(lib().encrypt_frames_static(ctx, _dptr(d_in), _dptr(d_out), nframes, _stream(stream)),
+           "encrypt_frames_static")
 
 
 def crypt_frames_host(ctx, direction: int, h_in, h_out, nframes: int, stream=None) -> None:

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -746,3 +747,133 @@ int vc_dbg_layout(const vc_ctx* c, int32_t* out8) {
 }
 
 }  // extern "C"
+
+// =============================================================================
+// encrypt_frames_static: encryption without any device allocation in the call.
+//
+// The per-pass scratch (keystream, shift tables, s_c, the two round buffers
+// and the tile aggregates) comes from one file-scope device array instead of
+// cudaMalloc.  Host code cannot use the array's name as a device address, so
+// the first call on each device looks the address up with
+// cudaGetSymbolAddress (with that device current) and caches it.
+// =============================================================================
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB, held by every device that loads the library
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) uint8_t g_vc_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+int static_scratch_address(void** out) {
+  int dev = 0;
+  VC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) {
+    set_err("device %d beyond the %d devices the static scratch supports", dev, kStaticMaxDevices);
+    return VC_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vc_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_err("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      return VC_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return VC_OK;
+}
+
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Static-scratch bytes one frame of a pass needs.
+size_t static_bytes_per_frame(const Layout& L) {
+  return round256((size_t)L.rounds * L.Npad) + 2 * round256((size_t)L.Npad) + round256((size_t)L.H * sizeof(int)) +
+         round256(sizeof(long long)) + 2 * round256((size_t)L.NT);
+}
+
+}  // namespace
+
+extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream) {
+  if (!c || nframes < 0 || (nframes > 0 && (!d_in || !d_out))) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  const Layout& L = c->L;
+  const size_t per_frame = static_bytes_per_frame(L);
+  if (per_frame > kStaticScratchBytes) {
+    set_err("encrypt_frames_static: one %dx%dx%d frame with %d rounds needs %zu bytes of scratch, the static "
+            "scratch holds %zu",
+            L.H, L.W, L.C, L.rounds, per_frame, kStaticScratchBytes);
+    return VC_ERR_UNSUPPORTED;
+  }
+  if (nframes == 0) return VC_OK;
+  void* base = nullptr;
+  int rc = static_scratch_address(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // keystream work of earlier overlapped calls (internal stream) comes first
+  VC_CUDA(cudaEventRecord(c->ev_entry, c->ks_stream));
+  VC_CUDA(cudaStreamWaitEvent(st, c->ev_entry, 0));
+  c->last = st;
+
+  const int F = (int)(kStaticScratchBytes / per_frame);
+  const vc::Tables tb = c->tables();
+  const long long ks_stride = (long long)L.rounds * L.Npad;
+  const int r = L.rounds;
+  const long long N = L.N;
+  for (int f0 = 0; f0 < nframes; f0 += F) {
+    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+    uint8_t* p = static_cast<uint8_t*>(base);
+    uint8_t* ks = p;
+    p += round256((size_t)nf * L.rounds * L.Npad);
+    uint8_t* buf[2];
+    buf[0] = p;
+    p += round256((size_t)nf * L.Npad);
+    buf[1] = p;
+    p += round256((size_t)nf * L.Npad);
+    int* kmod = reinterpret_cast<int*>(p);
+    p += round256((size_t)nf * L.H * sizeof(int));
+    long long* sc = reinterpret_cast<long long*>(p);
+    p += round256((size_t)nf * sizeof(long long));
+    uint8_t* agg[2];
+    agg[0] = p;
+    p += round256((size_t)nf * L.NT);
+    agg[1] = p;
+
+    const uint8_t* in = d_in + f0 * N;
+    uint8_t* out = d_out + f0 * N;
+    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, sc, kmod, st));
+    VC_CUDA(c->ks_lanes == 2 ? vc::launch_keystream(c->kind, L, tb, c->chains(), nf, ks, c->plcm_int, st)
+                             : vc::launch_keystream_thread(c->kind, L, tb, c->chains(), nf, ks, c->plcm_int, st));
+    const bool bounce = (r == 1) && (in == out);
+    uint8_t* final_out = bounce ? buf[0] : out;
+    const long long final_stride = bounce ? L.Npad : N;
+    for (int j = 0; j < r; j++) {
+      const uint8_t* src = j == 0 ? in : buf[(j - 1) & 1];
+      const long long ss = j == 0 ? N : L.Npad;
+      uint8_t* dst = j == r - 1 ? final_out : buf[j & 1];
+      const long long ds = j == r - 1 ? final_stride : L.Npad;
+      VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, ks + (long long)j * L.Npad, ks_stride, kmod,
+                                   j == 0 ? nullptr : agg[(j - 1) & 1], agg[j & 1], nf, st));
+    }
+    VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, agg[(r - 1) & 1], nf, st));
+    if (bounce)
+      VC_CUDA(cudaMemcpy2DAsync(out, (size_t)N, buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
+                                cudaMemcpyDeviceToDevice, st));
+  }
+  // later overlapped calls start their keystream after this call's
+  VC_CUDA(cudaEventRecord(c->ev_entry, st));
+  VC_CUDA(cudaStreamWaitEvent(c->ks_stream, c->ev_entry, 0));
+  c->frame += nframes;
+  return VC_OK;
+}
