@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--ks-lanes", type=int, default=2, choices=[1, 2], help="lanes per subframe in the keystream")
     ap.add_argument("--chunk", type=int, default=0, help="frames per pass (0 = automatic)")
     ap.add_argument("--no-overlap", action="store_true", help="keystream and rounds on one stream")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per round-kernel tile (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -63,6 +64,7 @@ def config(a, world: int) -> dict:
             "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
             "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
             "keystream_overlap": not a.no_overlap, "frames_per_pass": a.chunk or "auto",
+            "tile_rows": a.tile_rows or "auto",
             "l2": "inputs 425 MB > 129 MB L2, no flush"}
 
 
@@ -225,6 +227,7 @@ def run_ours(a) -> None:
     ciph = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
     ciph.set_option(B.VC_OPT_CHUNK, a.chunk)
     ciph.set_option(B.VC_OPT_OVERLAP, 0 if a.no_overlap else 1)
+    ciph.set_option(B.VC_OPT_TILE_ROWS, a.tile_rows)
     ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
     ciph.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
     stream = torch.cuda.current_stream()
@@ -275,6 +278,7 @@ def run_ours(a) -> None:
         ce = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
         ce.set_option(B.VC_OPT_CHUNK, a.chunk)
         ce.set_option(B.VC_OPT_OVERLAP, 0 if a.no_overlap else 1)
+        ce.set_option(B.VC_OPT_TILE_ROWS, a.tile_rows)
         ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
         ce.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
         for _ in range(max(1, a.warmup - 1)):

@@ -155,11 +155,16 @@ int enc_sync_status(vc_ctx* ctx);
  *                  internal stream while the rounds of the current pass run on
  *                  the caller's stream (the keystream does not depend on the
  *                  frames); 0 runs everything on the caller's stream.
+ * VC_OPT_TILE_ROWS: frame rows per tile of the round kernels, a power of two
+ *                  1..32 (capped by the 96 KB shared-memory tile budget);
+ *                  0 (default) takes the largest that fits.  Reading it back
+ *                  gives the rows in use.
  * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
 #define VC_OPT_KS_LANES 3
 #define VC_OPT_OVERLAP 4
+#define VC_OPT_TILE_ROWS 5
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */

@@ -54,8 +54,9 @@ bool key_valid(const vc_key& k) {
   return false;
 }
 
-// Geometry checks and the tile shape of the round kernels.
-int make_layout(const vc_layout& l, Layout* L) {
+// Geometry checks and the tile shape of the round kernels (tile_rows_max: 0 =
+// as many rows, up to 32, as fit the shared-memory budget).
+int make_layout(const vc_layout& l, Layout* L, int tile_rows_max = 0) {
   if (l.height < 1 || l.width < 1 || l.height > 16384 || l.width > 16384) return VC_ERR_LAYOUT;
   if (!(l.channels == 1 || l.channels == 3 || l.channels == 4)) return VC_ERR_LAYOUT;
   if (l.rounds < 1 || l.rounds > 16 || l.n_subframes < 1) return VC_ERR_LAYOUT;
@@ -66,7 +67,7 @@ int make_layout(const vc_layout& l, Layout* L) {
   if ((long long)l.channels * (P / l.n_subframes) < 2) return VC_ERR_LAYOUT;  // every subframe >= 2 bytes
   const long long rowb = (long long)l.width * l.channels;
   if (rowb > vc::kMaxRowBytes) return VC_ERR_LAYOUT;
-  int T = 32;
+  int T = tile_rows_max > 0 ? tile_rows_max : 32;
   while (T > 1 && (size_t)T * rowb > kTileBudget) T >>= 1;
   const int NT = (l.height + T - 1) / T;
   if (NT > vc::kMaxTiles) return VC_ERR_LAYOUT;
@@ -88,6 +89,8 @@ int make_layout(const vc_layout& l, Layout* L) {
 struct vc_ctx {
   int kind = 0;
   Layout L{};
+  vc_layout user_layout{};
+  int tile_rows = 0;  // 0 = automatic
   int dev = 0;
   // partition tables
   int* d_pi = nullptr;
@@ -387,6 +390,7 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
   if (!c) return VC_ERR_OOM;
   c->kind = key->kind;
   c->L = L;
+  c->user_layout = *layout;
   cudaGetDevice(&c->dev);
   const int n = L.n;
   const int nwords = L.P / 32 + 2;
@@ -641,6 +645,27 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       sync_all(c);
       c->overlap = value != 0;
       return VC_OK;
+    case VC_OPT_TILE_ROWS: {
+      if (value != 0 && (value < 1 || value > 32 || (value & (value - 1)))) return VC_ERR_ARG;
+      Layout L2{};
+      if (make_layout(c->user_layout, &L2, (int)value) != VC_OK) return VC_ERR_ARG;
+      sync_all(c);
+      int* fl = nullptr;
+      if (cudaMalloc(&fl, sizeof(int) * L2.NT) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("tile table allocation failed");
+        return VC_ERR_OOM;
+      }
+      // the partition tables other than the tile limits do not depend on the tile shape
+      VC_CUDA(vc::launch_build_tables(L2, c->d_pi, c->d_sbits, c->d_srank, fl, c->copy_stream));
+      VC_CUDA(cudaStreamSynchronize(c->copy_stream));
+      cudaFree(c->d_fixlim);
+      c->d_fixlim = fl;
+      free_scratch(c);
+      c->L = L2;
+      c->tile_rows = (int)value;
+      return VC_OK;
+    }
   }
   set_err("unknown option %d", option);
   return VC_ERR_ARG;
@@ -653,6 +678,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
     case VC_OPT_PLCM_INT: *value = c->plcm_int ? 1 : 0; return VC_OK;
     case VC_OPT_KS_LANES: *value = c->ks_lanes; return VC_OK;
     case VC_OPT_OVERLAP: *value = c->overlap ? 1 : 0; return VC_OK;
+    case VC_OPT_TILE_ROWS: *value = c->L.T; return VC_OK;
   }
   return VC_ERR_ARG;
 }

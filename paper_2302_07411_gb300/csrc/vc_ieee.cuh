@@ -29,6 +29,13 @@ __device__ __forceinline__ uint64_t ieee_bits(double v) { return (uint64_t)__dou
 __device__ __forceinline__ double ieee_double(uint64_t b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ uint64_t ieee_mulhi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
 __device__ __forceinline__ int ieee_clz64(uint64_t v) { return __clzll((long long)v); }
+// Leading zeros of v when its high word is non-zero, from the exponent of the
+// high word converted to binary32 with truncation (exact: floor(log2)).  The
+// conversion is several times faster than the integer leading-zero count on
+// this GPU.
+__device__ __forceinline__ int lz64_hi(uint64_t v) {
+  return 158 - (int)(__float_as_uint(__uint2float_rz((uint32_t)(v >> 32))) >> 23);
+}
 #else
 inline uint64_t ieee_bits(double v) {
   uint64_t b;
@@ -42,6 +49,7 @@ inline double ieee_double(uint64_t b) {
 }
 inline uint64_t ieee_mulhi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 inline int ieee_clz64(uint64_t v) { return v ? __builtin_clzll(v) : 64; }
+inline int lz64_hi(uint64_t v) { return __builtin_clz((uint32_t)(v >> 32)); }
 #endif
 
 constexpr uint64_t kMant52 = (1ull << 52) - 1;
@@ -186,7 +194,8 @@ __host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const Plc
   const uint64_t XR = refl ? (0ull - X) : X;      // 1 - x, exact
   const bool lo = small || XR < F.P;
   const uint64_t A = lo ? XR : XR - F.P;          // x (or 1 - x), or the exact x - p
-  const int lz = ieee_clz64(A);
+  const bool wide = (A >> 32) != 0;               // operand >= 2^-32 (else the hardware path)
+  const int lz = lz64_hi(wide ? A : (1ull << 32));
   const uint64_t An = A << (lz & 63);
   uint64_t ma = An >> 11;                         // 53 significant bits
   const uint32_t R = (uint32_t)An & 0x7FFu;       // dropped bits (zero unless x - p needs rounding)
@@ -223,7 +232,7 @@ __host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const Plc
     q >>= 1;
     e++;
   }
-  ok = (ex >= 1) && (ex <= 1022) && (small || A != 0) && (e >= 1);
+  ok = (ex >= 1) && (ex <= 1022) && (small || wide) && (e >= 1);
   return ((uint64_t)(e & 0x7FF) << 52) | (q & kMant52);
 }
 

@@ -892,12 +892,12 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
     const int sub = lane / L.T;
     const int astep = nw * rpw;
     if (L.W <= L.H && tt < Te) {
-      // one column per source row: 4 rows per iteration keep 4C loads in flight
-      for (int a = warp * rpw + sub; a < L.H; a += 4 * astep) {
-        uint8_t v[4][C];
-        int zo[4];
+      // one column per source row: 8 rows per iteration keep 8C loads in flight
+      for (int a = warp * rpw + sub; a < L.H; a += 8 * astep) {
+        uint8_t v[8][C];
+        int zo[8];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 8; u++) {
           const int au = a + u * astep;
           int o = a0 + tt - au;
           if (o < 0) o += L.H;
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 8; u++) {
           if (zo[u] < 0) continue;
           const int au = a + u * astep;
           uint8_t m = 0;
@@ -946,8 +946,17 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
   const int nchunks = (tend - base16 + 15) >> 4;
   const bool out_vec = ((reinterpret_cast<uintptr_t>(Out)) & 15) == 0;
   uint32_t run = 0;
+  // keystream of the thread's next full chunk, loaded one iteration ahead
+  auto ks_full = [&](int cc) -> uint4 {
+    const int s0 = base16 + 16 * cc;
+    if (cc < nchunks && s0 >= tstart && s0 + 16 <= tend) return *reinterpret_cast<const uint4*>(KS + s0);
+    return make_uint4(0u, 0u, 0u, 0u);
+  };
+  uint4 kv_next = ks_full(threadIdx.x);
   for (int cb = 0; cb < nchunks; cb += blockDim.x) {
     const int c = cb + threadIdx.x;
+    const uint4 kv = kv_next;
+    kv_next = ks_full(c + blockDim.x);
     int cs = base16 + 16 * c, ce = cs + 16;
     if (cs < tstart) cs = tstart;
     if (ce > tend) ce = tend;
@@ -972,7 +981,6 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
         const uint64_t msk = ((2ull << hb) - 1ull) & ~((1ull << lb) - 1ull);
         if ((win & msk) == 0) {
           fast = true;
-          const uint4 kv = *reinterpret_cast<const uint4*>(KS + cs);
           const int za = tt0 * rowb + zs;
           const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
           const uint32_t sh = (uint32_t)(za & 3) * 8u;

@@ -134,7 +134,7 @@ def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n
 
 # --------------------------------------------------------------------- whole frames
 
-def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False):
+def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0):
     F, H, W, C = X.shape
     ref_e = orc.OracleCipher(kind, key, H, W, C, n, r)
     ref_d = orc.OracleCipher(kind, key, H, W, C, n, r)
@@ -144,6 +144,9 @@ def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False):
     if chunk:
         g_e.set_chunk(chunk)
         g_d.set_chunk(chunk)
+    if tile_rows:
+        g_e.set_option(B.VC_OPT_TILE_ROWS, tile_rows)
+        g_d.set_option(B.VC_OPT_TILE_ROWS, 1 if tile_rows > 1 else 2)
     d = dev(X)
     Yg = g_e.encrypt(d, d if inplace else None)
     g_e.sync()
@@ -188,6 +191,14 @@ def test_config_smooth_576_clip(B, orc, kind, n):
 def test_odd_shapes(B, orc, kind, H, W, C, n, r):
     X = synth.uniform_frames(2, H, W, C, seed=H + W)
     _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 300 + n), X, n, r)
+
+
+@pytest.mark.parametrize("tile_rows", [1, 4, 8, 16])
+def test_tile_shapes_do_not_change_the_ciphertext(B, orc, tile_rows):
+    """Rows per round-kernel tile is a tuning option: any shape (and different
+    shapes for encryption and decryption) gives the oracle's bytes."""
+    X = synth.uniform_frames(2, 50, 44, 3, seed=17)
+    _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 17), X, 9, 5, tile_rows=tile_rows)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
