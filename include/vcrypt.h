@@ -123,6 +123,49 @@ int crypt_frames_host(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8
  * Errors: VC_ERR_ARG, VC_ERR_UNSUPPORTED (frame too large), VC_ERR_CUDA. */
 int encrypt_frames_static(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
 
+/* ---- ragged batches (many streams per launch) ----
+ * A batcher runs the frames of many streams -- each with its own key, layout
+ * (resolution, channels, subframes, rounds), map and direction -- with one
+ * launch per phase for the whole batch: frame schedules, shift tables, one
+ * keystream kernel over every subframe chain of every stream, then one
+ * persistent kernel per round over every (frame, tile) of every stream.  The
+ * sequence is captured once per batch shape as a CUDA graph and replayed with
+ * one graph launch per batch.  The results are byte-identical to running
+ * each job alone with encrypt_frames / decrypt_frames. */
+typedef struct {
+  vc_ctx* ctx;          /* the stream's context; at most one job per context per batch */
+  int32_t direction;    /* 0 = encrypt, 1 = decrypt */
+  const uint8_t* d_in;  /* nframes * N bytes, device */
+  uint8_t* d_out;       /* nframes * N bytes, device; may equal d_in unless the context has 1 round */
+  int32_t nframes;      /* >= 0; 0 leaves the job out */
+} vc_job;
+
+typedef struct vc_batcher vc_batcher;
+
+/* Create a batcher on the current device (owns its scratch pool, descriptor
+ * staging and graph cache).  Errors: VC_ERR_ARG, VC_ERR_OOM, VC_ERR_CUDA. */
+int vc_batcher_create(vc_batcher** out);
+
+/* Enqueue one batch on `stream`: equivalent to the jobs' encrypt_frames /
+ * decrypt_frames calls, advancing each context by its job's frames.  Returns
+ * once enqueued; the host-side job array may be reused at once.  Later calls
+ * on a context are ordered after the batch.  Errors: VC_ERR_ARG (null or
+ * repeated context, bad direction, in-place job of a 1-round context),
+ * VC_ERR_OOM, VC_ERR_CUDA. */
+int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stream);
+
+/* Batcher options.
+ * VC_BOPT_GRAPH:       1 (default) replay a captured CUDA graph per batch
+ *                      shape; 0 plain kernel launches.
+ * VC_BOPT_CTAS_PER_SM: CTAs per SM of the persistent round kernels; 0
+ *                      (default) = the occupancy maximum.  Errors: VC_ERR_ARG. */
+#define VC_BOPT_GRAPH 1
+#define VC_BOPT_CTAS_PER_SM 2
+int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
+
+/* Synchronise and free the batcher. */
+void vc_batcher_destroy(vc_batcher* b);
+
 /* Size in bytes of a checkpoint of the context's stream state (chaotic map
  * values, pending keystream bytes, PRBG_m, frame counter). */
 size_t enc_state_size(const vc_ctx* ctx);

@@ -19,6 +19,7 @@ _lib = None
 VC_OK = 0
 VC_PLCM, VC_2DLASM = 0, 1
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS = 1, 2, 3, 4, 5
+VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM = 1, 2
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
 
@@ -32,6 +33,11 @@ class VcError(RuntimeError):
 
 class vc_key(C.Structure):
     _fields_ = [("kind", C.c_int32), ("k", C.c_double * 4)]
+
+
+class vc_job(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("direction", C.c_int32), ("d_in", C.c_void_p), ("d_out", C.c_void_p),
+                ("nframes", C.c_int32)]
 
 
 class vc_layout(C.Structure):
@@ -53,6 +59,10 @@ def lib():
             "decrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "crypt_frames_host": (C.c_int, [p, i32, p, p, i32, p]),
             "encrypt_frames_static": (C.c_int, [p, p, p, i32, p]),
+            "vc_batcher_create": (C.c_int, [p]),
+            "vc_batch_submit": (C.c_int, [p, p, i32, p]),
+            "vc_batcher_set_option": (C.c_int, [p, i32, i64]),
+            "vc_batcher_destroy": (None, [p]),
             "enc_state_size": (sz, [p]),
             "enc_save_state": (C.c_int, [p, p, C.POINTER(C.c_size_t)]),
             "enc_load_state": (C.c_int, [p, p, sz]),
@@ -283,6 +293,55 @@ class Cipher:
         if getattr(self, "ctx", None):
             enc_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- ragged batches -------------------------------------------------------------
+
+def vc_batcher_create() -> C.c_void_p:
+    b = C.c_void_p()
+    _check(lib().vc_batcher_create(C.byref(b)), "vc_batcher_create")
+    return b
+
+
+def vc_batch_submit(batcher, jobs, stream=None) -> None:
+    """jobs: sequence of (Cipher or ctx, direction, d_in tensor, d_out tensor, nframes)."""
+    arr = (vc_job * max(1, len(jobs)))()
+    for k, (ctx, direction, d_in, d_out, nframes) in enumerate(jobs):
+        c = ctx.ctx if isinstance(ctx, Cipher) else ctx
+        arr[k] = vc_job(c, direction, _dptr(d_in).value, _dptr(d_out).value, nframes)
+    _check(lib().vc_batch_submit(batcher, arr, len(jobs), _stream(stream)), "vc_batch_submit")
+
+
+def vc_batcher_set_option(batcher, option: int, value: int) -> None:
+    _check(lib().vc_batcher_set_option(batcher, option, value), "vc_batcher_set_option")
+
+
+def vc_batcher_destroy(batcher) -> None:
+    lib().vc_batcher_destroy(batcher)
+
+
+class Batcher:
+    """Runs frames of many streams per launch (one CUDA graph replay per batch)."""
+
+    def __init__(self, graph: bool = True, ctas_per_sm: int = 0):
+        self.b = vc_batcher_create()
+        vc_batcher_set_option(self.b, VC_BOPT_GRAPH, 1 if graph else 0)
+        if ctas_per_sm:
+            vc_batcher_set_option(self.b, VC_BOPT_CTAS_PER_SM, ctas_per_sm)
+
+    def submit(self, jobs, stream=None) -> None:
+        vc_batch_submit(self.b, jobs, stream)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            vc_batcher_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -5,8 +5,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
+#include <unordered_set>
 #include <vector>
 
 #include "vc_internal.h"
@@ -118,6 +121,8 @@ struct vc_ctx {
   cudaEvent_t ev_ks[2] = {};   // keystream buffer b written
   cudaEvent_t ev_rd[2] = {};   // rounds reading buffer b done
   cudaEvent_t ev_entry = nullptr;
+  cudaEvent_t ev_batch = nullptr;  // recorded after a batch that used this context
+  bool batch_pending = false;
   int64_t passes = 0;
   // staging for host-buffer calls
   uint8_t* d_io[2] = {nullptr, nullptr};
@@ -317,6 +322,10 @@ int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t
 }
 
 int enter(vc_ctx* c, cudaStream_t st) {
+  if (c->batch_pending) {  // a batch on another stream advanced this context last
+    VC_CUDA(cudaStreamWaitEvent(st, c->ev_batch, 0));
+    c->batch_pending = false;
+  }
   c->last = st;
   if (c->overlap) {
     // the keystream side starts after what the caller enqueued before this call
@@ -420,7 +429,8 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
       cudaEventCreateWithFlags(&c->ev_ks[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rd[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rd[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_batch, cudaEventDisableTiming) != cudaSuccess) {
     enc_destroy(c);
     set_err("stream/event creation failed");
     return VC_ERR_CUDA;
@@ -712,6 +722,7 @@ void enc_destroy(vc_ctx* c) {
     if (c->ev_rd[b]) cudaEventDestroy(c->ev_rd[b]);
   }
   if (c->ev_entry) cudaEventDestroy(c->ev_entry);
+  if (c->ev_batch) cudaEventDestroy(c->ev_batch);
   delete c;
 }
 
@@ -847,6 +858,10 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
   int rc = static_scratch_address(&base);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->batch_pending) {
+    VC_CUDA(cudaStreamWaitEvent(st, c->ev_batch, 0));
+    c->batch_pending = false;
+  }
   // keystream work of earlier overlapped calls (internal stream) comes first
   VC_CUDA(cudaEventRecord(c->ev_entry, c->ks_stream));
   VC_CUDA(cudaStreamWaitEvent(st, c->ev_entry, 0));
@@ -903,3 +918,287 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
   c->frame += nframes;
   return VC_OK;
 }
+
+// =============================================================================
+// Ragged batches
+// =============================================================================
+
+struct vc_batcher {
+  int dev = 0, sms = 0;
+  vc::JobDesc* d_jobs = nullptr;
+  vc::BatchHdr* d_hdr = nullptr;
+  int jobs_cap = 0;
+  vc::JobDesc* h_jobs[2] = {nullptr, nullptr};  // pinned staging, alternating
+  vc::BatchHdr* h_hdr[2] = {nullptr, nullptr};
+  cudaEvent_t staged[2] = {nullptr, nullptr};   // staging b consumed by the device
+  int cur = 0;
+  uint8_t* d_pool = nullptr;
+  size_t pool_cap = 0;
+  bool use_graph = true;
+  int ctas_per_sm = 0;
+  cudaStream_t cap_stream = nullptr;
+  // graph cache: (jobs_cap, warps_cap, kmod_cap, rounds, grid, smem, staging) -> executable
+  std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
+  std::vector<cudaStream_t> last_streams;
+};
+
+namespace {
+
+int bucket(int v, int lo) {
+  int b = lo;
+  while (b < v) b <<= 1;
+  return b;
+}
+
+void drop_graphs(vc_batcher* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+int grow_jobs(vc_batcher* b, int need) {
+  if (need <= b->jobs_cap) return VC_OK;
+  const int cap = bucket(need, 64);
+  cudaDeviceSynchronize();
+  drop_graphs(b);  // the descriptor address is a kernel argument of the captured graphs
+  cudaFree(b->d_jobs);
+  for (int i = 0; i < 2; i++) cudaFreeHost(b->h_jobs[i]);
+  b->d_jobs = nullptr;
+  b->h_jobs[0] = b->h_jobs[1] = nullptr;
+  b->jobs_cap = 0;
+  if (cudaMalloc(&b->d_jobs, sizeof(vc::JobDesc) * cap) != cudaSuccess ||
+      cudaMallocHost(&b->h_jobs[0], sizeof(vc::JobDesc) * cap) != cudaSuccess ||
+      cudaMallocHost(&b->h_jobs[1], sizeof(vc::JobDesc) * cap) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("batch descriptor allocation failed");
+    return VC_ERR_OOM;
+  }
+  b->jobs_cap = cap;
+  return VC_OK;
+}
+
+size_t job_scratch_bytes(const Layout& L, int nf) {
+  return round256((size_t)nf * L.rounds * L.Npad) + 2 * round256((size_t)nf * L.Npad) +
+         round256((size_t)nf * L.H * sizeof(int)) + round256((size_t)nf * sizeof(long long)) +
+         2 * round256((size_t)nf * L.NT);
+}
+
+}  // namespace
+
+extern "C" {
+
+int vc_batcher_create(vc_batcher** out) {
+  if (!out) return VC_ERR_ARG;
+  *out = nullptr;
+  vc_batcher* b = new (std::nothrow) vc_batcher();
+  if (!b) return VC_ERR_OOM;
+  cudaGetDevice(&b->dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
+  bool ok = cudaMalloc(&b->d_hdr, sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaMallocHost(&b->h_hdr[0], sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaMallocHost(&b->h_hdr[1], sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->staged[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->staged[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok || grow_jobs(b, 64) != VC_OK) {
+    cudaGetLastError();
+    vc_batcher_destroy(b);
+    set_err("batcher creation failed");
+    return VC_ERR_OOM;
+  }
+  *out = b;
+  return VC_OK;
+}
+
+int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
+  if (!b) return VC_ERR_ARG;
+  switch (option) {
+    case VC_BOPT_GRAPH:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      b->use_graph = value != 0;
+      return VC_OK;
+    case VC_BOPT_CTAS_PER_SM:
+      if (value < 0 || value > 32) return VC_ERR_ARG;
+      b->ctas_per_sm = (int)value;
+      drop_graphs(b);
+      return VC_OK;
+  }
+  return VC_ERR_ARG;
+}
+
+int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stream) {
+  if (!b || njobs < 0 || (njobs > 0 && !jobs)) {
+    set_err("invalid argument");
+    return VC_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // validate and lay out the jobs
+  std::vector<int> live;
+  live.reserve(njobs);
+  std::unordered_set<const vc_ctx*> seen;
+  size_t pool_need = 0;
+  for (int j = 0; j < njobs; j++) {
+    const vc_job& J = jobs[j];
+    if (!J.ctx || (J.direction != 0 && J.direction != 1) || J.nframes < 0 ||
+        (J.nframes > 0 && (!J.d_in || !J.d_out))) {
+      set_err("invalid job %d", j);
+      return VC_ERR_ARG;
+    }
+    if (!seen.insert(J.ctx).second) {
+      set_err("job %d repeats a context", j);
+      return VC_ERR_ARG;
+    }
+    if (J.nframes == 0) continue;
+    if (J.ctx->L.rounds == 1 && J.d_in == J.d_out) {
+      set_err("job %d: in-place with one round is not supported in a batch", j);
+      return VC_ERR_ARG;
+    }
+    live.push_back(j);
+    pool_need += job_scratch_bytes(J.ctx->L, J.nframes);
+  }
+  const int nj = (int)live.size();
+  if (nj == 0) return VC_OK;
+  int rc = grow_jobs(b, nj);
+  if (rc) return rc;
+  if (pool_need > b->pool_cap) {
+    cudaDeviceSynchronize();
+    cudaFree(b->d_pool);
+    b->d_pool = nullptr;
+    b->pool_cap = 0;
+    const size_t cap = pool_need + pool_need / 4;
+    if (cudaMalloc(&b->d_pool, cap) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("batch scratch pool of %zu bytes failed", cap);
+      return VC_ERR_OOM;
+    }
+    b->pool_cap = cap;
+  }
+  // staging buffer `cur` must have been consumed by its previous batch
+  VC_CUDA(cudaEventSynchronize(b->staged[b->cur]));
+  vc::JobDesc* hj = b->h_jobs[b->cur];
+  vc::BatchHdr* hh = b->h_hdr[b->cur];
+  uint8_t* p = b->d_pool;
+  int warps = 0, tiles = 0, kmods = 0, rounds = 0;
+  size_t smem = 4096;  // the fix-up needs one byte per tile
+  for (int k = 0; k < nj; k++) {
+    const vc_job& J = jobs[live[k]];
+    vc_ctx* c = J.ctx;
+    const Layout& L = c->L;
+    const int nf = J.nframes;
+    vc::JobDesc d{};
+    d.L = L;
+    d.tb = c->tables();
+    d.ch = c->chains();
+    d.main = c->d_main;
+    d.kind = c->kind;
+    d.dir = J.direction;
+    d.nframes = nf;
+    d.in = J.d_in;
+    d.out = J.d_out;
+    d.ks = p;
+    p += round256((size_t)nf * L.rounds * L.Npad);
+    d.buf[0] = p;
+    p += round256((size_t)nf * L.Npad);
+    d.buf[1] = p;
+    p += round256((size_t)nf * L.Npad);
+    d.kmod = reinterpret_cast<int*>(p);
+    p += round256((size_t)nf * L.H * sizeof(int));
+    d.sc = reinterpret_cast<long long*>(p);
+    p += round256((size_t)nf * sizeof(long long));
+    d.agg[0] = p;
+    p += round256((size_t)nf * L.NT);
+    d.agg[1] = p;
+    p += round256((size_t)nf * L.NT);
+    d.warp_base = warps;
+    d.tile_base = tiles;
+    d.kmod_base = kmods;
+    warps += (L.n + 15) / 16;
+    tiles += nf * L.NT;
+    kmods += nf * L.H;
+    if (L.rounds > rounds) rounds = L.rounds;
+    const size_t sm = vc::round_smem_bytes(L);
+    if (sm > smem) smem = sm;
+    hj[k] = d;
+    // the batch runs after what the context's own calls enqueued on other streams
+    if (c->last && c->last != st) {
+      VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
+      VC_CUDA(cudaStreamWaitEvent(st, c->ev_entry, 0));
+    }
+  }
+  hh->njobs = nj;
+  hh->total_warps = warps;
+  hh->total_tiles = tiles;
+  hh->total_kmod = kmods;
+
+  vc::BatchShape sh;
+  sh.jobs_cap = bucket(nj, 64);
+  if (sh.jobs_cap > b->jobs_cap) sh.jobs_cap = b->jobs_cap;
+  sh.warps_cap = bucket(warps, 64);
+  sh.kmod_cap = bucket(kmods, 1024);
+  sh.rounds = rounds;
+  sh.smem = (smem + 16383) & ~(size_t)16383;
+  VC_CUDA(vc::prepare_batch_kernels(sh.smem));
+  int ctas = 0;
+  VC_CUDA(vc::batch_ctas_per_sm(sh.smem, &ctas));
+  if (ctas < 1) {
+    set_err("round kernel does not fit with %zu bytes of shared memory", sh.smem);
+    return VC_ERR_UNSUPPORTED;
+  }
+  if (b->ctas_per_sm > 0 && b->ctas_per_sm < ctas) ctas = b->ctas_per_sm;
+  sh.grid = b->sms * ctas;
+
+  const size_t jobs_bytes = sizeof(vc::JobDesc) * (size_t)sh.jobs_cap;
+  if (b->use_graph) {
+    const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, b->cur);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      VC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaMemcpyAsync(b->d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, b->cap_stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, b->cap_stream);
+      if (e == cudaSuccess) e = vc::launch_batch(b->d_jobs, b->d_hdr, sh, b->cap_stream);
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        set_err("batch graph capture failed: %s", cudaGetErrorString(e));
+        return VC_ERR_CUDA;
+      }
+      it = b->graphs.emplace(key, ge).first;
+    }
+    VC_CUDA(cudaGraphLaunch(it->second, st));
+  } else {
+    VC_CUDA(cudaMemcpyAsync(b->d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, st));
+    VC_CUDA(vc::launch_batch(b->d_jobs, b->d_hdr, sh, st));
+  }
+  VC_CUDA(cudaEventRecord(b->staged[b->cur], st));
+  b->cur ^= 1;
+  for (int k = 0; k < nj; k++) {
+    vc_ctx* c = jobs[live[k]].ctx;
+    c->frame += jobs[live[k]].nframes;
+    c->last = st;
+    VC_CUDA(cudaEventRecord(c->ev_batch, st));
+    c->batch_pending = true;
+  }
+  return VC_OK;
+}
+
+void vc_batcher_destroy(vc_batcher* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  drop_graphs(b);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_hdr);
+  cudaFree(b->d_pool);
+  for (int i = 0; i < 2; i++) {
+    cudaFreeHost(b->h_jobs[i]);
+    cudaFreeHost(b->h_hdr[i]);
+    if (b->staged[i]) cudaEventDestroy(b->staged[i]);
+  }
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -44,6 +44,38 @@ struct MainPrbg {
   int kind;
 };
 
+// One job of a ragged batch: nframes consecutive frames of one stream in one
+// direction, with its scratch in the batch's pool.  warp_base / tile_base /
+// kmod_base are the job's first index in the batch-wide work lists of the
+// keystream (16 subframes per warp), round (frame x tile) and shift-table
+// kernels; each list is the jobs' ranges laid end to end.
+struct JobDesc {
+  Layout L;
+  Tables tb;
+  Chains ch;
+  MainPrbg* main;
+  int kind, dir, nframes, pad0;
+  const uint8_t* in;
+  uint8_t* out;
+  uint8_t* ks;
+  long long* sc;
+  int* kmod;
+  uint8_t* buf[2];
+  uint8_t* agg[2];
+  int warp_base, tile_base, kmod_base, pad1;
+};
+
+struct BatchHdr {
+  int njobs, total_warps, total_tiles, total_kmod;
+};
+
+// Launch geometry of a batch: capacities (work beyond the header's totals
+// exits at once, so one captured graph serves every batch within them).
+struct BatchShape {
+  int jobs_cap, warps_cap, kmod_cap, rounds, grid;
+  size_t smem;
+};
+
 // Launchers (vc_kernels.cu).  All enqueue on `st` and return the launch error.
 cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* srank, int* fixlim, cudaStream_t st);
 cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cudaStream_t st);
@@ -62,6 +94,9 @@ cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
                              int nframes, cudaStream_t st);
 size_t round_smem_bytes(const Layout& L);
+cudaError_t prepare_batch_kernels(size_t smem);
+cudaError_t batch_ctas_per_sm(size_t smem, int* ctas);
+cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st);
 
 // Diagnostics: the chaotic primitives applied elementwise.
 cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st);

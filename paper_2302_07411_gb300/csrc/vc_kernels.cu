@@ -149,24 +149,34 @@ cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cuda
   return cudaGetLastError();
 }
 
-__global__ void k_frame_sc(MainPrbg* mp, int nframes, long long* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// s_c of the next nframes frames (Alg. 1), serially from PRBG_m.
+__device__ void frame_sc_serial(MainPrbg* mp, int nframes, long long* sc) {
   MainPrbg m = *mp;
   for (int f = 0; f < nframes; f++) sc[f] = 1 + (long long)(main_next_group(m) & 0xFFFFull);
   *mp = m;
 }
 
-// kmod[f][alpha] = floor(s_c * csin((2 pi alpha) / H)) mod W, in [0, W).
+__global__ void k_frame_sc(MainPrbg* mp, int nframes, long long* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  frame_sc_serial(mp, nframes, sc);
+}
+
+// floor(s_c * csin((2 pi alpha) / H)) mod W, in [0, W).
+__device__ __forceinline__ int kmod_of(const Layout& L, long long sc, int a) {
+  const double t = __ddiv_rn(__dmul_rn(kTwoPi, (double)a), (double)L.H);
+  const double v = __dmul_rn((double)sc, csin(t));
+  long long k = (long long)floor(v) % L.W;
+  if (k < 0) k += L.W;
+  return (int)k;
+}
+
+// kmod[f][alpha] for the pass's frames (Eq. 1 shift table).
 __global__ void k_kmod(Layout L, const long long* sc, int nframes, int* kmod) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nframes * L.H) return;
   const int f = (int)(idx / L.H);
   const int a = (int)(idx - (long long)f * L.H);
-  const double t = __ddiv_rn(__dmul_rn(kTwoPi, (double)a), (double)L.H);
-  const double v = __dmul_rn((double)sc[f], csin(t));
-  long long k = (long long)floor(v) % L.W;
-  if (k < 0) k += L.W;
-  kmod[idx] = (int)k;
+  kmod[idx] = kmod_of(L, sc[f], a);
 }
 
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
@@ -464,10 +474,8 @@ struct PairWriter {
 };
 
 template <int KIND, bool FX>
-__global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt >> 1;
-  const int side = gt & 1;
+__device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
+                                              uint8_t* ks, const int i, const int side) {
   if (i >= L.n) return;  // both lanes of a pair leave together
   const unsigned pmask = 3u << (threadIdx.x & 30);
   constexpr int STEP = KIND == 0 ? 6 : 12;
@@ -582,6 +590,12 @@ __global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, 
   }
 }
 
+template <int KIND, bool FX>
+__global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  ks_pair_chain<KIND, FX>(L, tb, ch, nframes, ks, gt >> 1, gt & 1);
+}
+
 // PLCM keystream on the integer pipes, lane-pair form with the writes of a
 // 24-byte group overlapped with the iterates of the next group: in the steady
 // loop a lane issues two iterates, stores the previous group (whose partner
@@ -589,10 +603,8 @@ __global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, 
 // hidden), then two more iterates.  The fallback for operands outside the
 // fixed-point range is checked once per group: the rare group that needs it
 // is recomputed step by step with the hardware division.
-__global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt >> 1;
-  const int side = gt & 1;
+__device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
+                                                 uint8_t* ks, const int i, const int side) {
   if (i >= L.n) return;
   const unsigned pmask = 3u << (threadIdx.x & 30);
   constexpr uint64_t M48 = 0xFFFFFFFFFFFFull;
@@ -710,6 +722,11 @@ __global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains c
     ch.carry[2 * i + 1] = c1;
     ch.carry_len[i] = clen;
   }
+}
+
+__global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1);
 }
 
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
@@ -862,10 +879,8 @@ __device__ __forceinline__ uint8_t enc_y_at(const Layout& L, const Tables& tb, c
 }
 
 template <int C>
-__global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
   const Layout& L = A.L;
-  const int f = blockIdx.y, t = blockIdx.x;
   const int rowb = L.W * C;
   const int a0 = t * L.T;
   const int Te = min(L.T, L.H - a0);
@@ -1102,6 +1117,12 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
   if (threadIdx.x == 0) A.agg_out[(long long)f * L.NT + t] = (uint8_t)run;
 }
 
+template <int C>
+__global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  enc_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
+}
+
 // [Z tile, 16-aligned][tile carries, NT bytes rounded to 16][row shifts, 32 ints][scan, 32 words]
 size_t round_smem_bytes(const Layout& L) {
   return (((size_t)L.T * L.W * L.C + 15) & ~(size_t)15) + ((L.NT + 15) & ~15) + 32 * sizeof(int) +
@@ -1132,10 +1153,8 @@ cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long
 }
 
 // After the last round: apply each tile's missing prefix in place.
-__global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb, uint8_t* out, long long out_stride,
-                                                             const uint8_t* agg) {
-  __shared__ uint8_t s_carry[kMaxTiles];
-  const int f = blockIdx.y, t = blockIdx.x;
+__device__ __forceinline__ void enc_fixup_tile(const Layout& L, const Tables& tb, uint8_t* out, long long out_stride,
+                                               const uint8_t* agg, const int f, const int t, uint8_t* s_carry) {
   if (threadIdx.x < 32) tile_carries(L, tb, agg + (long long)f * L.NT, s_carry);
   __syncthreads();
   if (t == 0) return;
@@ -1162,6 +1181,12 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb
   for (int k = body0 + nvec * 16 + threadIdx.x; k < lim; k += blockDim.x) O[k] ^= cy;
 }
 
+__global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb, uint8_t* out, long long out_stride,
+                                                             const uint8_t* agg) {
+  __shared__ uint8_t s_carry[kMaxTiles];
+  enc_fixup_tile(L, tb, out, out_stride, agg, blockIdx.y, blockIdx.x, s_carry);
+}
+
 cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
                              int nframes, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
@@ -1176,10 +1201,8 @@ cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long
 // with c_{q-1} replaced at a subframe start by the seed y of the last byte of
 // the next subframe (itself a non-first byte, so computable the same way).
 template <int C>
-__global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
   const Layout& L = A.L;
-  const int f = blockIdx.y, t = blockIdx.x;
   const int rowb = L.W * C;
   const int a0 = t * L.T;
   const int Te = min(L.T, L.H - a0);
@@ -1239,6 +1262,12 @@ __global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
 }
 
 template <int C>
+__global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  dec_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
+}
+
+template <int C>
 static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
   const size_t smem = round_smem_bytes(A.L);
   cudaError_t e = cudaFuncSetAttribute(k_dec_round<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1259,6 +1288,143 @@ cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long
     case 4: return dec_round_c<4>(A, nframes, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// =============================================================================
+// Ragged batch: many streams, frames, resolutions and both directions in one
+// launch per phase (schedule, shift tables, keystream, each round, fix-up).
+// The round kernels are persistent: a grid sized to the GPU walks the
+// batch-wide (job, frame, tile) list.
+// =============================================================================
+
+// largest j < nj with key(J[j]) <= x (keys are non-decreasing)
+template <typename Key>
+__device__ __forceinline__ int find_job(const JobDesc* J, int nj, int x, Key key) {
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (key(J[mid]) <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_batch_sc(const JobDesc* J, const BatchHdr* hdr) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < hdr->njobs && J[j].nframes > 0) frame_sc_serial(J[j].main, J[j].nframes, J[j].sc);
+}
+
+__global__ void k_batch_kmod(const JobDesc* J, const BatchHdr* hdr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= hdr->total_kmod) return;
+  const int j = find_job(J, hdr->njobs, idx, [](const JobDesc& d) { return d.kmod_base; });
+  const JobDesc& d = J[j];
+  const int local = idx - d.kmod_base;
+  const int f = local / d.L.H;
+  const int a = local - f * d.L.H;
+  d.kmod[local] = kmod_of(d.L, d.sc[f], a);
+}
+
+__global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHdr* hdr) {
+  const int w = blockIdx.x;
+  if (w >= hdr->total_warps) return;
+  const int j = find_job(J, hdr->njobs, w, [](const JobDesc& d) { return d.warp_base; });
+  const JobDesc& d = J[j];
+  const int i = (w - d.warp_base) * 16 + (threadIdx.x >> 1);
+  const int side = threadIdx.x & 1;
+  if (d.kind == 0)
+    ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side);
+  else
+    ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side);
+}
+
+// Round `step` of every job that has one (job rounds may differ): encryption
+// applies round `step`, decryption round r - 1 - step; the buffers alternate
+// as in a single-stream pass.
+__device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step) {
+  const Layout& L = d.L;
+  const int r = L.rounds;
+  const int jr = d.dir == 0 ? step : r - 1 - step;
+  RoundArgs A;
+  A.L = L;
+  A.tb = d.tb;
+  A.in = step == 0 ? d.in : d.buf[(step - 1) & 1];
+  A.in_stride = step == 0 ? (long long)L.N : L.Npad;
+  A.out = step == r - 1 ? d.out : d.buf[step & 1];
+  A.out_stride = step == r - 1 ? (long long)L.N : L.Npad;
+  A.ks = d.ks + (long long)jr * L.Npad;
+  A.ks_stride = (long long)r * L.Npad;
+  A.kmod = d.kmod;
+  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] : nullptr;
+  A.agg_out = d.dir == 0 ? d.agg[step & 1] : nullptr;
+  return A;
+}
+
+__global__ void __launch_bounds__(kRoundThreads) k_batch_round(const JobDesc* J, const BatchHdr* hdr, int step) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int total = hdr->total_tiles, nj = hdr->njobs;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = find_job(J, nj, item, [](const JobDesc& d) { return d.tile_base; });
+    const JobDesc& d = J[j];
+    if (step < d.L.rounds) {
+      const int local = item - d.tile_base;
+      const int f = local / d.L.NT;
+      const int t = local - f * d.L.NT;
+      const RoundArgs A = batch_round_args(d, step);
+      if (d.dir == 0) {
+        switch (d.L.C) {
+          case 1: enc_round_tile<1>(A, f, t, smem); break;
+          case 3: enc_round_tile<3>(A, f, t, smem); break;
+          default: enc_round_tile<4>(A, f, t, smem); break;
+        }
+      } else {
+        switch (d.L.C) {
+          case 1: dec_round_tile<1>(A, f, t, smem); break;
+          case 3: dec_round_tile<3>(A, f, t, smem); break;
+          default: dec_round_tile<4>(A, f, t, smem); break;
+        }
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next item
+  }
+}
+
+__global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J, const BatchHdr* hdr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int total = hdr->total_tiles, nj = hdr->njobs;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = find_job(J, nj, item, [](const JobDesc& d) { return d.tile_base; });
+    const JobDesc& d = J[j];
+    if (d.dir == 0) {
+      const int local = item - d.tile_base;
+      const int f = local / d.L.NT;
+      const int t = local - f * d.L.NT;
+      enc_fixup_tile(d.L, d.tb, d.out, d.L.N, d.agg[(d.L.rounds - 1) & 1], f, t, smem);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t prepare_batch_kernels(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+cudaError_t batch_ctas_per_sm(size_t smem, int* ctas) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_batch_round, kRoundThreads, smem);
+}
+
+cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st) {
+  k_batch_sc<<<(sh.jobs_cap + 31) / 32, 32, 0, st>>>(jobs, hdr);
+  k_batch_kmod<<<(sh.kmod_cap + 255) / 256, 256, 0, st>>>(jobs, hdr);
+  k_batch_ks<<<sh.warps_cap, 32, 0, st>>>(jobs, hdr);
+  for (int step = 0; step < sh.rounds; step++) k_batch_round<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+  k_batch_fixup<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr);
+  return cudaGetLastError();
 }
 
 // =============================================================================

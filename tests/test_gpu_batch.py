@@ -1,0 +1,100 @@
+"""Ragged batches (many streams per launch, captured CUDA graph): every job's
+output equals the same stream run alone, byte for byte, across resolutions,
+maps, directions, subframe counts and round counts, over several consecutive
+batches (graph replays) and mixed with single-stream calls."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+STREAMS = [  # (kind, H, W, C, n, rounds, direction, frames per batch)
+    (0, 48, 64, 3, 12, 5, 0, 2),
+    (1, 40, 40, 3, 4, 5, 1, 1),
+    (0, 96, 80, 3, 160, 5, 1, 2),
+    (0, 33, 47, 1, 5, 3, 0, 3),
+    (1, 64, 32, 4, 64, 2, 0, 1),
+    (0, 120, 90, 3, 30, 5, 0, 1),
+]
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_07411_gb300 import binding, build
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_solo_runs(B, graph):
+    batcher = B.Batcher(graph=graph)
+    mixed, solo, data = [], [], []
+    for s, (kind, H, W, C, n, r, direction, F) in enumerate(STREAMS):
+        key = synth.key_for_seed(kind, 500 + s)
+        mixed.append(B.Cipher(kind, key, H, W, C, n, r))
+        solo.append(B.Cipher(kind, key, H, W, C, n, r))
+        data.append(synth.uniform_frames(3 * F, H, W, C, seed=600 + s))
+    for tick in range(3):  # consecutive batches: graph replays, state carried
+        jobs, outs, refs = [], [], []
+        for s, (kind, H, W, C, n, r, direction, F) in enumerate(STREAMS):
+            x = torch.from_numpy(data[s][tick * F:(tick + 1) * F]).cuda()
+            y = torch.empty_like(x)
+            jobs.append((mixed[s], direction, x, y, F))
+            outs.append(y)
+            ref = solo[s].encrypt(x) if direction == 0 else solo[s].decrypt(x)
+            refs.append(ref)
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for s in range(len(STREAMS)):
+            assert torch.equal(outs[s], refs[s]), f"tick {tick}, stream {s}"
+    for s in range(len(STREAMS)):
+        assert mixed[s].frame_index == solo[s].frame_index == 3 * STREAMS[s][7]
+    for c in mixed + solo:
+        c.close()
+    batcher.close()
+
+
+def test_batch_round_trip_and_mixing_with_single_calls(B, orc):
+    """Encrypt in a batch, continue the same contexts with single-stream calls,
+    then decrypt everything in a batch; the oracle agrees on the ciphertext."""
+    batcher = B.Batcher()
+    shapes = [(0, 60, 60, 3, 8), (1, 30, 50, 3, 5)]
+    enc = [B.Cipher(k, synth.key_for_seed(k, 700 + i), H, W, C, n) for i, (k, H, W, C, n) in enumerate(shapes)]
+    dec = [B.Cipher(k, synth.key_for_seed(k, 700 + i), H, W, C, n) for i, (k, H, W, C, n) in enumerate(shapes)]
+    refs = [orc.OracleCipher(k, synth.key_for_seed(k, 700 + i), H, W, C, n) for i, (k, H, W, C, n) in enumerate(shapes)]
+    X = [synth.uniform_frames(4, H, W, C, seed=710 + i) for i, (k, H, W, C, n) in enumerate(shapes)]
+    Y = [torch.empty(x.shape, dtype=torch.uint8, device="cuda") for x in X]
+    d = [torch.from_numpy(x).cuda() for x in X]
+    batcher.submit([(enc[i], 0, d[i][:2].contiguous(), Y[i][:2], 2) for i in range(2)])
+    torch.cuda.synchronize()
+    for i in range(2):
+        enc[i].encrypt(d[i][2:].contiguous(), Y[i][2:])      # single-stream calls continue the streams
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert np.array_equal(Y[i].cpu().numpy(), refs[i].encrypt(X[i]))
+    Z = [torch.empty_like(y) for y in Y]
+    batcher.submit([(dec[i], 1, Y[i], Z[i], 4) for i in range(2)])
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert np.array_equal(Z[i].cpu().numpy(), X[i])
+    batcher.close()
+
+
+def test_batch_rejects_bad_jobs(B):
+    batcher = B.Batcher()
+    c = B.Cipher(0, synth.key_for_seed(0, 1), 16, 16, 3, 4)
+    x = torch.zeros((1, 16, 16, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.VcError):
+        batcher.submit([(c, 0, x, x.clone(), 1), (c, 0, x, x.clone(), 1)])  # same context twice
+    with pytest.raises(B.VcError):
+        batcher.submit([(c, 2, x, x.clone(), 1)])
+    batcher.close()
