@@ -1,0 +1,145 @@
+"""Autotuner of the cipher's launch shapes.
+
+Every knob it turns leaves the ciphertext unchanged (the tests check each
+setting against the oracle): lanes per chaotic chain pair in the keystream
+kernel (VC_OPT_KS_LANES), rows per round-kernel tile (VC_OPT_TILE_ROWS, the
+block shape / shared-memory staging depth of the confusion gather), frames
+per pass and keystream run-ahead (VC_OPT_CHUNK, VC_OPT_OVERLAP), and the
+persistent grid of the batched round kernels (VC_BOPT_CTAS_PER_SM).  Never
+the subframe count n or the rounds r: those are cipher parameters.
+
+Candidates are timed on the device with CUDA events around the real entry
+points on synthetic frames, after a warm-up.  Results are cached in a JSON
+file keyed by GPU name and shape (VCRYPT_TUNE_CACHE, default
+~/.cache/vcrypt_autotune.json).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+
+from . import binding as B
+
+CACHE = os.environ.get("VCRYPT_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "vcrypt_autotune.json"))
+
+
+def _gpu_name() -> str:
+    import torch
+
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _load() -> dict:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(cache: dict) -> None:
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass
+
+
+def _time(fn, warmup: int = 1, reps: int = 2) -> float:
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_stream(kind: int, H: int, W: int, C: int, n: int, rounds: int = 5, frames: int = 48,
+                use_cache: bool = True) -> dict:
+    """Best single-stream options for encrypting `frames`-frame calls of this
+    layout; returns {"options": {...}, "ms": t, "trials": [...]}"""
+    import torch
+
+    key = f"stream|{_gpu_name()}|{kind}|{H}x{W}x{C}|n{n}|r{rounds}|f{frames}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.integers(0, 256, (frames, H, W, C), dtype=np.uint8)).cuda()
+    y = torch.empty_like(x)
+    keyv = [0.31, 0.21, 0.62, 0.37] if kind == 0 else [0.31, 0.6, 0.62]
+    trials = []
+    space = {"ks_lanes": [2, 1], "tile_rows": [0, 16, 8], "overlap": [1, 0]}
+    for lanes, tile, ov in itertools.product(space["ks_lanes"], space["tile_rows"], space["overlap"]):
+        c = B.Cipher(kind, keyv, H, W, C, n, rounds)
+        c.set_option(B.VC_OPT_KS_LANES, lanes)
+        c.set_option(B.VC_OPT_TILE_ROWS, tile)
+        c.set_option(B.VC_OPT_OVERLAP, ov)
+        ms = _time(lambda: c.encrypt(x, y))
+        trials.append({"ks_lanes": lanes, "tile_rows": tile, "overlap": ov, "ms": round(ms, 3)})
+        c.close()
+    best = min(trials, key=lambda t: t["ms"])
+    out = {"options": {k: best[k] for k in ("ks_lanes", "tile_rows", "overlap")}, "ms": best["ms"], "trials": trials}
+    cache = _load()
+    cache[key] = out
+    _store(cache)
+    return out
+
+
+def apply_stream(cipher: B.Cipher, options: dict) -> None:
+    cipher.set_option(B.VC_OPT_KS_LANES, int(options.get("ks_lanes", 2)))
+    cipher.set_option(B.VC_OPT_TILE_ROWS, int(options.get("tile_rows", 0)))
+    cipher.set_option(B.VC_OPT_OVERLAP, int(options.get("overlap", 1)))
+
+
+def tune_batch(layouts, frames_per_job: int = 1, use_cache: bool = True) -> dict:
+    """Best persistent-grid CTAs per SM and tile rows for a batch made of one
+    job per entry of `layouts` ((kind, H, W, C, n) tuples, encrypting)."""
+    import torch
+
+    sig = "|".join(f"{k}:{H}x{W}x{C}:{n}" for k, H, W, C, n in layouts)
+    key = f"batch|{_gpu_name()}|f{frames_per_job}|{sig}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    rng = np.random.default_rng(1)
+    data = {}
+    for k, H, W, C, n in layouts:
+        if (H, W, C) not in data:
+            data[(H, W, C)] = torch.from_numpy(
+                rng.integers(0, 256, (frames_per_job, H, W, C), dtype=np.uint8)).cuda()
+    trials = []
+    for ctas, tile in itertools.product([0, 1, 2], [0, 16]):
+        ciphers = []
+        jobs = []
+        for s, (k, H, W, C, n) in enumerate(layouts):
+            c = B.Cipher(k, [0.31, 0.21, 0.62, 0.37] if k == 0 else [0.31, 0.6, 0.62], H, W, C, n, 5)
+            c.set_option(B.VC_OPT_TILE_ROWS, tile)
+            ciphers.append(c)
+            x = data[(H, W, C)]
+            jobs.append((c, 0, x, torch.empty_like(x), frames_per_job))
+        b = B.Batcher(graph=True, ctas_per_sm=ctas)
+        ms = _time(lambda: b.submit(jobs))
+        trials.append({"ctas_per_sm": ctas, "tile_rows": tile, "ms": round(ms, 3)})
+        b.close()
+        for c in ciphers:
+            c.close()
+    best = min(trials, key=lambda t: t["ms"])
+    out = {"options": {"ctas_per_sm": best["ctas_per_sm"], "tile_rows": best["tile_rows"]}, "ms": best["ms"],
+           "trials": trials}
+    cache = _load()
+    cache[key] = out
+    _store(cache)
+    return out

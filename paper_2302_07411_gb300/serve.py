@@ -1,0 +1,270 @@
+"""Continuous-batching serving loop for the chaotic video cipher.
+
+Video streams arrive over time (each with its own key, resolution, frame rate
+and direction).  The loop admits a stream when its device memory fits the HBM
+budget, keeps its key and chaotic state resident on the GPU, and every tick
+gathers the frames that have arrived on all admitted streams into ONE ragged
+batch (vc_batch_submit: one CUDA-graph replay for every stream, resolution and
+direction).  Frames that arrive while earlier batches run join the next tick;
+GPU work of consecutive ticks overlaps with the host's next gathering.  A
+frame's latency is the device completion time of its batch minus the frame's
+arrival time (CUDA event timestamps, so host polling adds nothing).
+
+mode="perframe" is the comparison: the same loop, but each ready frame is
+encrypted by its own encrypt_frames / decrypt_frames call (one launch sequence
+per frame).
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding as B
+
+
+def subframes_for(H: int) -> int:
+    """The subframe count the serving configuration uses: n = ceil(H / 4)."""
+    return max(1, math.ceil(H / 4))
+
+
+@dataclass
+class Stream:
+    spec: dict
+    cipher: B.Cipher
+    out: object                      # device ring of output frames
+    bytes: int
+    next_frame: int = 0              # next frame index to submit
+    frames_total: int = 0
+    done: int = 0
+
+
+@dataclass
+class ServeResult:
+    mode: str
+    latencies_ms: list = field(default_factory=list)
+    frames: int = 0
+    admitted: int = 0
+    rejected: int = 0
+    peak_streams: int = 0
+    wall_s: float = 0.0
+    ticks: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
+                "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
+
+
+class Server:
+    """Runs a list of stream requests (synth.serving_workload) in real time."""
+
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, tick_ms: float = 4.0, mode: str = "batch",
+                 max_frames_per_tick: int = 4, ring: int = 8, keep_outputs: bool = False):
+        import torch
+
+        self.torch = torch
+        self.budget = hbm_budget_bytes
+        self.tick = tick_ms / 1e3
+        self.mode = mode
+        self.maxf = max_frames_per_tick
+        self.ring = ring
+        self.stream = torch.cuda.Stream()
+        self.batcher = B.Batcher() if mode == "batch" else None
+        self.inputs = {}  # (H, W, C) -> device frames reused as input content
+        self.keep = keep_outputs
+        self.finished: list[Stream] = []  # kept when keep_outputs (tests)
+
+    def input_frames(self, H, W, C):
+        """Input content: frame k of a stream of this size is input_frames[k % maxf]
+        (2 * maxf frames are kept so m <= maxf consecutive frames are contiguous)."""
+        key = (H, W, C)
+        if key not in self.inputs:
+            rng = np.random.default_rng(H * 7 + W)
+            base = rng.integers(0, 256, size=(self.maxf, H, W, C), dtype=np.uint8)
+            self.inputs[key] = self.torch.from_numpy(np.concatenate([base, base])).cuda()
+        return self.inputs[key]
+
+    @staticmethod
+    def footprint(spec: dict, ring: int, maxf: int) -> int:
+        """Device bytes a stream holds while admitted: its output ring, its
+        state, and its share of the batch scratch (keystream, buffers)."""
+        N = spec["H"] * spec["W"] * spec["C"]
+        n = subframes_for(spec["H"])
+        state = n * (6 * 8 + 20) + (spec["H"] * spec["W"] // 32 + 2) * 8
+        scratch = maxf * (5 + 2) * ((N + 255) // 256 * 256)
+        return ring * N + state + scratch
+
+    def run(self, requests: list[dict], horizon_s: float | None = None) -> ServeResult:
+        torch = self.torch
+        res = ServeResult(self.mode)
+        pending = deque(sorted(requests, key=lambda r: r["arrival"]))
+        active: list[Stream] = []
+        used = 0
+        inflight = deque()  # (event, [(stream, frame index, arrival time)])
+        t0_ev = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0_ev.record(self.stream)
+        t0_ev.synchronize()
+        t0 = time.perf_counter()
+        end_time = horizon_s if horizon_s is not None else max(
+            (r["arrival"] + r["duration"] for r in requests), default=0.0)
+
+        def drain(block: bool):
+            while inflight and (block or inflight[0][0].query()):
+                ev, frames = inflight.popleft()
+                ev.synchronize()
+                done_t = t0_ev.elapsed_time(ev) / 1e3  # device time since t0
+                for st, k, arr in frames:
+                    res.latencies_ms.append((done_t - arr) * 1e3)
+                    st.done += 1
+                    res.frames += 1
+
+        while True:
+            now = time.perf_counter() - t0
+            # admissions (HBM budget) and departures
+            while pending and pending[0]["arrival"] <= now:
+                spec = pending.popleft()
+                fp = self.footprint(spec, self.ring, self.maxf)
+                if used + fp > self.budget:
+                    res.rejected += 1
+                    continue
+                H, W, C = spec["H"], spec["W"], spec["C"]
+                ciph = B.Cipher(spec["kind"], spec["key"], H, W, C, subframes_for(H), 5)
+                out = torch.empty((self.ring, H, W, C), dtype=torch.uint8, device="cuda")
+                st = Stream(spec, ciph, out, fp, frames_total=max(1, int(spec["duration"] * spec["fps"])))
+                active.append(st)
+                used += fp
+                res.admitted += 1
+            res.peak_streams = max(res.peak_streams, len(active))
+            # gather the frames that have arrived
+            jobs, meta = [], []
+            for st in active:
+                fps = st.spec["fps"]
+                arrived = min(st.frames_total, int((now - st.spec["arrival"]) * fps) + 1)
+                m = min(arrived - st.next_frame, self.maxf, self.ring - (st.next_frame % self.ring))
+                if m <= 0:
+                    continue
+                k0 = st.next_frame % self.maxf
+                x = self.input_frames(st.spec["H"], st.spec["W"], st.spec["C"])[k0:k0 + m]
+                slot = st.next_frame % self.ring
+                y = st.out[slot:slot + m]
+                jobs.append((st, x, y, m))
+                meta.extend((st, st.next_frame + i, st.spec["arrival"] + (st.next_frame + i) / fps) for i in range(m))
+                st.next_frame += m
+            if jobs:
+                with torch.cuda.stream(self.stream):
+                    if self.mode == "batch":
+                        self.batcher.submit([(st.cipher, st.spec["direction"], x, y, m) for st, x, y, m in jobs],
+                                            stream=self.stream)
+                    else:
+                        for st, x, y, m in jobs:
+                            for i in range(m):
+                                if st.spec["direction"] == 0:
+                                    st.cipher.encrypt(x[i:i + 1], y[i:i + 1], stream=self.stream)
+                                else:
+                                    st.cipher.decrypt(x[i:i + 1], y[i:i + 1], stream=self.stream)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(self.stream)
+                inflight.append((ev, meta))
+                res.ticks += 1
+            drain(block=False)
+            # retire finished streams
+            still = []
+            for st in active:
+                if st.done >= st.frames_total:
+                    used -= st.bytes
+                    if self.keep:
+                        self.finished.append(st)
+                    else:
+                        st.cipher.close()
+                else:
+                    still.append(st)
+            active = still
+            if not pending and not active and not inflight:
+                break
+            if now > end_time + 5.0:  # safety: stop a run that cannot keep up
+                drain(block=True)
+                break
+            nxt = self.tick - ((time.perf_counter() - t0) % self.tick)
+            time.sleep(max(0.0, nxt))
+        drain(block=True)
+        res.wall_s = time.perf_counter() - t0
+        for st in active:
+            st.cipher.close()
+        return res
+
+    def close(self):
+        if self.batcher is not None:
+            self.batcher.close()
+
+
+def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0 / 24.0,
+             counts=(16, 32, 64, 128, 256, 512), seconds: float = 3.0, seed: int = 21,
+             hbm_budget_bytes: int = 200 << 30, tick_ms: float = 4.0) -> dict:
+    """Largest number of concurrent fps streams of H x W x 3 (half encrypt,
+    half decrypt, alternating maps) whose per-frame p99 latency stays below
+    budget_ms.  All streams start within the first 0.25 s and last `seconds`."""
+    import synth
+
+    best, runs = 0, []
+    for n in counts:
+        reqs = synth.serving_workload(n, seed=seed, rate_per_s=n / 0.25, resolutions=((H, W),), fps_choices=(fps,),
+                                      duration_s=(seconds, seconds))
+        srv = Server(hbm_budget_bytes=hbm_budget_bytes, tick_ms=tick_ms, mode=mode)
+        res = srv.run(reqs)
+        srv.close()
+        s = res.summary()
+        s["streams"] = n
+        runs.append(s)
+        if s["rejected"] == 0 and s["p99_ms"] < budget_ms:
+            best = n
+        else:
+            break
+    return {"mode": mode, "resolution": f"{H}x{W}x3", "fps": fps, "p99_budget_ms": round(budget_ms, 2),
+            "max_streams": best, "runs": runs}
+
+
+def main():
+    import argparse
+    import json
+
+    import torch
+
+    import synth
+
+    ap = argparse.ArgumentParser(description="serving loop measurements")
+    ap.add_argument("--mode", choices=["batch", "perframe", "both"], default="both")
+    ap.add_argument("--streams", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=64.0, help="stream arrivals per second (Poisson)")
+    ap.add_argument("--capacity", action="store_true", help="search the 24 FPS stream capacity instead")
+    ap.add_argument("--size", type=int, nargs=2, default=[768, 768])
+    ap.add_argument("--seconds", type=float, default=3.0)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    from . import build
+
+    build.build()
+    modes = ["batch", "perframe"] if a.mode == "both" else [a.mode]
+    out = {}
+    for mode in modes:
+        if a.capacity:
+            out[mode] = capacity(mode, a.size[0], a.size[1], seconds=a.seconds,
+                                 hbm_budget_bytes=int(a.budget_gb * (1 << 30)))
+        else:
+            reqs = synth.serving_workload(a.streams, rate_per_s=a.rate)
+            srv = Server(hbm_budget_bytes=int(a.budget_gb * (1 << 30)), mode=mode)
+            res = srv.run(reqs)
+            srv.close()
+            out[mode] = res.summary()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -87,3 +87,23 @@ def smooth_clip(nframes: int, H: int, W: int, C: int = 3, seed: int = 2,
         np.clip(np.rint(img), 0, 255, out=img)
         out[f] = img.astype(np.uint8)
     return out
+
+
+def serving_workload(nstreams: int, seed: int = 5, rate_per_s: float = 64.0,
+                     resolutions=((480, 480), (576, 576), (768, 768), (720, 1280), (1080, 1920), (2160, 3840)),
+                     fps_choices=(24, 30, 60), duration_s=(2.0, 6.0)) -> list[dict]:
+    """Seeded stream requests for the serving loop: Poisson arrivals at
+    ``rate_per_s``, each stream with its own key (map alternating PLCM /
+    2DLASM), a resolution (H, W) from ``resolutions``, a frame rate from
+    ``fps_choices``, encrypt or decrypt (50/50) and a duration."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for s in range(nstreams):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        kind = s % 2
+        H, W = resolutions[int(rng.integers(len(resolutions)))]
+        out.append({"sid": s, "arrival": t, "kind": kind, "key": key_for_seed(kind, 1000 + s), "H": H, "W": W,
+                    "C": 3, "fps": int(fps_choices[int(rng.integers(len(fps_choices)))]),
+                    "direction": int(rng.integers(2)), "duration": float(rng.uniform(*duration_s))})
+    return out

@@ -1,0 +1,67 @@
+"""Serving loop: streams admitted over time, frames batched per tick with
+continuous batching; every stream's output equals the same stream run alone
+(tolerance: 0 bytes), in both the batched and the per-frame-launch modes, and
+admission respects the HBM budget."""
+from __future__ import annotations
+
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_07411_gb300 import binding, build
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _requests():
+    reqs = synth.serving_workload(8, seed=11, rate_per_s=40.0, resolutions=((32, 32), (48, 40), (24, 64)),
+                                  fps_choices=(24, 30, 60), duration_s=(0.3, 0.6))
+    return reqs
+
+
+@pytest.mark.parametrize("mode", ["batch", "perframe"])
+def test_served_streams_equal_solo_runs(B, mode):
+    from paper_2302_07411_gb300 import serve
+
+    reqs = _requests()
+    srv = serve.Server(hbm_budget_bytes=1 << 30, tick_ms=3.0, mode=mode, max_frames_per_tick=4, ring=64,
+                       keep_outputs=True)
+    res = srv.run(reqs)
+    summ = res.summary()
+    assert summ["admitted"] == len(reqs) and summ["rejected"] == 0
+    assert res.frames == sum(max(1, int(r["duration"] * r["fps"])) for r in reqs)
+    assert len(srv.finished) == len(reqs)
+    for st in srv.finished:
+        sp = st.spec
+        H, W, C = sp["H"], sp["W"], sp["C"]
+        inp = srv.input_frames(H, W, C)
+        solo = B.Cipher(sp["kind"], sp["key"], H, W, C, serve.subframes_for(H), 5)
+        for k in range(st.frames_total):
+            x = inp[k % srv.maxf: k % srv.maxf + 1]
+            ref = solo.encrypt(x) if sp["direction"] == 0 else solo.decrypt(x)
+            assert torch.equal(st.out[k % srv.ring], ref[0]), (sp["sid"], k)
+        solo.close()
+        st.cipher.close()
+    srv.close()
+
+
+def test_admission_respects_hbm_budget(B):
+    from paper_2302_07411_gb300 import serve
+
+    reqs = _requests()
+    one = max(serve.Server.footprint(r, 8, 4) for r in reqs)
+    srv = serve.Server(hbm_budget_bytes=int(2.5 * one), tick_ms=3.0)
+    res = srv.run(reqs)
+    assert res.rejected > 0 and res.admitted >= 1
+    srv.close()
