@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-serving", action="store_true", help="skip the 24 FPS serving-capacity leg")
     return ap.parse_args()
 
 
@@ -200,6 +201,27 @@ def load_peaks() -> dict:
         return {}
 
 
+def serving_capacity() -> dict:
+    """Concurrent 24 FPS 768x768x3 streams (half encrypt / half decrypt,
+    alternating PLCM / 2DLASM, n = 192) the serving loop sustains with
+    steady-state p99 per-frame latency under 41.7 ms: continuous batching (one
+    graph replay per 4 ms tick, keystream run-ahead) vs one launch sequence
+    per frame."""
+    from paper_2302_07411_gb300 import serve
+
+    out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
+    b = serve.capacity("batch", 768, 768, counts=(16, 32, 64, 128, 256), seconds=3.0)
+    p = serve.capacity("perframe", 768, 768, counts=(2, 4, 8, 16), seconds=2.5)
+    out["batched_streams"] = b["max_streams"]
+    out["per_frame_streams"] = p["max_streams"]
+    out["criterion"] = b["criterion"]
+    out["batched_runs"] = [{k: r.get(k) for k in ("streams", "steady_p50_ms", "steady_p99_ms", "first_frame_p99_ms",
+                                                  "fps")} for r in b["runs"]]
+    out["per_frame_runs"] = [{k: r.get(k) for k in ("streams", "steady_p50_ms", "steady_p99_ms", "fps")}
+                             for r in p["runs"]]
+    return out
+
+
 def run_ours(a) -> None:
     import numpy as np
     import torch
@@ -332,11 +354,16 @@ def run_ours(a) -> None:
         cpu = {"value": round(n_fr * H * W / s / 1e6, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                "sample": f"{n_fr} consecutive frames of the workload, single thread, {s:.1f} s"}
 
+    serving = None
+    if not a.no_serving and world == 1:
+        serving = serving_capacity()
+
     launches = sum(v["launches"] for v in prof.values())
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+u8", "data": "synthetic", "config": config(a, world),
             "roofline": roofline, "split": split, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "serving": serving,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
     ciph.close()

@@ -158,10 +158,31 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  * VC_BOPT_GRAPH:       1 (default) replay a captured CUDA graph per batch
  *                      shape; 0 plain kernel launches.
  * VC_BOPT_CTAS_PER_SM: CTAs per SM of the persistent round kernels; 0
- *                      (default) = the occupancy maximum.  Errors: VC_ERR_ARG. */
+ *                      (default) = the occupancy maximum.
+ * VC_BOPT_RUNAHEAD:    A > 0 keeps every stream's keystream (which does not
+ *                      depend on the frames) A frames ahead: each submit also
+ *                      launches, on an internal stream, the keystream of the
+ *                      stream's next frames into a device ring of 2A + 1
+ *                      frame slots, so a later batch only runs the rounds.
+ *                      A job may then ask for at most A frames, and a stream
+ *                      with keystream produced ahead accepts no single-stream
+ *                      calls or checkpoint (VC_ERR_SEQUENCE).  0 (default): off.
+ * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
+#define VC_BOPT_RUNAHEAD 3
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
+
+/* With run-ahead on: start producing the keystream of each context's next
+ * A frames now (e.g. right after a stream is admitted), on the batcher's
+ * internal stream.  Errors: VC_ERR_ARG (run-ahead off, null or repeated
+ * context), VC_ERR_OOM, VC_ERR_CUDA. */
+int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n);
+
+/* 1 if the keystream of the context's next nframes frames has been produced
+ * on the device (a batch using them will not wait for the producer), 0 if not
+ * yet, -code on error.  Never blocks. */
+int vc_batch_ready(vc_batcher* b, const vc_ctx* ctx, int32_t nframes);
 
 /* Synchronise and free the batcher. */
 void vc_batcher_destroy(vc_batcher* b);

@@ -19,7 +19,7 @@ _lib = None
 VC_OK = 0
 VC_PLCM, VC_2DLASM = 0, 1
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS = 1, 2, 3, 4, 5
-VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM = 1, 2
+VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD = 1, 2, 3
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
 
@@ -63,6 +63,8 @@ def lib():
             "vc_batch_submit": (C.c_int, [p, p, i32, p]),
             "vc_batcher_set_option": (C.c_int, [p, i32, i64]),
             "vc_batcher_destroy": (None, [p]),
+            "vc_batch_prefetch": (C.c_int, [p, p, i32]),
+            "vc_batch_ready": (C.c_int, [p, p, i32]),
             "enc_state_size": (sz, [p]),
             "enc_save_state": (C.c_int, [p, p, C.POINTER(C.c_size_t)]),
             "enc_load_state": (C.c_int, [p, p, sz]),
@@ -329,14 +331,28 @@ def vc_batcher_destroy(batcher) -> None:
 class Batcher:
     """Runs frames of many streams per launch (one CUDA graph replay per batch)."""
 
-    def __init__(self, graph: bool = True, ctas_per_sm: int = 0):
+    def __init__(self, graph: bool = True, ctas_per_sm: int = 0, runahead: int = 0):
         self.b = vc_batcher_create()
         vc_batcher_set_option(self.b, VC_BOPT_GRAPH, 1 if graph else 0)
         if ctas_per_sm:
             vc_batcher_set_option(self.b, VC_BOPT_CTAS_PER_SM, ctas_per_sm)
+        if runahead:
+            vc_batcher_set_option(self.b, VC_BOPT_RUNAHEAD, runahead)
 
     def submit(self, jobs, stream=None) -> None:
         vc_batch_submit(self.b, jobs, stream)
+
+    def prefetch(self, ciphers) -> None:
+        """Start producing the next run-ahead frames of keystream of these streams."""
+        arr = (C.c_void_p * max(1, len(ciphers)))(*[c.ctx.value for c in ciphers])
+        _check(lib().vc_batch_prefetch(self.b, arr, len(ciphers)), "vc_batch_prefetch")
+
+    def ready(self, cipher, nframes: int) -> bool:
+        """True if the keystream of the stream's next nframes frames exists on the device."""
+        r = lib().vc_batch_ready(self.b, cipher.ctx, nframes)
+        if r < 0:
+            raise VcError(-r, "vc_batch_ready")
+        return r == 1
 
     def close(self) -> None:
         if getattr(self, "b", None):

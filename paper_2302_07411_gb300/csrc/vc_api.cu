@@ -123,6 +123,21 @@ struct vc_ctx {
   cudaEvent_t ev_entry = nullptr;
   cudaEvent_t ev_batch = nullptr;  // recorded after a batch that used this context
   bool batch_pending = false;
+  // keystream run-ahead ring of the batcher: frame f's keystream, s_c and shift
+  // table live in slot f mod ring_cap; `produced` frames exist (the chaotic
+  // state has advanced that far), `frame` have been consumed.
+  uint8_t* ring_ks = nullptr;
+  long long* ring_sc = nullptr;
+  int* ring_kmod = nullptr;
+  int ring_cap = 0;
+  int64_t produced = 0;
+  // productions of the ring run on ks_stream; the last four are tracked so
+  // that readiness can be polled without blocking
+  static constexpr int kProdEv = 4;
+  cudaEvent_t ev_prod[kProdEv] = {};
+  int64_t prod_upto[kProdEv] = {};
+  int64_t nprod = 0;
+  int64_t produced_done = 0;  // frames known complete on the device
   int64_t passes = 0;
   // staging for host-buffer calls
   uint8_t* d_io[2] = {nullptr, nullptr};
@@ -321,7 +336,20 @@ int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t
   return end_pass(c, b, st);
 }
 
+// Single-stream calls generate the keystream inline: not while a batcher holds
+// keystream produced ahead for this context.
+int check_no_runahead(vc_ctx* c) {
+  if (c->produced != c->frame) {
+    set_err("a batcher holds %lld frames of keystream produced ahead for this stream; keep using the batcher",
+            (long long)(c->produced - c->frame));
+    return VC_ERR_SEQUENCE;
+  }
+  return VC_OK;
+}
+
 int enter(vc_ctx* c, cudaStream_t st) {
+  int rg = check_no_runahead(c);
+  if (rg) return rg;
   if (c->batch_pending) {  // a batch on another stream advanced this context last
     VC_CUDA(cudaStreamWaitEvent(st, c->ev_batch, 0));
     c->batch_pending = false;
@@ -354,6 +382,8 @@ int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nf
     if (rc) return rc;
   }
   c->frame += nframes;
+  c->produced = c->frame;
+  c->produced_done = c->frame;
   return VC_OK;
 }
 
@@ -430,7 +460,11 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
       cudaEventCreateWithFlags(&c->ev_rd[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rd[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_batch, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_batch, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_prod[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_prod[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_prod[2], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_prod[3], cudaEventDisableTiming) != cudaSuccess) {
     enc_destroy(c);
     set_err("stream/event creation failed");
     return VC_ERR_CUDA;
@@ -512,6 +546,8 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   VC_CUDA(cudaStreamSynchronize(c->copy_stream));
   VC_CUDA(cudaStreamSynchronize(st));
   c->frame += nframes;
+  c->produced = c->frame;
+  c->produced_done = c->frame;
   return VC_OK;
 }
 
@@ -535,6 +571,7 @@ int enc_save_state(vc_ctx* c, void* buf, size_t* len) {
     set_err("invalid argument");
     return VC_ERR_ARG;
   }
+  if (int rg = check_no_runahead(c)) return rg;
   sync_all(c);
   VC_CUDA(cudaGetLastError());
   const size_t n = (size_t)c->L.n;
@@ -584,6 +621,8 @@ int enc_load_state(vc_ctx* c, const void* buf, size_t len) {
   p += n * 2 * sizeof(uint64_t);
   VC_CUDA(cudaMemcpy(c->d_carry_len, p, n * sizeof(int), cudaMemcpyHostToDevice));
   c->frame = h.frame;
+  c->produced = h.frame;
+  c->produced_done = h.frame;
   return VC_OK;
 }
 
@@ -723,6 +762,11 @@ void enc_destroy(vc_ctx* c) {
   }
   if (c->ev_entry) cudaEventDestroy(c->ev_entry);
   if (c->ev_batch) cudaEventDestroy(c->ev_batch);
+  for (int i = 0; i < vc_ctx::kProdEv; i++)
+    if (c->ev_prod[i]) cudaEventDestroy(c->ev_prod[i]);
+  cudaFree(c->ring_ks);
+  cudaFree(c->ring_sc);
+  cudaFree(c->ring_kmod);
   delete c;
 }
 
@@ -767,6 +811,8 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
     if (rc) return rc;
   }
   c->frame += nframes;
+  c->produced = c->frame;
+  c->produced_done = c->frame;
   return VC_OK;
 }
 
@@ -854,8 +900,10 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
     return VC_ERR_UNSUPPORTED;
   }
   if (nframes == 0) return VC_OK;
+  int rc = check_no_runahead(c);
+  if (rc) return rc;
   void* base = nullptr;
-  int rc = static_scratch_address(&base);
+  rc = static_scratch_address(&base);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (c->batch_pending) {
@@ -916,6 +964,8 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
   VC_CUDA(cudaEventRecord(c->ev_entry, st));
   VC_CUDA(cudaStreamWaitEvent(c->ks_stream, c->ev_entry, 0));
   c->frame += nframes;
+  c->produced = c->frame;
+  c->produced_done = c->frame;
   return VC_OK;
 }
 
@@ -923,23 +973,32 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
 // Ragged batches
 // =============================================================================
 
-struct vc_batcher {
-  int dev = 0, sms = 0;
+namespace {
+
+// The launch lane of a batcher: device descriptors, pinned staging (two
+// alternating buffers) and the graphs captured for it.
+struct BatchLane {
   vc::JobDesc* d_jobs = nullptr;
   vc::BatchHdr* d_hdr = nullptr;
   int jobs_cap = 0;
-  vc::JobDesc* h_jobs[2] = {nullptr, nullptr};  // pinned staging, alternating
+  vc::JobDesc* h_jobs[2] = {nullptr, nullptr};
   vc::BatchHdr* h_hdr[2] = {nullptr, nullptr};
-  cudaEvent_t staged[2] = {nullptr, nullptr};   // staging b consumed by the device
+  cudaEvent_t staged[2] = {nullptr, nullptr};
   int cur = 0;
+  std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
+};
+
+}  // namespace
+
+struct vc_batcher {
+  int dev = 0, sms = 0;
+  BatchLane cons;
   uint8_t* d_pool = nullptr;
   size_t pool_cap = 0;
   bool use_graph = true;
   int ctas_per_sm = 0;
+  int runahead = 0;  // frames of keystream kept ahead per stream (0 = off)
   cudaStream_t cap_stream = nullptr;
-  // graph cache: (jobs_cap, warps_cap, kmod_cap, rounds, grid, smem, staging) -> executable
-  std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
-  std::vector<cudaStream_t> last_streams;
 };
 
 namespace {
@@ -950,36 +1009,210 @@ int bucket(int v, int lo) {
   return b;
 }
 
-void drop_graphs(vc_batcher* b) {
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-  b->graphs.clear();
+void drop_graphs(BatchLane& l) {
+  for (auto& kv : l.graphs) cudaGraphExecDestroy(kv.second);
+  l.graphs.clear();
 }
 
-int grow_jobs(vc_batcher* b, int need) {
-  if (need <= b->jobs_cap) return VC_OK;
+void free_lane(BatchLane& l) {
+  drop_graphs(l);
+  cudaFree(l.d_jobs);
+  cudaFree(l.d_hdr);
+  for (int i = 0; i < 2; i++) {
+    cudaFreeHost(l.h_jobs[i]);
+    cudaFreeHost(l.h_hdr[i]);
+    if (l.staged[i]) cudaEventDestroy(l.staged[i]);
+  }
+  l = BatchLane();
+}
+
+int init_lane(BatchLane& l) {
+  bool ok = cudaMalloc(&l.d_hdr, sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaMallocHost(&l.h_hdr[0], sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaMallocHost(&l.h_hdr[1], sizeof(vc::BatchHdr)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&l.staged[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&l.staged[1], cudaEventDisableTiming) == cudaSuccess;
+  return ok ? VC_OK : VC_ERR_OOM;
+}
+
+int grow_lane(BatchLane& l, int need) {
+  if (need <= l.jobs_cap) return VC_OK;
   const int cap = bucket(need, 64);
   cudaDeviceSynchronize();
-  drop_graphs(b);  // the descriptor address is a kernel argument of the captured graphs
-  cudaFree(b->d_jobs);
-  for (int i = 0; i < 2; i++) cudaFreeHost(b->h_jobs[i]);
-  b->d_jobs = nullptr;
-  b->h_jobs[0] = b->h_jobs[1] = nullptr;
-  b->jobs_cap = 0;
-  if (cudaMalloc(&b->d_jobs, sizeof(vc::JobDesc) * cap) != cudaSuccess ||
-      cudaMallocHost(&b->h_jobs[0], sizeof(vc::JobDesc) * cap) != cudaSuccess ||
-      cudaMallocHost(&b->h_jobs[1], sizeof(vc::JobDesc) * cap) != cudaSuccess) {
+  drop_graphs(l);  // the descriptor address is a kernel argument of the captured graphs
+  cudaFree(l.d_jobs);
+  for (int i = 0; i < 2; i++) cudaFreeHost(l.h_jobs[i]);
+  l.d_jobs = nullptr;
+  l.h_jobs[0] = l.h_jobs[1] = nullptr;
+  l.jobs_cap = 0;
+  if (cudaMalloc(&l.d_jobs, sizeof(vc::JobDesc) * cap) != cudaSuccess ||
+      cudaMallocHost(&l.h_jobs[0], sizeof(vc::JobDesc) * cap) != cudaSuccess ||
+      cudaMallocHost(&l.h_jobs[1], sizeof(vc::JobDesc) * cap) != cudaSuccess) {
     cudaGetLastError();
     set_err("batch descriptor allocation failed");
     return VC_ERR_OOM;
   }
-  b->jobs_cap = cap;
+  l.jobs_cap = cap;
   return VC_OK;
 }
 
-size_t job_scratch_bytes(const Layout& L, int nf) {
-  return round256((size_t)nf * L.rounds * L.Npad) + 2 * round256((size_t)nf * L.Npad) +
-         round256((size_t)nf * L.H * sizeof(int)) + round256((size_t)nf * sizeof(long long)) +
-         2 * round256((size_t)nf * L.NT);
+size_t job_scratch_bytes(const Layout& L, int nf, bool with_keystream) {
+  size_t b = 2 * round256((size_t)nf * L.Npad) + 2 * round256((size_t)nf * L.NT);
+  if (with_keystream)
+    b += round256((size_t)nf * L.rounds * L.Npad) + round256((size_t)nf * L.H * sizeof(int)) +
+         round256((size_t)nf * sizeof(long long));
+  return b;
+}
+
+int ensure_ring(vc_ctx* c, int cap) {
+  if (c->ring_cap >= cap) return VC_OK;
+  if (c->ring_cap > 0 && c->produced != c->frame) {
+    set_err("cannot grow a keystream ring that holds frames");
+    return VC_ERR_SEQUENCE;
+  }
+  sync_all(c);
+  cudaFree(c->ring_ks);
+  cudaFree(c->ring_sc);
+  cudaFree(c->ring_kmod);
+  c->ring_ks = nullptr;
+  c->ring_sc = nullptr;
+  c->ring_kmod = nullptr;
+  c->ring_cap = 0;
+  const Layout& L = c->L;
+  if (cudaMalloc(&c->ring_ks, (size_t)cap * L.rounds * L.Npad) != cudaSuccess ||
+      cudaMalloc(&c->ring_sc, (size_t)cap * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&c->ring_kmod, (size_t)cap * L.H * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("keystream ring allocation failed");
+    return VC_ERR_OOM;
+  }
+  c->ring_cap = cap;
+  return VC_OK;
+}
+
+// Non-blocking: advance produced_done over the completed productions.
+int poll_production(vc_ctx* c) {
+  for (int64_t k = c->nprod - vc_ctx::kProdEv; k < c->nprod; k++) {
+    if (k < 0) continue;
+    const int i = (int)(k % vc_ctx::kProdEv);
+    if (c->prod_upto[i] <= c->produced_done) continue;
+    const cudaError_t e = cudaEventQuery(c->ev_prod[i]);
+    if (e == cudaErrorNotReady) break;  // later ones are not done either
+    if (e != cudaSuccess) {
+      set_err("cudaEventQuery: %s", cudaGetErrorString(e));
+      return VC_ERR_CUDA;
+    }
+    c->produced_done = c->prod_upto[i];
+  }
+  return VC_OK;
+}
+
+bool production_busy(vc_ctx* c) {
+  if (c->nprod == 0) return false;
+  return cudaEventQuery(c->ev_prod[(c->nprod - 1) % vc_ctx::kProdEv]) == cudaErrorNotReady;
+}
+
+// Produce frames [produced, target) of the stream's keystream into its ring on
+// its own internal stream, after the batch that last read the ring's slots.
+int produce(vc_ctx* c, int64_t target) {
+  if (c->produced >= target) return VC_OK;
+  cudaStream_t ks = c->ks_stream;
+  if (c->produced == c->frame && c->last && !c->batch_pending) {  // single-stream work on this context first
+    VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
+    VC_CUDA(cudaStreamWaitEvent(ks, c->ev_entry, 0));
+  }
+  VC_CUDA(cudaStreamWaitEvent(ks, c->ev_batch, 0));
+  // at most kProdEv productions in flight (their events are tracked); the
+  // oldest is normally long done, this only blocks if it is not
+  if (c->nprod >= vc_ctx::kProdEv) {
+    const int i = (int)(c->nprod % vc_ctx::kProdEv);
+    if (c->prod_upto[i] > c->produced_done) {
+      VC_CUDA(cudaEventSynchronize(c->ev_prod[i]));
+      c->produced_done = c->prod_upto[i];
+    }
+  }
+  const int nf = (int)(target - c->produced);
+  const int slot0 = (int)(c->produced % c->ring_cap);
+  VC_CUDA(vc::launch_frame_schedule(c->L, c->d_main, nf, c->ring_sc, c->ring_kmod, ks, c->ring_cap, slot0));
+  VC_CUDA(vc::launch_keystream(c->kind, c->L, c->tables(), c->chains(), nf, c->ring_ks, c->plcm_int, ks, c->ring_cap,
+                               slot0));
+  const int i = (int)(c->nprod % vc_ctx::kProdEv);
+  VC_CUDA(cudaEventRecord(c->ev_prod[i], ks));
+  c->prod_upto[i] = target;
+  c->nprod++;
+  c->produced = target;
+  return VC_OK;
+}
+
+vc::JobDesc base_desc(vc_ctx* c) {
+  vc::JobDesc d{};
+  d.L = c->L;
+  d.tb = c->tables();
+  d.ch = c->chains();
+  d.main = c->d_main;
+  d.kind = c->kind;
+  return d;
+}
+
+// Stage `nj` descriptors (already in l.h_jobs[l.cur]) and launch them on st:
+// a captured graph per shape, or plain launches.
+int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int kmods, int rounds, size_t smem,
+                cudaStream_t st) {
+  vc::JobDesc* hj = l.h_jobs[l.cur];
+  vc::BatchHdr* hh = l.h_hdr[l.cur];
+  hh->njobs = nj;
+  hh->total_warps = warps;
+  hh->total_tiles = tiles;
+  hh->total_kmod = kmods;
+  vc::BatchShape sh;
+  sh.jobs_cap = bucket(nj, 64);
+  if (sh.jobs_cap > l.jobs_cap) sh.jobs_cap = l.jobs_cap;
+  sh.warps_cap = bucket(warps, 64);
+  sh.kmod_cap = bucket(kmods, 1024);
+  sh.rounds = rounds;
+  sh.smem = (smem + 16383) & ~(size_t)16383;
+  sh.grid = 1;
+  if (rounds > 0) {
+    VC_CUDA(vc::prepare_batch_kernels(sh.smem));
+    int ctas = 0;
+    VC_CUDA(vc::batch_ctas_per_sm(sh.smem, &ctas));
+    if (ctas < 1) {
+      set_err("round kernel does not fit with %zu bytes of shared memory", sh.smem);
+      return VC_ERR_UNSUPPORTED;
+    }
+    if (b->ctas_per_sm > 0 && b->ctas_per_sm < ctas) ctas = b->ctas_per_sm;
+    sh.grid = b->sms * ctas;
+  }
+  const size_t jobs_bytes = sizeof(vc::JobDesc) * (size_t)sh.jobs_cap;
+  if (b->use_graph) {
+    const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, l.cur);
+    auto it = l.graphs.find(key);
+    if (it == l.graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      VC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaMemcpyAsync(l.d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, b->cap_stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(l.d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, b->cap_stream);
+      if (e == cudaSuccess) e = vc::launch_batch(l.d_jobs, l.d_hdr, sh, b->cap_stream);
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        set_err("batch graph capture failed: %s", cudaGetErrorString(e));
+        return VC_ERR_CUDA;
+      }
+      it = l.graphs.emplace(key, ge).first;
+    }
+    VC_CUDA(cudaGraphLaunch(it->second, st));
+  } else {
+    VC_CUDA(cudaMemcpyAsync(l.d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(l.d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, st));
+    VC_CUDA(vc::launch_batch(l.d_jobs, l.d_hdr, sh, st));
+  }
+  VC_CUDA(cudaEventRecord(l.staged[l.cur], st));
+  l.cur ^= 1;
+  return VC_OK;
 }
 
 }  // namespace
@@ -993,13 +1226,9 @@ int vc_batcher_create(vc_batcher** out) {
   if (!b) return VC_ERR_OOM;
   cudaGetDevice(&b->dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
-  bool ok = cudaMalloc(&b->d_hdr, sizeof(vc::BatchHdr)) == cudaSuccess &&
-            cudaMallocHost(&b->h_hdr[0], sizeof(vc::BatchHdr)) == cudaSuccess &&
-            cudaMallocHost(&b->h_hdr[1], sizeof(vc::BatchHdr)) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->staged[0], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->staged[1], cudaEventDisableTiming) == cudaSuccess &&
+  bool ok = init_lane(b->cons) == VC_OK && grow_lane(b->cons, 64) == VC_OK &&
             cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
-  if (!ok || grow_jobs(b, 64) != VC_OK) {
+  if (!ok) {
     cudaGetLastError();
     vc_batcher_destroy(b);
     set_err("batcher creation failed");
@@ -1019,7 +1248,11 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
     case VC_BOPT_CTAS_PER_SM:
       if (value < 0 || value > 32) return VC_ERR_ARG;
       b->ctas_per_sm = (int)value;
-      drop_graphs(b);
+      drop_graphs(b->cons);
+      return VC_OK;
+    case VC_BOPT_RUNAHEAD:
+      if (value < 0 || value > 64) return VC_ERR_ARG;
+      b->runahead = (int)value;
       return VC_OK;
   }
   return VC_ERR_ARG;
@@ -1031,6 +1264,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     return VC_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const int A = b->runahead;
   // validate and lay out the jobs
   std::vector<int> live;
   live.reserve(njobs);
@@ -1052,12 +1286,20 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       set_err("job %d: in-place with one round is not supported in a batch", j);
       return VC_ERR_ARG;
     }
+    if (A > 0 && J.nframes > A) {
+      set_err("job %d asks for %d frames, more than the %d frames of keystream run-ahead", j, J.nframes, A);
+      return VC_ERR_ARG;
+    }
+    if (A == 0 && J.ctx->produced != J.ctx->frame) {
+      set_err("job %d: its stream holds keystream produced ahead; keep run-ahead on", j);
+      return VC_ERR_SEQUENCE;
+    }
     live.push_back(j);
-    pool_need += job_scratch_bytes(J.ctx->L, J.nframes);
+    pool_need += job_scratch_bytes(J.ctx->L, J.nframes, A == 0);
   }
   const int nj = (int)live.size();
   if (nj == 0) return VC_OK;
-  int rc = grow_jobs(b, nj);
+  int rc = grow_lane(b->cons, nj);
   if (rc) return rc;
   if (pool_need > b->pool_cap) {
     cudaDeviceSynchronize();
@@ -1072,10 +1314,33 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     }
     b->pool_cap = cap;
   }
-  // staging buffer `cur` must have been consumed by its previous batch
-  VC_CUDA(cudaEventSynchronize(b->staged[b->cur]));
-  vc::JobDesc* hj = b->h_jobs[b->cur];
-  vc::BatchHdr* hh = b->h_hdr[b->cur];
+  for (int k = 0; k < nj; k++) {
+    const vc_job& J = jobs[live[k]];
+    vc_ctx* c = J.ctx;
+    // the batch runs after what the context's single-stream calls enqueued on other streams
+    if (c->last && c->last != st && !c->batch_pending) {
+      VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
+      VC_CUDA(cudaStreamWaitEvent(st, c->ev_entry, 0));
+    }
+    if (A > 0) {
+      // frames not produced yet are produced now (with the look-ahead); the
+      // batch waits only if its frames are not known to be complete
+      rc = ensure_ring(c, 2 * A + 1);
+      if (rc) return rc;
+      if (c->produced < c->frame + J.nframes) {
+        rc = produce(c, c->frame + J.nframes + A);
+        if (rc) return rc;
+      }
+      rc = poll_production(c);
+      if (rc) return rc;
+      if (c->produced_done < c->frame + J.nframes)
+        VC_CUDA(cudaStreamWaitEvent(st, c->ev_prod[(c->nprod - 1) % vc_ctx::kProdEv], 0));
+    }
+  }
+
+  // ---- the batch: the rounds of every job (and the keystream when inline) ----
+  VC_CUDA(cudaEventSynchronize(b->cons.staged[b->cons.cur]));
+  vc::JobDesc* hj = b->cons.h_jobs[b->cons.cur];
   uint8_t* p = b->d_pool;
   int warps = 0, tiles = 0, kmods = 0, rounds = 0;
   size_t smem = 4096;  // the fix-up needs one byte per tile
@@ -1084,26 +1349,31 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     vc_ctx* c = J.ctx;
     const Layout& L = c->L;
     const int nf = J.nframes;
-    vc::JobDesc d{};
-    d.L = L;
-    d.tb = c->tables();
-    d.ch = c->chains();
-    d.main = c->d_main;
-    d.kind = c->kind;
+    vc::JobDesc d = base_desc(c);
     d.dir = J.direction;
     d.nframes = nf;
     d.in = J.d_in;
     d.out = J.d_out;
-    d.ks = p;
-    p += round256((size_t)nf * L.rounds * L.Npad);
+    if (A > 0) {
+      d.mode = 1;
+      d.ks = c->ring_ks;
+      d.sc = c->ring_sc;
+      d.kmod = c->ring_kmod;
+      d.ring_cap = c->ring_cap;
+      d.ring_slot0 = (int)(c->frame % c->ring_cap);
+    } else {
+      d.mode = 0;
+      d.ks = p;
+      p += round256((size_t)nf * L.rounds * L.Npad);
+      d.kmod = reinterpret_cast<int*>(p);
+      p += round256((size_t)nf * L.H * sizeof(int));
+      d.sc = reinterpret_cast<long long*>(p);
+      p += round256((size_t)nf * sizeof(long long));
+    }
     d.buf[0] = p;
     p += round256((size_t)nf * L.Npad);
     d.buf[1] = p;
     p += round256((size_t)nf * L.Npad);
-    d.kmod = reinterpret_cast<int*>(p);
-    p += round256((size_t)nf * L.H * sizeof(int));
-    d.sc = reinterpret_cast<long long*>(p);
-    p += round256((size_t)nf * sizeof(long long));
     d.agg[0] = p;
     p += round256((size_t)nf * L.NT);
     d.agg[1] = p;
@@ -1111,92 +1381,86 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     d.warp_base = warps;
     d.tile_base = tiles;
     d.kmod_base = kmods;
-    warps += (L.n + 15) / 16;
+    if (d.mode == 0) {
+      warps += (L.n + 15) / 16;
+      kmods += nf * L.H;
+    }
     tiles += nf * L.NT;
-    kmods += nf * L.H;
     if (L.rounds > rounds) rounds = L.rounds;
     const size_t sm = vc::round_smem_bytes(L);
     if (sm > smem) smem = sm;
     hj[k] = d;
-    // the batch runs after what the context's own calls enqueued on other streams
-    if (c->last && c->last != st) {
-      VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
-      VC_CUDA(cudaStreamWaitEvent(st, c->ev_entry, 0));
-    }
   }
-  hh->njobs = nj;
-  hh->total_warps = warps;
-  hh->total_tiles = tiles;
-  hh->total_kmod = kmods;
-
-  vc::BatchShape sh;
-  sh.jobs_cap = bucket(nj, 64);
-  if (sh.jobs_cap > b->jobs_cap) sh.jobs_cap = b->jobs_cap;
-  sh.warps_cap = bucket(warps, 64);
-  sh.kmod_cap = bucket(kmods, 1024);
-  sh.rounds = rounds;
-  sh.smem = (smem + 16383) & ~(size_t)16383;
-  VC_CUDA(vc::prepare_batch_kernels(sh.smem));
-  int ctas = 0;
-  VC_CUDA(vc::batch_ctas_per_sm(sh.smem, &ctas));
-  if (ctas < 1) {
-    set_err("round kernel does not fit with %zu bytes of shared memory", sh.smem);
-    return VC_ERR_UNSUPPORTED;
-  }
-  if (b->ctas_per_sm > 0 && b->ctas_per_sm < ctas) ctas = b->ctas_per_sm;
-  sh.grid = b->sms * ctas;
-
-  const size_t jobs_bytes = sizeof(vc::JobDesc) * (size_t)sh.jobs_cap;
-  if (b->use_graph) {
-    const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, b->cur);
-    auto it = b->graphs.find(key);
-    if (it == b->graphs.end()) {
-      cudaGraph_t g = nullptr;
-      cudaGraphExec_t ge = nullptr;
-      VC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaMemcpyAsync(b->d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, b->cap_stream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, b->cap_stream);
-      if (e == cudaSuccess) e = vc::launch_batch(b->d_jobs, b->d_hdr, sh, b->cap_stream);
-      const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
-      if (e == cudaSuccess) e = e2;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-      if (g) cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        set_err("batch graph capture failed: %s", cudaGetErrorString(e));
-        return VC_ERR_CUDA;
-      }
-      it = b->graphs.emplace(key, ge).first;
-    }
-    VC_CUDA(cudaGraphLaunch(it->second, st));
-  } else {
-    VC_CUDA(cudaMemcpyAsync(b->d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, st));
-    VC_CUDA(cudaMemcpyAsync(b->d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, st));
-    VC_CUDA(vc::launch_batch(b->d_jobs, b->d_hdr, sh, st));
-  }
-  VC_CUDA(cudaEventRecord(b->staged[b->cur], st));
-  b->cur ^= 1;
+  rc = launch_lane(b, b->cons, nj, warps, tiles, kmods, rounds, smem, st);
+  if (rc) return rc;
   for (int k = 0; k < nj; k++) {
-    vc_ctx* c = jobs[live[k]].ctx;
-    c->frame += jobs[live[k]].nframes;
+    const vc_job& J = jobs[live[k]];
+    vc_ctx* c = J.ctx;
+    c->frame += J.nframes;
+    if (A == 0) {
+      c->produced = c->frame;
+      c->produced_done = c->frame;
+    }
     c->last = st;
     VC_CUDA(cudaEventRecord(c->ev_batch, st));
     c->batch_pending = true;
   }
+  // ---- top-ups: each stream's keystream back to A frames ahead, on its own
+  // internal stream, coalesced (not while its previous production runs) ----
+  if (A > 0) {
+    for (int k = 0; k < nj; k++) {
+      vc_ctx* c = jobs[live[k]].ctx;
+      if (c->produced >= c->frame + A || production_busy(c)) continue;
+      rc = produce(c, c->frame + A);
+      if (rc) return rc;
+    }
+  }
   return VC_OK;
+}
+
+int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
+  if (!b || n < 0 || (n > 0 && !ctxs)) return VC_ERR_ARG;
+  const int A = b->runahead;
+  if (A <= 0) {
+    set_err("prefetch needs run-ahead (VC_BOPT_RUNAHEAD > 0)");
+    return VC_ERR_ARG;
+  }
+  std::unordered_set<const vc_ctx*> seen;
+  for (int k = 0; k < n; k++) {
+    vc_ctx* c = ctxs[k];
+    if (!c || !seen.insert(c).second) {
+      set_err("prefetch: null or repeated context");
+      return VC_ERR_ARG;
+    }
+    int rc = ensure_ring(c, 2 * A + 1);
+    if (rc) return rc;
+    // the next frame on its own (ready soonest), then the rest of the run-ahead
+    if (c->produced < c->frame + 1) {
+      rc = produce(c, c->frame + 1);
+      if (rc) return rc;
+    }
+    if (c->produced < c->frame + A && !production_busy(c)) {  // coalesced, like the top-ups
+      rc = produce(c, c->frame + A);
+      if (rc) return rc;
+    }
+  }
+  return VC_OK;
+}
+
+int vc_batch_ready(vc_batcher* b, const vc_ctx* c, int32_t nframes) {
+  if (!b || !c || nframes < 0) return -VC_ERR_ARG;
+  if (nframes == 0) return 1;
+  vc_ctx* cc = const_cast<vc_ctx*>(c);
+  const int rc = poll_production(cc);
+  if (rc) return -rc;
+  return cc->produced_done >= cc->frame + nframes ? 1 : 0;
 }
 
 void vc_batcher_destroy(vc_batcher* b) {
   if (!b) return;
   cudaDeviceSynchronize();
-  drop_graphs(b);
-  cudaFree(b->d_jobs);
-  cudaFree(b->d_hdr);
+  free_lane(b->cons);
   cudaFree(b->d_pool);
-  for (int i = 0; i < 2; i++) {
-    cudaFreeHost(b->h_jobs[i]);
-    cudaFreeHost(b->h_hdr[i]);
-    if (b->staged[i]) cudaEventDestroy(b->staged[i]);
-  }
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
 }

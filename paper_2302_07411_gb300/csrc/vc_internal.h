@@ -62,7 +62,10 @@ struct JobDesc {
   int* kmod;
   uint8_t* buf[2];
   uint8_t* agg[2];
-  int warp_base, tile_base, kmod_base, pad1;
+  int warp_base, tile_base, kmod_base;
+  int mode;                 // 0: keystream + rounds; 1: rounds on keystream already in the ring; 2: keystream only
+  int ring_cap, ring_slot0; // ks / sc / kmod frame slots: ring of ring_cap (0 = frames laid end to end)
+  int pad1, pad2;
 };
 
 struct BatchHdr {
@@ -70,7 +73,8 @@ struct BatchHdr {
 };
 
 // Launch geometry of a batch: capacities (work beyond the header's totals
-// exits at once, so one captured graph serves every batch within them).
+// exits at once, so one captured graph serves every batch within them);
+// rounds = 0 launches the keystream phases only.
 struct BatchShape {
   int jobs_cap, warps_cap, kmod_cap, rounds, grid;
   size_t smem;
@@ -79,10 +83,11 @@ struct BatchShape {
 // Launchers (vc_kernels.cu).  All enqueue on `st` and return the launch error.
 cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* srank, int* fixlim, cudaStream_t st);
 cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cudaStream_t st);
+// cap > 0: frame f's s_c / shift table / keystream go to slot (slot0 + f) mod cap of a ring.
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int cap = 0, int slot0 = 0);
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st);
+                             bool plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0);
 cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                                     bool plcm_int, cudaStream_t st);
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,

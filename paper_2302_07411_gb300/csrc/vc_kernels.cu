@@ -150,15 +150,15 @@ cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cuda
 }
 
 // s_c of the next nframes frames (Alg. 1), serially from PRBG_m.
-__device__ void frame_sc_serial(MainPrbg* mp, int nframes, long long* sc) {
+__device__ void frame_sc_serial(MainPrbg* mp, int nframes, long long* sc, int cap = 0, int slot0 = 0) {
   MainPrbg m = *mp;
-  for (int f = 0; f < nframes; f++) sc[f] = 1 + (long long)(main_next_group(m) & 0xFFFFull);
+  for (int f = 0; f < nframes; f++) sc[cap > 0 ? (slot0 + f) % cap : f] = 1 + (long long)(main_next_group(m) & 0xFFFFull);
   *mp = m;
 }
 
-__global__ void k_frame_sc(MainPrbg* mp, int nframes, long long* sc) {
+__global__ void k_frame_sc(MainPrbg* mp, int nframes, long long* sc, int cap, int slot0) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  frame_sc_serial(mp, nframes, sc);
+  frame_sc_serial(mp, nframes, sc, cap, slot0);
 }
 
 // floor(s_c * csin((2 pi alpha) / H)) mod W, in [0, W).
@@ -171,20 +171,21 @@ __device__ __forceinline__ int kmod_of(const Layout& L, long long sc, int a) {
 }
 
 // kmod[f][alpha] for the pass's frames (Eq. 1 shift table).
-__global__ void k_kmod(Layout L, const long long* sc, int nframes, int* kmod) {
+__global__ void k_kmod(Layout L, const long long* sc, int nframes, int* kmod, int cap, int slot0) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nframes * L.H) return;
   const int f = (int)(idx / L.H);
   const int a = (int)(idx - (long long)f * L.H);
-  kmod[idx] = kmod_of(L, sc[f], a);
+  const int slot = cap > 0 ? (slot0 + f) % cap : f;
+  kmod[(long long)slot * L.H + a] = kmod_of(L, sc[slot], a);
 }
 
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int cap, int slot0) {
   if (nframes <= 0) return cudaSuccess;
-  k_frame_sc<<<1, 32, 0, st>>>(main, nframes, sc);
+  k_frame_sc<<<1, 32, 0, st>>>(main, nframes, sc, cap, slot0);
   const long long tot = (long long)nframes * L.H;
-  k_kmod<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, sc, nframes, kmod);
+  k_kmod<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, sc, nframes, kmod, cap, slot0);
   return cudaGetLastError();
 }
 
@@ -473,9 +474,16 @@ struct PairWriter {
   }
 };
 
+// Keystream base of frame f of a call: frames laid end to end (cap = 0), or a
+// ring of cap frame slots starting at slot0 (the batches' run-ahead rings).
+__device__ __forceinline__ uint8_t* ks_frame(uint8_t* ks, const Layout& L, int f, int cap, int slot0) {
+  const int slot = cap > 0 ? (slot0 + f) % cap : f;
+  return ks + (long long)slot * L.rounds * L.Npad;
+}
+
 template <int KIND, bool FX>
 __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
-                                              uint8_t* ks, const int i, const int side) {
+                                              uint8_t* ks, const int i, const int side, int cap = 0, int slot0 = 0) {
   if (i >= L.n) return;  // both lanes of a pair leave together
   const unsigned pmask = 3u << (threadIdx.x & 30);
   constexpr int STEP = KIND == 0 ? 6 : 12;
@@ -526,7 +534,7 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
   };
 
   for (int f = 0; f < nframes; f++) {
-    w.fb = ks + (long long)f * L.rounds * L.Npad;
+    w.fb = ks_frame(ks, L, f, cap, slot0);
     w.j = 0;
     w.q = w.qs;
     w.acc = 0;
@@ -591,9 +599,10 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
 }
 
 template <int KIND, bool FX>
-__global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+__global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
+                                                int slot0) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  ks_pair_chain<KIND, FX>(L, tb, ch, nframes, ks, gt >> 1, gt & 1);
+  ks_pair_chain<KIND, FX>(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
 }
 
 // PLCM keystream on the integer pipes, lane-pair form with the writes of a
@@ -604,7 +613,8 @@ __global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, 
 // fixed-point range is checked once per group: the rare group that needs it
 // is recomputed step by step with the hardware division.
 __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
-                                                 uint8_t* ks, const int i, const int side) {
+                                                 uint8_t* ks, const int i, const int side, int cap = 0,
+                                                 int slot0 = 0) {
   if (i >= L.n) return;
   const unsigned pmask = 3u << (threadIdx.x & 30);
   constexpr uint64_t M48 = 0xFFFFFFFFFFFFull;
@@ -648,7 +658,7 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
   };
 
   for (int f = 0; f < nframes; f++) {
-    w.fb = ks + (long long)f * L.rounds * L.Npad;
+    w.fb = ks_frame(ks, L, f, cap, slot0);
     w.j = 0;
     w.q = w.qs;
     w.acc = 0;
@@ -724,21 +734,22 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
   }
 }
 
-__global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
+__global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
+                                                   int slot0) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1);
+  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
 }
 
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st) {
+                             bool plcm_int, cudaStream_t st, int cap, int slot0) {
   if (nframes <= 0) return cudaSuccess;
   const int blocks = (2 * L.n + 31) / 32;
   if (kind == 0 && plcm_int)
-    k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+    k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   else if (kind == 0)
-    k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+    k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   else
-    k_ks_pair<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+    k_ks_pair<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   return cudaGetLastError();
 }
 
@@ -1311,9 +1322,16 @@ __device__ __forceinline__ int find_job(const JobDesc* J, int nj, int x, Key key
   return lo;
 }
 
+// Jobs of mode 1 only consume keystream produced earlier into their ring;
+// the host gives them no keystream or shift-table work (zero-length ranges).
 __global__ void k_batch_sc(const JobDesc* J, const BatchHdr* hdr) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < hdr->njobs && J[j].nframes > 0) frame_sc_serial(J[j].main, J[j].nframes, J[j].sc);
+  if (j < hdr->njobs && J[j].nframes > 0 && J[j].mode != 1)
+    frame_sc_serial(J[j].main, J[j].nframes, J[j].sc, J[j].ring_cap, J[j].ring_slot0);
+}
+
+__device__ __forceinline__ int job_slot(const JobDesc& d, int f) {
+  return d.ring_cap > 0 ? (d.ring_slot0 + f) % d.ring_cap : f;
 }
 
 __global__ void k_batch_kmod(const JobDesc* J, const BatchHdr* hdr) {
@@ -1324,7 +1342,8 @@ __global__ void k_batch_kmod(const JobDesc* J, const BatchHdr* hdr) {
   const int local = idx - d.kmod_base;
   const int f = local / d.L.H;
   const int a = local - f * d.L.H;
-  d.kmod[local] = kmod_of(d.L, d.sc[f], a);
+  const int slot = job_slot(d, f);
+  d.kmod[(long long)slot * d.L.H + a] = kmod_of(d.L, d.sc[slot], a);
 }
 
 __global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHdr* hdr) {
@@ -1335,30 +1354,31 @@ __global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHd
   const int i = (w - d.warp_base) * 16 + (threadIdx.x >> 1);
   const int side = threadIdx.x & 1;
   if (d.kind == 0)
-    ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side);
+    ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
   else
-    ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side);
+    ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
 }
 
-// Round `step` of every job that has one (job rounds may differ): encryption
-// applies round `step`, decryption round r - 1 - step; the buffers alternate
-// as in a single-stream pass.
-__device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step) {
+// Round `step` of frame f of a job (job rounds may differ): encryption applies
+// round `step`, decryption round r - 1 - step; the buffers alternate as in a
+// single-stream pass.  Every pointer is offset to frame f.
+__device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step, int f) {
   const Layout& L = d.L;
   const int r = L.rounds;
   const int jr = d.dir == 0 ? step : r - 1 - step;
+  const int slot = job_slot(d, f);
   RoundArgs A;
   A.L = L;
   A.tb = d.tb;
-  A.in = step == 0 ? d.in : d.buf[(step - 1) & 1];
   A.in_stride = step == 0 ? (long long)L.N : L.Npad;
-  A.out = step == r - 1 ? d.out : d.buf[step & 1];
+  A.in = (step == 0 ? d.in : d.buf[(step - 1) & 1]) + f * A.in_stride;
   A.out_stride = step == r - 1 ? (long long)L.N : L.Npad;
-  A.ks = d.ks + (long long)jr * L.Npad;
-  A.ks_stride = (long long)r * L.Npad;
-  A.kmod = d.kmod;
-  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] : nullptr;
-  A.agg_out = d.dir == 0 ? d.agg[step & 1] : nullptr;
+  A.out = (step == r - 1 ? d.out : d.buf[step & 1]) + f * A.out_stride;
+  A.ks = d.ks + (long long)slot * r * L.Npad + (long long)jr * L.Npad;
+  A.ks_stride = 0;
+  A.kmod = d.kmod + (long long)slot * L.H;
+  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] + (long long)f * L.NT : nullptr;
+  A.agg_out = d.dir == 0 ? d.agg[step & 1] + (long long)f * L.NT : nullptr;
   return A;
 }
 
@@ -1372,18 +1392,18 @@ __global__ void __launch_bounds__(kRoundThreads) k_batch_round(const JobDesc* J,
       const int local = item - d.tile_base;
       const int f = local / d.L.NT;
       const int t = local - f * d.L.NT;
-      const RoundArgs A = batch_round_args(d, step);
+      const RoundArgs A = batch_round_args(d, step, f);
       if (d.dir == 0) {
         switch (d.L.C) {
-          case 1: enc_round_tile<1>(A, f, t, smem); break;
-          case 3: enc_round_tile<3>(A, f, t, smem); break;
-          default: enc_round_tile<4>(A, f, t, smem); break;
+          case 1: enc_round_tile<1>(A, 0, t, smem); break;
+          case 3: enc_round_tile<3>(A, 0, t, smem); break;
+          default: enc_round_tile<4>(A, 0, t, smem); break;
         }
       } else {
         switch (d.L.C) {
-          case 1: dec_round_tile<1>(A, f, t, smem); break;
-          case 3: dec_round_tile<3>(A, f, t, smem); break;
-          default: dec_round_tile<4>(A, f, t, smem); break;
+          case 1: dec_round_tile<1>(A, 0, t, smem); break;
+          case 3: dec_round_tile<3>(A, 0, t, smem); break;
+          default: dec_round_tile<4>(A, 0, t, smem); break;
         }
       }
     }
@@ -1422,8 +1442,11 @@ cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchSh
   k_batch_sc<<<(sh.jobs_cap + 31) / 32, 32, 0, st>>>(jobs, hdr);
   k_batch_kmod<<<(sh.kmod_cap + 255) / 256, 256, 0, st>>>(jobs, hdr);
   k_batch_ks<<<sh.warps_cap, 32, 0, st>>>(jobs, hdr);
-  for (int step = 0; step < sh.rounds; step++) k_batch_round<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
-  k_batch_fixup<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr);
+  if (sh.rounds > 0) {
+    for (int step = 0; step < sh.rounds; step++)
+      k_batch_round<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+    k_batch_fixup<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr);
+  }
   return cudaGetLastError();
 }
 

@@ -46,6 +46,8 @@ class Stream:
 class ServeResult:
     mode: str
     latencies_ms: list = field(default_factory=list)
+    arrivals_s: list = field(default_factory=list)   # frame arrival time of each latency sample
+    first_frame_ms: list = field(default_factory=list)  # per stream: latency of its first frame
     frames: int = 0
     admitted: int = 0
     rejected: int = 0
@@ -53,12 +55,23 @@ class ServeResult:
     wall_s: float = 0.0
     ticks: int = 0
 
-    def summary(self) -> dict:
+    def summary(self, steady_after_s: float | None = None) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
-                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
-                "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
+        out = {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
+               "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+               "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
+               "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
+        if self.first_frame_ms:
+            out["first_frame_p99_ms"] = round(float(np.percentile(self.first_frame_ms, 99)), 3)
+        if steady_after_s is not None:
+            arr = np.array(self.arrivals_s)
+            sel = lat[arr >= steady_after_s] if len(arr) == len(lat) else lat
+            if sel.size:
+                out["steady_after_s"] = steady_after_s
+                out["steady_frames"] = int(sel.size)
+                out["steady_p50_ms"] = round(float(np.percentile(sel, 50)), 3)
+                out["steady_p99_ms"] = round(float(np.percentile(sel, 99)), 3)
+        return out
 
 
 class Server:
@@ -75,10 +88,22 @@ class Server:
         self.maxf = max_frames_per_tick
         self.ring = ring
         self.stream = torch.cuda.Stream()
-        self.batcher = B.Batcher() if mode == "batch" else None
+        # keystream run-ahead: every stream's next max_frames_per_tick frames of
+        # keystream are produced before the frames arrive
+        self.batcher = B.Batcher(runahead=max_frames_per_tick) if mode == "batch" else None
         self.inputs = {}  # (H, W, C) -> device frames reused as input content
+        from concurrent.futures import ThreadPoolExecutor
+
+        self.pool = ThreadPoolExecutor(max_workers=2)
         self.keep = keep_outputs
         self.finished: list[Stream] = []  # kept when keep_outputs (tests)
+
+    def _open(self, spec: dict, fp: int) -> Stream:
+        torch = self.torch
+        H, W, C = spec["H"], spec["W"], spec["C"]
+        ciph = B.Cipher(spec["kind"], spec["key"], H, W, C, subframes_for(H), 5)
+        out = torch.empty((self.ring, H, W, C), dtype=torch.uint8, device="cuda")
+        return Stream(spec, ciph, out, fp, frames_total=max(1, int(spec["duration"] * spec["fps"])))
 
     def input_frames(self, H, W, C):
         """Input content: frame k of a stream of this size is input_frames[k % maxf]
@@ -104,6 +129,7 @@ class Server:
         torch = self.torch
         res = ServeResult(self.mode)
         pending = deque(sorted(requests, key=lambda r: r["arrival"]))
+        starting = deque()  # futures of streams whose context is being created
         active: list[Stream] = []
         used = 0
         inflight = deque()  # (event, [(stream, frame index, arrival time)])
@@ -122,6 +148,9 @@ class Server:
                 done_t = t0_ev.elapsed_time(ev) / 1e3  # device time since t0
                 for st, k, arr in frames:
                     res.latencies_ms.append((done_t - arr) * 1e3)
+                    res.arrivals_s.append(arr)
+                    if k == 0:
+                        res.first_frame_ms.append((done_t - arr) * 1e3)
                     st.done += 1
                     res.frames += 1
 
@@ -134,22 +163,33 @@ class Server:
                 if used + fp > self.budget:
                     res.rejected += 1
                     continue
-                H, W, C = spec["H"], spec["W"], spec["C"]
-                ciph = B.Cipher(spec["kind"], spec["key"], H, W, C, subframes_for(H), 5)
-                out = torch.empty((self.ring, H, W, C), dtype=torch.uint8, device="cuda")
-                st = Stream(spec, ciph, out, fp, frames_total=max(1, int(spec["duration"] * spec["fps"])))
-                active.append(st)
                 used += fp
                 res.admitted += 1
+                # context creation (key schedule on the GPU) off the loop's thread
+                starting.append(self.pool.submit(self._open, spec, fp))
+            newly = []
+            while starting and starting[0].done():
+                newly.append(starting.popleft().result())
+            if newly and self.batcher is not None:
+                self.batcher.prefetch([st.cipher for st in newly])  # keystream of their first frames
+            active.extend(newly)
             res.peak_streams = max(res.peak_streams, len(active))
             # gather the frames that have arrived
-            jobs, meta = [], []
+            jobs, meta, starved = [], [], []
             for st in active:
                 fps = st.spec["fps"]
                 arrived = min(st.frames_total, int((now - st.spec["arrival"]) * fps) + 1)
                 m = min(arrived - st.next_frame, self.maxf, self.ring - (st.next_frame % self.ring))
                 if m <= 0:
                     continue
+                if self.batcher is not None:
+                    # only frames whose keystream is already on the device, so a
+                    # stream still being produced does not hold up the others
+                    while m > 0 and not self.batcher.ready(st.cipher, m):
+                        m -= 1
+                    if m == 0:
+                        starved.append(st)
+                        continue
                 k0 = st.next_frame % self.maxf
                 x = self.input_frames(st.spec["H"], st.spec["W"], st.spec["C"])[k0:k0 + m]
                 slot = st.next_frame % self.ring
@@ -157,6 +197,8 @@ class Server:
                 jobs.append((st, x, y, m))
                 meta.extend((st, st.next_frame + i, st.spec["arrival"] + (st.next_frame + i) / fps) for i in range(m))
                 st.next_frame += m
+            if starved:
+                self.batcher.prefetch([st.cipher for st in starved])  # no-op while their keystream is coming
             if jobs:
                 with torch.cuda.stream(self.stream):
                     if self.mode == "batch":
@@ -186,7 +228,7 @@ class Server:
                 else:
                     still.append(st)
             active = still
-            if not pending and not active and not inflight:
+            if not pending and not active and not inflight and not starting:
                 break
             if now > end_time + 5.0:  # safety: stop a run that cannot keep up
                 drain(block=True)
@@ -200,33 +242,40 @@ class Server:
         return res
 
     def close(self):
+        self.pool.shutdown(wait=True)
         if self.batcher is not None:
             self.batcher.close()
 
 
 def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0 / 24.0,
-             counts=(16, 32, 64, 128, 256, 512), seconds: float = 3.0, seed: int = 21,
-             hbm_budget_bytes: int = 200 << 30, tick_ms: float = 4.0) -> dict:
+             counts=(16, 32, 64, 128, 256, 512), seconds: float = 4.0, seed: int = 21,
+             hbm_budget_bytes: int = 200 << 30, tick_ms: float = 4.0, ramp_s: float = 0.5,
+             warm_s: float = 1.0) -> dict:
     """Largest number of concurrent fps streams of H x W x 3 (half encrypt,
-    half decrypt, alternating maps) whose per-frame p99 latency stays below
-    budget_ms.  All streams start within the first 0.25 s and last `seconds`."""
+    half decrypt, alternating maps) whose steady-state per-frame p99 latency
+    stays below budget_ms.  Streams arrive uniformly over ramp_s seconds and
+    last `seconds`; "steady" counts the frames arriving after ramp_s + warm_s.
+    Time to first frame is reported separately."""
     import synth
 
     best, runs = 0, []
+    steady_from = ramp_s + warm_s
     for n in counts:
-        reqs = synth.serving_workload(n, seed=seed, rate_per_s=n / 0.25, resolutions=((H, W),), fps_choices=(fps,),
-                                      duration_s=(seconds, seconds))
+        reqs = synth.serving_workload(n, seed=seed, rate_per_s=n / ramp_s, resolutions=((H, W),),
+                                      fps_choices=(fps,), duration_s=(seconds, seconds))
         srv = Server(hbm_budget_bytes=hbm_budget_bytes, tick_ms=tick_ms, mode=mode)
         res = srv.run(reqs)
         srv.close()
-        s = res.summary()
+        s = res.summary(steady_after_s=steady_from)
         s["streams"] = n
         runs.append(s)
-        if s["rejected"] == 0 and s["p99_ms"] < budget_ms:
+        p99 = s.get("steady_p99_ms", s["p99_ms"])
+        if s["rejected"] == 0 and p99 < budget_ms:
             best = n
         else:
             break
     return {"mode": mode, "resolution": f"{H}x{W}x3", "fps": fps, "p99_budget_ms": round(budget_ms, 2),
+            "criterion": f"p99 of frames arriving after {steady_from:g} s (admission ramp {ramp_s:g} s)",
             "max_streams": best, "runs": runs}
 
 
@@ -244,7 +293,7 @@ def main():
     ap.add_argument("--rate", type=float, default=64.0, help="stream arrivals per second (Poisson)")
     ap.add_argument("--capacity", action="store_true", help="search the 24 FPS stream capacity instead")
     ap.add_argument("--size", type=int, nargs=2, default=[768, 768])
-    ap.add_argument("--seconds", type=float, default=3.0)
+    ap.add_argument("--seconds", type=float, default=4.0)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     a = ap.parse_args()
     torch.cuda.set_device(0)
@@ -262,7 +311,7 @@ def main():
             srv = Server(hbm_budget_bytes=int(a.budget_gb * (1 << 30)), mode=mode)
             res = srv.run(reqs)
             srv.close()
-            out[mode] = res.summary()
+            out[mode] = res.summary(steady_after_s=1.5)
     print(json.dumps(out))
 
 

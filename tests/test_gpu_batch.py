@@ -34,16 +34,18 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_batch_equals_solo_runs(B, graph):
-    batcher = B.Batcher(graph=graph)
+@pytest.mark.parametrize("graph,runahead", [(True, 0), (False, 0), (True, 3), (False, 4)])
+def test_batch_equals_solo_runs(B, graph, runahead):
+    """runahead > 0: each submit also produces the streams' next keystream
+    frames into device rings on an internal stream; later batches consume them."""
+    batcher = B.Batcher(graph=graph, runahead=runahead)
     mixed, solo, data = [], [], []
     for s, (kind, H, W, C, n, r, direction, F) in enumerate(STREAMS):
         key = synth.key_for_seed(kind, 500 + s)
         mixed.append(B.Cipher(kind, key, H, W, C, n, r))
         solo.append(B.Cipher(kind, key, H, W, C, n, r))
         data.append(synth.uniform_frames(3 * F, H, W, C, seed=600 + s))
-    for tick in range(3):  # consecutive batches: graph replays, state carried
+    for tick in range(3):  # consecutive batches: graph replays, state carried, rings wrap
         jobs, outs, refs = [], [], []
         for s, (kind, H, W, C, n, r, direction, F) in enumerate(STREAMS):
             x = torch.from_numpy(data[s][tick * F:(tick + 1) * F]).cuda()
@@ -97,4 +99,44 @@ def test_batch_rejects_bad_jobs(B):
         batcher.submit([(c, 0, x, x.clone(), 1), (c, 0, x, x.clone(), 1)])  # same context twice
     with pytest.raises(B.VcError):
         batcher.submit([(c, 2, x, x.clone(), 1)])
+    batcher.close()
+
+
+def test_runahead_guards_single_stream_calls(B):
+    batcher = B.Batcher(runahead=2)
+    c = B.Cipher(0, synth.key_for_seed(0, 2), 16, 16, 3, 4)
+    x = torch.zeros((2, 16, 16, 3), dtype=torch.uint8, device="cuda")
+    batcher.submit([(c, 0, x, torch.empty_like(x), 2)])
+    batcher.prefetch([c])     # keystream of the next 2 frames produced ahead
+    with pytest.raises(B.VcError) as e:
+        c.encrypt(x)          # its keystream is already produced ahead by the batcher
+    assert e.value.code == 7  # VC_ERR_SEQUENCE
+    with pytest.raises(B.VcError):
+        batcher.submit([(c, 0, torch.zeros((3, 16, 16, 3), dtype=torch.uint8, device="cuda"),
+                         torch.empty((3, 16, 16, 3), dtype=torch.uint8, device="cuda"), 3)])  # more than run-ahead
+    batcher.close()
+
+
+def test_prefetch_and_ready(B, orc):
+    """prefetch produces a new stream's keystream ahead; ready() reports when a
+    batch would not wait; the ciphertext is the oracle's."""
+    import time
+
+    batcher = B.Batcher(runahead=3)
+    key = synth.key_for_seed(1, 3)
+    c = B.Cipher(1, key, 24, 40, 3, 6)
+    ref = orc.OracleCipher(1, key, 24, 40, 3, 6)
+    X = synth.uniform_frames(6, 24, 40, 3, seed=4)
+    batcher.prefetch([c])
+    t0 = time.time()
+    while not batcher.ready(c, 3):
+        assert time.time() - t0 < 30
+        time.sleep(0.001)
+    assert not batcher.ready(c, 4)  # beyond the run-ahead nothing is produced
+    d = torch.from_numpy(X).cuda()
+    out = torch.empty_like(d)
+    for k in range(2):
+        batcher.submit([(c, 0, d[3 * k:3 * k + 3], out[3 * k:3 * k + 3], 3)])
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref.encrypt(X))
     batcher.close()
