@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="frames per pass (0 = automatic)")
     ap.add_argument("--no-overlap", action="store_true", help="keystream and rounds on one stream")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per round-kernel tile (0 = automatic)")
+    ap.add_argument("--ks-sm-warps", type=int, default=-1,
+                    help="keystream CTAs of this many warps, each holding a whole SM (0 = share all SMs, -1 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -65,7 +67,7 @@ def config(a, world: int) -> dict:
             "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
             "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
             "keystream_overlap": not a.no_overlap, "frames_per_pass": a.chunk or "auto",
-            "tile_rows": a.tile_rows or "auto",
+            "tile_rows": a.tile_rows or "auto", "ks_sm_warps": a.ks_sm_warps if a.ks_sm_warps >= 0 else "auto",
             "l2": "inputs 425 MB > 129 MB L2, no flush"}
 
 
@@ -252,6 +254,7 @@ def run_ours(a) -> None:
     ciph.set_option(B.VC_OPT_TILE_ROWS, a.tile_rows)
     ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
     ciph.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
+    ciph.set_option(B.VC_OPT_KS_SM_WARPS, a.ks_sm_warps)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -303,6 +306,7 @@ def run_ours(a) -> None:
         ce.set_option(B.VC_OPT_TILE_ROWS, a.tile_rows)
         ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
         ce.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
+        ce.set_option(B.VC_OPT_KS_SM_WARPS, a.ks_sm_warps)
         for _ in range(max(1, a.warmup - 1)):
             ce.crypt_host(0, h_in, h_out, stream=stream)
         if world > 1:

@@ -174,8 +174,10 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
- * A frames now (e.g. right after a stream is admitted), on the batcher's
- * internal stream.  Errors: VC_ERR_ARG (run-ahead off, null or repeated
+ * A frames now (e.g. right after a stream is admitted), on the context's
+ * internal keystream stream: the next frame alone first, the rest queued
+ * behind it.  A call for a context whose production is still in flight adds
+ * nothing.  Errors: VC_ERR_ARG (run-ahead off, null or repeated
  * context), VC_ERR_OOM, VC_ERR_CUDA. */
 int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n);
 
@@ -223,12 +225,22 @@ int enc_sync_status(vc_ctx* ctx);
  *                  1..32 (capped by the 96 KB shared-memory tile budget);
  *                  0 (default) takes the largest that fits.  Reading it back
  *                  gives the rows in use.
+ * VC_OPT_KS_SM_WARPS: -1..8.  k > 0 runs the keystream of each pass in CTAs
+ *                  of k warps that each occupy a whole SM (they claim all of
+ *                  its shared memory), on an internal stream of the device's
+ *                  highest priority, so that the round kernels of the previous
+ *                  pass run on the other SMs instead of taking issue slots from
+ *                  the latency-bound chains; 0 lets both share every SM on a
+ *                  normal-priority stream; -1 (default) takes 4 warps (one per
+ *                  SM sub-partition) when overlapping and those CTAs fill at
+ *                  most half of the SMs, else 0.
  * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
 #define VC_OPT_KS_LANES 3
 #define VC_OPT_OVERLAP 4
 #define VC_OPT_TILE_ROWS 5
+#define VC_OPT_KS_SM_WARPS 6
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */

@@ -117,6 +117,11 @@ struct vc_ctx {
   uint8_t* d_buf[2] = {nullptr, nullptr};
   uint8_t* d_agg[2] = {nullptr, nullptr};
   bool overlap = true;
+  // > 0: the pass keystream runs in CTAs of this many warps that each hold a
+  // whole SM, on a ks_stream of the device's highest priority; -1: 4 warps
+  // (one per SM sub-partition) when those CTAs fill at most half the SMs
+  int ks_sm_warps = -1;
+  int num_sms = 0;
   cudaStream_t ks_stream = nullptr;
   cudaEvent_t ev_ks[2] = {};   // keystream buffer b written
   cudaEvent_t ev_rd[2] = {};   // rounds reading buffer b done
@@ -217,6 +222,29 @@ int pass_frames(const vc_ctx* c, int nframes) {
   return nframes < f ? nframes : f;
 }
 
+// Pass sizes of a call of nframes frames with passes of at most F frames.  With
+// overlap and automatic sizing the last passes shrink by a factor of about
+// 3/4 each, down to about F/4: the rounds of the last pass are the only ones
+// that no keystream overlaps, while each shrinking pass's rounds still hide
+// behind the (serial) keystream of the next one.
+void pass_plan(const vc_ctx* c, int nframes, int F, std::vector<int>& plan) {
+  plan.clear();
+  std::vector<int> tail;  // ascending: tail[0] is the last pass
+  if (c->chunk == 0 && c->overlap && F >= 4) {
+    for (int t = (F + 3) / 4; t < F; t = (4 * t + 2) / 3) tail.push_back(t);
+  }
+  long long tsum = 0;
+  for (int t : tail) tsum += t;
+  while (!tail.empty() && nframes - tsum < F) {  // keep at least one full-size pass ahead of the tail
+    tsum -= tail.back();
+    tail.pop_back();
+  }
+  const int body = nframes - (int)tsum;
+  const int np = (body + F - 1) / F;
+  for (int k = 0; k < np; k++) plan.push_back(body / np + (k < body % np ? 1 : 0));
+  for (int k = (int)tail.size() - 1; k >= 0; k--) plan.push_back(tail[k]);
+}
+
 cudaEvent_t pool_event(vc_ctx* c) {
   if (!c->pool.empty()) {
     cudaEvent_t e = c->pool.back();
@@ -249,6 +277,14 @@ struct StageMark {
   }
 };
 
+// Warps per SM-holding keystream CTA for this context (0: shared SMs).
+int ks_warps_in_use(const vc_ctx* c) {
+  if (c->ks_sm_warps >= 0) return c->ks_sm_warps;
+  if (!c->overlap) return 0;
+  const int ctas = (2 * c->L.n + 127) / 128;
+  return 2 * ctas <= c->num_sms ? 4 : 0;
+}
+
 // Keystream side of a pass into buffer b: s_c and shift tables (Alg. 1), then
 // r * S_i bytes per subframe and frame (Sec. 3).
 int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
@@ -260,7 +296,8 @@ int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
   {
     StageMark m(c, ks, 1, 1);
     VC_CUDA(c->ks_lanes == 2
-                ? vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks)
+                ? vc::launch_keystream(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks, 0, 0,
+                                       ks_warps_in_use(c))
                 : vc::launch_keystream_thread(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks));
   }
   return VC_OK;
@@ -376,10 +413,13 @@ int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nf
   rc = enter(c, st);
   if (rc) return rc;
   const long long N = c->L.N;
-  for (int f0 = 0; f0 < nframes; f0 += F) {
-    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+  std::vector<int> plan;
+  pass_plan(c, nframes, F, plan);
+  long long f0 = 0;
+  for (const int nf : plan) {
     rc = run_pass(c, dir, d_in + f0 * N, N, d_out + f0 * N, N, nf, st);
     if (rc) return rc;
+    f0 += nf;
   }
   c->frame += nframes;
   c->produced = c->frame;
@@ -454,7 +494,10 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
     return VC_ERR_CUDA;
   }
   for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-  if (cudaStreamCreateWithFlags(&c->ks_stream, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (cudaStreamCreateWithPriority(&c->ks_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ks[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ks[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rd[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -530,9 +573,11 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   // copy stream: H2D(k) ... D2H(k); compute stream st: pass(k).  Buffers alternate.
   cudaEvent_t* h2d = c->ev;      // [2]
   cudaEvent_t* done = c->ev + 2; // [2]
-  int k = 0;
-  for (int f0 = 0; f0 < nframes; f0 += F, k++) {
-    const int nf = (nframes - f0) < F ? (nframes - f0) : F;
+  std::vector<int> plan;
+  pass_plan(c, nframes, F, plan);
+  long long f0 = 0;
+  for (int k = 0; k < (int)plan.size(); f0 += plan[k], k++) {
+    const int nf = plan[k];
     uint8_t* buf = c->d_io[k & 1];
     VC_CUDA(cudaMemcpyAsync(buf, h_in + (size_t)f0 * N, nf * N, cudaMemcpyHostToDevice, c->copy_stream));
     VC_CUDA(cudaEventRecord(h2d[k & 1], c->copy_stream));
@@ -694,6 +739,18 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       sync_all(c);
       c->overlap = value != 0;
       return VC_OK;
+    case VC_OPT_KS_SM_WARPS: {
+      if (value < -1 || value > 8) return VC_ERR_ARG;
+      sync_all(c);
+      int least = 0, greatest = 0;
+      VC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      cudaStream_t s2 = nullptr;
+      VC_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, value != 0 ? greatest : least));
+      cudaStreamDestroy(c->ks_stream);
+      c->ks_stream = s2;
+      c->ks_sm_warps = (int)value;
+      return VC_OK;
+    }
     case VC_OPT_TILE_ROWS: {
       if (value != 0 && (value < 1 || value > 32 || (value & (value - 1)))) return VC_ERR_ARG;
       Layout L2{};
@@ -728,6 +785,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
     case VC_OPT_KS_LANES: *value = c->ks_lanes; return VC_OK;
     case VC_OPT_OVERLAP: *value = c->overlap ? 1 : 0; return VC_OK;
     case VC_OPT_TILE_ROWS: *value = c->L.T; return VC_OK;
+    case VC_OPT_KS_SM_WARPS: *value = c->ks_sm_warps; return VC_OK;
   }
   return VC_ERR_ARG;
 }
@@ -1435,11 +1493,15 @@ int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
     int rc = ensure_ring(c, 2 * A + 1);
     if (rc) return rc;
     // the next frame on its own (ready soonest), then the rest of the run-ahead
+    // queued behind it; a repeated call while a production is in flight adds
+    // nothing (coalesced, like the top-ups)
+    bool issued = false;
     if (c->produced < c->frame + 1) {
       rc = produce(c, c->frame + 1);
       if (rc) return rc;
+      issued = true;
     }
-    if (c->produced < c->frame + A && !production_busy(c)) {  // coalesced, like the top-ups
+    if (c->produced < c->frame + A && (issued || !production_busy(c))) {
       rc = produce(c, c->frame + A);
       if (rc) return rc;
     }

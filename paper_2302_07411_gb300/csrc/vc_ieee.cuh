@@ -11,7 +11,9 @@
 //    inv = floor(2^115 / mb) gives a quotient estimate within one unit
 //    (Granlund & Montgomery, "Division by invariant integers using
 //    multiplication", PLDI 1994), one correction step makes it exact, and the
-//    remainder decides round-to-nearest-even;
+//    remainder decides round-to-nearest-even; the PLCM step instead carries
+//    the reciprocal to 128 bits, rounded up, so that the product alone
+//    decides the rounding (no correction step);
 //  * subtraction a - b, a >= b > 0: alignment with 10 guard bits and a sticky
 //    bit, then rounding of the dropped bits (the classical guard/round/sticky
 //    scheme of IEEE adders).
@@ -55,10 +57,12 @@ inline int lz64_hi(uint64_t v) { return __builtin_clz((uint32_t)(v >> 32)); }
 constexpr uint64_t kMant52 = (1ull << 52) - 1;
 
 // A positive normal binary64 divisor: mantissa with the hidden bit, biased
-// exponent and inv = floor(2^115 / mb) (in (2^62, 2^63]).
+// exponent, inv = floor(2^115 / mb) (in (2^62, 2^63]) and the 128-bit
+// reciprocal rc_hi 2^64 + rc_lo = ceil(2^179 / mb) (in (2^126, 2^127]).
 struct Divisor {
   uint64_t mb;
   uint64_t inv;
+  uint64_t rc_hi, rc_lo;
   int eb;
 };
 
@@ -79,12 +83,34 @@ __host__ __device__ inline uint64_t recip115(uint64_t m) {
   return q;
 }
 
+// ceil(2^179 / m) for m in [2^52, 2^53) as two words, from inv = floor(2^115 / m):
+// 64 more quotient bits of the long division, rounded up if a remainder is left.
+__host__ __device__ inline void recip179_ceil(uint64_t m, uint64_t inv, uint64_t& hi, uint64_t& lo) {
+  uint64_t r = 0 - inv * m;  // 2^115 - inv m, exact: it lies in [0, m) and 2^115 is 0 mod 2^64
+  uint64_t q = 0;
+  for (int i = 0; i < 64; i++) {
+    r <<= 1;
+    q <<= 1;
+    if (r >= m) {
+      r -= m;
+      q |= 1;
+    }
+  }
+  hi = inv;
+  lo = q;
+  if (r != 0) {
+    lo++;
+    if (lo == 0) hi++;
+  }
+}
+
 __host__ __device__ inline Divisor make_divisor(double b) {
   const uint64_t bb = ieee_bits(b);
   Divisor d;
   d.eb = (int)(bb >> 52);
   d.mb = (bb & kMant52) | (1ull << 52);
   d.inv = recip115(d.mb);
+  recip179_ceil(d.mb, d.inv, d.rc_hi, d.rc_lo);
   return d;
 }
 
@@ -188,7 +214,7 @@ __host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const Plc
   const int ex = (int)(xb >> 52);
   const uint64_t m = (xb & kMant52) | (1ull << 52);
   const int sx = ex - 1011;                 // x = m 2^(sx - 64) in Q0.64 when 0 <= sx <= 11
-  const bool small = sx < 0;                // x < 2^-12 < p: always the x/p branch
+  const bool small = sx < 0;                // x < 2^-12 < p: always the x/p branch, operand x itself
   const uint64_t X = m << (sx & 15);
   const bool refl = xb > 0x3FE0000000000000ull;  // x > 1/2
   const uint64_t XR = refl ? (0ull - X) : X;      // 1 - x, exact
@@ -197,42 +223,35 @@ __host__ __device__ __forceinline__ uint64_t plcm_fx_step(uint64_t xb, const Plc
   const bool wide = (A >> 32) != 0;               // operand >= 2^-32 (else the hardware path)
   const int lz = lz64_hi(wide ? A : (1ull << 32));
   const uint64_t An = A << (lz & 63);
-  uint64_t ma = An >> 11;                         // 53 significant bits
-  const uint32_t R = (uint32_t)An & 0x7FFu;       // dropped bits (zero unless x - p needs rounding)
-  ma += (R > 0x400u || (R == 0x400u && (ma & 1))) ? 1 : 0;
-  int ea = 1022 - lz;
-  if (ma == (1ull << 53)) {
-    ma = 1ull << 52;
-    ea++;
-  }
-  if (small) {
-    ma = m;
-    ea = ex;
-  }
-  // RN(a / b), b = p on the x/p branch, q on the (x - p)/q branch.
-  // q53 = floor(ma 2^53 / mb) in [2^52, 2^54) (estimate within one, then one
-  // correction).  ma >= mb: the result is q53 / 2 rounded (its fraction is
-  // bit 0 of q53 plus less than a half unit, and a quotient of two 53-bit
-  // numbers is never exactly halfway); ma < mb: q53 rounded by the remainder.
+  // RN to 53 significant bits: add just under half a unit plus the unit's
+  // parity (ties to even); a carry out of bit 63 (rounding up to the next
+  // binade, about 2^-42 per step) is left to the hardware path
+  const uint64_t Ar = An + (0x3FFull + ((An >> 11) & 1));
+  const bool carry = Ar < An;
+  const uint64_t ma = small ? m : (Ar >> 11);
+  const int ea = small ? ex : 1022 - lz;
+  // RN(a / b), b = p on the x/p branch, q on the (x - p)/q branch.  With
+  // t = ma 2^53 / mb and RC = ceil(2^179 / mb), v = ma RC / 2^126 = t + eps,
+  // 0 <= eps < ma / 2^126 < 2^-73.  The fraction of t is a multiple of 1/mb
+  // (> 2^-53) and never 1/2 (that would need 2^54 | mb), so floor(v) =
+  // floor(t) and frac(v) >= 1/2 iff frac(t) > 1/2.  ma >= mb (t >= 2^53): the
+  // result is (floor(t) + 1) >> 1 (a quotient of two 53-bit numbers is never
+  // halfway); ma < mb: floor(t) rounded up iff frac(t) > 1/2.  A quotient
+  // that rounds up to 2^53 (the next binade) is left to the hardware path.
   const uint64_t mb = lo ? F.dp.mb : F.dq.mb;
-  const uint64_t inv = lo ? F.dp.inv : F.dq.inv;
+  const uint64_t rh = lo ? F.dp.rc_hi : F.dq.rc_hi;
+  const uint64_t rl = lo ? F.dp.rc_lo : F.dq.rc_lo;
   const int eb = lo ? F.dp.eb : F.dq.eb;
-  const uint64_t lo64 = ma * inv;
-  const uint64_t hi64 = ieee_mulhi(ma, inv);
-  uint64_t q = (hi64 << 2) | (lo64 >> 62);
-  uint64_t rem = (ma << 53) - q * mb;  // exact: the true value lies in [0, 2 mb)
-  if (rem >= mb) {
-    q++;
-    rem -= mb;
-  }
-  const bool big = q >= (1ull << 53);  // ma >= mb
-  int e = ea - eb + (big ? 1023 : 1022);
-  q = big ? ((q + 1) >> 1) : (q + (((rem << 1) > mb) ? 1 : 0));
-  if (q == (1ull << 53)) {
-    q >>= 1;
-    e++;
-  }
-  ok = (ex >= 1) && (ex <= 1022) && (small || wide) && (e >= 1);
+  const bool big = ma >= mb;
+  // ma RC = hi1 2^128 + (lo1 + hi2) 2^64 + (low word, not needed)
+  const uint64_t lo1 = ma * rh, hi1 = ieee_mulhi(ma, rh);
+  const uint64_t hi2 = ieee_mulhi(ma, rl);
+  const uint64_t mid = lo1 + hi2;
+  const uint64_t top = hi1 + (mid < lo1 ? 1 : 0);
+  uint64_t q = (top << 2) | (mid >> 62);  // floor(v)
+  q = big ? ((q >> 1) + (q & 1)) : (q + ((mid >> 61) & 1));
+  const int e = ea - eb + (big ? 1023 : 1022);
+  ok = (ex >= 1) && (ex <= 1022) && (small || (wide && !carry)) && (q < (1ull << 53)) && (e >= 1);
   return ((uint64_t)(e & 0x7FF) << 52) | (q & kMant52);
 }
 

@@ -86,8 +86,11 @@ cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cuda
 // cap > 0: frame f's s_c / shift table / keystream go to slot (slot0 + f) mod cap of a ring.
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
                                   cudaStream_t st, int cap = 0, int slot0 = 0);
+// sm_warps > 0: CTAs of sm_warps warps, each holding all of an SM's shared
+// memory so that no round CTA shares its SM (the chains are latency-bound and
+// lose issue slots to co-resident round warps); 0: one-warp CTAs anywhere.
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0);
+                             bool plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0, int sm_warps = 0);
 cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                                     bool plcm_int, cudaStream_t st);
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,

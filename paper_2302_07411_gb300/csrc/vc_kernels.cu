@@ -13,6 +13,8 @@
 // q / C; subframe i owns bytes [C pi_i, C pi_{i+1}), pi_i = floor(i P / n).
 #include <cstdint>
 
+#include <type_traits>
+
 #include "vc_internal.h"
 #include "vc_maps.cuh"
 
@@ -455,6 +457,13 @@ struct PairWriter {
     if (side == 0) a[2] = w2;
     q += 24;
   }
+  // put24_raw at a word boundary with nothing pending (q mod 8 = 0, own = 0).
+  __device__ __forceinline__ void put24_aligned(uint64_t c0, uint64_t c1, uint64_t c2) {
+    uint64_t* a = reinterpret_cast<uint64_t*>(word_ptr(q));
+    a[side] = side ? c1 : c0;
+    if (side == 0) a[2] = c2;
+    q += 24;
+  }
   // Append 24 bytes c0 | c1 | c2 (little-endian order).
   __device__ __forceinline__ void put24(uint64_t c0, uint64_t c1, uint64_t c2) {
     const int sh = 8 * (q & 7);
@@ -672,42 +681,71 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
       clen -= take;
       rem -= take;
     }
+    // G groups of 24 bytes; ALIGNED: the range position is a word boundary,
+    // so the group's three words need no funnel shifts.  FULL: every lane of
+    // the warp runs this same loop the same number of times, so the partner
+    // exchange can name the whole warp (a shuffle restricted to the lane pair
+    // costs about 60 cycles more per iterate)
+    auto run_groups = [&](long long G, auto aligned, auto full) {
+      const unsigned mk = decltype(full)::value ? 0xFFFFFFFFu : pmask;
+      auto put = [&](uint64_t c0, uint64_t c1, uint64_t c2) {
+        if (decltype(aligned)::value)
+          w.put24_aligned(c0, c1, c2);
+        else
+          w.put24_raw(c0, c1, c2);
+      };
+      uint64_t o0, o1, o2, s0, s1, s2;
+      {  // first group
+        const uint64_t x0 = xb;
+        bool k0, k1, k2, k3;
+        uint64_t a = plcm_fx_step(x0, F, k0);
+        uint64_t b = plcm_fx_step(a, F, k1);
+        uint64_t c = plcm_fx_step(b, F, k2);
+        uint64_t d = plcm_fx_step(c, F, k3);
+        if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
+        xb = d;
+        pack(a, b, c, d, o0, o1, o2);
+        s0 = __shfl_xor_sync(mk, o0, 1);
+        s1 = __shfl_xor_sync(mk, o1, 1);
+        s2 = __shfl_xor_sync(mk, o2, 1);
+      }
+      for (long long g = 1; g < G; g++) {
+        const uint64_t x0 = xb;
+        bool k0, k1, k2, k3;
+        uint64_t a = plcm_fx_step(x0, F, k0);
+        uint64_t b = plcm_fx_step(a, F, k1);
+        put(o0 ^ s0, o1 ^ s1, o2 ^ s2);  // previous group, off the chain
+        uint64_t c = plcm_fx_step(b, F, k2);
+        uint64_t d = plcm_fx_step(c, F, k3);
+        if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
+        xb = d;
+        pack(a, b, c, d, o0, o1, o2);
+        s0 = __shfl_xor_sync(mk, o0, 1);
+        s1 = __shfl_xor_sync(mk, o1, 1);
+        s2 = __shfl_xor_sync(mk, o2, 1);
+      }
+      put(o0 ^ s0, o1 ^ s1, o2 ^ s2);
+    };
     while (rem > 0) {
       if (rem >= 24 && w.fast_ok()) {
         long long G = (w.qe - w.q) / 24;
         if (G > rem / 24) G = rem / 24;
-        // first group
-        uint64_t o0, o1, o2, s0, s1, s2;
-        {
-          const uint64_t x0 = xb;
-          bool k0, k1, k2, k3;
-          uint64_t a = plcm_fx_step(x0, F, k0);
-          uint64_t b = plcm_fx_step(a, F, k1);
-          uint64_t c = plcm_fx_step(b, F, k2);
-          uint64_t d = plcm_fx_step(c, F, k3);
-          if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
-          xb = d;
-          pack(a, b, c, d, o0, o1, o2);
-          s0 = __shfl_xor_sync(pmask, o0, 1);
-          s1 = __shfl_xor_sync(pmask, o1, 1);
-          s2 = __shfl_xor_sync(pmask, o2, 1);
+        const bool aligned = (w.q & 7) == 0;
+        // warp-uniform loop: all 32 lanes here together with the same count and phase
+        const unsigned key = (unsigned)G * 2u + (aligned ? 1u : 0u);
+        bool uniform = false;
+        if (__activemask() == 0xFFFFFFFFu)
+          uniform = __reduce_min_sync(0xFFFFFFFFu, key) == __reduce_max_sync(0xFFFFFFFFu, key);
+        if (uniform) {
+          if (aligned)
+            run_groups(G, std::true_type{}, std::true_type{});
+          else
+            run_groups(G, std::false_type{}, std::true_type{});
+        } else if (aligned) {
+          run_groups(G, std::true_type{}, std::false_type{});
+        } else {
+          run_groups(G, std::false_type{}, std::false_type{});
         }
-        for (long long g = 1; g < G; g++) {
-          const uint64_t x0 = xb;
-          bool k0, k1, k2, k3;
-          uint64_t a = plcm_fx_step(x0, F, k0);
-          uint64_t b = plcm_fx_step(a, F, k1);
-          w.put24_raw(o0 ^ s0, o1 ^ s1, o2 ^ s2);  // previous group, off the chain
-          uint64_t c = plcm_fx_step(b, F, k2);
-          uint64_t d = plcm_fx_step(c, F, k3);
-          if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
-          xb = d;
-          pack(a, b, c, d, o0, o1, o2);
-          s0 = __shfl_xor_sync(pmask, o0, 1);
-          s1 = __shfl_xor_sync(pmask, o1, 1);
-          s2 = __shfl_xor_sync(pmask, o2, 1);
-        }
-        w.put24_raw(o0 ^ s0, o1 ^ s1, o2 ^ s2);
         w.end_of_range_check();
         rem -= 24 * G;
       } else {
@@ -740,9 +778,58 @@ __global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains c
   ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
 }
 
+// The same chains in CTAs of up to 8 warps launched with the SM's whole
+// shared memory (unused): one CTA per SM, and no other kernel's CTA that needs
+// shared memory can join it.
+__global__ void __launch_bounds__(256) k_ks_plcm_fx_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+                                                       int cap, int slot0) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_ks_pair_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
+                                                    int slot0) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  ks_pair_chain<KIND, false>(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
+}
+
+static int reserve_smem_bytes() {
+  static int bytes[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 0;
+  if (bytes[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+    bytes[dev] = v;
+  }
+  return bytes[dev];
+}
+
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st, int cap, int slot0) {
+                             bool plcm_int, cudaStream_t st, int cap, int slot0, int sm_warps) {
   if (nframes <= 0) return cudaSuccess;
+  if (sm_warps > 0) {
+    const int threads = 32 * (sm_warps > 8 ? 8 : sm_warps);
+    const int blocks = (2 * L.n + threads - 1) / threads;
+    const int smem = reserve_smem_bytes();
+    cudaError_t e;
+    if (kind == 0 && plcm_int) {
+      e = cudaFuncSetAttribute(k_ks_plcm_fx_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      k_ks_plcm_fx_sm<<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+    } else if (kind == 0) {
+      e = cudaFuncSetAttribute(k_ks_pair_sm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      k_ks_pair_sm<0><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+    } else {
+      e = cudaFuncSetAttribute(k_ks_pair_sm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      k_ks_pair_sm<1><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+    }
+    return cudaGetLastError();
+  }
   const int blocks = (2 * L.n + 31) / 32;
   if (kind == 0 && plcm_int)
     k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);

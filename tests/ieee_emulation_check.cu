@@ -96,7 +96,21 @@ int main(int argc, char** argv) {
       case 4: x = std::ldexp(U(g), -(int)(g() % 1000)); break;
       case 5: x = 0.5 + 1e-12 * (U(g) - 0.5); break;
       case 6: x = (1.0 - p) * (1.0 + 1e-13 * (U(g) - 0.5)); break;
-      default: x = from_bits(g() & 0x3FEFFFFFFFFFFFFFull); break;
+      case 7:
+        if ((i & 8) && (i & 64)) {  // exact quotients: x / p or (x - p) / q a power of two
+          const int k = 1 + (int)(g() % 6);
+          x = (i & 16) ? std::ldexp(p, -k) : p + std::ldexp(q, -k);
+          if (i & 32) x = 1.0 - x;
+        } else if (i & 8) {  // x / p (or (x - p) / q) close to a rounding midpoint or a binade edge
+          const double y = 0.5 + 0.5 * U(g);
+          const double yh = y + std::ldexp(1.0, -54) * (1.0 + (double)(g() % 5) - 2.0);
+          x = (i & 16) ? yh * p : p + yh * q;
+          if (i & 32) x = 1.0 - x;
+        } else {
+          x = from_bits(g() & 0x3FEFFFFFFFFFFFFFull);
+        }
+        break;
+      default: x = U(g); break;
     }
     double xr = x > 0.5 ? 1.0 - x : x;
     const double want = xr < p ? xr / p : (xr - p) / q;

@@ -109,10 +109,13 @@ def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
 
 @pytest.mark.parametrize("kind,plcm_int,lanes", [(0, 1, 2), (0, 0, 2), (1, 1, 2), (0, 1, 1), (0, 0, 1), (1, 1, 1)])
 @pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
-                                               (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6), (33, 47, 3, 61, 5, 3)])
+                                               (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6), (33, 47, 3, 61, 5, 3),
+                                               (48, 48, 3, 16, 5, 3), (80, 88, 1, 16, 5, 3)])
 def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n, r, frames):
     """Sec. 3 byte streams and Alg. 1's s_c per frame, across frames (the left
-    over bytes of an iterate carry over, R7), for every keystream kernel form."""
+    over bytes of an iterate carry over, R7), for every keystream kernel form.
+    48x48x3 with n = 16 fills a warp with equal word-aligned ranges; 80x88x1
+    with n = 16 has equal ranges whose frames start 2 bytes into an iterate."""
     key = synth.key_for_seed(kind, 200 + n)
     ref = orc.OracleCipher(kind, key, H, W, C, n, r)
     g = B.Cipher(kind, key, H, W, C, n, r)
@@ -134,7 +137,7 @@ def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n
 
 # --------------------------------------------------------------------- whole frames
 
-def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0):
+def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0, ks_sm_warps=0):
     F, H, W, C = X.shape
     ref_e = orc.OracleCipher(kind, key, H, W, C, n, r)
     ref_d = orc.OracleCipher(kind, key, H, W, C, n, r)
@@ -147,6 +150,10 @@ def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_r
     if tile_rows:
         g_e.set_option(B.VC_OPT_TILE_ROWS, tile_rows)
         g_d.set_option(B.VC_OPT_TILE_ROWS, 1 if tile_rows > 1 else 2)
+    if ks_sm_warps:
+        g_e.set_option(B.VC_OPT_KS_SM_WARPS, ks_sm_warps)
+        g_d.set_option(B.VC_OPT_KS_SM_WARPS, ks_sm_warps)
+        assert g_e.get_option(B.VC_OPT_KS_SM_WARPS) == ks_sm_warps
     d = dev(X)
     Yg = g_e.encrypt(d, d if inplace else None)
     g_e.sync()
@@ -199,6 +206,15 @@ def test_tile_shapes_do_not_change_the_ciphertext(B, orc, tile_rows):
     shapes for encryption and decryption) gives the oracle's bytes."""
     X = synth.uniform_frames(2, 50, 44, 3, seed=17)
     _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 17), X, 9, 5, tile_rows=tile_rows)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("warps", [1, 4, 8])
+def test_keystream_on_reserved_sms(B, orc, kind, warps):
+    """Keystream CTAs that each hold a whole SM (several passes, so keystream
+    and rounds overlap across the two streams) give the oracle's bytes."""
+    X = synth.uniform_frames(6, 48, 40, 3, seed=23)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 23), X, 37, 5, chunk=2, ks_sm_warps=warps)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
