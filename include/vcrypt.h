@@ -214,6 +214,12 @@ int enc_sync_status(vc_ctx* ctx);
  * VC_OPT_PLCM_INT: 1 (default) evaluates the PLCM division and subtraction of
  *                  Eq. 5 exactly on the integer pipes, 0 uses the binary64
  *                  pipe; both give identical bits (IEEE-754 round to nearest).
+ *                  2 and 3 are test modes: the integer form computes each
+ *                  range and then rewrites it through its exact fallback, for
+ *                  every subframe (2) or the odd-numbered ones only (3, lanes
+ *                  of one warp take different paths), so the fallback
+ *                  (normally taken about once in 2^30 iterates) is exercised;
+ *                  the bytes are again identical.
  * VC_OPT_KS_LANES: lanes per subframe chain pair in the keystream kernel:
  *                  2 (default, one lane per chaotic map) or 1 (one thread runs
  *                  both maps of the pair).

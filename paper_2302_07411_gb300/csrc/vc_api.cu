@@ -151,7 +151,7 @@ struct vc_ctx {
   cudaEvent_t ev[6] = {};
   int64_t frame = 0;
   cudaStream_t last = nullptr;
-  bool plcm_int = true;
+  int plcm_int = 1;  // 0 binary64 pipe, 1 integer pipes, 2/3 integer pipes + forced exact fallback (tests)
   int ks_lanes = 2;
   // stage profiling: recorded (stage, start, end) event pairs and a free pool
   bool prof = false;
@@ -727,8 +727,8 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       }
       return enc_set_chunk(c, value < 1 || value > 65535 ? -1 : (int32_t)value);
     case VC_OPT_PLCM_INT:
-      if (value != 0 && value != 1) return VC_ERR_ARG;
-      c->plcm_int = value != 0;
+      if (value < 0 || value > 3) return VC_ERR_ARG;
+      c->plcm_int = (int)value;
       return VC_OK;
     case VC_OPT_KS_LANES:
       if (value != 1 && value != 2) return VC_ERR_ARG;
@@ -781,7 +781,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
   if (!c || !value) return VC_ERR_ARG;
   switch (option) {
     case VC_OPT_CHUNK: *value = c->chunk; return VC_OK;
-    case VC_OPT_PLCM_INT: *value = c->plcm_int ? 1 : 0; return VC_OK;
+    case VC_OPT_PLCM_INT: *value = c->plcm_int; return VC_OK;
     case VC_OPT_KS_LANES: *value = c->ks_lanes; return VC_OK;
     case VC_OPT_OVERLAP: *value = c->overlap ? 1 : 0; return VC_OK;
     case VC_OPT_TILE_ROWS: *value = c->L.T; return VC_OK;

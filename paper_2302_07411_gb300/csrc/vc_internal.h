@@ -86,13 +86,16 @@ cudaError_t launch_key_schedule(int kind, MainPrbg* main, Chains ch, int n, cuda
 // cap > 0: frame f's s_c / shift table / keystream go to slot (slot0 + f) mod cap of a ring.
 cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, long long* sc, int* kmod,
                                   cudaStream_t st, int cap = 0, int slot0 = 0);
+// plcm_int: 0 binary64 pipe, 1 integer pipes, 2 integer pipes with every
+// iterate sent through the exact fallback, 3 the same for odd subframes only
+// (test modes of the lane-pair form).
 // sm_warps > 0: CTAs of sm_warps warps, each holding all of an SM's shared
 // memory so that no round CTA shares its SM (the chains are latency-bound and
 // lose issue slots to co-resident round warps); 0: one-warp CTAs anywhere.
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0, int sm_warps = 0);
+                             int plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0, int sm_warps = 0);
 cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                                    bool plcm_int, cudaStream_t st);
+                                    int plcm_int, cudaStream_t st);
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
                              const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st);

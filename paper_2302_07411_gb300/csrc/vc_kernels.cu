@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(32) k_ks_pair(Layout L, Tables tb, Chains ch, 
 // is recomputed step by step with the hardware division.
 __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
                                                  uint8_t* ks, const int i, const int side, int cap = 0,
-                                                 int slot0 = 0) {
+                                                 int slot0 = 0, int force_fallback = 0) {
   if (i >= L.n) return;
   const unsigned pmask = 3u << (threadIdx.x & 30);
   constexpr uint64_t M48 = 0xFFFFFFFFFFFFull;
@@ -632,7 +632,11 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
   const double qd = ch.par[4 * i + 2 * side + 1];
   uint64_t xb = (uint64_t)__double_as_longlong(ch.st[2 * i + side]);
   PlcmFx F;
-  const bool fx_ok = make_plcm_fx(p, qd, F);
+  // force_fallback (a test mode): 1 = every fixed-point iterate counts as out
+  // of range, so each range is computed and then rewritten by the exact
+  // fallback; 2 = the same for odd subframes only (pairs of one warp diverge)
+  const bool forced = force_fallback == 1 || (force_fallback == 2 && (i & 1));
+  const bool fx_ok = make_plcm_fx(p, qd, F) && !forced;
   uint64_t c0 = ch.carry[2 * i], c1 = ch.carry[2 * i + 1];
   int clen = ch.carry_len[i];
 
@@ -685,7 +689,11 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
     // so the group's three words need no funnel shifts.  FULL: every lane of
     // the warp runs this same loop the same number of times, so the partner
     // exchange can name the whole warp (a shuffle restricted to the lane pair
-    // costs about 60 cycles more per iterate)
+    // costs about 60 cycles more per iterate).  The loop body is one basic
+    // block: iteration g computes group g, packs and exchanges group g - 1 and
+    // stores group g - 2; the fixed-point range flags are accumulated, and a
+    // pair with an iterate outside it (about 2^-30 per iterate) redoes the
+    // range step by step with the exact fallback.
     auto run_groups = [&](long long G, auto aligned, auto full) {
       const unsigned mk = decltype(full)::value ? 0xFFFFFFFFu : pmask;
       auto put = [&](uint64_t c0, uint64_t c1, uint64_t c2) {
@@ -694,37 +702,83 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
         else
           w.put24_raw(c0, c1, c2);
       };
-      uint64_t o0, o1, o2, s0, s1, s2;
-      {  // first group
-        const uint64_t x0 = xb;
+      const uint64_t x_start = xb;
+      const int q_start = w.q, j_start = w.j;
+      const uint64_t acc_start = w.acc;
+      const uint32_t own_start = w.own;
+      bool good = fx_ok;
+      uint64_t ra, rb, rc, rd;              // iterates of the previous group
+      uint64_t o0 = 0, o1 = 0, o2 = 0, s0 = 0, s1 = 0, s2 = 0;  // own and partner words of the one before
+      {
         bool k0, k1, k2, k3;
-        uint64_t a = plcm_fx_step(x0, F, k0);
-        uint64_t b = plcm_fx_step(a, F, k1);
-        uint64_t c = plcm_fx_step(b, F, k2);
-        uint64_t d = plcm_fx_step(c, F, k3);
-        if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
-        xb = d;
-        pack(a, b, c, d, o0, o1, o2);
+        ra = plcm_fx_step(xb, F, k0);
+        rb = plcm_fx_step(ra, F, k1);
+        rc = plcm_fx_step(rb, F, k2);
+        rd = plcm_fx_step(rc, F, k3);
+        good &= k0 & k1 & k2 & k3;
+        xb = rd;
+      }
+      if (G >= 2) {
+        bool k0, k1, k2, k3;
+        const uint64_t a = plcm_fx_step(xb, F, k0);
+        const uint64_t b = plcm_fx_step(a, F, k1);
+        pack(ra, rb, rc, rd, o0, o1, o2);
         s0 = __shfl_xor_sync(mk, o0, 1);
         s1 = __shfl_xor_sync(mk, o1, 1);
         s2 = __shfl_xor_sync(mk, o2, 1);
-      }
-      for (long long g = 1; g < G; g++) {
-        const uint64_t x0 = xb;
-        bool k0, k1, k2, k3;
-        uint64_t a = plcm_fx_step(x0, F, k0);
-        uint64_t b = plcm_fx_step(a, F, k1);
-        put(o0 ^ s0, o1 ^ s1, o2 ^ s2);  // previous group, off the chain
-        uint64_t c = plcm_fx_step(b, F, k2);
-        uint64_t d = plcm_fx_step(c, F, k3);
-        if (!(fx_ok && k0 && k1 && k2 && k3)) fix_group(x0, a, b, c, d);
+        const uint64_t c = plcm_fx_step(b, F, k2);
+        const uint64_t d = plcm_fx_step(c, F, k3);
+        good &= k0 & k1 & k2 & k3;
         xb = d;
-        pack(a, b, c, d, o0, o1, o2);
+        ra = a;
+        rb = b;
+        rc = c;
+        rd = d;
+      }
+      for (long long g = 2; g < G; g++) {
+        bool k0, k1, k2, k3;
+        const uint64_t a = plcm_fx_step(xb, F, k0);
+        const uint64_t b = plcm_fx_step(a, F, k1);
+        put(o0 ^ s0, o1 ^ s1, o2 ^ s2);  // group g - 2
+        pack(ra, rb, rc, rd, o0, o1, o2);  // group g - 1
         s0 = __shfl_xor_sync(mk, o0, 1);
         s1 = __shfl_xor_sync(mk, o1, 1);
         s2 = __shfl_xor_sync(mk, o2, 1);
+        const uint64_t c = plcm_fx_step(b, F, k2);
+        const uint64_t d = plcm_fx_step(c, F, k3);
+        good &= k0 & k1 & k2 & k3;
+        xb = d;
+        ra = a;
+        rb = b;
+        rc = c;
+        rd = d;
       }
+      if (G >= 2) put(o0 ^ s0, o1 ^ s1, o2 ^ s2);
+      pack(ra, rb, rc, rd, o0, o1, o2);
+      s0 = __shfl_xor_sync(mk, o0, 1);
+      s1 = __shfl_xor_sync(mk, o1, 1);
+      s2 = __shfl_xor_sync(mk, o2, 1);
       put(o0 ^ s0, o1 ^ s1, o2 ^ s2);
+      // every lane of mk takes part in the exchange (no short circuit)
+      const int partner_good = __shfl_xor_sync(mk, good ? 1 : 0, 1);
+      const bool pair_good = good && partner_good != 0;
+      if (!pair_good) {  // both lanes of the pair: rewrite the range exactly
+        xb = x_start;
+        w.q = q_start;
+        w.j = j_start;
+        w.acc = acc_start;
+        w.own = own_start;
+        for (long long g = 0; g < G; g++) {
+          uint64_t a, b, c, d;
+          fix_group(xb, a, b, c, d);
+          xb = d;
+          pack(a, b, c, d, o0, o1, o2);
+          s0 = __shfl_xor_sync(pmask, o0, 1);
+          s1 = __shfl_xor_sync(pmask, o1, 1);
+          s2 = __shfl_xor_sync(pmask, o2, 1);
+          put(o0 ^ s0, o1 ^ s1, o2 ^ s2);
+        }
+      }
     };
     while (rem > 0) {
       if (rem >= 24 && w.fast_ok()) {
@@ -773,18 +827,18 @@ __device__ __forceinline__ void ks_plcm_fx_chain(const Layout& L, const Tables& 
 }
 
 __global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
-                                                   int slot0) {
+                                                   int slot0, int force_fallback) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
+  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0, force_fallback);
 }
 
 // The same chains in CTAs of up to 8 warps launched with the SM's whole
 // shared memory (unused): one CTA per SM, and no other kernel's CTA that needs
 // shared memory can join it.
 __global__ void __launch_bounds__(256) k_ks_plcm_fx_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                                                       int cap, int slot0) {
+                                                       int cap, int slot0, int force_fallback) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
+  ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0, force_fallback);
 }
 
 template <int KIND>
@@ -808,7 +862,7 @@ static int reserve_smem_bytes() {
 }
 
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                             bool plcm_int, cudaStream_t st, int cap, int slot0, int sm_warps) {
+                             int plcm_int, cudaStream_t st, int cap, int slot0, int sm_warps) {
   if (nframes <= 0) return cudaSuccess;
   if (sm_warps > 0) {
     const int threads = 32 * (sm_warps > 8 ? 8 : sm_warps);
@@ -818,7 +872,8 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
     if (kind == 0 && plcm_int) {
       e = cudaFuncSetAttribute(k_ks_plcm_fx_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
-      k_ks_plcm_fx_sm<<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+      k_ks_plcm_fx_sm<<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0,
+                                                     plcm_int >= 2 ? plcm_int - 1 : 0);
     } else if (kind == 0) {
       e = cudaFuncSetAttribute(k_ks_pair_sm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
@@ -832,7 +887,7 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
   }
   const int blocks = (2 * L.n + 31) / 32;
   if (kind == 0 && plcm_int)
-    k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+    k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0, plcm_int >= 2 ? plcm_int - 1 : 0);
   else if (kind == 0)
     k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   else
@@ -843,7 +898,7 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
 // The earlier one-thread-per-subframe form (both maps in one thread), kept for
 // comparison measurements.
 cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
-                                    bool plcm_int, cudaStream_t st) {
+                                    int plcm_int, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
   const int blocks = (L.n + 31) / 32;
   if (kind == 0 && plcm_int)

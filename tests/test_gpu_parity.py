@@ -107,7 +107,8 @@ def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
     return out
 
 
-@pytest.mark.parametrize("kind,plcm_int,lanes", [(0, 1, 2), (0, 0, 2), (1, 1, 2), (0, 1, 1), (0, 0, 1), (1, 1, 1)])
+@pytest.mark.parametrize("kind,plcm_int,lanes", [(0, 1, 2), (0, 0, 2), (0, 2, 2), (0, 3, 2), (1, 1, 2), (0, 1, 1),
+                                                (0, 0, 1), (1, 1, 1)])
 @pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
                                                (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6), (33, 47, 3, 61, 5, 3),
                                                (48, 48, 3, 16, 5, 3), (80, 88, 1, 16, 5, 3)])
@@ -137,7 +138,7 @@ def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n
 
 # --------------------------------------------------------------------- whole frames
 
-def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0, ks_sm_warps=0):
+def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0, ks_sm_warps=0, plcm_int=None):
     F, H, W, C = X.shape
     ref_e = orc.OracleCipher(kind, key, H, W, C, n, r)
     ref_d = orc.OracleCipher(kind, key, H, W, C, n, r)
@@ -150,6 +151,9 @@ def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_r
     if tile_rows:
         g_e.set_option(B.VC_OPT_TILE_ROWS, tile_rows)
         g_d.set_option(B.VC_OPT_TILE_ROWS, 1 if tile_rows > 1 else 2)
+    if plcm_int is not None:
+        g_e.set_option(B.VC_OPT_PLCM_INT, plcm_int)
+        g_d.set_option(B.VC_OPT_PLCM_INT, plcm_int)
     if ks_sm_warps:
         g_e.set_option(B.VC_OPT_KS_SM_WARPS, ks_sm_warps)
         g_d.set_option(B.VC_OPT_KS_SM_WARPS, ks_sm_warps)
@@ -215,6 +219,16 @@ def test_keystream_on_reserved_sms(B, orc, kind, warps):
     and rounds overlap across the two streams) give the oracle's bytes."""
     X = synth.uniform_frames(6, 48, 40, 3, seed=23)
     _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 23), X, 37, 5, chunk=2, ks_sm_warps=warps)
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("H,W,C,n", [(48, 48, 3, 16), (96, 96, 3, 64)])
+def test_exact_fallback_in_full_warps(B, orc, mode, H, W, C, n):
+    """Equal word-aligned ranges fill whole warps (the warp-wide exchange); the
+    exact fallback rewrites every range (mode 2) or only the odd subframes'
+    (mode 3, so lane pairs of one warp take different paths)."""
+    X = synth.uniform_frames(4, H, W, C, seed=29)
+    _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 29), X, n, 5, chunk=2, plcm_int=mode)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
