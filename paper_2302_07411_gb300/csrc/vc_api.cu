@@ -84,6 +84,9 @@ int make_layout(const vc_layout& l, Layout* L, int tile_rows_max = 0) {
   L->Npad = (N + 255) & ~255LL;
   L->T = T;
   L->NT = NT;
+  // a window of m pixels holds at most floor(m n / P) + 1 subframe starts
+  const long long tile_starts = (long long)T * l.width * l.n_subframes / P + 2;
+  L->SC = tile_starts <= vc::kMaxSeedSlots ? (int)((tile_starts + 15) & ~15LL) : 0;
   return VC_OK;
 }
 

@@ -9,6 +9,7 @@ namespace vc {
 constexpr int kMaxTiles = 4096;   // tiles (row bands of the round kernels) per frame
 constexpr int kMaxRowBytes = 96 * 1024;
 constexpr int kRoundThreads = 256;
+constexpr int kMaxSeedSlots = 1024;  // subframe seeds per tile kept in shared memory (more: computed in place)
 
 // Frame geometry and the subframe partition (pi_i = floor(i P / n) pixels).
 struct Layout {
@@ -18,6 +19,7 @@ struct Layout {
   long long Npad;     // stride of internal per-frame buffers (multiple of 256)
   int T;              // rows per tile of the round kernels (power of two <= 32)
   int NT;             // tiles per frame = ceil(H / T)
+  int SC;             // shared-memory seed slots per tile (>= the subframe starts in any tile; 0: none)
 };
 
 // Read-only per-layout tables built on the device at init.

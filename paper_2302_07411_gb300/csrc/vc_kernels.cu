@@ -991,6 +991,18 @@ __device__ __forceinline__ int mod_h(int v, int H) {
   return v < 0 ? v + H : v;
 }
 
+// Subframe starts at pixels < p: #{i : floor(i P / n) < p} = min(n, ceil(p n / P)).
+__device__ __forceinline__ int starts_before(const Layout& L, int p) {
+  const long long r = ((long long)p * L.n + L.P - 1) / L.P;
+  return r < L.n ? (int)r : L.n;
+}
+
+// Bytes j of the word holding chunk bytes w0 .. w0 + 3 with w0 + j >= k.
+__device__ __forceinline__ uint32_t mask_from(int k, int w0) {
+  const int kk = k - w0;
+  return kk <= 0 ? 0xFFFFFFFFu : (kk >= 4 ? 0u : (0xFFFFFFFFu << (8 * kk)));
+}
+
 // Byte-wise a + b mod 256 in each of the four bytes of a word.
 __device__ __forceinline__ uint32_t vadd4(uint32_t a, uint32_t b) {
   return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
@@ -1041,16 +1053,31 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   uint8_t* s_carry = smem + (((size_t)L.T * rowb + 15) & ~(size_t)15);
   int* s_kmod = reinterpret_cast<int*>(s_carry + ((L.NT + 15) & ~15));
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(s_kmod + 32);
+  uint8_t* s_seed = reinterpret_cast<uint8_t*>(s_warp + 32);
 
   const uint8_t* X = A.in + f * A.in_stride;
   uint8_t* Out = A.out + f * A.out_stride;
   const uint8_t* KS = A.ks + f * A.ks_stride;
   const int* kmod = A.kmod + (long long)f * L.H;
   const bool fix = A.agg_in != nullptr;
+  // subframes s_lo .. s_hi - 1 start in this tile's pixels
+  const int s_lo = starts_before(L, a0 * L.W), s_hi = starts_before(L, (a0 + Te) * L.W);
+  const bool seeded = L.SC > 0;
 
   if (fix && threadIdx.x < 32) tile_carries(L, A.tb, A.agg_in + (long long)f * L.NT, s_carry);
   if (threadIdx.x < Te) s_kmod[threadIdx.x] = kmod[a0 + threadIdx.x];
   __syncthreads();
+
+  // ---- seeds (Eq. 3 with the seed of reading R9) of the subframes starting
+  // here: the pre-diffusion byte at the end of the next subframe, read
+  // through Eq. 1 from the previous round's output
+  if (seeded) {
+    for (int k = threadIdx.x; k < s_hi - s_lo; k += blockDim.x) {
+      const int s = s_lo + k;
+      const int nx = (s + 1 == L.n) ? 0 : s + 1;
+      s_seed[k] = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, C * __ldg(&A.tb.pi[nx + 1]) - 1);
+    }
+  }
 
   // ---- gather: Z[tt][o] = X[(a0 + tt - o) mod H][o] -------------------------
   {
@@ -1135,24 +1162,45 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
     bool fast = false;
     if (len == 16 && (cs & 15) == 0) {
       // fast path: the chunk lies in one row, its rotated source bytes do not
-      // wrap, and no subframe starts inside it
+      // wrap (or the row is whole words, so they wrap word-wise), and at most
+      // one subframe starts inside it (its seed is in shared memory)
       const int off = cs - tstart;
       const int tt0 = off / rowb;
       const int e0 = off - tt0 * rowb;
       int zs = e0 - s_kmod[tt0] * C;
       if (zs < 0) zs += rowb;
-      if (e0 + 16 <= rowb && zs + 16 <= rowb) {
+      const bool nowrap = zs + 16 <= rowb;
+      if (e0 + 16 <= rowb && (nowrap || (rowb & 3) == 0)) {
         const int pfirst = (cs + C - 1) / C, plast = (cs + 15) / C;
         const int wq = pfirst >> 5;
         const uint64_t win = (uint64_t)__ldg(&A.tb.sbits[wq]) | ((uint64_t)__ldg(&A.tb.sbits[wq + 1]) << 32);
+        const int rk = __ldg(&A.tb.srank[wq]);
         const int lb = pfirst - (wq << 5), hb = plast - (wq << 5);
-        const uint64_t msk = ((2ull << hb) - 1ull) & ~((1ull << lb) - 1ull);
-        if ((win & msk) == 0) {
+        const uint64_t sw = win & ((2ull << hb) - 1ull) & ~((1ull << lb) - 1ull);
+        const int nst = __popcll(sw);
+        if (nst == 0 || (nst == 1 && seeded)) {
           fast = true;
-          const int za = tt0 * rowb + zs;
-          const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
-          const uint32_t sh = (uint32_t)(za & 3) * 8u;
-          const uint32_t z0 = zw[0], z1 = zw[1], z2 = zw[2], z3 = zw[3], z4 = zw[4];
+          uint32_t z0, z1, z2, z3, z4;
+          uint32_t sh;
+          if (nowrap) {
+            const int za = tt0 * rowb + zs;
+            const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
+            sh = (uint32_t)(za & 3) * 8u;
+            z0 = zw[0];
+            z1 = zw[1];
+            z2 = zw[2];
+            z3 = zw[3];
+            z4 = zw[4];
+          } else {  // whole-word row: the five words wrap around its end
+            const uint32_t* zr = reinterpret_cast<const uint32_t*>(Z + tt0 * rowb);
+            const int rw = rowb >> 2, wi = zs >> 2;
+            sh = (uint32_t)(zs & 3) * 8u;
+            z0 = zr[wi];
+            z1 = zr[wi + 1 < rw ? wi + 1 : wi + 1 - rw];
+            z2 = zr[wi + 2 < rw ? wi + 2 : wi + 2 - rw];
+            z3 = zr[wi + 3 < rw ? wi + 3 : wi + 3 - rw];
+            z4 = zr[wi + 4 < rw ? wi + 4 : wi + 4 - rw];
+          }
           const uint32_t y0 = __funnelshift_r(z0, z1, sh), y1 = __funnelshift_r(z1, z2, sh);
           const uint32_t y2 = __funnelshift_r(z2, z3, sh), y3 = __funnelshift_r(z3, z4, sh);
           uint32_t d0 = kv.x ^ vadd4(y0, kv.x), d1 = kv.y ^ vadd4(y1, kv.y);
@@ -1168,11 +1216,33 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
           d1 ^= bcast3(d0);
           d2 ^= bcast3(d1);
           d3 ^= bcast3(d2);
+          if (nst == 1) {
+            // byte k starts subframe s: from k on the chain is seed ^ d_k ^ ..,
+            // i.e. the chunk prefix xor (seed ^ prefix at k - 1); bytes before
+            // k still miss the incoming prefix
+            const int b = __ffsll((long long)sw) - 1;
+            const int k = C * ((wq << 5) + b) - cs;
+            const int s = rk + __popcll(win & ((1ull << b) - 1ull));
+            uint32_t pk = 0;
+            if (k > 0) {
+              const int km = k - 1;
+              const uint32_t wsel = km < 4 ? d0 : (km < 8 ? d1 : (km < 12 ? d2 : d3));
+              pk = (wsel >> (8 * (km & 3))) & 0xFFu;
+            }
+            const uint32_t V = ((uint32_t)s_seed[s - s_lo] ^ pk) * 0x01010101u;
+            d0 ^= V & mask_from(k, 0);
+            d1 ^= V & mask_from(k, 4);
+            d2 ^= V & mask_from(k, 8);
+            d3 ^= V & mask_from(k, 12);
+            fse = k;
+            agg = 0x100u | (d3 >> 24);
+          } else {
+            agg = d3 >> 24;
+          }
           pre[0] = d0;
           pre[1] = d1;
           pre[2] = d2;
           pre[3] = d3;
-          agg = d3 >> 24;
         }
       }
     }
@@ -1214,9 +1284,13 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
           if (st) {
             const int wq = pix >> 5;
             const int s = __ldg(&A.tb.srank[wq]) + __popc(__ldg(&A.tb.sbits[wq]) & ((1u << (pix & 31)) - 1u));
-            const int nx = (s + 1 == L.n) ? 0 : s + 1;
-            const int sb = C * __ldg(&A.tb.pi[nx + 1]) - 1;
-            const uint8_t sd = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, sb);
+            uint8_t sd;
+            if (seeded) {
+              sd = s_seed[s - s_lo];
+            } else {
+              const int nx = (s + 1 == L.n) ? 0 : s + 1;
+              sd = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, C * __ldg(&A.tb.pi[nx + 1]) - 1);
+            }
             v = (uint32_t)(sd ^ d);
             if (!has) {
               has = true;
@@ -1251,19 +1325,13 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
       const uint32_t ev = E & 0xFFu;
       const uint32_t evx4 = ev * 0x01010101u;
 #pragma unroll
-      for (int w4 = 0; w4 < 4; w4++) {
-        // bytes k < fse of the chunk still miss the prefix E
-        const int k0 = w4 * 4;
-        uint32_t msk = 0;
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (k0 + b < fse) msk |= 0xFFu << (8 * b);
-        pre[w4] ^= evx4 & msk;
-      }
+      for (int w4 = 0; w4 < 4; w4++) pre[w4] ^= evx4 & ~mask_from(fse, 4 * w4);  // bytes before fse miss E
       if (len == 16 && (cs & 15) == 0 && out_vec) {
         *reinterpret_cast<uint4*>(Out + cs) = make_uint4(pre[0], pre[1], pre[2], pre[3]);
       } else {
-        for (int k = 0; k < len; k++) Out[cs + k] = (uint8_t)(pre[k >> 2] >> (8 * (k & 3)));
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (k < len) Out[cs + k] = (uint8_t)(pre[k >> 2] >> (8 * (k & 3)));
       }
     }
   }
@@ -1277,9 +1345,10 @@ __global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
 }
 
 // [Z tile, 16-aligned][tile carries, NT bytes rounded to 16][row shifts, 32 ints][scan, 32 words]
+// [subframe seeds, SC bytes]
 size_t round_smem_bytes(const Layout& L) {
   return (((size_t)L.T * L.W * L.C + 15) & ~(size_t)15) + ((L.NT + 15) & ~15) + 32 * sizeof(int) +
-         32 * sizeof(uint32_t);
+         32 * sizeof(uint32_t) + (size_t)L.SC;
 }
 
 template <int C>
