@@ -231,7 +231,7 @@ int enc_sync_status(vc_ctx* ctx);
  *                  1..32 (capped by the 96 KB shared-memory tile budget);
  *                  0 (default) takes the largest that fits.  Reading it back
  *                  gives the rows in use.
- * VC_OPT_KS_SM_WARPS: -1..8.  k > 0 runs the keystream of each pass in CTAs
+ * VC_OPT_KS_SM_WARPS: -1..4.  k > 0 runs the keystream of each pass in CTAs
  *                  of k warps that each occupy a whole SM (they claim all of
  *                  its shared memory), on an internal stream of the device's
  *                  highest priority, so that the round kernels of the previous

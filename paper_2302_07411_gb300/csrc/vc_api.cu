@@ -743,7 +743,7 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       c->overlap = value != 0;
       return VC_OK;
     case VC_OPT_KS_SM_WARPS: {
-      if (value < -1 || value > 8) return VC_ERR_ARG;
+      if (value < -1 || value > 4) return VC_ERR_ARG;
       sync_all(c);
       int least = 0, greatest = 0;
       VC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));

@@ -91,7 +91,7 @@ cudaError_t launch_frame_schedule(const Layout& L, MainPrbg* main, int nframes, 
 // plcm_int: 0 binary64 pipe, 1 integer pipes, 2 integer pipes with every
 // iterate sent through the exact fallback, 3 the same for odd subframes only
 // (test modes of the lane-pair form).
-// sm_warps > 0: CTAs of sm_warps warps, each holding all of an SM's shared
+// sm_warps > 0: CTAs of sm_warps (<= 4) warps, each holding all of an SM's shared
 // memory so that no round CTA shares its SM (the chains are latency-bound and
 // lose issue slots to co-resident round warps); 0: one-warp CTAs anywhere.
 cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,

@@ -832,17 +832,18 @@ __global__ void __launch_bounds__(32) k_ks_plcm_fx(Layout L, Tables tb, Chains c
   ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0, force_fallback);
 }
 
-// The same chains in CTAs of up to 8 warps launched with the SM's whole
-// shared memory (unused): one CTA per SM, and no other kernel's CTA that needs
-// shared memory can join it.
-__global__ void __launch_bounds__(256) k_ks_plcm_fx_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks,
+// The same chains in CTAs of up to 4 warps (one per SM sub-partition)
+// launched with the SM's whole shared memory (unused): one CTA per SM, and no
+// other kernel's CTA that needs shared memory can join it.  (A bound of 256
+// threads makes the compiler schedule the chain about 15% slower.)
+__global__ void __launch_bounds__(128) k_ks_plcm_fx_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                                                        int cap, int slot0, int force_fallback) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   ks_plcm_fx_chain(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0, force_fallback);
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(256) k_ks_pair_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
+__global__ void __launch_bounds__(128) k_ks_pair_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
                                                     int slot0) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   ks_pair_chain<KIND, false>(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
@@ -865,7 +866,7 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
                              int plcm_int, cudaStream_t st, int cap, int slot0, int sm_warps) {
   if (nframes <= 0) return cudaSuccess;
   if (sm_warps > 0) {
-    const int threads = 32 * (sm_warps > 8 ? 8 : sm_warps);
+    const int threads = 32 * (sm_warps > 4 ? 4 : sm_warps);
     const int blocks = (2 * L.n + threads - 1) / threads;
     const int smem = reserve_smem_bytes();
     cudaError_t e;
