@@ -30,6 +30,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# k_ks_plcm_fx_sm: warp instructions per iterate and lane (ncu) and the
+# dependency chain of one iterate in cycles (clock64 probe of plcm_fx_step)
+PLCM_INSTR_PER_ITER = 115.0
+PLCM_ITER_CYCLES = 251.0
+# its DRAM read + write bytes per frame of keystream (ncu, 40-frame launch at
+# 768x768x3, n = 4096): scaled to the bench's launches by their frames
+PLCM_KS_DRAM_BYTES_PER_FRAME = (797_952 + 297_627_648) / 40
+
 METRIC = "5-round enc Mpixel/s"
 
 
@@ -335,17 +343,36 @@ def run_ours(a) -> None:
     else:
         iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 keystream bytes
     achieved_iter = iters / (ks_ms_step * 1e-3)
-    # FP64 ceiling: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz = 629e9 FP64 instr/s;
-    # binary64 instructions per map iteration (branch-free PLCM: 2 compares,
-    # 2 subtractions, one IEEE division of ~8 FP64 instructions) ~ 12.
-    fp64_per_iter = 12.0 if a.map == "plcm" else 60.0
-    peak_fp64 = 152 * 2 * 2.07e9
-    peak_iter = peak_fp64 / fp64_per_iter
-    roofline = {"bound": "alu", "kernel": "k_keystream", "unit": "Giter/s",
-                "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
-                "frac": round(achieved_iter / peak_iter, 4), "traffic": None,
-                "peak_basis": f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration",
-                "launch_ms": round(ks_ms, 3), "launches_per_step": ks_launches // max(1, a.steps)}
+    clock = 2.07e9  # maximum SM clock (Hz)
+    if a.map == "plcm":
+        # integer-pipe kernel: issue ceiling = 152 SMs x 4 schedulers x 1 warp
+        # instruction per clock x 32 lanes / warp instructions per iterate and lane
+        # (ncu count for k_ks_plcm_fx_sm at this workload, profiles/)
+        instr_per_iter = PLCM_INSTR_PER_ITER
+        peak_iter = 152 * 4 * clock * 32 / instr_per_iter
+        basis = (f"integer issue: 152 SM x 4 schedulers x 2.07 GHz x 32 lanes / {instr_per_iter:.0f} "
+                 f"instructions per iterate")
+        # what binds at this chain count: 2n chains, each one dependent iterate
+        # after another (PLCM_ITER_CYCLES: one iterate's dependency chain, clock64 probe)
+        chains = 2 * a.n
+        lat = {"chains": chains, "cycles_per_iterate": PLCM_ITER_CYCLES,
+               "ceiling": round(chains * clock / PLCM_ITER_CYCLES / 1e9, 4),
+               "frac": round(achieved_iter / (chains * clock / PLCM_ITER_CYCLES), 4)}
+    else:
+        # binary64 kernel: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz over ~60 binary64
+        # instructions per 2DLASM iterate (two csin of a degree-17/16 Horner chain)
+        fp64_per_iter = 60.0
+        peak_iter = 152 * 2 * clock / fp64_per_iter
+        basis = f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration"
+        lat = None
+    per_launch = ks_launches // max(1, a.steps)
+    traffic = None
+    if a.map == "plcm" and a.size == 768 and a.n == 4096 and a.rounds == 5:
+        traffic = round(PLCM_KS_DRAM_BYTES_PER_FRAME * F / per_launch)
+    roofline = {"bound": "alu", "kernel": "k_ks_plcm_fx_sm" if a.map == "plcm" else "k_ks_pair_sm<2DLASM>",
+                "unit": "Giter/s", "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
+                "frac": round(achieved_iter / peak_iter, 4), "traffic": traffic, "peak_basis": basis,
+                "latency_bound": lat, "launch_ms": round(ks_ms, 3), "launches_per_step": per_launch}
     hbm = peaks.get("hbm_gbs")
     alg_bytes = 2 * N * F  # plaintext read once + ciphertext written once
     split = {"keystream_ms": round(ks_ms_step, 3), "rounds_ms": round(rd_ms, 3), "schedule_ms": round(sc_ms, 3),
