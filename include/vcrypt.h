@@ -237,9 +237,18 @@ int enc_sync_status(vc_ctx* ctx);
  *                  highest priority, so that the round kernels of the previous
  *                  pass run on the other SMs instead of taking issue slots from
  *                  the latency-bound chains; 0 lets both share every SM on a
- *                  normal-priority stream; -1 (default) takes 4 warps (one per
- *                  SM sub-partition) when overlapping and those CTAs fill at
- *                  most half of the SMs, else 0.
+ *                  normal-priority stream; -1 (default) chooses when
+ *                  overlapping: PLCM 4 warps (one per SM sub-partition) if
+ *                  those CTAs fill at most half of the SMs; 2DLASM (bound by
+ *                  the SM's binary64 pipe) 2 warps if at least an eighth of
+ *                  the SMs stay free, else as PLCM; otherwise 0.
+ * VC_OPT_RUNAHEAD_CALLS: 1 (default) with overlap: at the end of a call the
+ *                  keystream of the next call's first pass is generated on the
+ *                  internal stream, so it overlaps this call's last rounds; the
+ *                  chain state from before it is kept on the device, and a
+ *                  checkpoint, a batch, or an option that reallocates scratch
+ *                  first undoes it exactly (nothing is observable but time);
+ *                  0 turns it off (and undoes one that is pending).
  * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
@@ -247,6 +256,7 @@ int enc_sync_status(vc_ctx* ctx);
 #define VC_OPT_OVERLAP 4
 #define VC_OPT_TILE_ROWS 5
 #define VC_OPT_KS_SM_WARPS 6
+#define VC_OPT_RUNAHEAD_CALLS 7
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */

@@ -147,6 +147,13 @@ struct vc_ctx {
   int64_t nprod = 0;
   int64_t produced_done = 0;  // frames known complete on the device
   int64_t passes = 0;
+  // keystream run-ahead across calls: at the end of a call the first pass of
+  // the next one (spec_frames frames) is generated into buffer spec_b; the next
+  // call's rounds take its frames (spec_used so far).  d_snap holds the chain
+  // state from before it, so that it can be undone exactly.
+  bool spec_enabled = true;
+  int spec_b = -1, spec_frames = 0, spec_used = 0;
+  uint8_t* d_snap = nullptr;
   // staging for host-buffer calls
   uint8_t* d_io[2] = {nullptr, nullptr};
   int io_cap = 0;
@@ -193,8 +200,12 @@ void free_scratch(vc_ctx* c) {
   c->cap = 0;
 }
 
+int spec_rollback(vc_ctx* c);
+
 int ensure_scratch(vc_ctx* c, int frames) {
   if (frames <= c->cap) return VC_OK;
+  int rc = spec_rollback(c);
+  if (rc) return rc;
   sync_all(c);
   free_scratch(c);
   const Layout& L = c->L;
@@ -280,12 +291,20 @@ struct StageMark {
   }
 };
 
-// Warps per SM-holding keystream CTA for this context (0: shared SMs).
+// Warps per SM-holding keystream CTA for this context (0: shared SMs).  PLCM
+// chains are latency-bound: 4 warps (one per scheduler) per SM when those CTAs
+// leave half the SMs to the rounds.  2DLASM chains are bound by the SM's
+// binary64 pipe: 2 warps per SM when at least an eighth of the SMs stay free.
 int ks_warps_in_use(const vc_ctx* c) {
   if (c->ks_sm_warps >= 0) return c->ks_sm_warps;
   if (!c->overlap) return 0;
-  const int ctas = (2 * c->L.n + 127) / 128;
-  return 2 * ctas <= c->num_sms ? 4 : 0;
+  const int lanes = 2 * c->L.n;
+  if (c->kind == VC_2DLASM) {
+    const int ctas2 = (lanes + 63) / 64;
+    if (ctas2 + (c->num_sms + 7) / 8 <= c->num_sms) return 2;
+  }
+  const int ctas4 = (lanes + 127) / 128;
+  return 2 * ctas4 <= c->num_sms ? 4 : 0;
 }
 
 // Keystream side of a pass into buffer b: s_c and shift tables (Alg. 1), then
@@ -336,44 +355,171 @@ int end_pass(vc_ctx* c, int b, cudaStream_t st) {
   return VC_OK;
 }
 
-// One pass over nf <= cap frames (encrypt when dir == 0).  in/out strides in bytes.
-int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride, int nf,
-             cudaStream_t st) {
+// The rounds of one pass over nf frames whose keystream, s_c and shift tables
+// are frames f_off .. f_off + nf - 1 of buffer b (encrypt when dir == 0).
+// in/out strides in bytes.
+int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride,
+                int nf, cudaStream_t st, int b, int f_off) {
   const Layout& L = c->L;
   const vc::Tables tb = c->tables();
   const long long ks_stride = (long long)L.rounds * L.Npad;
+  const uint8_t* ksb = c->d_ks[b] + (long long)f_off * ks_stride;
+  const int* kmod = c->d_kmod[b] + (long long)f_off * L.H;
+  const int r = L.rounds;
+  StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
+  // with one round and in == out, the round cannot write its own input: go through a buffer
+  const bool bounce = (r == 1) && (in == out);
+  uint8_t* final_out = bounce ? c->d_buf[0] : out;
+  const long long final_stride = bounce ? L.Npad : out_stride;
+  for (int step = 0; step < r; step++) {
+    const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
+    const long long ss = step == 0 ? in_stride : L.Npad;
+    uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
+    const long long ds = step == r - 1 ? final_stride : L.Npad;
+    if (dir == 0) {
+      const int j = step;
+      VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
+                                   step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
+    } else {
+      const int j = r - 1 - step;
+      VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod, nf, st));
+    }
+  }
+  if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
+  if (bounce)
+    VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
+                              cudaMemcpyDeviceToDevice, st));
+  return VC_OK;
+}
+
+// One pass over nf <= cap frames (encrypt when dir == 0).  in/out strides in bytes.
+int run_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride, int nf,
+             cudaStream_t st) {
   int rc = VC_OK;
   const int b = begin_pass(c, nf, st, &rc);
   if (rc) return rc;
-  const uint8_t* ksb = c->d_ks[b];
-  const int* kmod = c->d_kmod[b];
-  const int r = L.rounds;
-  {
-    StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
-    // with one round and in == out, the round cannot write its own input: go through a buffer
-    const bool bounce = (r == 1) && (in == out);
-    uint8_t* final_out = bounce ? c->d_buf[0] : out;
-    const long long final_stride = bounce ? L.Npad : out_stride;
-    for (int step = 0; step < r; step++) {
-      const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
-      const long long ss = step == 0 ? in_stride : L.Npad;
-      uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
-      const long long ds = step == r - 1 ? final_stride : L.Npad;
-      if (dir == 0) {
-        const int j = step;
-        VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
-                                     step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
-      } else {
-        const int j = r - 1 - step;
-        VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod, nf, st));
-      }
-    }
-    if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
-    if (bounce)
-      VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
-                                cudaMemcpyDeviceToDevice, st));
-  }
+  rc = rounds_pass(c, dir, in, in_stride, out, out_stride, nf, st, b, 0);
+  if (rc) return rc;
   return end_pass(c, b, st);
+}
+
+// ---- keystream run-ahead across calls ----
+
+// [MainPrbg][chain state][carries][carry lengths], each 256-byte aligned
+size_t snap_part(size_t v) { return (v + 255) & ~(size_t)255; }
+size_t snap_bytes(const vc_ctx* c) {
+  const size_t n = (size_t)c->L.n;
+  return snap_part(sizeof(vc::MainPrbg)) + snap_part(n * sizeof(double) * c->state_words()) +
+         snap_part(n * 2 * sizeof(uint64_t)) + snap_part(n * sizeof(int));
+}
+
+// Copy the chain state to (save) or from (!save) the snapshot, on stream s.
+int snap_copy(vc_ctx* c, bool save, cudaStream_t s) {
+  const size_t n = (size_t)c->L.n;
+  void* live[4] = {c->d_main, c->d_st, c->d_carry, c->d_carry_len};
+  const size_t sz[4] = {sizeof(vc::MainPrbg), n * sizeof(double) * c->state_words(), n * 2 * sizeof(uint64_t),
+                        n * sizeof(int)};
+  uint8_t* p = c->d_snap;
+  for (int k = 0; k < 4; k++) {
+    VC_CUDA(cudaMemcpyAsync(save ? (void*)p : live[k], save ? live[k] : (const void*)p, sz[k],
+                            cudaMemcpyDeviceToDevice, s));
+    p += snap_part(sz[k]);
+  }
+  return VC_OK;
+}
+
+// At the end of a call: generate the keystream of the next call's first pass
+// (nf frames) on ks_stream, keeping the state from before it.
+int spec_issue(vc_ctx* c, int nf) {
+  if (!c->overlap || !c->spec_enabled || c->spec_frames > 0 || nf <= 0 || nf > c->cap ||
+      c->produced != c->frame)
+    return VC_OK;
+  if (!c->d_snap) {
+    if (cudaMalloc(&c->d_snap, snap_bytes(c)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_snap = nullptr;
+      return VC_OK;  // no run-ahead without room for the snapshot
+    }
+  }
+  const int b = (int)(c->passes & 1);
+  cudaStream_t ks = c->ks_stream;
+  VC_CUDA(cudaStreamWaitEvent(ks, c->ev_rd[b], 0));
+  int rc = snap_copy(c, true, ks);
+  if (rc) return rc;
+  rc = keystream_stage(c, b, nf, ks);
+  if (rc) return rc;
+  VC_CUDA(cudaEventRecord(c->ev_ks[b], ks));
+  c->passes++;
+  c->spec_b = b;
+  c->spec_frames = nf;
+  c->spec_used = 0;
+  return VC_OK;
+}
+
+// Rounds of nf (<= the frames left) run-ahead frames.
+int spec_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride,
+              int nf, cudaStream_t st) {
+  const int b = c->spec_b;
+  VC_CUDA(cudaStreamWaitEvent(st, c->ev_ks[b], 0));
+  int rc = rounds_pass(c, dir, in, in_stride, out, out_stride, nf, st, b, c->spec_used);
+  if (rc) return rc;
+  rc = end_pass(c, b, st);
+  if (rc) return rc;
+  c->spec_used += nf;
+  if (c->spec_used == c->spec_frames) {
+    c->spec_frames = c->spec_used = 0;
+    c->spec_b = -1;
+  }
+  return VC_OK;
+}
+
+// Undo the run-ahead: the state returns to frame c->frame (the snapshot, then
+// the keystream of the frames already taken once more).
+int spec_rollback(vc_ctx* c) {
+  if (c->spec_frames == 0) return VC_OK;
+  cudaStream_t ks = c->ks_stream;
+  int rc = snap_copy(c, false, ks);
+  if (rc) return rc;
+  if (c->spec_used > 0) {
+    VC_CUDA(cudaStreamWaitEvent(ks, c->ev_rd[c->spec_b], 0));
+    rc = keystream_stage(c, c->spec_b, c->spec_used, ks);
+    if (rc) return rc;
+  }
+  VC_CUDA(cudaStreamSynchronize(ks));
+  c->spec_frames = c->spec_used = 0;
+  c->spec_b = -1;
+  return VC_OK;
+}
+
+// Drop the run-ahead whose state is about to be overwritten.
+void spec_discard(vc_ctx* c) {
+  if (c->spec_frames == 0) return;
+  cudaStreamSynchronize(c->ks_stream);
+  c->spec_frames = c->spec_used = 0;
+  c->spec_b = -1;
+}
+
+// Pass sizes of a call: first the run-ahead frames still held (first_spec),
+// then the plan of the rest.  *next_first: the first pass of a call of the same
+// size, the run-ahead to issue at its end.
+void call_plan(const vc_ctx* c, int nframes, int F, std::vector<int>& plan, bool* first_spec, int* next_first) {
+  plan.clear();
+  *first_spec = false;
+  int rest = nframes;
+  if (c->spec_frames > c->spec_used) {
+    const int k = std::min(c->spec_frames - c->spec_used, nframes);
+    plan.push_back(k);
+    *first_spec = true;
+    rest -= k;
+  }
+  std::vector<int> tail;
+  if (rest > 0) {
+    pass_plan(c, rest, F, tail);
+    plan.insert(plan.end(), tail.begin(), tail.end());
+  }
+  std::vector<int> full;
+  pass_plan(c, nframes, F, full);
+  *next_first = full.empty() ? 0 : full[0];
 }
 
 // Single-stream calls generate the keystream inline: not while a batcher holds
@@ -417,17 +563,21 @@ int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nf
   if (rc) return rc;
   const long long N = c->L.N;
   std::vector<int> plan;
-  pass_plan(c, nframes, F, plan);
+  bool first_spec = false;
+  int next_first = 0;
+  call_plan(c, nframes, F, plan, &first_spec, &next_first);
   long long f0 = 0;
-  for (const int nf : plan) {
-    rc = run_pass(c, dir, d_in + f0 * N, N, d_out + f0 * N, N, nf, st);
+  for (size_t k = 0; k < plan.size(); k++) {
+    const int nf = plan[k];
+    rc = (k == 0 && first_spec) ? spec_pass(c, dir, d_in + f0 * N, N, d_out + f0 * N, N, nf, st)
+                                : run_pass(c, dir, d_in + f0 * N, N, d_out + f0 * N, N, nf, st);
     if (rc) return rc;
     f0 += nf;
   }
   c->frame += nframes;
   c->produced = c->frame;
   c->produced_done = c->frame;
-  return VC_OK;
+  return spec_issue(c, next_first);
 }
 
 }  // namespace
@@ -577,7 +727,22 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   cudaEvent_t* h2d = c->ev;      // [2]
   cudaEvent_t* done = c->ev + 2; // [2]
   std::vector<int> plan;
-  pass_plan(c, nframes, F, plan);
+  bool first_spec = false;
+  int next_first = 0;
+  call_plan(c, nframes, F, plan, &first_spec, &next_first);
+  if (c->io_cap < plan[0]) {  // a run-ahead pass can be larger than this call's passes
+    cudaStreamSynchronize(c->copy_stream);
+    cudaFree(c->d_io[0]);
+    cudaFree(c->d_io[1]);
+    c->d_io[0] = c->d_io[1] = nullptr;
+    c->io_cap = 0;
+    if (cudaMalloc(&c->d_io[0], plan[0] * N) != cudaSuccess || cudaMalloc(&c->d_io[1], plan[0] * N) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("staging allocation failed");
+      return VC_ERR_OOM;
+    }
+    c->io_cap = plan[0];
+  }
   long long f0 = 0;
   for (int k = 0; k < (int)plan.size(); f0 += plan[k], k++) {
     const int nf = plan[k];
@@ -585,17 +750,20 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
     VC_CUDA(cudaMemcpyAsync(buf, h_in + (size_t)f0 * N, nf * N, cudaMemcpyHostToDevice, c->copy_stream));
     VC_CUDA(cudaEventRecord(h2d[k & 1], c->copy_stream));
     VC_CUDA(cudaStreamWaitEvent(st, h2d[k & 1], 0));
-    rc = run_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st);
+    rc = (k == 0 && first_spec) ? spec_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st)
+                                : run_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st);
     if (rc) return rc;
     VC_CUDA(cudaEventRecord(done[k & 1], st));
     VC_CUDA(cudaStreamWaitEvent(c->copy_stream, done[k & 1], 0));
     VC_CUDA(cudaMemcpyAsync(h_out + (size_t)f0 * N, buf, nf * N, cudaMemcpyDeviceToHost, c->copy_stream));
   }
-  VC_CUDA(cudaStreamSynchronize(c->copy_stream));
-  VC_CUDA(cudaStreamSynchronize(st));
   c->frame += nframes;
   c->produced = c->frame;
   c->produced_done = c->frame;
+  rc = spec_issue(c, next_first);
+  if (rc) return rc;
+  VC_CUDA(cudaStreamSynchronize(c->copy_stream));
+  VC_CUDA(cudaStreamSynchronize(st));
   return VC_OK;
 }
 
@@ -620,6 +788,7 @@ int enc_save_state(vc_ctx* c, void* buf, size_t* len) {
     return VC_ERR_ARG;
   }
   if (int rg = check_no_runahead(c)) return rg;
+  if (int rs = spec_rollback(c)) return rs;
   sync_all(c);
   VC_CUDA(cudaGetLastError());
   const size_t n = (size_t)c->L.n;
@@ -657,6 +826,7 @@ int enc_load_state(vc_ctx* c, const void* buf, size_t len) {
     return VC_ERR_STATE;
   }
   sync_all(c);
+  spec_discard(c);
   const size_t n = (size_t)c->L.n;
   const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof(h);
   VC_CUDA(cudaMemcpy(c->d_main, p, sizeof(vc::MainPrbg), cudaMemcpyHostToDevice));
@@ -737,11 +907,23 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (value != 1 && value != 2) return VC_ERR_ARG;
       c->ks_lanes = (int)value;
       return VC_OK;
-    case VC_OPT_OVERLAP:
+    case VC_OPT_OVERLAP: {
       if (value != 0 && value != 1) return VC_ERR_ARG;
+      int rs = spec_rollback(c);
+      if (rs) return rs;
       sync_all(c);
       c->overlap = value != 0;
       return VC_OK;
+    }
+    case VC_OPT_RUNAHEAD_CALLS: {
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      if (value == 0) {
+        int rs = spec_rollback(c);
+        if (rs) return rs;
+      }
+      c->spec_enabled = value != 0;
+      return VC_OK;
+    }
     case VC_OPT_KS_SM_WARPS: {
       if (value < -1 || value > 4) return VC_ERR_ARG;
       sync_all(c);
@@ -758,6 +940,8 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && (value < 1 || value > 32 || (value & (value - 1)))) return VC_ERR_ARG;
       Layout L2{};
       if (make_layout(c->user_layout, &L2, (int)value) != VC_OK) return VC_ERR_ARG;
+      int rs = spec_rollback(c);
+      if (rs) return rs;
       sync_all(c);
       int* fl = nullptr;
       if (cudaMalloc(&fl, sizeof(int) * L2.NT) != cudaSuccess) {
@@ -789,6 +973,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
     case VC_OPT_OVERLAP: *value = c->overlap ? 1 : 0; return VC_OK;
     case VC_OPT_TILE_ROWS: *value = c->L.T; return VC_OK;
     case VC_OPT_KS_SM_WARPS: *value = c->ks_sm_warps; return VC_OK;
+    case VC_OPT_RUNAHEAD_CALLS: *value = c->spec_enabled ? 1 : 0; return VC_OK;
   }
   return VC_ERR_ARG;
 }
@@ -828,6 +1013,7 @@ void enc_destroy(vc_ctx* c) {
   cudaFree(c->ring_ks);
   cudaFree(c->ring_sc);
   cudaFree(c->ring_kmod);
+  cudaFree(c->d_snap);
   delete c;
 }
 
@@ -857,7 +1043,9 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
   cudaStream_t st = (cudaStream_t)stream;
   const Layout& L = c->L;
   const int F = pass_frames(c, nframes);
-  int rc = ensure_scratch(c, F);
+  int rc = spec_rollback(c);
+  if (rc) return rc;
+  rc = ensure_scratch(c, F);
   if (rc) return rc;
   rc = enter(c, st);
   if (rc) return rc;
@@ -962,6 +1150,8 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
   }
   if (nframes == 0) return VC_OK;
   int rc = check_no_runahead(c);
+  if (rc) return rc;
+  rc = spec_rollback(c);  // keystream this context generated ahead for its next call
   if (rc) return rc;
   void* base = nullptr;
   rc = static_scratch_address(&base);
@@ -1360,7 +1550,12 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
   }
   const int nj = (int)live.size();
   if (nj == 0) return VC_OK;
-  int rc = grow_lane(b->cons, nj);
+  int rc = VC_OK;
+  for (int k = 0; k < nj; k++) {  // single-stream calls' keystream generated ahead: undone
+    rc = spec_rollback(jobs[live[k]].ctx);
+    if (rc) return rc;
+  }
+  rc = grow_lane(b->cons, nj);
   if (rc) return rc;
   if (pool_need > b->pool_cap) {
     cudaDeviceSynchronize();
@@ -1493,7 +1688,9 @@ int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
       set_err("prefetch: null or repeated context");
       return VC_ERR_ARG;
     }
-    int rc = ensure_ring(c, 2 * A + 1);
+    int rc = spec_rollback(c);
+    if (rc) return rc;
+    rc = ensure_ring(c, 2 * A + 1);
     if (rc) return rc;
     // the next frame on its own (ready soonest), then the rest of the run-ahead
     // queued behind it; a repeated call while a production is in flight adds
