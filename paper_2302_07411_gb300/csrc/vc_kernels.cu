@@ -1423,6 +1423,22 @@ cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long
 // Y is elementwise in the ciphertext C of the round: y_q = (b xor c_q xor c_{q-1}) - b,
 // with c_{q-1} replaced at a subframe start by the seed y of the last byte of
 // the next subframe (itself a non-first byte, so computable the same way).
+// Byte-wise a - b mod 256 in each of the eight bytes of a word.
+__device__ __forceinline__ uint64_t vsub8(uint64_t a, uint64_t b) {
+  constexpr uint64_t Hb = 0x8080808080808080ull;
+  return ((a | Hb) - (b & ~Hb)) ^ ((a ^ ~b) & Hb);
+}
+
+// Decryption round (Eq. 4 then Eq. 2), one CTA per (row band of the output
+// frame X, frame): X[a][o] = Y[alpha][beta] with alpha = (a + o) mod H and
+// beta = (o + k(alpha)) mod W, where y_q = ((b ^ c_q ^ c_{q-1}) - b) mod 256 and,
+// at a subframe start, c_{q-1} is replaced by the seed: the decrypted byte at
+// the end of the next subframe (reading R10; never itself a start, S_i >= 2).
+// Band row tt takes one pixel from every ciphertext row, so the lanes of a
+// warp read runs of consecutive pixels of a row.  Four rows are handled per
+// iteration in phases (row shifts, then ciphertext and
+// keystream words, then the result) so that a lane keeps several rows of
+// loads in flight instead of one dependent round trip per row.
 template <int C>
 __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
   const Layout& L = A.L;
@@ -1439,33 +1455,93 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   const int rpw = 32 / L.T;
   const int tt = lane & (L.T - 1);
   const int sub = lane / L.T;
-  for (int alpha = warp * rpw + sub; alpha < L.H; alpha += nw * rpw) {
-    if (tt >= Te) continue;
-    int o = alpha - (a0 + tt);
-    if (o < 0) o += L.H;
-    const int km = __ldg(&kmod[alpha]);
-    for (; o < L.W; o += L.H) {
-      int beta = o + km;
-      if (beta >= L.W) beta -= L.W;
-      const int pix = alpha * L.W + beta;
-      const int qb = pix * C;
-      uint8_t prev;
-      if ((__ldg(&A.tb.sbits[pix >> 5]) >> (pix & 31)) & 1u) {
-        const int wq = pix >> 5;
-        const int s = __ldg(&A.tb.srank[wq]) + __popc(__ldg(&A.tb.sbits[wq]) & ((1u << (pix & 31)) - 1u));
-        const int nx = (s + 1 == L.n) ? 0 : s + 1;
-        const int sb = C * __ldg(&A.tb.pi[nx + 1]) - 1;
-        const uint8_t bs = KS[sb];
-        prev = (uint8_t)((uint8_t)(bs ^ Cin[sb] ^ Cin[sb - 1]) - bs);
-      } else {
-        prev = Cin[qb - 1];
+  const int astep = nw * rpw;
+  auto decrypt_pixel = [&](int pix, int o, uint32_t sw) {
+    const int qb = pix * C;
+    uint8_t prev;
+    if ((sw >> (pix & 31)) & 1u) {  // subframe start: the seed
+      const int s = __ldg(&A.tb.srank[pix >> 5]) + __popc(sw & ((1u << (pix & 31)) - 1u));
+      const int nx = (s + 1 == L.n) ? 0 : s + 1;
+      const int sb = C * __ldg(&A.tb.pi[nx + 1]) - 1;
+      const uint8_t bs = KS[sb];
+      prev = (uint8_t)((uint8_t)(bs ^ Cin[sb] ^ Cin[sb - 1]) - bs);
+    } else {
+      prev = Cin[qb - 1];
+    }
+    uint8_t* dst = Xt + tt * rowb + o * C;
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+      const uint8_t cq = Cin[qb + c];
+      const uint8_t b = KS[qb + c];
+      dst[c] = (uint8_t)((uint8_t)(b ^ cq ^ prev) - b);
+      prev = cq;
+    }
+  };
+  // ciphertext bytes q-1 .. q+C-1 and keystream bytes q .. q+C-1 of a pixel as
+  // two aligned words each (frame bases 4-byte aligned, away from the frame
+  // ends); bytes one by one otherwise
+  const bool words = ((reinterpret_cast<uintptr_t>(Cin) | reinterpret_cast<uintptr_t>(KS)) & 3) == 0;
+  if (L.W <= L.H) {
+    // one pixel per ciphertext row and band row, U rows per iteration
+    constexpr int U = 4;
+    for (int alpha = warp * rpw + sub; alpha < L.H; alpha += U * astep) {
+      int pix[U], ov[U];
+      uint32_t c0[U], c1[U], k0[U], k1[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int al = alpha + u * astep;
+        int o = al - (a0 + tt);
+        if (o < 0) o += L.H;
+        ov[u] = (tt < Te && al < L.H && o < L.W) ? o : -1;
+        int beta = 0;
+        if (ov[u] >= 0) {
+          beta = o + __ldg(&kmod[al]);
+          if (beta >= L.W) beta -= L.W;
+        }
+        pix[u] = al * L.W + beta;
       }
 #pragma unroll
-      for (int c = 0; c < C; c++) {
-        const uint8_t cq = Cin[qb + c];
-        const uint8_t b = KS[qb + c];
-        Xt[tt * rowb + o * C + c] = (uint8_t)((uint8_t)(b ^ cq ^ prev) - b);
-        prev = cq;
+      for (int u = 0; u < U; u++) {
+        const int qb = pix[u] * C;
+        if (ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
+          const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - 1) & ~3));
+          const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
+          c0[u] = __ldg(cw);
+          c1[u] = __ldg(cw + 1);
+          k0[u] = __ldg(kw);
+          k1[u] = __ldg(kw + 1);
+        } else {
+          c0[u] = c1[u] = k0[u] = k1[u] = 0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (ov[u] < 0) continue;
+        const int p = pix[u], qb = p * C;
+        const uint32_t sw = __ldg(&A.tb.sbits[p >> 5]);
+        if (((sw >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
+          decrypt_pixel(p, ov[u], sw);
+          continue;
+        }
+        const uint64_t c = ((uint64_t)c1[u] << 32 | c0[u]) >> (8 * ((qb - 1) & 3));
+        const uint64_t b = ((uint64_t)k1[u] << 32 | k0[u]) >> (8 * (qb & 3));
+        const uint64_t y = vsub8(b ^ (c >> 8) ^ c, b);
+        uint8_t* dst = Xt + tt * rowb + ov[u] * C;
+#pragma unroll
+        for (int k = 0; k < C; k++) dst[k] = (uint8_t)(y >> (8 * k));
+      }
+    }
+  } else {
+    for (int alpha = warp * rpw + sub; alpha < L.H; alpha += astep) {
+      if (tt >= Te) continue;
+      int o = alpha - (a0 + tt);
+      if (o < 0) o += L.H;
+      const int km = __ldg(&kmod[alpha]);
+      for (; o < L.W; o += L.H) {
+        int beta = o + km;
+        if (beta >= L.W) beta -= L.W;
+        const int pix = alpha * L.W + beta;
+        decrypt_pixel(pix, o, __ldg(&A.tb.sbits[pix >> 5]));
       }
     }
   }
@@ -1473,14 +1549,14 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   // write the tile's rows (contiguous bytes)
   const int tstart = a0 * rowb;
   const int nb = Te * rowb;
-  uint8_t* dst = Out + tstart;
-  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+  uint8_t* dstg = Out + tstart;
+  if ((reinterpret_cast<uintptr_t>(dstg) & 15) == 0) {
     const int nvec = nb >> 4;
     for (int k = threadIdx.x; k < nvec; k += blockDim.x)
-      reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(Xt)[k];
-    for (int k = nvec * 16 + threadIdx.x; k < nb; k += blockDim.x) dst[k] = Xt[k];
+      reinterpret_cast<uint4*>(dstg)[k] = reinterpret_cast<const uint4*>(Xt)[k];
+    for (int k = nvec * 16 + threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
   } else {
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) dst[k] = Xt[k];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
   }
 }
 
@@ -1579,7 +1655,7 @@ __device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step
   const int r = L.rounds;
   const int jr = d.dir == 0 ? step : r - 1 - step;
   const int slot = job_slot(d, f);
-  RoundArgs A;
+  RoundArgs A{};
   A.L = L;
   A.tb = d.tb;
   A.in_stride = step == 0 ? (long long)L.N : L.Npad;
