@@ -222,7 +222,7 @@ def serving_capacity() -> dict:
     from paper_2302_07411_gb300 import serve
 
     out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
-    b = serve.capacity("batch", 768, 768, counts=(16, 32, 64, 128, 256), seconds=3.0)
+    b = serve.capacity("batch", 768, 768, counts=(16, 32, 64, 96, 128, 160, 192, 224, 256), seconds=3.0)
     p = serve.capacity("perframe", 768, 768, counts=(2, 4, 8, 16), seconds=2.5)
     out["batched_streams"] = b["max_streams"]
     out["per_frame_streams"] = p["max_streams"]
