@@ -189,6 +189,51 @@ int vc_batch_ready(vc_batcher* b, const vc_ctx* ctx, int32_t nframes);
 /* Synchronise and free the batcher. */
 void vc_batcher_destroy(vc_batcher* b);
 
+/* ---- serving: the per-tick work of a continuous-batching loop ----
+ * Real time (Sec. 6): every frame of a stream must be done within its frame
+ * time (41.7 ms at 24 FPS).  A server holds many streams; each tick it takes,
+ * for every stream, the frames that have arrived by the stream's clock
+ * (frame k arrives at t_arrival + k / fps seconds after the server's
+ * creation) and, in batch mode, whose keystream run-ahead is on the device,
+ * and submits them as one ragged batch (mode 0) or as one encrypt_frames /
+ * decrypt_frames call per frame (mode 1, for comparison).  Per-frame latency =
+ * device completion time (CUDA event) - arrival time.  All calls are on the
+ * host thread that drives the loop.
+ *
+ * vc_server_create: max_frames_per_tick 1..64 (also the keystream run-ahead of
+ *   mode 0); stream = the CUDA stream the work is enqueued on.  Records the
+ *   time origin (synchronises it).  Errors: VC_ERR_ARG, VC_ERR_OOM, VC_ERR_CUDA.
+ * vc_server_add: registers a stream (the context stays owned by the caller and
+ *   must outlive its registration).  Frame k is read from frame k mod src_period
+ *   of d_src, which holds src_period + max_frames_per_tick - 1 frames of
+ *   frame_bytes bytes (so a tick's frames are contiguous), and written to frame
+ *   k mod ring_frames of d_ring.  *id receives the stream's handle.  Mode 0
+ *   starts producing its keystream.  Errors: VC_ERR_ARG (and those of
+ *   vc_batch_prefetch).
+ * vc_server_tick: now = seconds since creation (host clock); *frames_submitted
+ *   receives the number of frames submitted (may be 0).  Errors: those of
+ *   vc_batch_submit / encrypt_frames / decrypt_frames, VC_ERR_CUDA.
+ * vc_server_drain: returns up to cap completed frames (stream id, frame index,
+ *   arrival time in s, latency in ms), oldest first; block = 1 waits for the
+ *   oldest tick in flight.  Errors: VC_ERR_ARG, VC_ERR_CUDA.
+ * vc_server_stream_done: 1 when all frames_total frames of the stream have
+ *   completed, 0 otherwise, -VC_ERR_ARG for a bad handle.
+ * vc_server_remove: unregisters a stream (waits for its frames in flight);
+ *   the caller may then destroy its context.  Errors: VC_ERR_ARG.
+ * vc_server_inflight: ticks submitted and not yet drained. */
+typedef struct vc_server vc_server;
+int vc_server_create(int32_t mode, int32_t max_frames_per_tick, void* stream, vc_server** out);
+int vc_server_add(vc_server* s, vc_ctx* ctx, int32_t direction, int64_t frame_bytes, const uint8_t* d_src,
+                  int32_t src_period, uint8_t* d_ring, int32_t ring_frames, double fps, double t_arrival,
+                  int64_t frames_total, int32_t* id);
+int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted);
+int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int64_t* frames, double* arrival_s,
+                    double* latency_ms, int32_t* n);
+int vc_server_stream_done(const vc_server* s, int32_t id);
+int vc_server_remove(vc_server* s, int32_t id);
+int32_t vc_server_inflight(const vc_server* s);
+void vc_server_destroy(vc_server* s);
+
 /* Size in bytes of a checkpoint of the context's stream state (chaotic map
  * values, pending keystream bytes, PRBG_m, frame counter). */
 size_t enc_state_size(const vc_ctx* ctx);

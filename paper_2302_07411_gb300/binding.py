@@ -84,6 +84,16 @@ def lib():
             "vc_dbg_lasm": (C.c_int, [p, p, i64, p]),
             "vc_dbg_keystream": (C.c_int, [p, p, p, i32, p]),
             "vc_dbg_layout": (C.c_int, [p, p]),
+            "vc_server_create": (C.c_int, [i32, i32, p, p]),
+            "vc_server_add": (C.c_int, [p, p, i32, i64, p, i32, p, i32, C.c_double, C.c_double, i64,
+                                        C.POINTER(C.c_int32)]),
+            "vc_server_tick": (C.c_int, [p, C.c_double, C.POINTER(C.c_int32)]),
+            "vc_server_drain": (C.c_int, [p, i32, i32, p, p, p, p, C.POINTER(C.c_int32)]),
+            "vc_server_stream_done": (C.c_int, [p, i32]),
+            "vc_server_remove": (C.c_int, [p, i32]),
+            "vc_server_inflight": (i32, [p]),
+            "vc_server_destroy": (None, [p]),
+            "vc_dbg_server_stats": (C.c_int, [p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -359,6 +369,83 @@ class Batcher:
         if getattr(self, "b", None):
             vc_batcher_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NativeServer:
+    """Per-tick work of the serving loop in libvcrypt (vc_server_*): mode 0
+    batches every ready frame of every stream into one submission per tick,
+    mode 1 makes one encrypt/decrypt call per frame."""
+
+    def __init__(self, mode: int, max_frames_per_tick: int, stream):
+        import numpy as np
+
+        self._np = np
+        h = C.c_void_p()
+        _check(lib().vc_server_create(mode, max_frames_per_tick, _stream(stream), C.byref(h)), "vc_server_create")
+        self.s = h
+        self._cap = 4096
+        self._ids = np.empty(self._cap, dtype=np.int32)
+        self._frames = np.empty(self._cap, dtype=np.int64)
+        self._arr = np.empty(self._cap, dtype=np.float64)
+        self._lat = np.empty(self._cap, dtype=np.float64)
+
+    def add(self, cipher, direction: int, frame_bytes: int, d_src, src_period: int, d_ring, ring_frames: int,
+            fps: float, t_arrival: float, frames_total: int) -> int:
+        i = C.c_int32()
+        _check(lib().vc_server_add(self.s, cipher.ctx, direction, frame_bytes, _dptr(d_src), src_period, _dptr(d_ring),
+                                   ring_frames, fps, t_arrival, frames_total, C.byref(i)), "vc_server_add")
+        return i.value
+
+    def tick(self, now: float) -> int:
+        n = C.c_int32()
+        _check(lib().vc_server_tick(self.s, now, C.byref(n)), "vc_server_tick")
+        return n.value
+
+    def drain(self, block: bool = False):
+        """(ids, frame indices, arrival s, latency ms) of completed frames."""
+        np = self._np
+        out = [], [], [], []
+        while True:
+            n = C.c_int32()
+            _check(lib().vc_server_drain(self.s, 1 if block else 0, self._cap, self._ids.ctypes.data,
+                                         self._frames.ctypes.data, self._arr.ctypes.data, self._lat.ctypes.data,
+                                         C.byref(n)), "vc_server_drain")
+            k = n.value
+            for dst, src in zip(out, (self._ids, self._frames, self._arr, self._lat)):
+                dst.append(src[:k].copy())
+            if k < self._cap or not block and k == 0:
+                break
+        return tuple(np.concatenate(x) if x else np.empty(0) for x in out)
+
+    def stream_done(self, i: int) -> bool:
+        r = lib().vc_server_stream_done(self.s, i)
+        if r < 0:
+            raise VcError(-r, "vc_server_stream_done")
+        return r == 1
+
+    def remove(self, i: int) -> None:
+        _check(lib().vc_server_remove(self.s, i), "vc_server_remove")
+
+    def inflight(self) -> int:
+        return lib().vc_server_inflight(self.s)
+
+    def host_stats(self) -> dict:
+        """Host ms per part of the ticks since the last call (vc_dbg_server_stats)."""
+        ms = (C.c_double * 4)()
+        t = C.c_int64()
+        _check(lib().vc_dbg_server_stats(self.s, ms, C.byref(t)), "vc_dbg_server_stats")
+        return {"ticks": t.value, "clocks_ms": ms[0], "prefetch_ms": ms[1], "submit_ms": ms[2], "event_ms": ms[3]}
+
+    def close(self) -> None:
+        if getattr(self, "s", None):
+            lib().vc_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -1,0 +1,300 @@
+// vc_server.cu -- the per-tick work of a continuous-batching serving loop in
+// native code, on top of the library's public C ABI (vcrypt.h).
+//
+// The paper's target is real-time video (every frame of a 24 FPS stream within
+// its 41.7 ms frame time, Sec. 6).  A server holds many independent streams;
+// each tick it takes, for every stream, the frames that have arrived by its
+// frame clock and whose keystream run-ahead is ready, and submits them as one
+// ragged batch (vc_batch_submit: one launch per phase over all streams), or,
+// for comparison, as one encrypt_frames / decrypt_frames call per frame.
+// Completion is timed with CUDA events against an event recorded at creation,
+// so per-frame latency = device completion time - arrival time.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <deque>
+#include <vector>
+
+#include "vcrypt.h"
+#include "vcrypt_debug.h"
+
+namespace {
+
+struct SrvStream {
+  vc_ctx* ctx = nullptr;
+  int dir = 0;
+  long long N = 0;  // bytes per frame
+  const uint8_t* src = nullptr;
+  int src_period = 1;
+  uint8_t* ring = nullptr;
+  int ring_frames = 1;
+  double fps = 24.0, t_arr = 0.0;
+  int64_t total = 0, next = 0, done = 0;
+  bool active = false;
+};
+
+struct SrvFrame {
+  int32_t id;
+  int64_t frame;
+  double arrival;
+};
+
+struct SrvTick {
+  cudaEvent_t ev = nullptr;
+  std::vector<SrvFrame> frames;
+  size_t taken = 0;  // frames already returned by a partial drain
+};
+
+}  // namespace
+
+struct vc_server {
+  int mode = 0;  // 0 batch, 1 one call per frame
+  int maxf = 4;
+  cudaStream_t st = nullptr;
+  vc_batcher* b = nullptr;
+  cudaEvent_t t0 = nullptr;
+  std::vector<SrvStream> streams;
+  std::deque<SrvTick> inflight;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<vc_job> jobs;
+  std::vector<int32_t> job_stream;  // stream index of each job
+  std::vector<vc_ctx*> starved;
+  double host_ms[4] = {0, 0, 0, 0};  // readiness and job building, prefetch, submission, completion event
+  int64_t host_ticks = 0;
+};
+
+namespace {
+
+double ms_since(std::chrono::steady_clock::time_point a) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+}
+
+cudaEvent_t srv_event(vc_server* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vc_server_create(int32_t mode, int32_t max_frames_per_tick, void* stream, vc_server** out) {
+  if (!out || (mode != 0 && mode != 1) || max_frames_per_tick < 1 || max_frames_per_tick > 64) return VC_ERR_ARG;
+  *out = nullptr;
+  vc_server* s = new vc_server;
+  s->mode = mode;
+  s->maxf = max_frames_per_tick;
+  s->st = (cudaStream_t)stream;
+  if (mode == 0) {
+    int rc = vc_batcher_create(&s->b);
+    if (rc == VC_OK) rc = vc_batcher_set_option(s->b, VC_BOPT_RUNAHEAD, max_frames_per_tick);
+    if (rc != VC_OK) {
+      vc_server_destroy(s);
+      return rc;
+    }
+  }
+  if (cudaEventCreate(&s->t0) != cudaSuccess || cudaEventRecord(s->t0, s->st) != cudaSuccess ||
+      cudaEventSynchronize(s->t0) != cudaSuccess) {
+    cudaGetLastError();
+    vc_server_destroy(s);
+    return VC_ERR_CUDA;
+  }
+  *out = s;
+  return VC_OK;
+}
+
+int vc_server_add(vc_server* s, vc_ctx* ctx, int32_t direction, int64_t frame_bytes, const uint8_t* d_src,
+                  int32_t src_period, uint8_t* d_ring, int32_t ring_frames, double fps, double t_arrival,
+                  int64_t frames_total, int32_t* id) {
+  if (!s || !ctx || !id || (direction != 0 && direction != 1) || frame_bytes < 1 || !d_src || src_period < 1 ||
+      !d_ring || ring_frames < 1 || !(fps > 0.0) || frames_total < 1)
+    return VC_ERR_ARG;
+  SrvStream t;
+  t.ctx = ctx;
+  t.dir = direction;
+  t.N = frame_bytes;
+  t.src = d_src;
+  t.src_period = src_period;
+  t.ring = d_ring;
+  t.ring_frames = ring_frames;
+  t.fps = fps;
+  t.t_arr = t_arrival;
+  t.total = frames_total;
+  t.active = true;
+  if (s->mode == 0) {
+    vc_ctx* c = ctx;
+    int rc = vc_batch_prefetch(s->b, &c, 1);  // keystream of its first frames now
+    if (rc) return rc;
+  }
+  s->streams.push_back(t);
+  *id = (int32_t)(s->streams.size() - 1);
+  return VC_OK;
+}
+
+int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
+  if (!s) return VC_ERR_ARG;
+  if (frames_submitted) *frames_submitted = 0;
+  s->jobs.clear();
+  s->job_stream.clear();
+  s->starved.clear();
+  auto t_start = std::chrono::steady_clock::now();
+  s->host_ticks++;
+  SrvTick tick;
+  for (size_t i = 0; i < s->streams.size(); i++) {
+    SrvStream& t = s->streams[i];
+    if (!t.active || t.next >= t.total) continue;
+    int64_t arrived = (int64_t)std::floor((now - t.t_arr) * t.fps) + 1;
+    if (arrived > t.total) arrived = t.total;
+    int64_t m = arrived - t.next;
+    if (m <= 0) continue;
+    const int slot = (int)(t.next % t.ring_frames);
+    if (m > s->maxf) m = s->maxf;
+    if (m > t.ring_frames - slot) m = t.ring_frames - slot;
+    if (s->mode == 0) {
+      // only frames whose keystream is on the device: a stream whose keystream
+      // is still being produced does not hold up the others
+      while (m > 0) {
+        const int r = vc_batch_ready(s->b, t.ctx, (int32_t)m);
+        if (r < 0) return -r;
+        if (r == 1) break;
+        m--;
+      }
+      if (m == 0) {
+        s->starved.push_back(t.ctx);
+        continue;
+      }
+    }
+    const int k0 = (int)(t.next % t.src_period);
+    vc_job j;
+    j.ctx = t.ctx;
+    j.direction = t.dir;
+    j.d_in = t.src + (size_t)k0 * t.N;
+    j.d_out = t.ring + (size_t)slot * t.N;
+    j.nframes = (int32_t)m;
+    s->jobs.push_back(j);
+    s->job_stream.push_back((int32_t)i);
+    for (int64_t k = 0; k < m; k++) tick.frames.push_back(SrvFrame{(int32_t)i, t.next + k, t.t_arr + (t.next + k) / t.fps});
+    t.next += m;
+  }
+  s->host_ms[0] += ms_since(t_start);
+  t_start = std::chrono::steady_clock::now();
+  if (!s->starved.empty()) {  // no-op for a stream whose production is in flight
+    int rc = vc_batch_prefetch(s->b, s->starved.data(), (int32_t)s->starved.size());
+    if (rc) return rc;
+  }
+  s->host_ms[1] += ms_since(t_start);
+  if (s->jobs.empty()) return VC_OK;
+  t_start = std::chrono::steady_clock::now();
+  if (s->mode == 0) {
+    int rc = vc_batch_submit(s->b, s->jobs.data(), (int32_t)s->jobs.size(), s->st);
+    if (rc) return rc;
+  } else {
+    for (size_t q = 0; q < s->jobs.size(); q++) {
+      const vc_job& j = s->jobs[q];
+      const long long N = s->streams[s->job_stream[q]].N;
+      for (int k = 0; k < j.nframes; k++) {
+        const uint8_t* in = j.d_in + (size_t)k * N;
+        uint8_t* out = j.d_out + (size_t)k * N;
+        int rc = j.direction == 0 ? encrypt_frames(j.ctx, in, out, 1, s->st) : decrypt_frames(j.ctx, in, out, 1, s->st);
+        if (rc) return rc;
+      }
+    }
+  }
+  s->host_ms[2] += ms_since(t_start);
+  t_start = std::chrono::steady_clock::now();
+  tick.ev = srv_event(s);
+  if (!tick.ev || cudaEventRecord(tick.ev, s->st) != cudaSuccess) {
+    cudaGetLastError();
+    return VC_ERR_CUDA;
+  }
+  s->host_ms[3] += ms_since(t_start);
+  if (frames_submitted) *frames_submitted = (int32_t)tick.frames.size();
+  s->inflight.push_back(std::move(tick));
+  return VC_OK;
+}
+
+int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int64_t* frames, double* arrival_s,
+                    double* latency_ms, int32_t* n_out) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && (!ids || !frames || !arrival_s || !latency_ms))) return VC_ERR_ARG;
+  int32_t n = 0;
+  while (!s->inflight.empty() && n < cap) {
+    SrvTick& tk = s->inflight.front();
+    cudaError_t e = block ? cudaEventSynchronize(tk.ev) : cudaEventQuery(tk.ev);
+    if (e == cudaErrorNotReady) break;
+    if (e != cudaSuccess) return VC_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->t0, tk.ev) != cudaSuccess) return VC_ERR_CUDA;
+    const double done_s = ms / 1e3;
+    while (tk.taken < tk.frames.size() && n < cap) {
+      const SrvFrame& f = tk.frames[tk.taken++];
+      ids[n] = f.id;
+      frames[n] = f.frame;
+      arrival_s[n] = f.arrival;
+      latency_ms[n] = (done_s - f.arrival) * 1e3;
+      s->streams[f.id].done++;
+      n++;
+    }
+    if (tk.taken == tk.frames.size()) {
+      s->ev_pool.push_back(tk.ev);
+      s->inflight.pop_front();
+    }
+  }
+  *n_out = n;
+  return VC_OK;
+}
+
+int vc_server_stream_done(const vc_server* s, int32_t id) {
+  if (!s || id < 0 || id >= (int32_t)s->streams.size()) return -VC_ERR_ARG;
+  const SrvStream& t = s->streams[id];
+  return t.done >= t.total ? 1 : 0;
+}
+
+int vc_server_remove(vc_server* s, int32_t id) {
+  if (!s || id < 0 || id >= (int32_t)s->streams.size()) return VC_ERR_ARG;
+  SrvStream& t = s->streams[id];
+  if (t.done < t.next) {  // its frames still in flight: wait for them
+    for (const SrvTick& tk : s->inflight)
+      for (size_t k = tk.taken; k < tk.frames.size(); k++)
+        if (tk.frames[k].id == id) {
+          cudaEventSynchronize(tk.ev);
+          break;
+        }
+  }
+  t.active = false;
+  t.ctx = nullptr;
+  return VC_OK;
+}
+
+int32_t vc_server_inflight(const vc_server* s) { return s ? (int32_t)s->inflight.size() : 0; }
+
+int vc_dbg_server_stats(vc_server* s, double* ms4, int64_t* ticks) {
+  if (!s || !ms4 || !ticks) return VC_ERR_ARG;
+  for (int k = 0; k < 4; k++) {
+    ms4[k] = s->host_ms[k];
+    s->host_ms[k] = 0;
+  }
+  *ticks = s->host_ticks;
+  s->host_ticks = 0;
+  return VC_OK;
+}
+
+void vc_server_destroy(vc_server* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  for (SrvTick& tk : s->inflight)
+    if (tk.ev) cudaEventDestroy(tk.ev);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  if (s->t0) cudaEventDestroy(s->t0);
+  if (s->b) vc_batcher_destroy(s->b);
+  delete s;
+}
+
+}  // extern "C"
