@@ -36,11 +36,13 @@ int vc_dbg_keystream(vc_ctx* ctx, uint8_t* d_ks, int64_t* d_sc, int32_t nframes,
  * memory bytes}. */
 int vc_dbg_layout(const vc_ctx* ctx, int32_t* out8);
 
-/* Host milliseconds a vc_server spent per part of its ticks since the last
- * read (ms4: frame clocks, readiness and job building; prefetch of starved
- * streams; the submission; the completion event) and the ticks; resets them.
+/* Since the last read (then reset): host milliseconds a vc_server spent per
+ * part of its ticks (ms6[0..3]: frame clocks, readiness and job building;
+ * prefetch of starved streams; the submission; the completion event), the
+ * summed device milliseconds from each drained tick's first enqueued work to
+ * its completion (ms6[4]) over ms6[5] ticks, and the ticks (*ticks).
  * Errors: VC_ERR_ARG. */
-int vc_dbg_server_stats(vc_server* s, double* ms4, int64_t* ticks);
+int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks);
 
 #ifdef __cplusplus
 }

@@ -437,10 +437,11 @@ class NativeServer:
 
     def host_stats(self) -> dict:
         """Host ms per part of the ticks since the last call (vc_dbg_server_stats)."""
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * 6)()
         t = C.c_int64()
         _check(lib().vc_dbg_server_stats(self.s, ms, C.byref(t)), "vc_dbg_server_stats")
-        return {"ticks": t.value, "clocks_ms": ms[0], "prefetch_ms": ms[1], "submit_ms": ms[2], "event_ms": ms[3]}
+        return {"ticks": t.value, "clocks_ms": ms[0], "prefetch_ms": ms[1], "submit_ms": ms[2], "event_ms": ms[3],
+                "gpu_ms_per_tick": ms[4] / ms[5] if ms[5] else 0.0}
 
     def close(self) -> None:
         if getattr(self, "s", None):

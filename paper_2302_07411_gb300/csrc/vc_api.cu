@@ -1,6 +1,7 @@
 // vc_api.cu -- the C ABI of include/vcrypt.h and include/vcrypt_debug.h:
 // argument checks, device memory of a stream context, and the order of the
 // kernel launches of one pass (Alg. 1 / Alg. 2 on the GPU).
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -1236,7 +1237,7 @@ struct BatchLane {
   vc::BatchHdr* h_hdr[2] = {nullptr, nullptr};
   cudaEvent_t staged[2] = {nullptr, nullptr};
   int cur = 0;
-  std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, int, int, int, int, size_t, int, int>, cudaGraphExec_t> graphs;
 };
 
 }  // namespace
@@ -1408,14 +1409,19 @@ vc::JobDesc base_desc(vc_ctx* c) {
 // Stage `nj` descriptors (already in l.h_jobs[l.cur]) and launch them on st:
 // a captured graph per shape, or plain launches.
 int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int kmods, int rounds, size_t smem,
-                cudaStream_t st) {
+                cudaStream_t st, const int* vbeg, const int* vend, int variants) {
   vc::JobDesc* hj = l.h_jobs[l.cur];
   vc::BatchHdr* hh = l.h_hdr[l.cur];
   hh->njobs = nj;
   hh->total_warps = warps;
   hh->total_tiles = tiles;
   hh->total_kmod = kmods;
+  for (int v = 0; v < vc::kBatchVariants; v++) {
+    hh->vbeg[v] = vbeg[v];
+    hh->vend[v] = vend[v];
+  }
   vc::BatchShape sh;
+  sh.variants = variants;
   sh.jobs_cap = bucket(nj, 64);
   if (sh.jobs_cap > l.jobs_cap) sh.jobs_cap = l.jobs_cap;
   sh.warps_cap = bucket(warps, 64);
@@ -1436,7 +1442,8 @@ int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int k
   }
   const size_t jobs_bytes = sizeof(vc::JobDesc) * (size_t)sh.jobs_cap;
   if (b->use_graph) {
-    const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, l.cur);
+    const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, l.cur,
+                                     sh.variants);
     auto it = l.graphs.find(key);
     if (it == l.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1550,6 +1557,12 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
   }
   const int nj = (int)live.size();
   if (nj == 0) return VC_OK;
+  // jobs ordered by round-kernel variant (direction, channels): each variant's
+  // tiles form one range
+  std::stable_sort(live.begin(), live.end(), [&](int x, int y) {
+    return vc::batch_variant(jobs[x].direction, jobs[x].ctx->L.C) <
+           vc::batch_variant(jobs[y].direction, jobs[y].ctx->L.C);
+  });
   int rc = VC_OK;
   for (int k = 0; k < nj; k++) {  // single-stream calls' keystream generated ahead: undone
     rc = spec_rollback(jobs[live[k]].ctx);
@@ -1598,13 +1611,19 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
   VC_CUDA(cudaEventSynchronize(b->cons.staged[b->cons.cur]));
   vc::JobDesc* hj = b->cons.h_jobs[b->cons.cur];
   uint8_t* p = b->d_pool;
-  int warps = 0, tiles = 0, kmods = 0, rounds = 0;
+  int warps = 0, tiles = 0, kmods = 0, rounds = 0, variants = 0;
+  int vbeg[vc::kBatchVariants], vend[vc::kBatchVariants];
+  for (int v = 0; v < vc::kBatchVariants; v++) vbeg[v] = vend[v] = 0;
   size_t smem = 4096;  // the fix-up needs one byte per tile
   for (int k = 0; k < nj; k++) {
     const vc_job& J = jobs[live[k]];
     vc_ctx* c = J.ctx;
     const Layout& L = c->L;
     const int nf = J.nframes;
+    const int v = vc::batch_variant(J.direction, L.C);
+    if (!(variants & (1 << v))) vbeg[v] = tiles;
+    variants |= 1 << v;
+    vend[v] = tiles + nf * L.NT;
     vc::JobDesc d = base_desc(c);
     d.dir = J.direction;
     d.nframes = nf;
@@ -1647,7 +1666,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     if (sm > smem) smem = sm;
     hj[k] = d;
   }
-  rc = launch_lane(b, b->cons, nj, warps, tiles, kmods, rounds, smem, st);
+  rc = launch_lane(b, b->cons, nj, warps, tiles, kmods, rounds, smem, st, vbeg, vend, variants);
   if (rc) return rc;
   for (int k = 0; k < nj; k++) {
     const vc_job& J = jobs[live[k]];

@@ -70,8 +70,14 @@ struct JobDesc {
   int pad1, pad2;
 };
 
+// Round-kernel variants: (direction, channels) -> index dir * 3 + {C=1: 0, 3: 1, 4: 2}.
+constexpr int kBatchVariants = 6;
+__host__ __device__ inline int batch_variant(int dir, int C) { return dir * 3 + (C == 1 ? 0 : (C == 3 ? 1 : 2)); }
+
 struct BatchHdr {
   int njobs, total_warps, total_tiles, total_kmod;
+  // the jobs are ordered by variant: its tiles are [vbeg[v], vend[v])
+  int vbeg[kBatchVariants], vend[kBatchVariants];
 };
 
 // Launch geometry of a batch: capacities (work beyond the header's totals
@@ -79,6 +85,7 @@ struct BatchHdr {
 // rounds = 0 launches the keystream phases only.
 struct BatchShape {
   int jobs_cap, warps_cap, kmod_cap, rounds, grid;
+  int variants;  // bit v set: a round kernel of variant v is launched
   size_t smem;
 };
 

@@ -1670,33 +1670,49 @@ __device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step
   return A;
 }
 
-__global__ void __launch_bounds__(kRoundThreads) k_batch_round(const JobDesc* J, const BatchHdr* hdr, int step) {
+// One round of every tile of the batch's jobs of one (direction, channels)
+// variant: their tiles are the contiguous range [vbeg, vend) (jobs ordered by
+// variant), so each variant is a lean kernel like the single-stream ones.
+template <int DIR, int C>
+__global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc* J, const BatchHdr* hdr, int step) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int total = hdr->total_tiles, nj = hdr->njobs;
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int j = find_job(J, nj, item, [](const JobDesc& d) { return d.tile_base; });
-    const JobDesc& d = J[j];
-    if (step < d.L.rounds) {
-      const int local = item - d.tile_base;
-      const int f = local / d.L.NT;
-      const int t = local - f * d.L.NT;
-      const RoundArgs A = batch_round_args(d, step, f);
-      if (d.dir == 0) {
-        switch (d.L.C) {
-          case 1: enc_round_tile<1>(A, 0, t, smem); break;
-          case 3: enc_round_tile<3>(A, 0, t, smem); break;
-          default: enc_round_tile<4>(A, 0, t, smem); break;
-        }
-      } else {
-        switch (d.L.C) {
-          case 1: dec_round_tile<1>(A, 0, t, smem); break;
-          case 3: dec_round_tile<3>(A, 0, t, smem); break;
-          default: dec_round_tile<4>(A, 0, t, smem); break;
-        }
+  // the item's round arguments, built once per CTA and read by every thread as
+  // shared-memory broadcasts (a per-thread copy would live in local memory)
+  __shared__ RoundArgs sA;
+  __shared__ int s_item[2];  // the round applies, tile
+  constexpr int v = DIR * 3 + (C == 1 ? 0 : (C == 3 ? 1 : 2));
+  const int beg = hdr->vbeg[v], end = hdr->vend[v], nj = hdr->njobs;
+  for (int item = beg + blockIdx.x; item < end; item += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int j = find_job(J, nj, item, [](const JobDesc& d) { return d.tile_base; });
+      const JobDesc& d = J[j];
+      s_item[0] = step < d.L.rounds;
+      if (step < d.L.rounds) {
+        const int local = item - d.tile_base;
+        const int f = local / d.L.NT;
+        s_item[1] = local - f * d.L.NT;
+        sA = batch_round_args(d, step, f);
       }
     }
-    __syncthreads();  // shared memory is reused by the next item
+    __syncthreads();
+    if (s_item[0]) {
+      if (DIR == 0)
+        enc_round_tile<C>(sA, 0, s_item[1], smem);
+      else
+        dec_round_tile<C>(sA, 0, s_item[1], smem);
+    }
+    __syncthreads();  // shared memory (and sA) is reused by the next item
   }
+}
+
+template <int DIR, int C>
+static cudaError_t batch_round_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_batch_round<DIR, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int DIR, int C>
+static cudaError_t batch_round_ctas(size_t smem, int* ctas) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_batch_round<DIR, C>, kRoundThreads, smem);
 }
 
 __global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J, const BatchHdr* hdr) {
@@ -1716,14 +1732,30 @@ __global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J,
 }
 
 cudaError_t prepare_batch_kernels(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_batch_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = batch_round_attr<0, 1>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<0, 3>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<0, 4>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<1, 1>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<1, 3>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<1, 4>(smem);
   return e;
 }
 
+// CTAs per SM every round-kernel variant reaches with this shared memory.
 cudaError_t batch_ctas_per_sm(size_t smem, int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_batch_round, kRoundThreads, smem);
+  int c[kBatchVariants];
+  cudaError_t e = batch_round_ctas<0, 1>(smem, &c[0]);
+  if (e == cudaSuccess) e = batch_round_ctas<0, 3>(smem, &c[1]);
+  if (e == cudaSuccess) e = batch_round_ctas<0, 4>(smem, &c[2]);
+  if (e == cudaSuccess) e = batch_round_ctas<1, 1>(smem, &c[3]);
+  if (e == cudaSuccess) e = batch_round_ctas<1, 3>(smem, &c[4]);
+  if (e == cudaSuccess) e = batch_round_ctas<1, 4>(smem, &c[5]);
+  if (e != cudaSuccess) return e;
+  int m = c[0];
+  for (int k = 1; k < kBatchVariants; k++) m = c[k] < m ? c[k] : m;
+  *ctas = m;
+  return cudaSuccess;
 }
 
 cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st) {
@@ -1731,8 +1763,14 @@ cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchSh
   k_batch_kmod<<<(sh.kmod_cap + 255) / 256, 256, 0, st>>>(jobs, hdr);
   k_batch_ks<<<sh.warps_cap, 32, 0, st>>>(jobs, hdr);
   if (sh.rounds > 0) {
-    for (int step = 0; step < sh.rounds; step++)
-      k_batch_round<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+    for (int step = 0; step < sh.rounds; step++) {
+      if (sh.variants & (1 << 0)) k_batch_round<0, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 1)) k_batch_round<0, 3><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 2)) k_batch_round<0, 4><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 3)) k_batch_round<1, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 4)) k_batch_round<1, 3><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 5)) k_batch_round<1, 4><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+    }
     k_batch_fixup<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr);
   }
   return cudaGetLastError();

@@ -42,6 +42,7 @@ struct SrvFrame {
 };
 
 struct SrvTick {
+  cudaEvent_t ev0 = nullptr;  // before the submission
   cudaEvent_t ev = nullptr;
   std::vector<SrvFrame> frames;
   size_t taken = 0;  // frames already returned by a partial drain
@@ -63,6 +64,8 @@ struct vc_server {
   std::vector<vc_ctx*> starved;
   double host_ms[4] = {0, 0, 0, 0};  // readiness and job building, prefetch, submission, completion event
   int64_t host_ticks = 0;
+  double gpu_ms = 0;  // device time from a tick's first enqueued work to its completion, summed
+  int64_t gpu_ticks = 0;
 };
 
 namespace {
@@ -193,6 +196,11 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
   s->host_ms[1] += ms_since(t_start);
   if (s->jobs.empty()) return VC_OK;
   t_start = std::chrono::steady_clock::now();
+  tick.ev0 = srv_event(s);
+  if (!tick.ev0 || cudaEventRecord(tick.ev0, s->st) != cudaSuccess) {
+    cudaGetLastError();
+    return VC_ERR_CUDA;
+  }
   if (s->mode == 0) {
     int rc = vc_batch_submit(s->b, s->jobs.data(), (int32_t)s->jobs.size(), s->st);
     if (rc) return rc;
@@ -230,8 +238,12 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
     cudaError_t e = block ? cudaEventSynchronize(tk.ev) : cudaEventQuery(tk.ev);
     if (e == cudaErrorNotReady) break;
     if (e != cudaSuccess) return VC_ERR_CUDA;
-    float ms = 0.f;
+    float ms = 0.f, dur = 0.f;
     if (cudaEventElapsedTime(&ms, s->t0, tk.ev) != cudaSuccess) return VC_ERR_CUDA;
+    if (tk.taken == 0 && tk.ev0 && cudaEventElapsedTime(&dur, tk.ev0, tk.ev) == cudaSuccess) {
+      s->gpu_ms += dur;
+      s->gpu_ticks++;
+    }
     const double done_s = ms / 1e3;
     while (tk.taken < tk.frames.size() && n < cap) {
       const SrvFrame& f = tk.frames[tk.taken++];
@@ -244,6 +256,7 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
     }
     if (tk.taken == tk.frames.size()) {
       s->ev_pool.push_back(tk.ev);
+      if (tk.ev0) s->ev_pool.push_back(tk.ev0);
       s->inflight.pop_front();
     }
   }
@@ -275,12 +288,16 @@ int vc_server_remove(vc_server* s, int32_t id) {
 
 int32_t vc_server_inflight(const vc_server* s) { return s ? (int32_t)s->inflight.size() : 0; }
 
-int vc_dbg_server_stats(vc_server* s, double* ms4, int64_t* ticks) {
-  if (!s || !ms4 || !ticks) return VC_ERR_ARG;
+int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks) {
+  if (!s || !ms6 || !ticks) return VC_ERR_ARG;
   for (int k = 0; k < 4; k++) {
-    ms4[k] = s->host_ms[k];
+    ms6[k] = s->host_ms[k];
     s->host_ms[k] = 0;
   }
+  ms6[4] = s->gpu_ms;
+  ms6[5] = (double)s->gpu_ticks;
+  s->gpu_ms = 0;
+  s->gpu_ticks = 0;
   *ticks = s->host_ticks;
   s->host_ticks = 0;
   return VC_OK;
@@ -289,8 +306,10 @@ int vc_dbg_server_stats(vc_server* s, double* ms4, int64_t* ticks) {
 void vc_server_destroy(vc_server* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
-  for (SrvTick& tk : s->inflight)
+  for (SrvTick& tk : s->inflight) {
     if (tk.ev) cudaEventDestroy(tk.ev);
+    if (tk.ev0) cudaEventDestroy(tk.ev0);
+  }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->t0) cudaEventDestroy(s->t0);
   if (s->b) vc_batcher_destroy(s->b);

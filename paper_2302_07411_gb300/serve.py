@@ -72,7 +72,9 @@ class ServeResult:
             out["tick_host_p99_ms"] = round(float(np.percentile(self.tick_host_ms, 99)), 3)
         if self.native_ms.get("ticks"):
             t = self.native_ms["ticks"]
-            out["native_tick_ms"] = {k: round(v / t, 4) for k, v in self.native_ms.items() if k != "ticks"}
+            out["native_tick_ms"] = {k: round(v / t, 4) for k, v in self.native_ms.items()
+                                     if k not in ("ticks", "gpu_ms_per_tick")}
+            out["gpu_ms_per_tick"] = round(self.native_ms.get("gpu_ms_per_tick", 0.0), 4)
         if steady_after_s is not None:
             arr = np.array(self.arrivals_s)
             sel = lat[arr >= steady_after_s] if len(arr) == len(lat) else lat
