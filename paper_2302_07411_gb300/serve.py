@@ -226,12 +226,13 @@ class Server:
 def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0 / 24.0,
              counts=(16, 32, 64, 128, 256, 512), seconds: float = 4.0, seed: int = 21,
              hbm_budget_bytes: int = 200 << 30, tick_ms: float = 4.0, ramp_s: float = 0.5,
-             warm_s: float = 1.0, cipher_options: dict | None = None) -> dict:
+             warm_s: float = 1.0, cipher_options: dict | None = None, kinds=(0, 1)) -> dict:
     """Largest number of concurrent fps streams of H x W x 3 (half encrypt,
-    half decrypt, alternating maps) whose steady-state per-frame p99 latency
-    stays below budget_ms.  Streams arrive uniformly over ramp_s seconds and
-    last `seconds`; "steady" counts the frames arriving after ramp_s + warm_s.
-    Time to first frame is reported separately."""
+    half decrypt, maps cycling through `kinds`: PLCM 0, 2DLASM 1) whose
+    steady-state per-frame p99 latency stays below budget_ms.  Streams arrive
+    uniformly over ramp_s seconds and last `seconds`; "steady" counts the
+    frames arriving after ramp_s + warm_s.  Time to first frame is reported
+    separately."""
     import synth
 
     best, runs = 0, []
@@ -246,6 +247,11 @@ def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0
     for n in counts:
         reqs = synth.serving_workload(n, seed=seed, rate_per_s=n / ramp_s, resolutions=((H, W),),
                                       fps_choices=(fps,), duration_s=(seconds, seconds))
+        for k, r in enumerate(reqs):  # maps cycle through `kinds`, each stream keyed for its map
+            kind = kinds[k % len(kinds)]
+            if r["kind"] != kind:
+                r["kind"] = kind
+                r["key"] = synth.key_for_seed(kind, 1000 + r["sid"])
         srv = Server(hbm_budget_bytes=hbm_budget_bytes, tick_ms=tick_ms, mode=mode, cipher_options=cipher_options)
         res = srv.run(reqs)
         srv.close()
