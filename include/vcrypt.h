@@ -324,6 +324,44 @@ int enc_profile_enable(vc_ctx* ctx, int32_t enable);
  * the counters.  Errors: VC_ERR_ARG, VC_ERR_CUDA. */
 int enc_profile_read(vc_ctx* ctx, double* ms3, int64_t* launches3);
 
+/* ---- statistical and security measures (Sec. 4, Sec. 5) on the device ----
+ * Frames are nframes x height x width x channels uint8 (HWC, frames
+ * contiguous), device pointers; results are per frame and channel, in that
+ * order, in caller-owned device arrays.  Stream-ordered.  Errors: VC_ERR_ARG
+ * (shapes, null pointers), VC_ERR_CUDA.
+ *
+ * vc_stats_histogram: counts z[f][c][0..255] (uint32, 256 per frame and
+ *   channel), and from them (each may be NULL) chi^2 = sum (z - e)^2 / e with
+ *   e = pixels / 256 (Sec. 4.1), the histogram variance
+ *   1/256^2 sum_i sum_j (z_i - z_j)^2 / 2 (Sec. 4.1) and the Shannon entropy
+ *   sum p log2(1/p) (Sec. 4.3).
+ * vc_stats_correlation: correlation coefficient cov(x, y) / sqrt(D(x) D(y))
+ *   (1/N moments) of adjacent pixel pairs (Sec. 4.2): direction 0 horizontal
+ *   (right neighbour), 1 vertical (lower), 2 diagonal (lower right).  d_pairs
+ *   holds npairs pixel indices (row * width + column) of the pairs' first
+ *   pixels (the paper samples them at random; indices whose pair leaves the
+ *   frame are skipped), or is NULL for all pairs of the frame (npairs ignored).
+ *   d_sums: scratch of 6 uint64 per frame and channel (exact moment sums, and
+ *   the pairs used).
+ * vc_stats_local_entropy: the (k, T_B) local entropy (Sec. 4.3) of one channel:
+ *   the mean over nblocks blocks of side x side pixels, top-left corners
+ *   d_blocks[2b], d_blocks[2b + 1] (row, column; chosen at random by the
+ *   caller), of each block's entropy; d_block_ent receives nframes x nblocks
+ *   block entropies (NaN for a block outside the frame), d_mean the means.
+ * vc_stats_npcr_uaci: NPCR = #{a != b} / pixels x 100 and UACI =
+ *   sum |a - b| / (pixels x 255) x 100 (Sec. 5.2) between frames of a and b;
+ *   d_sums: scratch of 2 uint64 per frame and channel. */
+int vc_stats_histogram(const uint8_t* d_frames, int32_t nframes, int32_t height, int32_t width, int32_t channels,
+                       uint32_t* d_hist, double* d_chi2, double* d_var, double* d_entropy, void* stream);
+int vc_stats_correlation(const uint8_t* d_frames, int32_t nframes, int32_t height, int32_t width, int32_t channels,
+                         int32_t direction, const int32_t* d_pairs, int64_t npairs, uint64_t* d_sums, double* d_r,
+                         void* stream);
+int vc_stats_local_entropy(const uint8_t* d_frames, int32_t nframes, int32_t height, int32_t width, int32_t channels,
+                           int32_t channel, const int32_t* d_blocks, int32_t nblocks, int32_t side,
+                           double* d_block_ent, double* d_mean, void* stream);
+int vc_stats_npcr_uaci(const uint8_t* d_a, const uint8_t* d_b, int32_t nframes, int32_t height, int32_t width,
+                       int32_t channels, uint64_t* d_sums, double* d_npcr, double* d_uaci, void* stream);
+
 /* Release the context and its device memory (synchronises its stream). */
 void enc_destroy(vc_ctx* ctx);
 

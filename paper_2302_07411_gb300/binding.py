@@ -94,6 +94,10 @@ def lib():
             "vc_server_inflight": (i32, [p]),
             "vc_server_destroy": (None, [p]),
             "vc_dbg_server_stats": (C.c_int, [p, p, p]),
+            "vc_stats_histogram": (C.c_int, [p, i32, i32, i32, i32, p, p, p, p, p]),
+            "vc_stats_correlation": (C.c_int, [p, i32, i32, i32, i32, i32, p, i64, p, p, p]),
+            "vc_stats_local_entropy": (C.c_int, [p, i32, i32, i32, i32, i32, p, i32, i32, p, p, p]),
+            "vc_stats_npcr_uaci": (C.c_int, [p, p, i32, i32, i32, i32, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -453,3 +457,67 @@ class NativeServer:
             self.close()
         except Exception:
             pass
+
+
+# ---- statistical measures of Sec. 4 and Sec. 5 on the device -----------------
+
+def _frames_shape(t):
+    if t.dim() == 3:
+        t = t.unsqueeze(0)
+    F, H, W, Cc = t.shape
+    return t, F, H, W, Cc
+
+
+def stats_histogram(frames, stream=None):
+    """(counts [F, C, 256] uint32 as int32, chi^2 [F, C], variance [F, C],
+    entropy [F, C]) of device HWC uint8 frames."""
+    import torch
+
+    t, F, H, W, Cc = _frames_shape(frames)
+    hist = torch.empty((F, Cc, 256), dtype=torch.int32, device=t.device)
+    chi2, var, ent = (torch.empty((F, Cc), dtype=torch.float64, device=t.device) for _ in range(3))
+    _check(lib().vc_stats_histogram(_dptr(t), F, H, W, Cc, _dptr(hist), _dptr(chi2), _dptr(var), _dptr(ent),
+                                    _stream(stream)), "vc_stats_histogram")
+    return hist, chi2, var, ent
+
+
+def stats_correlation(frames, direction: int, pairs=None, stream=None):
+    """Adjacent-pixel correlation [F, C]; direction 0 H, 1 V, 2 D; pairs: device
+    int32 first-pixel indices, or None for every pair."""
+    import torch
+
+    t, F, H, W, Cc = _frames_shape(frames)
+    sums = torch.empty((F, Cc, 6), dtype=torch.int64, device=t.device)
+    r = torch.empty((F, Cc), dtype=torch.float64, device=t.device)
+    n = 0 if pairs is None else pairs.numel()
+    _check(lib().vc_stats_correlation(_dptr(t), F, H, W, Cc, direction, _dptr(pairs) if pairs is not None else None,
+                                      n, _dptr(sums), _dptr(r), _stream(stream)), "vc_stats_correlation")
+    return r
+
+
+def stats_local_entropy(frames, channel: int, blocks, side: int, stream=None):
+    """(block entropies [F, k], means [F]) of one channel; blocks: device int32
+    [k, 2] top-left (row, column) corners."""
+    import torch
+
+    t, F, H, W, Cc = _frames_shape(frames)
+    k = blocks.shape[0]
+    be = torch.empty((F, k), dtype=torch.float64, device=t.device)
+    mean = torch.empty((F,), dtype=torch.float64, device=t.device)
+    _check(lib().vc_stats_local_entropy(_dptr(t), F, H, W, Cc, channel, _dptr(blocks), k, side, _dptr(be), _dptr(mean),
+                                        _stream(stream)), "vc_stats_local_entropy")
+    return be, mean
+
+
+def stats_npcr_uaci(a, b, stream=None):
+    """(NPCR [F, C], UACI [F, C]) in percent between device frames a and b."""
+    import torch
+
+    ta, F, H, W, Cc = _frames_shape(a)
+    tb, *_ = _frames_shape(b)
+    sums = torch.empty((F, Cc, 2), dtype=torch.int64, device=ta.device)
+    npcr = torch.empty((F, Cc), dtype=torch.float64, device=ta.device)
+    uaci = torch.empty((F, Cc), dtype=torch.float64, device=ta.device)
+    _check(lib().vc_stats_npcr_uaci(_dptr(ta), _dptr(tb), F, H, W, Cc, _dptr(sums), _dptr(npcr), _dptr(uaci),
+                                    _stream(stream)), "vc_stats_npcr_uaci")
+    return npcr, uaci
