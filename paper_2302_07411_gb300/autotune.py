@@ -4,7 +4,8 @@ Every knob it turns leaves the ciphertext unchanged (the tests check each
 setting against the oracle): lanes per chaotic chain pair in the keystream
 kernel (VC_OPT_KS_LANES), rows per round-kernel tile (VC_OPT_TILE_ROWS, the
 block shape / shared-memory staging depth of the confusion gather), frames
-per pass and keystream run-ahead (VC_OPT_CHUNK, VC_OPT_OVERLAP), and the
+per pass and keystream run-ahead (VC_OPT_CHUNK, VC_OPT_OVERLAP), SMs held by
+the keystream (VC_OPT_KS_SM_WARPS), and the
 persistent grid of the batched round kernels (VC_BOPT_CTAS_PER_SM).  Never
 the subframe count n or the rounds r: those are cipher parameters.
 
@@ -81,17 +82,21 @@ def tune_stream(kind: int, H: int, W: int, C: int, n: int, rounds: int = 5, fram
     y = torch.empty_like(x)
     keyv = [0.31, 0.21, 0.62, 0.37] if kind == 0 else [0.31, 0.6, 0.62]
     trials = []
-    space = {"ks_lanes": [2, 1], "tile_rows": [0, 16, 8], "overlap": [1, 0]}
-    for lanes, tile, ov in itertools.product(space["ks_lanes"], space["tile_rows"], space["overlap"]):
+    # overlap 0 runs everything on the caller's stream (no SM holding); with
+    # overlap the keystream CTAs may hold whole SMs (-1 = the library's choice)
+    modes = [(0, 0)] + [(1, w) for w in (-1, 0, 2, 4)]
+    for lanes, tile, (ov, smw) in itertools.product([2, 1], [0, 16, 8], modes):
         c = B.Cipher(kind, keyv, H, W, C, n, rounds)
         c.set_option(B.VC_OPT_KS_LANES, lanes)
         c.set_option(B.VC_OPT_TILE_ROWS, tile)
         c.set_option(B.VC_OPT_OVERLAP, ov)
+        c.set_option(B.VC_OPT_KS_SM_WARPS, smw)
         ms = _time(lambda: c.encrypt(x, y))
-        trials.append({"ks_lanes": lanes, "tile_rows": tile, "overlap": ov, "ms": round(ms, 3)})
+        trials.append({"ks_lanes": lanes, "tile_rows": tile, "overlap": ov, "ks_sm_warps": smw, "ms": round(ms, 3)})
         c.close()
     best = min(trials, key=lambda t: t["ms"])
-    out = {"options": {k: best[k] for k in ("ks_lanes", "tile_rows", "overlap")}, "ms": best["ms"], "trials": trials}
+    out = {"options": {k: best[k] for k in ("ks_lanes", "tile_rows", "overlap", "ks_sm_warps")}, "ms": best["ms"],
+           "trials": trials}
     cache = _load()
     cache[key] = out
     _store(cache)
@@ -102,6 +107,7 @@ def apply_stream(cipher: B.Cipher, options: dict) -> None:
     cipher.set_option(B.VC_OPT_KS_LANES, int(options.get("ks_lanes", 2)))
     cipher.set_option(B.VC_OPT_TILE_ROWS, int(options.get("tile_rows", 0)))
     cipher.set_option(B.VC_OPT_OVERLAP, int(options.get("overlap", 1)))
+    cipher.set_option(B.VC_OPT_KS_SM_WARPS, int(options.get("ks_sm_warps", -1)))
 
 
 def tune_batch(layouts, frames_per_job: int = 1, use_cache: bool = True) -> dict:

@@ -31,8 +31,8 @@ def test_stream_tuning_is_cached_and_exact(B, orc, tmp_path, monkeypatch):
 
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     res = autotune.tune_stream(0, 64, 80, 3, 16, frames=6)
-    assert set(res["options"]) == {"ks_lanes", "tile_rows", "overlap"}
-    assert len(res["trials"]) == 12 and all(t["ms"] > 0 for t in res["trials"])
+    assert set(res["options"]) == {"ks_lanes", "tile_rows", "overlap", "ks_sm_warps"}
+    assert len(res["trials"]) == 30 and all(t["ms"] > 0 for t in res["trials"])
     assert autotune.tune_stream(0, 64, 80, 3, 16, frames=6) == res  # served from the cache
     assert json.load(open(tmp_path / "tune.json"))
     key = synth.key_for_seed(0, 90)
