@@ -1486,7 +1486,7 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
     constexpr int U = 4;
     for (int alpha = warp * rpw + sub; alpha < L.H; alpha += U * astep) {
       int pix[U], ov[U];
-      uint32_t c0[U], c1[U], k0[U], k1[U];
+      uint32_t c0[U], c1[U], k0[U], k1[U], sw[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int al = alpha + u * astep;
@@ -1503,6 +1503,7 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int qb = pix[u] * C;
+        sw[u] = ov[u] >= 0 ? __ldg(&A.tb.sbits[pix[u] >> 5]) : 0u;  // start bits, with the data
         if (ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
           const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - 1) & ~3));
           const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
@@ -1518,9 +1519,8 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
       for (int u = 0; u < U; u++) {
         if (ov[u] < 0) continue;
         const int p = pix[u], qb = p * C;
-        const uint32_t sw = __ldg(&A.tb.sbits[p >> 5]);
-        if (((sw >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
-          decrypt_pixel(p, ov[u], sw);
+        if (((sw[u] >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
+          decrypt_pixel(p, ov[u], sw[u]);
           continue;
         }
         const uint64_t c = ((uint64_t)c1[u] << 32 | c0[u]) >> (8 * ((qb - 1) & 3));
