@@ -37,11 +37,11 @@ sys.path.insert(0, ROOT)
 
 # k_ks_plcm_fx_sm: warp instructions per iterate and lane (ncu) and the
 # dependency chain of one iterate in cycles (clock64 probe of plcm_fx_step)
-PLCM_INSTR_PER_ITER = 115.0
+PLCM_INSTR_PER_ITER = 113.0
 PLCM_ITER_CYCLES = 251.0
 # its DRAM read + write bytes per frame of keystream (ncu, 40-frame launch at
 # 768x768x3, n = 4096): scaled to the bench's launches by their frames
-PLCM_KS_DRAM_BYTES_PER_FRAME = (797_952 + 297_627_648) / 40
+PLCM_KS_DRAM_BYTES_PER_FRAME = (365_568 + 297_627_904) / 40
 
 METRIC = "5-round enc Mpixel/s"
 
