@@ -284,6 +284,22 @@ def test_invalid_arguments_are_errors(B):
     assert e.value.code == 2
 
 
+@pytest.mark.parametrize("kind,H,W,n", [(0, 2160, 3840, 540), (1, 1080, 1920, 270), (0, 1080, 1920, 4096)])
+def test_largest_frames(B, orc, kind, H, W, n):
+    """The serving workload's largest frames (rows of 11,520 bytes: 8-row tiles,
+    wider than tall), two frames per call: equal to the oracle byte for byte,
+    and decryption returns the plaintext."""
+    X = synth.smooth_clip(2, H, W, 3, seed=13)
+    key = synth.key_for_seed(kind, 13)
+    g = B.Cipher(kind, key, H, W, 3, n, 5)
+    Y = host(g.encrypt(dev(X)))
+    assert np.array_equal(Y, orc.OracleCipher(kind, key, H, W, 3, n, 5).encrypt(X))
+    dd = B.Cipher(kind, key, H, W, 3, n, 5)
+    assert np.array_equal(host(dd.decrypt(dev(Y))), X)
+    g.close()
+    dd.close()
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_full_size_768_n4096_sampled(B, orc, kind):
     """The benchmark's launch configuration (768 x 768 x 3, n = 4096, r = 5, many
