@@ -156,9 +156,12 @@ struct vc_ctx {
   int spec_b = -1, spec_frames = 0, spec_used = 0;
   uint8_t* d_snap = nullptr;
   // staging for host-buffer calls
-  uint8_t* d_io[2] = {nullptr, nullptr};
+  static constexpr int kIoBufs = 3;
+  uint8_t* d_io[kIoBufs] = {nullptr, nullptr, nullptr};
   int io_cap = 0;
-  cudaStream_t copy_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // uploads (and table builds)
+  cudaStream_t d2h_stream = nullptr;   // downloads of host-buffer calls
+  cudaEvent_t ev_io[3 * kIoBufs] = {};
   cudaEvent_t ev[6] = {};
   int64_t frame = 0;
   cudaStream_t last = nullptr;
@@ -185,6 +188,7 @@ void sync_all(vc_ctx* c) {
   if (c->last) cudaStreamSynchronize(c->last);
   if (c->ks_stream) cudaStreamSynchronize(c->ks_stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
 
 void free_scratch(vc_ctx* c) {
@@ -642,12 +646,14 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
     set_err("device allocation failed");
     return VC_ERR_OOM;
   }
-  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking) != cudaSuccess) {
     enc_destroy(c);
     set_err("stream creation failed");
     return VC_ERR_CUDA;
   }
   for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  for (auto& e : c->ev_io) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
@@ -697,6 +703,28 @@ int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nfr
   return crypt_device(ctx, 1, d_in, d_out, nframes, stream);
 }
 
+// Host staging buffers for passes of up to `frames` frames.
+int ensure_io(vc_ctx* c, int frames) {
+  if (c->io_cap >= frames) return VC_OK;
+  cudaStreamSynchronize(c->copy_stream);
+  if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
+  for (auto& b : c->d_io) {
+    cudaFree(b);
+    b = nullptr;
+  }
+  c->io_cap = 0;
+  const size_t N = (size_t)c->L.N;
+  for (auto& b : c->d_io) {
+    if (cudaMalloc(&b, (size_t)frames * N) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("staging allocation failed");
+      return VC_ERR_OOM;
+    }
+  }
+  c->io_cap = frames;
+  return VC_OK;
+}
+
 int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
                       void* stream) {
   if (!c || nframes < 0 || (direction != 0 && direction != 1) || (nframes > 0 && (!h_in || !h_out))) {
@@ -711,58 +739,42 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   rc = enter(c, st);
   if (rc) return rc;
   const size_t N = (size_t)c->L.N;
-  if (c->io_cap < F) {
-    cudaStreamSynchronize(c->copy_stream);
-    cudaFree(c->d_io[0]);
-    cudaFree(c->d_io[1]);
-    c->d_io[0] = c->d_io[1] = nullptr;
-    c->io_cap = 0;
-    if (cudaMalloc(&c->d_io[0], F * N) != cudaSuccess || cudaMalloc(&c->d_io[1], F * N) != cudaSuccess) {
-      cudaGetLastError();
-      set_err("staging allocation failed");
-      return VC_ERR_OOM;
-    }
-    c->io_cap = F;
-  }
-  // copy stream: H2D(k) ... D2H(k); compute stream st: pass(k).  Buffers alternate.
-  cudaEvent_t* h2d = c->ev;      // [2]
-  cudaEvent_t* done = c->ev + 2; // [2]
   std::vector<int> plan;
   bool first_spec = false;
   int next_first = 0;
   call_plan(c, nframes, F, plan, &first_spec, &next_first);
-  if (c->io_cap < plan[0]) {  // a run-ahead pass can be larger than this call's passes
-    cudaStreamSynchronize(c->copy_stream);
-    cudaFree(c->d_io[0]);
-    cudaFree(c->d_io[1]);
-    c->d_io[0] = c->d_io[1] = nullptr;
-    c->io_cap = 0;
-    if (cudaMalloc(&c->d_io[0], plan[0] * N) != cudaSuccess || cudaMalloc(&c->d_io[1], plan[0] * N) != cudaSuccess) {
-      cudaGetLastError();
-      set_err("staging allocation failed");
-      return VC_ERR_OOM;
-    }
-    c->io_cap = plan[0];
-  }
+  rc = ensure_io(c, std::max(F, plan[0]));  // a run-ahead pass can be larger than this call's passes
+  if (rc) return rc;
+  // Three streams and three staging buffers: uploads (copy_stream), passes
+  // (st, in place in the buffer) and downloads (d2h_stream) of consecutive
+  // passes overlap; a buffer is uploaded again once its download is done.
+  constexpr int kIo = vc_ctx::kIoBufs;
+  cudaEvent_t* up = c->ev_io;             // upload k done
+  cudaEvent_t* done = c->ev_io + kIo;     // pass k done
+  cudaEvent_t* down = c->ev_io + 2 * kIo; // download k done
   long long f0 = 0;
   for (int k = 0; k < (int)plan.size(); f0 += plan[k], k++) {
     const int nf = plan[k];
-    uint8_t* buf = c->d_io[k & 1];
+    const int b = k % kIo;
+    uint8_t* buf = c->d_io[b];
+    if (k >= kIo) VC_CUDA(cudaStreamWaitEvent(c->copy_stream, down[b], 0));
     VC_CUDA(cudaMemcpyAsync(buf, h_in + (size_t)f0 * N, nf * N, cudaMemcpyHostToDevice, c->copy_stream));
-    VC_CUDA(cudaEventRecord(h2d[k & 1], c->copy_stream));
-    VC_CUDA(cudaStreamWaitEvent(st, h2d[k & 1], 0));
+    VC_CUDA(cudaEventRecord(up[b], c->copy_stream));
+    VC_CUDA(cudaStreamWaitEvent(st, up[b], 0));
     rc = (k == 0 && first_spec) ? spec_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st)
                                 : run_pass(c, direction, buf, (long long)N, buf, (long long)N, nf, st);
     if (rc) return rc;
-    VC_CUDA(cudaEventRecord(done[k & 1], st));
-    VC_CUDA(cudaStreamWaitEvent(c->copy_stream, done[k & 1], 0));
-    VC_CUDA(cudaMemcpyAsync(h_out + (size_t)f0 * N, buf, nf * N, cudaMemcpyDeviceToHost, c->copy_stream));
+    VC_CUDA(cudaEventRecord(done[b], st));
+    VC_CUDA(cudaStreamWaitEvent(c->d2h_stream, done[b], 0));
+    VC_CUDA(cudaMemcpyAsync(h_out + (size_t)f0 * N, buf, nf * N, cudaMemcpyDeviceToHost, c->d2h_stream));
+    VC_CUDA(cudaEventRecord(down[b], c->d2h_stream));
   }
   c->frame += nframes;
   c->produced = c->frame;
   c->produced_done = c->frame;
   rc = spec_issue(c, next_first);
   if (rc) return rc;
+  VC_CUDA(cudaStreamSynchronize(c->d2h_stream));
   VC_CUDA(cudaStreamSynchronize(c->copy_stream));
   VC_CUDA(cudaStreamSynchronize(st));
   return VC_OK;
@@ -851,6 +863,7 @@ int enc_sync_status(vc_ctx* c) {
   if (!c) return VC_ERR_ARG;
   cudaError_t e = c->last ? cudaStreamSynchronize(c->last) : cudaSuccess;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  if (e == cudaSuccess && c->d2h_stream) e = cudaStreamSynchronize(c->d2h_stream);
   if (e == cudaSuccess && c->ks_stream) e = cudaStreamSynchronize(c->ks_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -983,8 +996,7 @@ void enc_destroy(vc_ctx* c) {
   if (!c) return;
   sync_all(c);
   free_scratch(c);
-  cudaFree(c->d_io[0]);
-  cudaFree(c->d_io[1]);
+  for (auto b : c->d_io) cudaFree(b);
   cudaFree(c->d_pi);
   cudaFree(c->d_sbits);
   cudaFree(c->d_srank);
@@ -996,12 +1008,15 @@ void enc_destroy(vc_ctx* c) {
   cudaFree(c->d_carry_len);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_io)
+    if (e) cudaEventDestroy(e);
   for (auto& m : c->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
   if (c->ks_stream) cudaStreamDestroy(c->ks_stream);
   for (int b = 0; b < 2; b++) {
     if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
