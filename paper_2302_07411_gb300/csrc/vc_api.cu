@@ -1266,6 +1266,7 @@ struct vc_batcher {
   int ctas_per_sm = 0;
   int runahead = 0;  // frames of keystream kept ahead per stream (0 = off)
   cudaStream_t cap_stream = nullptr;
+  std::map<size_t, int> ctas_for_smem;  // round-kernel CTAs per SM by shared-memory size (queried once)
 };
 
 namespace {
@@ -1445,9 +1446,15 @@ int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int k
   sh.smem = (smem + 16383) & ~(size_t)16383;
   sh.grid = 1;
   if (rounds > 0) {
-    VC_CUDA(vc::prepare_batch_kernels(sh.smem));
     int ctas = 0;
-    VC_CUDA(vc::batch_ctas_per_sm(sh.smem, &ctas));
+    auto hit = b->ctas_for_smem.find(sh.smem);
+    if (hit != b->ctas_for_smem.end()) {
+      ctas = hit->second;
+    } else {
+      VC_CUDA(vc::prepare_batch_kernels(sh.smem));
+      VC_CUDA(vc::batch_ctas_per_sm(sh.smem, &ctas));
+      b->ctas_for_smem[sh.smem] = ctas;
+    }
     if (ctas < 1) {
       set_err("round kernel does not fit with %zu bytes of shared memory", sh.smem);
       return VC_ERR_UNSUPPORTED;

@@ -13,12 +13,41 @@
 // q / C; subframe i owns bytes [C pi_i, C pi_{i+1}), pi_i = floor(i P / n).
 #include <cstdint>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "vc_internal.h"
 #include "vc_maps.cuh"
 
 namespace vc {
+
+// cudaFuncSetAttribute(func, MaxDynamicSharedMemorySize, bytes) only when a
+// kernel needs more than it was last allowed on the current device (the call
+// costs host time on every launch otherwise).
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void*>, int> g_smem_allowed;
+
+template <typename K>
+static cudaError_t allow_smem(K* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_pair(dev, reinterpret_cast<const void*>(func));
+  {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    auto it = g_smem_allowed.find(key);
+    if (it != g_smem_allowed.end() && it->second >= bytes) return cudaSuccess;
+  }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int& v = g_smem_allowed[key];
+    if (bytes > v) v = bytes;
+  }
+  return e;
+}
 
 // =============================================================================
 // Partition tables
@@ -872,16 +901,16 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
     const int smem = reserve_smem_bytes();
     cudaError_t e;
     if (kind == 0 && plcm_int) {
-      e = cudaFuncSetAttribute(k_ks_plcm_fx_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = allow_smem(k_ks_plcm_fx_sm, smem);
       if (e != cudaSuccess) return e;
       k_ks_plcm_fx_sm<<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0,
                                                      plcm_int >= 2 ? plcm_int - 1 : 0);
     } else if (kind == 0) {
-      e = cudaFuncSetAttribute(k_ks_pair_sm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = allow_smem(k_ks_pair_sm<0>, smem);
       if (e != cudaSuccess) return e;
       k_ks_pair_sm<0><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
     } else {
-      e = cudaFuncSetAttribute(k_ks_pair_sm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = allow_smem(k_ks_pair_sm<1>, smem);
       if (e != cudaSuccess) return e;
       k_ks_pair_sm<1><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
     }
@@ -1356,7 +1385,7 @@ size_t round_smem_bytes(const Layout& L) {
 template <int C>
 static cudaError_t enc_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
   const size_t smem = round_smem_bytes(A.L);
-  cudaError_t e = cudaFuncSetAttribute(k_enc_round<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_enc_round<C>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(A.L.NT, nframes);
   k_enc_round<C><<<grid, kRoundThreads, smem, st>>>(A);
@@ -1570,7 +1599,7 @@ __global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
 template <int C>
 static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
   const size_t smem = round_smem_bytes(A.L);
-  cudaError_t e = cudaFuncSetAttribute(k_dec_round<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_dec_round<C>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(A.L.NT, nframes);
   k_dec_round<C><<<grid, kRoundThreads, smem, st>>>(A);
@@ -1708,7 +1737,7 @@ __global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc*
 
 template <int DIR, int C>
 static cudaError_t batch_round_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_batch_round<DIR, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return allow_smem(k_batch_round<DIR, C>, (int)smem);
 }
 
 template <int DIR, int C>
@@ -1733,7 +1762,7 @@ __global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J,
 }
 
 cudaError_t prepare_batch_kernels(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_batch_fixup, (int)smem);
   if (e == cudaSuccess) e = batch_round_attr<0, 1>(smem);
   if (e == cudaSuccess) e = batch_round_attr<0, 3>(smem);
   if (e == cudaSuccess) e = batch_round_attr<0, 4>(smem);
