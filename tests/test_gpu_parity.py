@@ -47,6 +47,29 @@ def test_csin_bitwise(B, orc):
     assert np.array_equal(got[idx].view(np.uint64), exp.view(np.uint64))
 
 
+def test_csin_reduction_edges(B, orc):
+    """Arguments where the reduction decides, every one against the oracle:
+    u = t*2/pi within a few ulp of a half-integer (the rounding of u + 1/2 and
+    its floor pick the quadrant), t within a few ulp of a multiple of PIO2_HI
+    (t - k*PIO2_HI cancels), the 2DLASM argument range [-24, 3] (negative k),
+    signed zeros and large arguments."""
+    rng = np.random.default_rng(103)
+    pio2_hi = float.fromhex("0x1.921fb544p+0")
+    m = np.arange(-300, 301, dtype=np.float64)
+    nudges = np.arange(-4, 5, dtype=np.int64)
+    half = ((m + 0.5) * (np.pi / 2)).view(np.int64)
+    mult = (m * pio2_hi).view(np.int64)
+    t = np.concatenate([(half[:, None] + nudges[None, :]).ravel().view(np.float64),
+                        (mult[:, None] + nudges[None, :]).ravel().view(np.float64),
+                        rng.uniform(-24.0, 3.0, 50000), -rng.uniform(0, 2 * np.pi, 10000),
+                        np.array([-0.0, -1e-300, 400.0, -400.0, 402.1, 1e6, -1e6])])
+    out = torch.empty(t.size, dtype=torch.float64, device="cuda")
+    B.vc_dbg_csin(dev(t), out)
+    got = host(out)
+    exp = np.array([orc.csin(float(v)) for v in t])
+    assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 def test_plcm_step_bitwise(B, orc, variant):
     """Eq. 5 on the binary64 pipe (0) and on the integer pipes (1) == oracle,
