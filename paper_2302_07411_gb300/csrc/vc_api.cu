@@ -315,6 +315,7 @@ int ks_warps_in_use(const vc_ctx* c) {
 // Keystream side of a pass into buffer b: s_c and shift tables (Alg. 1), then
 // r * S_i bytes per subframe and frame (Sec. 3).
 int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
+  vc::NvtxRange range("vc.keystream");
   const Layout& L = c->L;
   {
     StageMark m(c, ks, 0, 2);
@@ -365,6 +366,7 @@ int end_pass(vc_ctx* c, int b, cudaStream_t st) {
 // in/out strides in bytes.
 int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint8_t* out, long long out_stride,
                 int nf, cudaStream_t st, int b, int f_off) {
+  vc::NvtxRange range("vc.rounds");
   const Layout& L = c->L;
   const vc::Tables tb = c->tables();
   const long long ks_stride = (long long)L.rounds * L.Npad;
@@ -1384,6 +1386,7 @@ bool production_busy(vc_ctx* c) {
 // its own internal stream, after the batch that last read the ring's slots.
 int produce(vc_ctx* c, int64_t target) {
   if (c->produced >= target) return VC_OK;
+  vc::NvtxRange range("vc.keystream");
   cudaStream_t ks = c->ks_stream;
   if (c->produced == c->frame && c->last && !c->batch_pending) {  // single-stream work on this context first
     VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
@@ -1539,6 +1542,7 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
 }
 
 int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stream) {
+  vc::NvtxRange range("vc.batch");
   if (!b || njobs < 0 || (njobs > 0 && !jobs)) {
     set_err("invalid argument");
     return VC_ERR_ARG;

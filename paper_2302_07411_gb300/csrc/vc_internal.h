@@ -3,8 +3,20 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace vc {
+
+// An NVTX range over the host-side issue of one stage (keystream, rounds, a
+// batch, a serving tick), so profilers can select kernels by stage
+// (ncu --nvtx --nvtx-include "vc.keystream/").  Header-only NVTX v3: a few
+// nanoseconds when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxTiles = 4096;   // tiles (row bands of the round kernels) per frame
 constexpr int kMaxRowBytes = 96 * 1024;

@@ -17,6 +17,7 @@
 #include <deque>
 #include <vector>
 
+#include "vc_internal.h"
 #include "vcrypt.h"
 #include "vcrypt_debug.h"
 
@@ -143,6 +144,7 @@ int vc_server_add(vc_server* s, vc_ctx* ctx, int32_t direction, int64_t frame_by
 }
 
 int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
+  vc::NvtxRange range("vc.tick");
   if (!s) return VC_ERR_ARG;
   if (frames_submitted) *frames_submitted = 0;
   s->jobs.clear();

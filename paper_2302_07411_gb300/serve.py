@@ -53,6 +53,8 @@ class ServeResult:
     frames: int = 0
     admitted: int = 0
     rejected: int = 0
+    failed: int = 0        # admitted streams whose context could not be created (error kept in `errors`)
+    errors: list = field(default_factory=list)
     peak_streams: int = 0
     wall_s: float = 0.0
     ticks: int = 0
@@ -64,7 +66,7 @@ class ServeResult:
         out = {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
-               "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
+               "failed": self.failed, "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
         if self.first_frame_ms:
             out["first_frame_p99_ms"] = round(float(np.percentile(self.first_frame_ms, 99)), 3)
         if self.tick_host_ms:
@@ -177,9 +179,16 @@ class Server:
                     used += fp
                     res.admitted += 1
                     # context creation (key schedule on the GPU) off the loop's thread
-                    starting.append(self.pool.submit(self._open, spec, fp))
-                while starting and starting[0].done():
-                    st = starting.popleft().result()
+                    starting.append((self.pool.submit(self._open, spec, fp), fp))
+                while starting and starting[0][0].done():
+                    fut, fp = starting.popleft()
+                    try:
+                        st = fut.result()
+                    except Exception as e:  # e.g. a key outside the valid ranges: this stream only
+                        res.failed += 1
+                        res.errors.append(f"{type(e).__name__}: {e}")
+                        used -= fp
+                        continue
                     H, W, C = st.spec["H"], st.spec["W"], st.spec["C"]
                     st.sid = srv.add(st.cipher, st.spec["direction"], H * W * C, self.input_frames(H, W, C),
                                      self.maxf, st.out, self.ring, float(st.spec["fps"]), st.spec["arrival"],

@@ -140,3 +140,48 @@ def test_prefetch_and_ready(B, orc):
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref.encrypt(X))
     batcher.close()
+
+
+def test_config_64_streams_mixed_resolutions(B, orc):
+    """64 streams, each with its own key, resolutions cycling 480x480,
+    576x576, 768x768 and 1920x1080 (3 channels), n = ceil(H/4), both maps and
+    both directions, one frame per stream per tick, two ticks through one
+    captured graph with keystream run-ahead: every output equals the stream
+    run alone, and one stream of each resolution and map equals the oracle."""
+    import math
+
+    res = [(480, 480), (576, 576), (768, 768), (1080, 1920)]
+    batcher = B.Batcher(graph=True, runahead=2)
+    streams = []
+    for s in range(64):
+        H, W = res[s % 4]
+        kind, direction = (s // 4) % 2, (s // 8) % 2
+        key = synth.key_for_seed(kind, 900 + s)
+        n = math.ceil(H / 4)
+        streams.append(dict(kind=kind, direction=direction, key=key, H=H, W=W, n=n,
+                            mixed=B.Cipher(kind, key, H, W, 3, n), solo=B.Cipher(kind, key, H, W, 3, n),
+                            X=synth.uniform_frames(2, H, W, 3, seed=1000 + s)))
+    batcher.prefetch([st["mixed"] for st in streams])
+    first = {}
+    for tick in range(2):
+        jobs, outs, refs = [], [], []
+        for st in streams:
+            x = torch.from_numpy(st["X"][tick:tick + 1]).cuda()
+            y = torch.empty_like(x)
+            jobs.append((st["mixed"], st["direction"], x, y, 1))
+            outs.append(y)
+            refs.append(st["solo"].encrypt(x) if st["direction"] == 0 else st["solo"].decrypt(x))
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for s in range(64):
+            assert torch.equal(outs[s], refs[s]), f"tick {tick}, stream {s}"
+        if tick == 0:
+            first = {s: outs[s].cpu().numpy() for s in range(64)}
+    for s in (0, 1, 2, 3, 4, 5, 6, 7):  # each resolution with each map, encrypting
+        st = streams[s]
+        ref = orc.OracleCipher(st["kind"], st["key"], st["H"], st["W"], 3, st["n"])
+        assert np.array_equal(first[s], ref.encrypt(st["X"][:1])), f"stream {s}"
+    for st in streams:
+        st["mixed"].close()
+        st["solo"].close()
+    batcher.close()

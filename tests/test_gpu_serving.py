@@ -65,3 +65,38 @@ def test_admission_respects_hbm_budget(B):
     res = srv.run(reqs)
     assert res.rejected > 0 and res.admitted >= 1
     srv.close()
+
+
+@pytest.mark.parametrize("mode", ["batch", "perframe"])
+def test_failed_stream_setup_leaves_the_others_served(B, mode):
+    """A fault on the host side of the loop: two requests carry keys outside
+    the valid ranges, so their context creation fails on the worker thread.
+    The loop counts them as failed, returns their HBM budget, and serves every
+    other stream exactly as it would alone."""
+    from paper_2302_07411_gb300 import serve
+
+    reqs = _requests()
+    bad = {reqs[2]["sid"], reqs[5]["sid"]}
+    for r in reqs:
+        if r["sid"] in bad:
+            r["key"] = [1.5, 0.3, 0.4, 0.2] if r["kind"] == 0 else [0.5, 2.0, 0.5, 0.0]  # x0 >= 1 / mu outside
+    srv = serve.Server(hbm_budget_bytes=1 << 30, tick_ms=3.0, mode=mode, max_frames_per_tick=4, ring=64,
+                       keep_outputs=True)
+    res = srv.run(reqs)
+    summ = res.summary()
+    assert summ["admitted"] == len(reqs) and summ["failed"] == 2 and len(res.errors) == 2
+    good = [r for r in reqs if r["sid"] not in bad]
+    assert res.frames == sum(max(1, int(r["duration"] * r["fps"])) for r in good)
+    assert sorted(st.spec["sid"] for st in srv.finished) == sorted(r["sid"] for r in good)
+    for st in srv.finished:
+        sp = st.spec
+        H, W, C = sp["H"], sp["W"], sp["C"]
+        inp = srv.input_frames(H, W, C)
+        solo = B.Cipher(sp["kind"], sp["key"], H, W, C, serve.subframes_for(H), 5)
+        for k in range(st.frames_total):
+            x = inp[k % srv.maxf: k % srv.maxf + 1]
+            ref = solo.encrypt(x) if sp["direction"] == 0 else solo.decrypt(x)
+            assert torch.equal(st.out[k % srv.ring], ref[0]), (sp["sid"], k)
+        solo.close()
+        st.cipher.close()
+    srv.close()
