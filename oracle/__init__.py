@@ -24,8 +24,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PLCM, DLASM = 0, 1
-PRBG_PLCM_PAIR, PRBG_LASM_PAIR, PRBG_LASM_SINGLE = 0, 1, 2
+PLCM, DLASM, LOGISTIC = 0, 1, 2
+PRBG_PLCM_PAIR, PRBG_LASM_PAIR, PRBG_LASM_SINGLE, PRBG_LOGI_PAIR = 0, 1, 2, 3
 
 # gcc flags: one IEEE rounding per operation, no contraction into fma, no
 # fast-math reassociation.
@@ -63,6 +63,7 @@ def lib():
             "orc_constants": (None, [p]),
             "orc_plcm_step": (d, [d, d]),
             "orc_lasm_step": (None, [p, p, d]),
+            "orc_logistic_step": (d, [d, d]),
             "orc_mantissa_bytes": (None, [d, p]),
             "orc_prbg_init": (None, [p, i32, p]),
             "orc_prbg_bytes": (None, [p, p, u64]),
@@ -126,6 +127,12 @@ def lasm_step(x: float, y: float, mu: float) -> tuple[float, float]:
     xs, ys = C.c_double(x), C.c_double(y)
     lib().orc_lasm_step(C.byref(xs), C.byref(ys), float(mu))
     return xs.value, ys.value
+
+
+def logistic_step(x: float, r: float) -> float:
+    """The logistic map x' = (r x)(1 - x), the third map of the strategy
+    (Sec. 7, advantage iii)."""
+    return lib().orc_logistic_step(float(x), float(r))
 
 
 def mantissa_bytes(v: float) -> bytes:
@@ -227,7 +234,8 @@ def undiffuse(Xc: np.ndarray, ks_list, n: int) -> np.ndarray:
 class OracleCipher:
     """One video stream of the cipher (Alg. 1 + Alg. 2, executed serially).
 
-    kind: PLCM (key = x0^1, p^1, x0^2, p^2) or DLASM (key = x0, mu, y0).
+    kind: PLCM (key = x0^1, p^1, x0^2, p^2), DLASM (key = x0, mu, y0) or
+    LOGISTIC (key = x0^1, r^1, x0^2, r^2).
     Frames are H x W x C uint8 arrays; state advances one frame per call.
     """
 

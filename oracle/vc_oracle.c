@@ -11,6 +11,9 @@
  * Every step is written in the order the paper states it:
  *   Eq. 5      PLCM map                          -> plcm_step()
  *   Eq. 6      2DLASM map                        -> lasm_step()
+ *   Sec. 7 iii a third map, the logistic map (parity unpinned by the paper:
+ *              it names no other map; pinned by closed forms)
+ *                                                 -> logistic_step()
  *   Sec. 3     PRBG byte construction (6 mantissa bytes per iterate, XOR of the
  *              two maps' byte streams)           -> prbg_*()
  *   Alg. 1     main thread: PRBG_m keyed by K, parameters P_m, per-frame s_c
@@ -147,6 +150,12 @@ void orc_mantissa_bytes(double v, uint8_t out[6]) {
   for (k = 0; k < 6; k++) out[k] = (uint8_t)((bits >> (8 * k)) & 0xffu);
 }
 
+/* A third map for the same strategy (Sec. 7, advantage iii: the strategy works
+ * with other chaotic maps): the logistic map x' = r x (1 - x), r in [3.9, 4],
+ * evaluated left to right, (r * x) * (1 - x).  Its PRBG is built like the
+ * PLCM's: a pair of maps, 6 mantissa bytes per iterate, XORed. */
+double orc_logistic_step(double x, double r) { return (r * x) * (1.0 - x); }
+
 /* ------------------------------------------------------------------------ */
 /* PRBGs (Sec. 3): continuous byte streams.                                  */
 /* ------------------------------------------------------------------------ */
@@ -158,6 +167,14 @@ static void prbg_refill(orc_prbg* g) {
     /* iterate both PLCMs, XOR their 6-byte groups */
     g->s[0] = orc_plcm_step(g->s[0], g->s[1]);
     g->s[2] = orc_plcm_step(g->s[2], g->s[3]);
+    orc_mantissa_bytes(g->s[0], a);
+    orc_mantissa_bytes(g->s[2], b);
+    for (k = 0; k < 6; k++) g->buf[k] = a[k] ^ b[k];
+    g->len = 6;
+  } else if (g->kind == ORC_PRBG_LOGI_PAIR) {
+    /* iterate both logistic maps, XOR their 6-byte groups */
+    g->s[0] = orc_logistic_step(g->s[0], g->s[1]);
+    g->s[2] = orc_logistic_step(g->s[2], g->s[3]);
     orc_mantissa_bytes(g->s[0], a);
     orc_mantissa_bytes(g->s[2], b);
     for (k = 0; k < 6; k++) g->buf[k] = a[k] ^ b[k];
@@ -235,6 +252,11 @@ int orc_key_valid(int kind, const double* k) {
                 (mu >= 0.44 && mu <= 0.93) || mu == 1.0;
     return k[0] > 0.0 && k[0] < 1.0 && k[2] > 0.0 && k[2] < 1.0 && mu_ok;
   }
+  if (kind == ORC_LOGISTIC) {
+    /* x0 in (0,1) (0 and 1 are absorbing); r in [3.9, 4] */
+    return k[0] > 0.0 && k[0] < 1.0 && k[1] >= 3.9 && k[1] <= 4.0 &&
+           k[2] > 0.0 && k[2] < 1.0 && k[3] >= 3.9 && k[3] <= 4.0;
+  }
   return 0;
 }
 
@@ -262,6 +284,10 @@ int orc_ctx_init(orc_ctx* c, int kind, const double* key, int H, int W, int C, i
     /* K = (x0^1, p^1, x0^2, p^2): PRBG_m is a PLCM pair */
     mparams[0] = key[0]; mparams[1] = key[1]; mparams[2] = key[2]; mparams[3] = key[3];
     orc_prbg_init(&c->main, ORC_PRBG_PLCM_PAIR, mparams);
+  } else if (kind == ORC_LOGISTIC) {
+    /* K = (x0^1, r^1, x0^2, r^2): PRBG_m is a logistic pair */
+    mparams[0] = key[0]; mparams[1] = key[1]; mparams[2] = key[2]; mparams[3] = key[3];
+    orc_prbg_init(&c->main, ORC_PRBG_LOGI_PAIR, mparams);
   } else {
     /* K = (x0, mu, y0): PRBG_m is a single 2DLASM, emitting x then y */
     mparams[0] = key[0]; mparams[1] = key[2]; mparams[2] = key[1];
@@ -278,6 +304,15 @@ int orc_ctx_init(orc_ctx* c, int kind, const double* key, int H, int W, int C, i
       prm[0] = u1; prm[1] = 0.05 + 0.4 * u2;
       prm[2] = u3; prm[3] = 0.05 + 0.4 * u4;
       orc_prbg_init(&c->sub[i], ORC_PRBG_PLCM_PAIR, prm);
+    } else if (kind == ORC_LOGISTIC) {
+      /* as the PLCM's: x0 = u, r = 3.9 + 0.1 u, each from its own group */
+      double u1 = group_to_unit(next_group(&c->main));
+      double u2 = group_to_unit(next_group(&c->main));
+      double u3 = group_to_unit(next_group(&c->main));
+      double u4 = group_to_unit(next_group(&c->main));
+      prm[0] = u1; prm[1] = 3.9 + 0.1 * u2;
+      prm[2] = u3; prm[3] = 3.9 + 0.1 * u4;
+      orc_prbg_init(&c->sub[i], ORC_PRBG_LOGI_PAIR, prm);
     } else {
       double u1 = group_to_unit(next_group(&c->main));
       double u2 = group_to_unit(next_group(&c->main));

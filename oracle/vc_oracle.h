@@ -11,13 +11,14 @@
 extern "C" {
 #endif
 
-enum { ORC_PLCM = 0, ORC_2DLASM = 1 };
-enum { ORC_PRBG_PLCM_PAIR = 0, ORC_PRBG_LASM_PAIR = 1, ORC_PRBG_LASM_SINGLE = 2 };
+enum { ORC_PLCM = 0, ORC_2DLASM = 1, ORC_LOGISTIC = 2 };
+enum { ORC_PRBG_PLCM_PAIR = 0, ORC_PRBG_LASM_PAIR = 1, ORC_PRBG_LASM_SINGLE = 2, ORC_PRBG_LOGI_PAIR = 3 };
 
 /* A PRBG: map state s[] plus the not yet consumed bytes of its last iterate.
  *  PLCM pair:     s = {x1, p1, x2, p2}
  *  2DLASM pair:   s = {x1, y1, mu1, x2, y2, mu2}
- *  2DLASM single: s = {x, y, mu} */
+ *  2DLASM single: s = {x, y, mu}
+ *  logistic pair: s = {x1, r1, x2, r2} */
 typedef struct {
   int32_t kind;
   int32_t pos, len;
@@ -38,6 +39,7 @@ double orc_cos_coef(int k);
 void orc_constants(double* out5);
 double orc_plcm_step(double x, double p);
 void orc_lasm_step(double* x, double* y, double mu);
+double orc_logistic_step(double x, double r);
 void orc_mantissa_bytes(double v, uint8_t out[6]);
 
 void orc_prbg_init(orc_prbg* g, int kind, const double* params);

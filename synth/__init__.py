@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
 
 This module holds none of the cipher's arithmetic: it only draws keys inside the
-paper's valid parameter ranges (Eq. 5, Eq. 6) and makes HWC uint8 video frames.
+paper's valid parameter ranges (Eq. 5, Eq. 6; the logistic map's r in [3.9, 4])
+and makes HWC uint8 video frames.
 The paper's own inputs (its test images and the trace-library videos of its
 speed evaluation, Sec. 3) are not available; these generators stand in for
 them:
@@ -15,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-PLCM, DLASM = 0, 1
+PLCM, DLASM, LOGISTIC = 0, 1, 2
 
 
 def key_for_seed(kind: int, seed: int) -> list[float]:
@@ -25,6 +26,8 @@ def key_for_seed(kind: int, seed: int) -> list[float]:
     p ~ U(0.01, 0.49) avoiding |p - 0.25| < 1e-3, for both maps.
     2DLASM (Eq. 6): x0, y0 ~ U(0.01, 0.99), mu ~ U(0.44, 0.93); returned as
     (x0, mu, y0), the order of the paper's key.
+    Logistic map (the third map): x0 ~ U(0.01, 0.99) avoiding |x0 - 0.5| < 1e-3
+    and r ~ U(3.9, 4.0), for both maps.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
 
@@ -42,6 +45,9 @@ def key_for_seed(kind: int, seed: int) -> list[float]:
         mu = float(rng.uniform(0.44, 0.93))
         y0 = float(rng.uniform(0.01, 0.99))
         return [x0, mu, y0]
+    if kind == LOGISTIC:
+        return [draw(0.01, 0.99, 0.5), float(rng.uniform(3.9, 4.0)),
+                draw(0.01, 0.99, 0.5), float(rng.uniform(3.9, 4.0))]
     raise ValueError(kind)
 
 

@@ -1,8 +1,9 @@
 """An independent pure-Python restatement of the cipher's keystream (Sec. 3,
-Eq. 5, Eq. 6) used only to cross-check the C oracle against compiler effects
-(contraction, excess precision).  Python floats are IEEE binary64 with one
-rounding per operation and no fused multiply-add.  This is not the oracle's
-pin by itself (the pins are the closed forms and bounds in test_oracle_pins.py).
+Eq. 5, Eq. 6, and the logistic map of the third PRBG) used only to cross-check
+the C oracle against compiler effects (contraction, excess precision).  Python
+floats are IEEE binary64 with one rounding per operation and no fused
+multiply-add.  This is not the oracle's pin by itself (the pins are the closed
+forms and bounds in test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -53,6 +54,10 @@ def lasm(x: float, y: float, mu: float):
     return xn, yn
 
 
+def logistic(x: float, r: float) -> float:
+    return (r * x) * (1.0 - x)
+
+
 def mbytes(v: float) -> bytes:
     return struct.pack("<d", v)[:6]
 
@@ -72,4 +77,12 @@ def lasm_pair_stream(x1, y1, m1, x2, y2, m2, nbytes):
         x2, y2 = lasm(x2, y2, m2)
         out += bytes(a ^ b for a, b in zip(mbytes(x1), mbytes(x2)))
         out += bytes(a ^ b for a, b in zip(mbytes(y1), mbytes(y2)))
+    return bytes(out[:nbytes])
+
+
+def logistic_pair_stream(x1, r1, x2, r2, nbytes):
+    out = bytearray()
+    while len(out) < nbytes:
+        x1, x2 = logistic(x1, r1), logistic(x2, r2)
+        out += bytes(a ^ b for a, b in zip(mbytes(x1), mbytes(x2)))
     return bytes(out[:nbytes])

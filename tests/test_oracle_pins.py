@@ -178,6 +178,61 @@ def test_lasm_fixed_points(orc):
     assert abs(mpmath.mpf(y) - mpmath.sin(3 * mpmath.pi * 0.7 * 0.3 * 0.7)) < 1e-15
 
 
+# --------------------------------------------------------------------- logistic map (third map)
+
+def test_logistic_orbit_at_r4_follows_the_doubling_closed_form(orc):
+    """Sec. 7 iii (a third map): at r = 4, x = sin^2(theta) maps to sin^2(2 theta),
+    so x_n = sin^2(2^n theta_0) with theta_0 = asin(sqrt(x_0)).  One binary64 step
+    adds at most 3 * 2^-53 and the map's slope is at most 4, so after n steps the
+    orbit is within 4^n * 2^-53 of the closed form (doubled here).  Catches a
+    wrong factor, (1 + x) for (1 - x), or r applied twice."""
+    mpmath.mp.prec = 200
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        x0 = float(rng.uniform(0.01, 0.99))
+        th = mpmath.asin(mpmath.sqrt(mpmath.mpf(x0)))
+        x = x0
+        for n in range(1, 13):
+            x = orc.logistic_step(x, 4.0)
+            exact = mpmath.sin(2 ** n * th) ** 2
+            assert abs(mpmath.mpf(x) - exact) <= 2 * 4.0 ** n * 2.0 ** -53, (x0, n)
+
+
+def test_logistic_fixed_point_and_two_cycle(orc):
+    """For r in [3.9, 4]: x* = 1 - 1/r is fixed and x+- = (r + 1 +- sqrt((r - 3)(r + 1))) / (2r)
+    swap (closed forms of the map's orbits; they pin the r-dependence that the
+    r = 4 test cannot).  The slope there is at most 4 in size, so the images
+    stay within 3 ulp-sized units plus 4 times the rounding of the start."""
+    mpmath.mp.prec = 200
+    for r in np.linspace(3.9, 4.0, 41):
+        r = float(r)
+        R = mpmath.mpf(r)
+        xs = 1 - 1 / R
+        got = orc.logistic_step(float(xs), r)
+        assert abs(mpmath.mpf(got) - xs) <= 4 * 2.0 ** -53 + 4 * abs(mpmath.mpf(float(xs)) - xs)
+        d = mpmath.sqrt((R - 3) * (R + 1))
+        xp, xm = (R + 1 + d) / (2 * R), (R + 1 - d) / (2 * R)
+        got = orc.logistic_step(float(xp), r)
+        assert abs(mpmath.mpf(got) - xm) <= 4 * 2.0 ** -53 + 4 * abs(mpmath.mpf(float(xp)) - xp)
+
+
+def test_logistic_key_schedule(orc):
+    """The third map's key schedule, read like R8: PRBG_m is the logistic pair
+    keyed by K = (x0^1, r^1, x0^2, r^2); subframe i gets (u1, 3.9 + 0.1 u2, u3,
+    3.9 + 0.1 u4) from four consecutive 6-byte groups, u = (U + 1/2) 2^-48."""
+    key = [0.3141, 3.95, 0.7182, 3.99]
+    n = 5
+    stream = orc.prbg_bytes(orc.PRBG_LOGI_PAIR, key, 6 * 4 * n)
+    groups = [int.from_bytes(stream[6 * g: 6 * g + 6], "little") for g in range(4 * n)]
+    u = [float(Fraction(2 * U + 1, 1 << 49)) for U in groups]
+    c = orc.OracleCipher(orc.LOGISTIC, key, 8, 8, 3, n, rounds=1)
+    for i in range(n):
+        prm = c.sub_params(i)
+        assert prm[0] == u[4 * i] and prm[2] == u[4 * i + 2]
+        assert prm[1] == 3.9 + 0.1 * u[4 * i + 1] and prm[3] == 3.9 + 0.1 * u[4 * i + 3]
+        assert 3.9 <= prm[1] < 4.0 and 3.9 <= prm[3] < 4.0
+
+
 # --------------------------------------------------------------------- bytes and PRBGs
 
 def test_mantissa_bytes_closed_form(orc):
@@ -207,8 +262,10 @@ def test_prbg_pairing_and_continuity(orc):
     all-zero stream); the stream is continuous across requests of any size."""
     assert orc.prbg_bytes(orc.PRBG_PLCM_PAIR, [0.3, 0.2, 0.3, 0.2], 600) == bytes(600)
     assert orc.prbg_bytes(orc.PRBG_LASM_PAIR, [0.3, 0.6, 0.7, 0.3, 0.6, 0.7], 600) == bytes(600)
+    assert orc.prbg_bytes(orc.PRBG_LOGI_PAIR, [0.3, 3.93, 0.3, 3.93], 600) == bytes(600)
     for kind, prm in ((orc.PRBG_PLCM_PAIR, [0.31, 0.21, 0.62, 0.37]),
-                      (orc.PRBG_LASM_PAIR, [0.31, 0.21, 0.62, 0.77, 0.4, 0.51])):
+                      (orc.PRBG_LASM_PAIR, [0.31, 0.21, 0.62, 0.77, 0.4, 0.51]),
+                      (orc.PRBG_LOGI_PAIR, [0.31, 3.91, 0.62, 3.97])):
         whole = orc.prbg_bytes(kind, prm, 1000)
         assert orc.prbg_bytes(kind, prm, 1000, chunks=[1, 5, 7, 11, 0, 13, 963]) == whole
         assert orc.prbg_bytes(kind, prm, 1000, chunks=[500, 500]) == whole
@@ -234,6 +291,8 @@ def test_keystreams_match_independent_python_restatement(orc):
     assert orc.prbg_bytes(orc.PRBG_PLCM_PAIR, prm, 6000) == pyref.plcm_pair_stream(*prm, 6000)
     prm2 = [0.11, 0.23, 0.61, 0.77, 0.41, 0.87]
     assert orc.prbg_bytes(orc.PRBG_LASM_PAIR, prm2, 3000) == pyref.lasm_pair_stream(*prm2, 3000)
+    prm3 = [0.123456789, 3.9271828, 0.87654321, 3.9914159]
+    assert orc.prbg_bytes(orc.PRBG_LOGI_PAIR, prm3, 6000) == pyref.logistic_pair_stream(*prm3, 6000)
 
 
 # --------------------------------------------------------------------- key schedule
@@ -289,6 +348,10 @@ def test_key_and_layout_validation(orc):
     assert not orc.key_valid(orc.DLASM, [0.3, 0.39, 0.6])
     assert not orc.key_valid(orc.DLASM, [0.3, 0.95, 0.6])
     assert not orc.key_valid(orc.DLASM, [0.0, 0.5, 0.6])
+    assert orc.key_valid(orc.LOGISTIC, [0.3, 3.9, 0.6, 4.0])
+    assert not orc.key_valid(orc.LOGISTIC, [0.3, 3.8, 0.6, 3.95])
+    assert not orc.key_valid(orc.LOGISTIC, [0.3, 3.95, 0.6, 4.01])
+    assert not orc.key_valid(orc.LOGISTIC, [1.0, 3.95, 0.6, 3.95])
     assert orc.layout_valid(480, 480, 3, 4)
     assert not orc.layout_valid(4, 4, 1, 16)  # 1-byte subframes
     assert orc.layout_valid(4, 4, 1, 8)
@@ -440,7 +503,7 @@ def test_undiffusion_inverts_diffusion(orc):
 
 # --------------------------------------------------------------------- whole cipher
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("H,W,C,n,rounds", [(16, 16, 3, 4, 5), (12, 20, 3, 7, 5), (9, 5, 1, 3, 2),
                                              (8, 8, 4, 64, 5), (10, 10, 3, 1, 5), (7, 13, 3, 91, 1)])
 def test_round_trip(orc, kind, H, W, C, n, rounds):
