@@ -43,6 +43,7 @@ PLCM_ITER_CYCLES = 251.0
 # 768x768x3, n = 4096): scaled to the bench's launches by their frames
 PLCM_KS_DRAM_BYTES_PER_FRAME = (365_568 + 297_627_904) / 40
 
+MAP_KIND = {"plcm": 0, "2dlasm": 1, "logistic": 2}  # VC_PLCM, VC_2DLASM, VC_LOGISTIC
 METRIC = "5-round enc Mpixel/s"
 
 
@@ -52,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--map", choices=["plcm", "2dlasm"], default="plcm")
+    ap.add_argument("--map", choices=["plcm", "2dlasm", "logistic"], default="plcm")
     ap.add_argument("--frames", type=int, default=240)
     ap.add_argument("--size", type=int, default=768)
     ap.add_argument("--n", type=int, default=4096)
@@ -144,7 +145,7 @@ def time_oracle(a, budget_s: float, seed_frames):
     import oracle
     import synth
 
-    kind = 0 if a.map == "plcm" else 1
+    kind = MAP_KIND[a.map]
     c = oracle.OracleCipher(kind, synth.key_for_seed(kind, 100), a.size, a.size, 3, a.n, a.rounds)
     done, t0 = 0, time.perf_counter()
     while True:
@@ -262,7 +263,7 @@ def run_ours(a) -> None:
     from paper_2302_07411_gb300 import build as cuda_build
 
     cuda_build.build()
-    kind = B.VC_PLCM if a.map == "plcm" else B.VC_2DLASM
+    kind = MAP_KIND[a.map]
     F, H, W, Cc = a.frames, a.size, a.size, 3
     N = H * W * Cc
     X = synth.smooth_clip(F, H, W, Cc, seed=3)
@@ -362,8 +363,8 @@ def run_ours(a) -> None:
     ks_ms = prof["keystream"]["ms"] / ks_launches            # per launch
     rd_ms = prof["rounds"]["ms"] / max(1, a.steps)
     sc_ms = prof["schedule"]["ms"] / max(1, a.steps)
-    if a.map == "plcm":
-        iters = F * (a.rounds * N) / 6.0 * 2  # two PLCM iterations per 6 keystream bytes
+    if a.map != "2dlasm":
+        iters = F * (a.rounds * N) / 6.0 * 2  # two map iterations per 6 keystream bytes (PLCM, logistic)
     else:
         iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 keystream bytes
     achieved_iter = iters / (ks_ms_step * 1e-3)
@@ -384,8 +385,9 @@ def run_ours(a) -> None:
                "frac": round(achieved_iter / (chains * clock / PLCM_ITER_CYCLES), 4)}
     else:
         # binary64 kernel: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz over ~60 binary64
-        # instructions per 2DLASM iterate (two csin of a degree-17/16 Horner chain)
-        fp64_per_iter = 60.0
+        # instructions per 2DLASM iterate (two csin of a degree-17/16 Horner chain),
+        # 3 per logistic iterate (two products and a difference)
+        fp64_per_iter = 60.0 if a.map == "2dlasm" else 3.0
         peak_iter = 152 * 2 * clock / fp64_per_iter
         basis = f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration"
         lat = None
@@ -393,7 +395,8 @@ def run_ours(a) -> None:
     traffic = None
     if a.map == "plcm" and a.size == 768 and a.n == 4096 and a.rounds == 5:
         traffic = round(PLCM_KS_DRAM_BYTES_PER_FRAME * F / per_launch)
-    roofline = {"bound": "alu", "kernel": "k_ks_plcm_fx_sm" if a.map == "plcm" else "k_ks_pair_sm<2DLASM>",
+    roofline = {"bound": "alu", "kernel": {"plcm": "k_ks_plcm_fx_sm", "2dlasm": "k_ks_pair_sm<2DLASM>",
+                                           "logistic": "k_ks_pair_sm<logistic>"}[a.map],
                 "unit": "Giter/s", "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
                 "frac": round(achieved_iter / peak_iter, 4), "traffic": traffic, "peak_basis": basis,
                 "latency_bound": lat, "launch_ms": round(ks_ms, 3), "launches_per_step": per_launch}

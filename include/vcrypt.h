@@ -36,7 +36,7 @@ extern "C" {
 /* ---- status codes ---- */
 #define VC_OK 0
 #define VC_ERR_ARG 1        /* null pointer, negative count, bad enum */
-#define VC_ERR_KEY_RANGE 2  /* key outside the valid ranges of Eq. 5 / Eq. 6 */
+#define VC_ERR_KEY_RANGE 2  /* key outside the valid ranges of its map (Eq. 5, Eq. 6, logistic), or no such map */
 #define VC_ERR_LAYOUT 3     /* H, W < 1; C not in {1,3,4}; n < 1; a subframe below 2 bytes; sizes too large */
 #define VC_ERR_CUDA 4       /* a CUDA runtime call failed (message: vc_last_error) */
 #define VC_ERR_OOM 5        /* device or host allocation failed */
@@ -49,9 +49,13 @@ extern "C" {
 #define VC_PLCM 0   /* key k = {x0^1, p^1, x0^2, p^2}: x0 in (0,1), p in (0, 1/2)        (Eq. 5) */
 #define VC_2DLASM 1 /* key k = {x0, mu, y0, unused}: x0, y0 in (0,1),
                        mu in [.37,.38] u [.4,.42] u [.44,.93] u {1}                       (Eq. 6) */
+#define VC_LOGISTIC 2 /* key k = {x0^1, r^1, x0^2, r^2}: x0 in (0,1), r in [3.9, 4]; the
+                         logistic map x' = (r x)(1 - x) in the PLCM's place, as the paper
+                         allows other chaotic maps (Sec. 7, advantage iii); per subframe
+                         x0 = u, r = 3.9 + 0.1 u from PRBG_m as for the PLCM */
 
 typedef struct {
-  int32_t kind;  /* VC_PLCM or VC_2DLASM */
+  int32_t kind;  /* VC_PLCM, VC_2DLASM or VC_LOGISTIC */
   double k[4];   /* the key K of Alg. 1 (Sec. 5.1: four or three doubles) */
 } vc_key;
 

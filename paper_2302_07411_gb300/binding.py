@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libvcrypt.so")
 _lib = None
 
 VC_OK = 0
-VC_PLCM, VC_2DLASM = 0, 1
+VC_PLCM, VC_2DLASM, VC_LOGISTIC = 0, 1, 2
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS, VC_OPT_KS_SM_WARPS = 1, 2, 3, 4, 5, 6
 VC_OPT_RUNAHEAD_CALLS = 7
 VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD = 1, 2, 3

@@ -55,6 +55,11 @@ bool key_valid(const vc_key& k) {
                        mu == 1.0;
     return k.k[0] > 0.0 && k.k[0] < 1.0 && k.k[2] > 0.0 && k.k[2] < 1.0 && mu_ok;
   }
+  if (k.kind == VC_LOGISTIC) {
+    for (int i = 0; i < 4; i += 2)
+      if (!(k.k[i] > 0.0 && k.k[i] < 1.0 && k.k[i + 1] >= 3.9 && k.k[i + 1] <= 4.0)) return false;
+    return true;
+  }
   return false;
 }
 
@@ -178,8 +183,10 @@ struct vc_ctx {
 
   vc::Tables tables() const { return vc::Tables{d_pi, d_sbits, d_srank, d_fixlim}; }
   vc::Chains chains() const { return vc::Chains{d_st, d_par, d_carry, d_carry_len}; }
-  int state_words() const { return kind == VC_PLCM ? 2 : 4; }
-  int par_words() const { return kind == VC_PLCM ? 4 : 2; }
+  // PLCM and logistic pairs: x per map, (p, 1/2 - p) or (r, 0) per map;
+  // 2DLASM pairs: (x, y) per map, pi * mu per map
+  int state_words() const { return kind == VC_2DLASM ? 4 : 2; }
+  int par_words() const { return kind == VC_2DLASM ? 2 : 4; }
 };
 
 namespace {
@@ -304,7 +311,7 @@ int ks_warps_in_use(const vc_ctx* c) {
   if (c->ks_sm_warps >= 0) return c->ks_sm_warps;
   if (!c->overlap) return 0;
   const int lanes = 2 * c->L.n;
-  if (c->kind == VC_2DLASM) {
+  if (c->kind == VC_2DLASM) {  // ~60 binary64 operations per step: four warps per SM saturate the pipe
     const int ctas2 = (lanes + 63) / 64;
     if (ctas2 + (c->num_sms + 7) / 8 <= c->num_sms) return 2;
   }
@@ -676,7 +683,7 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
   }
   vc::MainPrbg m{};
   m.kind = key->kind;
-  if (key->kind == VC_PLCM) {
+  if (key->kind == VC_PLCM || key->kind == VC_LOGISTIC) {
     for (int i = 0; i < 4; i++) m.s[i] = key->k[i];
   } else {  // K = (x0, mu, y0) -> state (x, y, mu)
     m.s[0] = key->k[0];

@@ -52,7 +52,7 @@ struct Chains {
 
 // PRBG_m of Alg. 1 (one per stream).
 struct MainPrbg {
-  double s[4];        // PLCM pair {x1, p1, x2, p2}; 2DLASM single {x, y, mu, 0}
+  double s[4];        // PLCM pair {x1, p1, x2, p2}; 2DLASM single {x, y, mu, 0}; logistic pair {x1, r1, x2, r2}
   uint64_t carry[2];  // unconsumed bytes, first byte lowest
   int carry_len;
   int kind;

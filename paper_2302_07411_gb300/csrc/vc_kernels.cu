@@ -117,6 +117,12 @@ __device__ uint64_t main_next_group(MainPrbg& m) {
       m.carry[0] = mant48(m.s[0]) ^ mant48(m.s[2]);
       m.carry[1] = 0;
       m.carry_len = 6;
+    } else if (m.kind == 2) {  // logistic pair, 6 bytes per iterate
+      m.s[0] = logistic_step(m.s[0], m.s[1]);
+      m.s[2] = logistic_step(m.s[2], m.s[3]);
+      m.carry[0] = mant48(m.s[0]) ^ mant48(m.s[2]);
+      m.carry[1] = 0;
+      m.carry_len = 6;
     } else {  // single 2DLASM, x bytes then y bytes
       lasm_step(m.s[0], m.s[1], __dmul_rn(kPi, m.s[2]));
       const uint64_t vx = mant48(m.s[0]), vy = mant48(m.s[1]);
@@ -152,6 +158,17 @@ __global__ void k_key_schedule(int kind, MainPrbg* mp, Chains ch, int n) {
       ch.par[4 * i + 1] = __dsub_rn(0.5, p1);
       ch.par[4 * i + 2] = p2;
       ch.par[4 * i + 3] = __dsub_rn(0.5, p2);
+    } else if (kind == 2) {  // logistic pair: x0 = u, r = 3.9 + 0.1 u
+      const double u1 = unit_of(main_next_group(m));
+      const double u2 = unit_of(main_next_group(m));
+      const double u3 = unit_of(main_next_group(m));
+      const double u4 = unit_of(main_next_group(m));
+      ch.st[2 * i] = u1;
+      ch.st[2 * i + 1] = u3;
+      ch.par[4 * i] = __dadd_rn(3.9, __dmul_rn(0.1, u2));
+      ch.par[4 * i + 1] = 0.0;
+      ch.par[4 * i + 2] = __dadd_rn(3.9, __dmul_rn(0.1, u4));
+      ch.par[4 * i + 3] = 0.0;
     } else {
       const double u1 = unit_of(main_next_group(m));
       const double u2 = unit_of(main_next_group(m));
@@ -300,11 +317,11 @@ template <int KIND, bool INTDIV>
 __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
-  constexpr int STEP = KIND == 0 ? 6 : 12;  // bytes per iterate of the pair
+  constexpr int STEP = KIND == 1 ? 12 : 6;  // bytes per iterate of the pair (2DLASM: x and y)
   const int qstart = L.C * tb.pi[i];
   const int qend = L.C * tb.pi[i + 1];
   double x1, x2, y1 = 0, y2 = 0, p1 = 0, q1 = 0, p2 = 0, q2 = 0, pm1 = 0, pm2 = 0;
-  if (KIND == 0) {
+  if (KIND != 1) {  // PLCM: p, 1/2 - p per map; logistic: r, 0 per map
     x1 = ch.st[2 * i];
     x2 = ch.st[2 * i + 1];
     p1 = ch.par[4 * i];
@@ -350,7 +367,11 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
     }
     // 2. whole iterates
     while (rem >= STEP) {
-      if (KIND == 0) {
+      if (KIND == 2) {
+        x1 = logistic_step(x1, p1);
+        x2 = logistic_step(x2, p2);
+        w.put(mant48(x1) ^ mant48(x2), 6);
+      } else if (KIND == 0) {
         if (INTDIV) {
           x1 = plcm_step_int(x1, m1);
           x2 = plcm_step_int(x2, m2);
@@ -370,7 +391,12 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
     // 3. a last, partly used iterate; its other bytes carry over
     if (rem > 0) {
       uint64_t lo, hi;
-      if (KIND == 0) {
+      if (KIND == 2) {
+        x1 = logistic_step(x1, p1);
+        x2 = logistic_step(x2, p2);
+        lo = mant48(x1) ^ mant48(x2);
+        hi = 0;
+      } else if (KIND == 0) {
         if (INTDIV) {
           x1 = plcm_step_int(x1, m1);
           x2 = plcm_step_int(x2, m2);
@@ -397,7 +423,7 @@ __global__ void __launch_bounds__(32) k_keystream(Layout L, Tables tb, Chains ch
       rem = 0;
     }
   }
-  if (KIND == 0) {
+  if (KIND != 1) {
     ch.st[2 * i] = x1;
     ch.st[2 * i + 1] = x2;
   } else {
@@ -524,18 +550,18 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
                                               uint8_t* ks, const int i, const int side, int cap = 0, int slot0 = 0) {
   if (i >= L.n) return;  // both lanes of a pair leave together
   const unsigned pmask = 3u << (threadIdx.x & 30);
-  constexpr int STEP = KIND == 0 ? 6 : 12;
+  constexpr int STEP = KIND == 1 ? 12 : 6;  // 2DLASM: x and y per iterate
 
   double x = 0, y = 0, p = 0, qd = 0, pm = 0;
   uint64_t xb = 0;
   PlcmFx F{};
   bool fx_ok = false;
-  if (KIND == 0) {
+  if (KIND != 1) {  // PLCM (p, 1/2 - p) or logistic (r, 0) per map
     x = ch.st[2 * i + side];
     p = ch.par[4 * i + 2 * side];
     qd = ch.par[4 * i + 2 * side + 1];
     xb = (uint64_t)__double_as_longlong(x);
-    if (FX) fx_ok = make_plcm_fx(p, qd, F);
+    if (FX && KIND == 0) fx_ok = make_plcm_fx(p, qd, F);
   } else {
     x = ch.st[4 * i + 2 * side];
     y = ch.st[4 * i + 2 * side + 1];
@@ -553,7 +579,9 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
 
   // one PLCM iterate of this lane's map; the pair's XORed 6-byte group
   auto plcm_next = [&]() -> uint64_t {
-    if (FX) {
+    if (KIND == 2) {
+      xb = (uint64_t)__double_as_longlong(logistic_step(__longlong_as_double((long long)xb), p));
+    } else if (FX) {
       bool ok = true;
       uint64_t nb = fx_ok ? plcm_fx_step(xb, F, ok) : 0;
       if (!fx_ok || !ok) nb = (uint64_t)__double_as_longlong(plcm_step(__longlong_as_double((long long)xb), p, qd));
@@ -589,7 +617,7 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
     while (rem > 0) {
       if (rem >= 24 && w.fast_ok()) {
         uint64_t a0, a1, a2, a3;
-        if (KIND == 0) {
+        if (KIND != 1) {
           a0 = plcm_next();
           a1 = plcm_next();
           a2 = plcm_next();
@@ -602,7 +630,7 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
         rem -= 24;
       } else {
         uint64_t lo, hi = 0;
-        if (KIND == 0) {
+        if (KIND != 1) {
           lo = plcm_next();
         } else {
           uint64_t vx, vy;
@@ -623,7 +651,7 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
       }
     }
   }
-  if (KIND == 0) {
+  if (KIND != 1) {
     ch.st[2 * i + side] = __longlong_as_double((long long)xb);
   } else {
     ch.st[4 * i + 2 * side] = x;
@@ -909,6 +937,10 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
       e = allow_smem(k_ks_pair_sm<0>, smem);
       if (e != cudaSuccess) return e;
       k_ks_pair_sm<0><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+    } else if (kind == 2) {
+      e = allow_smem(k_ks_pair_sm<2>, smem);
+      if (e != cudaSuccess) return e;
+      k_ks_pair_sm<2><<<blocks, threads, smem, st>>>(L, tb, ch, nframes, ks, cap, slot0);
     } else {
       e = allow_smem(k_ks_pair_sm<1>, smem);
       if (e != cudaSuccess) return e;
@@ -921,6 +953,8 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
     k_ks_plcm_fx<<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0, plcm_int >= 2 ? plcm_int - 1 : 0);
   else if (kind == 0)
     k_ks_pair<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
+  else if (kind == 2)
+    k_ks_pair<2, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   else
     k_ks_pair<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks, cap, slot0);
   return cudaGetLastError();
@@ -936,6 +970,8 @@ cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains
     k_keystream<0, true><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   else if (kind == 0)
     k_keystream<0, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
+  else if (kind == 2)
+    k_keystream<2, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   else
     k_keystream<1, false><<<blocks, 32, 0, st>>>(L, tb, ch, nframes, ks);
   return cudaGetLastError();
@@ -1673,6 +1709,8 @@ __global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHd
   const int side = threadIdx.x & 1;
   if (d.kind == 0)
     ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+  else if (d.kind == 2)
+    ks_pair_chain<2, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
   else
     ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
 }

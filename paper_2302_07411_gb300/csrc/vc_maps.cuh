@@ -115,6 +115,12 @@ __device__ __forceinline__ double plcm_step_int(double x, const PlcmMap& m) {
   return r;
 }
 
+// ---- the logistic map, a third map for the same strategy -------------------
+// x' = (r x)(1 - x), left to right; r in [3.9, 4].
+__device__ __forceinline__ double logistic_step(double x, double r) {
+  return __dmul_rn(__dmul_rn(r, x), __dsub_rn(1.0, x));
+}
+
 // ---- 2DLASM, Eq. 6 ----------------------------------------------------------
 // pm = RN(pi * mu).  x' = csin(((pm*(y+3))*x)*(1-x)); y' uses the new x'.
 __device__ __forceinline__ void lasm_step(double& x, double& y, double pm) {

@@ -20,6 +20,8 @@ STREAMS = [  # (kind, H, W, C, n, rounds, direction, frames per batch)
     (0, 33, 47, 1, 5, 3, 0, 3),
     (1, 64, 32, 4, 64, 2, 0, 1),
     (0, 120, 90, 3, 30, 5, 0, 1),
+    (2, 56, 72, 3, 24, 5, 0, 2),
+    (2, 30, 30, 3, 9, 4, 1, 1),
 ]
 
 

@@ -131,7 +131,7 @@ def _oracle_ks_to_frame_layout(ks_cat, bounds, rounds, N):
 
 
 @pytest.mark.parametrize("kind,plcm_int,lanes", [(0, 1, 2), (0, 0, 2), (0, 2, 2), (0, 3, 2), (1, 1, 2), (0, 1, 1),
-                                                (0, 0, 1), (1, 1, 1)])
+                                                (0, 0, 1), (1, 1, 1), (2, 1, 2), (2, 1, 1)])
 @pytest.mark.parametrize("H,W,C,n,r,frames", [(16, 16, 3, 4, 5, 3), (17, 23, 3, 5, 5, 4), (9, 31, 1, 13, 3, 5),
                                                (12, 12, 4, 144, 1, 3), (48, 40, 3, 7, 2, 6), (33, 47, 3, 61, 5, 3),
                                                (48, 48, 3, 16, 5, 3), (80, 88, 1, 16, 5, 3)])
@@ -194,7 +194,7 @@ def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_r
     g_d.close()
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_config_single_480_frame(B, orc, kind):
     """480 x 480 x 3, uniform random bytes (seed 1), key from seed 1, n = 4, r = 5:
     encrypt and decrypt bit-exact against the oracle."""
@@ -211,7 +211,7 @@ def test_config_smooth_576_clip(B, orc, kind, n):
     _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 2 + n), X, n, 5)
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("H,W,C,n,r", [
     (17, 23, 3, 5, 5),     # odd sizes, one tile
     (100, 37, 3, 91, 2),   # several tiles, ragged last tile, tiny subframes
@@ -235,7 +235,7 @@ def test_tile_shapes_do_not_change_the_ciphertext(B, orc, tile_rows):
     _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 17), X, 9, 5, tile_rows=tile_rows)
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("warps", [1, 2, 4])
 def test_keystream_on_reserved_sms(B, orc, kind, warps):
     """Keystream CTAs that each hold a whole SM (several passes, so keystream
@@ -254,7 +254,7 @@ def test_exact_fallback_in_full_warps(B, orc, mode, H, W, C, n):
     _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 29), X, n, 5, chunk=2, plcm_int=mode)
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_chunked_and_in_place(B, orc, kind):
     """Frames processed in passes of 2 and in place give the same stream."""
     X = synth.uniform_frames(5, 40, 56, 3, seed=9)
@@ -305,9 +305,16 @@ def test_invalid_arguments_are_errors(B):
     with pytest.raises(B.VcError) as e:
         B.Cipher(1, [0.3, 0.39, 0.5], 16, 16)
     assert e.value.code == 2
+    with pytest.raises(B.VcError) as e:
+        B.Cipher(2, [0.3, 3.8, 0.5, 3.95], 16, 16)  # r outside [3.9, 4]
+    assert e.value.code == 2
+    with pytest.raises(B.VcError) as e:
+        B.Cipher(3, [0.3, 0.2, 0.5, 0.2], 16, 16)  # no such map
+    assert e.value.code == 2
 
 
-@pytest.mark.parametrize("kind,H,W,n", [(0, 2160, 3840, 540), (1, 1080, 1920, 270), (0, 1080, 1920, 4096)])
+@pytest.mark.parametrize("kind,H,W,n", [(0, 2160, 3840, 540), (1, 1080, 1920, 270), (0, 1080, 1920, 4096),
+                                        (2, 1080, 1920, 270)])
 def test_largest_frames(B, orc, kind, H, W, n):
     """The serving workload's largest frames (rows of 11,520 bytes: 8-row tiles,
     wider than tall), two frames per call: equal to the oracle byte for byte,
@@ -323,7 +330,7 @@ def test_largest_frames(B, orc, kind, H, W, n):
     dd.close()
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_full_size_768_n4096_sampled(B, orc, kind):
     """The benchmark's launch configuration (768 x 768 x 3, n = 4096, r = 5, many
     frames per pass): all 24 frames round-trip; the first 3 equal the oracle
