@@ -155,13 +155,13 @@ def main():
 
     ap = argparse.ArgumentParser(description="robustness and round-count curves")
     ap.add_argument("--out", default=None)
-    ap.add_argument("--map", choices=["plcm", "2dlasm"], default="plcm")
+    ap.add_argument("--map", choices=["plcm", "2dlasm", "logistic"], default="plcm")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     from . import build
 
     build.build()
-    kind = 0 if a.map == "plcm" else 1
+    kind = {"plcm": 0, "2dlasm": 1, "logistic": 2}[a.map]
     res = {"map": a.map, "noise": noise_robustness(kind), "data_loss": data_loss(kind),
            "error_propagation": error_propagation(kind), "rounds": rounds_sweep(kind)}
     text = json.dumps(res, indent=1)
