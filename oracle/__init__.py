@@ -78,6 +78,9 @@ def lib():
             "orc_unconfuse": (None, [i32, i32, i32, p, p, p]),
             "orc_diffuse": (None, [i32, i32, i32, i32, p, p, p]),
             "orc_undiffuse": (None, [i32, i32, i32, i32, p, p, p]),
+            "orc_diffuse_pc": (None, [i32, i32, i32, i32, p, p, p]),
+            "orc_undiffuse_pc": (None, [i32, i32, i32, i32, p, p, p]),
+            "orc_ctx_set_chains": (i32, [p, i32]),
             "orc_encrypt_frame": (i32, [p, p, p, p]),
             "orc_decrypt_frame": (i32, [p, p, p, p]),
             "orc_frame_keystream": (i32, [p, p, p]),
@@ -229,17 +232,39 @@ def undiffuse(Xc: np.ndarray, ks_list, n: int) -> np.ndarray:
     return out
 
 
+def diffuse_pc(Y: np.ndarray, ks_list, n: int) -> np.ndarray:
+    """Eq. 3 with one chain per colour channel (the alternative reading)."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint8)
+    H, W, Cc = Y.shape
+    keep, ptrs = _ks_ptrs(ks_list)
+    out = np.empty_like(Y)
+    lib().orc_diffuse_pc(H, W, Cc, n, ptrs, _ptr(Y), _ptr(out))
+    return out
+
+
+def undiffuse_pc(Xc: np.ndarray, ks_list, n: int) -> np.ndarray:
+    """Eq. 4 with one chain per colour channel."""
+    Xc = np.ascontiguousarray(Xc, dtype=np.uint8)
+    H, W, Cc = Xc.shape
+    keep, ptrs = _ks_ptrs(ks_list)
+    out = np.empty_like(Xc)
+    lib().orc_undiffuse_pc(H, W, Cc, n, ptrs, _ptr(Xc), _ptr(out))
+    return out
+
+
 # ---------------------------------------------------------------- the cipher
 
 class OracleCipher:
     """One video stream of the cipher (Alg. 1 + Alg. 2, executed serially).
 
     kind: PLCM (key = x0^1, p^1, x0^2, p^2), DLASM (key = x0, mu, y0) or
-    LOGISTIC (key = x0^1, r^1, x0^2, r^2).
+    LOGISTIC (key = x0^1, r^1, x0^2, r^2).  per_channel selects one diffusion
+    chain per colour channel instead of the byte chain (reading R4).
     Frames are H x W x C uint8 arrays; state advances one frame per call.
     """
 
-    def __init__(self, kind: int, key, H: int, W: int, C_: int = 3, n: int = 4, rounds: int = 5):
+    def __init__(self, kind: int, key, H: int, W: int, C_: int = 3, n: int = 4, rounds: int = 5,
+                 per_channel: bool = False):
         self.kind, self.H, self.W, self.C, self.n, self.rounds = kind, H, W, C_, n, rounds
         self._buf = np.zeros(lib().orc_ctx_size(n), dtype=np.uint8)
         k = np.zeros(4, dtype=np.float64)
@@ -249,6 +274,8 @@ class OracleCipher:
             raise ValueError("key outside the valid ranges of Eq. 5 / Eq. 6")
         if rc == 2:
             raise ValueError("invalid layout")
+        if per_channel and lib().orc_ctx_set_chains(_ptr(self._buf), 1) != 0:
+            raise ValueError("per-channel chains need at least 2 pixels per subframe")
         self.N = H * W * C_
         self.last_sc = None
 

@@ -23,6 +23,9 @@
  *   Eq. 3      diffusion with ciphertext feedback, seed s_d from the last pixel
  *              of subframe (i+1) mod n (Alg. 2)  -> orc_diffuse()
  *   Eq. 4      inverse diffusion                 -> orc_undiffuse()
+ *   Eq. 3/4, the per-channel reading (one chain per colour channel; a variant
+ *              kept beside the default byte chains) -> orc_diffuse_pc(),
+ *                                                    orc_undiffuse_pc()
  *   Alg. 1/2   r rounds of confusion then diffusion per frame
  *                                                 -> orc_encrypt_frame()
  *
@@ -278,7 +281,7 @@ int orc_ctx_init(orc_ctx* c, int kind, const double* key, int H, int W, int C, i
   int i;
   if (!orc_key_valid(kind, key)) return 1;
   if (!orc_layout_valid(H, W, C, n, rounds)) return 2;
-  c->kind = kind; c->H = H; c->W = W; c->C = C; c->n = n; c->rounds = rounds;
+  c->kind = kind; c->H = H; c->W = W; c->C = C; c->n = n; c->rounds = rounds; c->chains = 0;
   c->P = (int64_t)H * W; c->N = c->P * C; c->frame = 0;
   if (kind == ORC_PLCM) {
     /* K = (x0^1, p^1, x0^2, p^2): PRBG_m is a PLCM pair */
@@ -415,6 +418,62 @@ void orc_undiffuse(int H, int W, int C, int n, const uint8_t* const* ks, const u
   }
 }
 
+/* Eq. 3 with one chain per channel (the alternative to the byte-chain
+ * reading): byte ch of pixel p of subframe i follows byte ch of pixel p - 1;
+ * the first pixel's byte ch follows byte ch of the last pixel of subframe
+ * (i+1) mod n of the confused frame Y.  Keystream bytes as in orc_diffuse. */
+void orc_diffuse_pc(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Y, uint8_t* Xo) {
+  int64_t P = (int64_t)H * W;
+  int i;
+  for (i = 0; i < n; i++) {
+    int64_t start = C * ((i * P) / n), end = C * (((i + 1) * P) / n);
+    int64_t nxt = (i + 1) % n;
+    int64_t seed_pixel = C * (((nxt + 1) * P) / n) - C; /* first byte of the last pixel of subframe nxt */
+    int64_t q;
+    for (q = start; q < end; q++) {
+      int64_t ch = (q - start) % C;
+      uint8_t b = ks[i][q - start];
+      uint8_t prev = (q < start + C) ? Y[seed_pixel + ch] : Xo[q - C];
+      Xo[q] = (uint8_t)(b ^ (uint8_t)(Y[q] + b) ^ prev);
+    }
+  }
+}
+
+/* Eq. 4 per channel: every pixel but the first from the ciphertext alone, then
+ * each subframe's first pixel with the seed pixel recovered from subframe
+ * (i+1) mod n (which must hold at least 2 pixels). */
+void orc_undiffuse_pc(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Xc, uint8_t* Y) {
+  int64_t P = (int64_t)H * W;
+  int i;
+  for (i = 0; i < n; i++) {
+    int64_t start = C * ((i * P) / n), end = C * (((i + 1) * P) / n);
+    int64_t q;
+    for (q = start + C; q < end; q++) {
+      uint8_t b = ks[i][q - start];
+      Y[q] = (uint8_t)((uint8_t)(b ^ Xc[q] ^ Xc[q - C]) - b);
+    }
+  }
+  for (i = 0; i < n; i++) {
+    int64_t start = C * ((i * P) / n);
+    int64_t nxt = (i + 1) % n;
+    int64_t seed_pixel = C * (((nxt + 1) * P) / n) - C;
+    int ch;
+    for (ch = 0; ch < C; ch++) {
+      uint8_t b = ks[i][ch];
+      Y[start + ch] = (uint8_t)((uint8_t)(b ^ Xc[start + ch] ^ Y[seed_pixel + ch]) - b);
+    }
+  }
+}
+
+/* Select the diffusion chains of a context: 0 = bytes (R4, the default),
+ * 1 = per channel, which needs every subframe to hold at least 2 pixels. */
+int orc_ctx_set_chains(orc_ctx* c, int chains) {
+  if (chains != 0 && chains != 1) return 1;
+  if (chains == 1 && c->P / c->n < 2) return 2;
+  c->chains = chains;
+  return 0;
+}
+
 /* Per frame: s_c from PRBG_m, then r*S_i fresh bytes from each PRBG_a^i. */
 static int frame_schedule(orc_ctx* c, int64_t* sc_out, int64_t* k, uint8_t** ks_all) {
   int i;
@@ -450,7 +509,10 @@ int orc_encrypt_frame(orc_ctx* c, const uint8_t* in, uint8_t* out, int64_t* sc_o
       ksr[i] = ks_all[i] + j * Si;
     }
     orc_confuse(c->H, c->W, c->C, k, out, Y);
-    orc_diffuse(c->H, c->W, c->C, c->n, ksr, Y, out);
+    if (c->chains == 1)
+      orc_diffuse_pc(c->H, c->W, c->C, c->n, ksr, Y, out);
+    else
+      orc_diffuse(c->H, c->W, c->C, c->n, ksr, Y, out);
   }
   c->frame++;
 done:
@@ -473,7 +535,10 @@ int orc_decrypt_frame(orc_ctx* c, const uint8_t* in, uint8_t* out, int64_t* sc_o
       int64_t Si = c->C * (pi_at(c, i + 1) - pi_at(c, i));
       ksr[i] = ks_all[i] + j * Si;
     }
-    orc_undiffuse(c->H, c->W, c->C, c->n, ksr, out, Y);
+    if (c->chains == 1)
+      orc_undiffuse_pc(c->H, c->W, c->C, c->n, ksr, out, Y);
+    else
+      orc_undiffuse(c->H, c->W, c->C, c->n, ksr, out, Y);
     orc_unconfuse(c->H, c->W, c->C, k, Y, out);
   }
   c->frame++;

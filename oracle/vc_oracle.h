@@ -28,6 +28,7 @@ typedef struct {
 
 typedef struct {
   int32_t kind, H, W, C, n, rounds;
+  int32_t chains; /* diffusion chains: 0 = one per subframe over its bytes (R4), 1 = one per channel */
   int64_t P, N, frame;
   orc_prbg main;  /* PRBG_m of Alg. 1 */
   orc_prbg sub[]; /* PRBG_a^i of Alg. 2, i = 0..n-1 */
@@ -56,6 +57,9 @@ void orc_confuse(int H, int W, int C, const int64_t* k, const uint8_t* X, uint8_
 void orc_unconfuse(int H, int W, int C, const int64_t* k, const uint8_t* Y, uint8_t* X);
 void orc_diffuse(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Y, uint8_t* Xo);
 void orc_undiffuse(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Xc, uint8_t* Y);
+void orc_diffuse_pc(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Y, uint8_t* Xo);
+void orc_undiffuse_pc(int H, int W, int C, int n, const uint8_t* const* ks, const uint8_t* Xc, uint8_t* Y);
+int orc_ctx_set_chains(orc_ctx* c, int chains);
 int orc_encrypt_frame(orc_ctx* c, const uint8_t* in, uint8_t* out, int64_t* sc_out);
 int orc_decrypt_frame(orc_ctx* c, const uint8_t* in, uint8_t* out, int64_t* sc_out);
 int orc_frame_keystream(orc_ctx* c, uint8_t* out, int64_t* sc_out);

@@ -501,6 +501,91 @@ def test_undiffusion_inverts_diffusion(orc):
         assert np.array_equal(orc.undiffuse(orc.diffuse(Y, ks, n), ks, n), Y)
 
 
+def test_per_channel_diffusion_is_a_channel_xor_scan_of_d(orc):
+    """The per-channel reading of Eq. 3: for each channel, c_p = s xor d_start xor
+    ... xor d_p over the subframe's pixels, d = b xor ((y + b) mod 256), s = the
+    channel's byte of the last pixel of subframe (i+1) mod n of Y.  Checked with
+    b = 0 (a plain per-channel prefix XOR) and random b (catches a stride of 1
+    instead of C, a seed from the wrong byte, or channels mixed)."""
+    rng = np.random.default_rng(15)
+    for H, W, C, n in ((9, 11, 3, 5), (16, 16, 3, 1), (12, 7, 4, 12), (6, 6, 1, 4)):
+        Y = rng.integers(0, 256, (H, W, C), dtype=np.uint8)
+        bnd = _bounds(H, W, C, n)
+        for zero in (True, False):
+            ks = [(np.zeros if zero else lambda m: rng.integers(0, 256, m, dtype=np.uint8))(bnd[i + 1] - bnd[i])
+                  .astype(np.uint8) for i in range(n)]
+            out = orc.diffuse_pc(Y, ks, n).ravel()
+            y = Y.ravel()
+            for i in range(n):
+                b = ks[i]
+                d = b ^ ((y[bnd[i]:bnd[i + 1]].astype(np.uint16) + b) & 255).astype(np.uint8)
+                seed = y[bnd[(i + 1) % n + 1] - C: bnd[(i + 1) % n + 1]]
+                d = d.reshape(-1, C)
+                d[0] ^= seed
+                exp = np.bitwise_xor.accumulate(d, axis=0).ravel()
+                assert np.array_equal(out[bnd[i]:bnd[i + 1]], exp), (H, W, C, n, i, zero)
+
+
+def test_per_channel_undiffusion_inverts(orc):
+    rng = np.random.default_rng(16)
+    for H, W, C, n in ((9, 11, 3, 5), (4, 4, 1, 8), (5, 5, 3, 1), (16, 9, 4, 16), (6, 5, 3, 15)):
+        Y = rng.integers(0, 256, (H, W, C), dtype=np.uint8)
+        bnd = _bounds(H, W, C, n)
+        ks = [rng.integers(0, 256, bnd[i + 1] - bnd[i], dtype=np.uint8) for i in range(n)]
+        assert np.array_equal(orc.undiffuse_pc(orc.diffuse_pc(Y, ks, n), ks, n), Y)
+
+
+def test_per_channel_cipher_with_one_channel_is_the_byte_chain(orc):
+    """With C = 1 a pixel is a byte, so both readings are the same cipher."""
+    import synth
+
+    for kind in (0, 1):
+        key = synth.key_for_seed(kind, 31)
+        X = synth.uniform_frames(3, 13, 17, 1, seed=32)
+        a = orc.OracleCipher(kind, key, 13, 17, 1, 6, 5).encrypt(X)
+        b = orc.OracleCipher(kind, key, 13, 17, 1, 6, 5, per_channel=True).encrypt(X)
+        assert np.array_equal(a, b)
+
+
+def test_per_channel_cipher_keeps_channels_apart(orc):
+    """Confusion moves whole pixels and each chain stays in its channel, so a
+    change in channel 0 of one plaintext pixel leaves channels 1 and 2 of the
+    ciphertext unchanged and spreads over channel 0 (the behaviour the byte
+    chain of R4 avoids: there every channel changes)."""
+    import synth
+
+    key = synth.key_for_seed(0, 33)
+    X = synth.uniform_frames(1, 32, 32, 3, seed=34)
+    X2 = X.copy()
+    X2[0, 5, 7, 0] ^= 1
+    for per_channel in (True, False):
+        a = orc.OracleCipher(0, key, 32, 32, 3, 4, 5, per_channel=per_channel).encrypt(X)
+        b = orc.OracleCipher(0, key, 32, 32, 3, 4, 5, per_channel=per_channel).encrypt(X2)
+        changed = (a != b).mean(axis=(0, 1, 2))
+        if per_channel:
+            assert changed[1] == 0 and changed[2] == 0 and changed[0] > 0.98
+        else:
+            assert (changed > 0.98).all()
+
+
+@pytest.mark.parametrize("H,W,C,n,rounds", [(16, 16, 3, 4, 5), (12, 20, 3, 7, 5), (8, 8, 4, 32, 5),
+                                             (10, 10, 3, 1, 5), (7, 13, 3, 45, 1)])
+def test_per_channel_round_trip(orc, H, W, C, n, rounds):
+    import synth
+
+    for kind in (0, 1, 2):
+        key = synth.key_for_seed(kind, 35)
+        X = synth.uniform_frames(2, H, W, C, seed=36)
+        Y = orc.OracleCipher(kind, key, H, W, C, n, rounds, per_channel=True).encrypt(X)
+        assert np.array_equal(orc.OracleCipher(kind, key, H, W, C, n, rounds, per_channel=True).decrypt(Y), X)
+
+
+def test_per_channel_needs_two_pixels_per_subframe(orc):
+    with pytest.raises(ValueError):
+        orc.OracleCipher(0, [0.3, 0.2, 0.6, 0.4], 4, 4, 3, 16, per_channel=True)
+    orc.OracleCipher(0, [0.3, 0.2, 0.6, 0.4], 4, 4, 3, 8, per_channel=True)
+
+
 # --------------------------------------------------------------------- whole cipher
 
 @pytest.mark.parametrize("kind", [0, 1, 2])
