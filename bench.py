@@ -67,6 +67,8 @@ def parse():
                     help="keystream CTAs of this many warps, each holding a whole SM (0 = share all SMs, -1 = auto)")
     ap.add_argument("--direction", choices=["enc", "dec"], default="enc",
                     help="dec times decryption of the clip's ciphertext (not the headline metric)")
+    ap.add_argument("--diffusion", choices=["bytes", "per-channel"], default="bytes",
+                    help="diffusion chains: over the subframe's bytes (default) or one per colour channel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -83,7 +85,7 @@ def config(a, world: int) -> dict:
             "frames": a.frames, "height": a.size, "width": a.size, "channels": 3,
             "n_subframes": a.n, "rounds": a.rounds, "map": a.map, "parallelism": f"replicas{world}",
             "keystream_overlap": not a.no_overlap, "frames_per_pass": a.chunk or "auto",
-            "direction": a.direction, "tile_rows": a.tile_rows or "auto", "ks_sm_warps": a.ks_sm_warps if a.ks_sm_warps >= 0 else "auto",
+            "direction": a.direction, "diffusion": a.diffusion, "tile_rows": a.tile_rows or "auto", "ks_sm_warps": a.ks_sm_warps if a.ks_sm_warps >= 0 else "auto",
             "l2": "inputs 425 MB > 129 MB L2, no flush"}
 
 
@@ -146,7 +148,8 @@ def time_oracle(a, budget_s: float, seed_frames):
     import synth
 
     kind = MAP_KIND[a.map]
-    c = oracle.OracleCipher(kind, synth.key_for_seed(kind, 100), a.size, a.size, 3, a.n, a.rounds)
+    c = oracle.OracleCipher(kind, synth.key_for_seed(kind, 100), a.size, a.size, 3, a.n, a.rounds,
+                            per_channel=a.diffusion == "per-channel")
     done, t0 = 0, time.perf_counter()
     while True:
         c.encrypt(seed_frames[done % len(seed_frames)])
@@ -277,11 +280,13 @@ def run_ours(a) -> None:
     ciph.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
     ciph.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
     ciph.set_option(B.VC_OPT_KS_SM_WARPS, a.ks_sm_warps)
+    ciph.set_option(B.VC_OPT_DIFFUSION, 1 if a.diffusion == "per-channel" else 0)
     stream = torch.cuda.current_stream()
     if a.direction == "dec":
         # ciphertext of the clip from a separate encrypting context; every step
         # decrypts it again (the context's keystream moves on, the work is the same)
         ce0 = B.Cipher(kind, key, H, W, Cc, a.n, a.rounds)
+        ce0.set_option(B.VC_OPT_DIFFUSION, 1 if a.diffusion == "per-channel" else 0)
         ce0.encrypt(d_in, d_out, stream=stream)
         torch.cuda.synchronize()
         ce0.close()
@@ -340,6 +345,7 @@ def run_ours(a) -> None:
         ce.set_option(B.VC_OPT_PLCM_INT, 0 if a.plcm_fp64 else 1)
         ce.set_option(B.VC_OPT_KS_LANES, a.ks_lanes)
         ce.set_option(B.VC_OPT_KS_SM_WARPS, a.ks_sm_warps)
+        ce.set_option(B.VC_OPT_DIFFUSION, 1 if a.diffusion == "per-channel" else 0)
         for _ in range(max(1, a.warmup - 1)):
             ce.crypt_host(0 if a.direction == "enc" else 1, h_in, h_out, stream=stream)
         if world > 1:

@@ -298,6 +298,18 @@ int enc_sync_status(vc_ctx* ctx);
  *                  checkpoint, a batch, or an option that reallocates scratch
  *                  first undoes it exactly (nothing is observable but time);
  *                  0 turns it off (and undoes one that is pending).
+ * VC_OPT_DIFFUSION: 0 (default) diffuses each subframe as one chain over its
+ *                  bytes in memory order (the cipher of Eq. 3 / Eq. 4 as read
+ *                  here); 1 runs one chain per colour channel over the
+ *                  subframe's pixels, seeded by the same channel of the last
+ *                  pixel of the next subframe (a variant: a plaintext change
+ *                  in one channel then never reaches the others).  1 needs at
+ *                  least 2 pixels in every subframe (else VC_ERR_LAYOUT) and
+ *                  runs through encrypt_frames, decrypt_frames and
+ *                  crypt_frames_host only (vc_batch_submit and
+ *                  encrypt_frames_static return VC_ERR_UNSUPPORTED).  The
+ *                  decrypting context must use the value the encrypting one
+ *                  used; checkpoints do not record it.
  * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */
 #define VC_OPT_CHUNK 1
 #define VC_OPT_PLCM_INT 2
@@ -306,6 +318,7 @@ int enc_sync_status(vc_ctx* ctx);
 #define VC_OPT_TILE_ROWS 5
 #define VC_OPT_KS_SM_WARPS 6
 #define VC_OPT_RUNAHEAD_CALLS 7
+#define VC_OPT_DIFFUSION 8
 
 /* Set / read a tuning option.  Options never change the ciphertext.
  * Errors: VC_ERR_ARG (unknown option or value out of range). */

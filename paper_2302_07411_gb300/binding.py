@@ -19,7 +19,7 @@ _lib = None
 VC_OK = 0
 VC_PLCM, VC_2DLASM, VC_LOGISTIC = 0, 1, 2
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS, VC_OPT_KS_SM_WARPS = 1, 2, 3, 4, 5, 6
-VC_OPT_RUNAHEAD_CALLS = 7
+VC_OPT_RUNAHEAD_CALLS, VC_OPT_DIFFUSION = 7, 8
 VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD = 1, 2, 3
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}

@@ -171,6 +171,7 @@ struct vc_ctx {
   int64_t frame = 0;
   cudaStream_t last = nullptr;
   int plcm_int = 1;  // 0 binary64 pipe, 1 integer pipes, 2/3 integer pipes + forced exact fallback (tests)
+  bool diff_pc = false;  // diffusion chains: false = over the subframe's bytes (R4), true = one per channel
   int ks_lanes = 2;
   // stage profiling: recorded (stage, start, end) event pairs and a free pool
   bool prof = false;
@@ -380,6 +381,19 @@ int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint
   const uint8_t* ksb = c->d_ks[b] + (long long)f_off * ks_stride;
   const int* kmod = c->d_kmod[b] + (long long)f_off * L.H;
   const int r = L.rounds;
+  if (c->diff_pc) {  // per-channel chains: two kernels per round through d_buf[0]
+    StageMark rounds_mark(c, st, 2, 2 * r);
+    for (int step = 0; step < r; step++) {
+      const uint8_t* src = step == 0 ? in : c->d_buf[1];
+      const long long ss = step == 0 ? in_stride : L.Npad;
+      uint8_t* dst = step == r - 1 ? out : c->d_buf[1];
+      const long long ds = step == r - 1 ? out_stride : L.Npad;
+      const int j = dir == 0 ? step : r - 1 - step;
+      VC_CUDA(vc::launch_pc_round(dir == 0, L, tb, src, ss, c->d_buf[0], dst, ds, ksb + (long long)j * L.Npad,
+                                  ks_stride, kmod, nf, st));
+    }
+    return VC_OK;
+  }
   StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
   // with one round and in == out, the round cannot write its own input: go through a buffer
   const bool bounce = (r == 1) && (in == out);
@@ -938,6 +952,14 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       c->overlap = value != 0;
       return VC_OK;
     }
+    case VC_OPT_DIFFUSION:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      if (value == 1 && c->L.P / c->L.n < 2) {
+        set_err("per-channel diffusion needs at least 2 pixels in every subframe");
+        return VC_ERR_LAYOUT;
+      }
+      c->diff_pc = value == 1;
+      return VC_OK;
     case VC_OPT_RUNAHEAD_CALLS: {
       if (value != 0 && value != 1) return VC_ERR_ARG;
       if (value == 0) {
@@ -997,6 +1019,7 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
     case VC_OPT_TILE_ROWS: *value = c->L.T; return VC_OK;
     case VC_OPT_KS_SM_WARPS: *value = c->ks_sm_warps; return VC_OK;
     case VC_OPT_RUNAHEAD_CALLS: *value = c->spec_enabled ? 1 : 0; return VC_OK;
+    case VC_OPT_DIFFUSION: *value = c->diff_pc ? 1 : 0; return VC_OK;
   }
   return VC_ERR_ARG;
 }
@@ -1164,6 +1187,10 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
   if (!c || nframes < 0 || (nframes > 0 && (!d_in || !d_out))) {
     set_err("invalid argument");
     return VC_ERR_ARG;
+  }
+  if (c->diff_pc) {
+    set_err("per-channel diffusion runs through encrypt_frames / decrypt_frames only");
+    return VC_ERR_UNSUPPORTED;
   }
   const Layout& L = c->L;
   const size_t per_frame = static_bytes_per_frame(L);
@@ -1573,6 +1600,10 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       return VC_ERR_ARG;
     }
     if (J.nframes == 0) continue;
+    if (J.ctx->diff_pc) {
+      set_err("job %d: per-channel diffusion runs through encrypt_frames / decrypt_frames only", j);
+      return VC_ERR_UNSUPPORTED;
+    }
     if (J.ctx->L.rounds == 1 && J.d_in == J.d_out) {
       set_err("job %d: in-place with one round is not supported in a batch", j);
       return VC_ERR_ARG;

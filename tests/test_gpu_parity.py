@@ -161,13 +161,17 @@ def test_keystream_and_confusion_seeds(B, orc, kind, plcm_int, lanes, H, W, C, n
 
 # --------------------------------------------------------------------- whole frames
 
-def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0, ks_sm_warps=0, plcm_int=None):
+def _check_enc_dec(B, orc, kind, key, X, n, r, chunk=None, inplace=False, tile_rows=0, ks_sm_warps=0, plcm_int=None,
+                   per_channel=False):
     F, H, W, C = X.shape
-    ref_e = orc.OracleCipher(kind, key, H, W, C, n, r)
-    ref_d = orc.OracleCipher(kind, key, H, W, C, n, r)
+    ref_e = orc.OracleCipher(kind, key, H, W, C, n, r, per_channel=per_channel)
+    ref_d = orc.OracleCipher(kind, key, H, W, C, n, r, per_channel=per_channel)
     Y_ref = ref_e.encrypt(X)
     g_e = B.Cipher(kind, key, H, W, C, n, r)
     g_d = B.Cipher(kind, key, H, W, C, n, r)
+    if per_channel:
+        g_e.set_option(B.VC_OPT_DIFFUSION, 1)
+        g_d.set_option(B.VC_OPT_DIFFUSION, 1)
     if chunk:
         g_e.set_chunk(chunk)
         g_d.set_chunk(chunk)
@@ -225,6 +229,51 @@ def test_config_smooth_576_clip(B, orc, kind, n):
 def test_odd_shapes(B, orc, kind, H, W, C, n, r):
     X = synth.uniform_frames(2, H, W, C, seed=H + W)
     _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 300 + n), X, n, r)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("H,W,C,n,r", [
+    (16, 16, 3, 4, 5),
+    (17, 23, 3, 5, 5),     # odd sizes
+    (100, 37, 3, 91, 2),   # ragged subframes
+    (45, 200, 3, 300, 5),  # W > H
+    (200, 45, 1, 12, 5),   # C = 1 (equal to the byte chain)
+    (31, 31, 4, 1, 5),     # n = 1: seeds from its own last pixel
+    (64, 64, 1, 2048, 3),  # 2-pixel subframes (the minimum)
+    (70, 70, 3, 2450, 5),  # 2-pixel subframes, 3 channels
+    (33, 65, 3, 7, 1),     # one round, in place below
+])
+def test_per_channel_diffusion(B, orc, kind, H, W, C, n, r):
+    """The per-channel diffusion variant (VC_OPT_DIFFUSION = 1) against the
+    oracle's per-channel reading, encrypt and decrypt, in place for one round."""
+    X = synth.uniform_frames(2, H, W, C, seed=H * W + n)
+    _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 400 + n), X, n, r, per_channel=True, inplace=(r == 1))
+
+
+def test_per_channel_diffusion_clip_in_passes(B, orc):
+    """A 576 x 576 x 3 smooth clip, n = 8, 5 frames in passes of 2."""
+    X = synth.smooth_clip(5, 576, 576, 3, seed=41)
+    _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 41), X, 8, 5, chunk=2, per_channel=True)
+
+
+def test_per_channel_diffusion_limits(B):
+    c = B.Cipher(0, synth.key_for_seed(0, 42), 4, 4, 3, 16)  # one pixel per subframe
+    with pytest.raises(B.VcError) as e:
+        c.set_option(B.VC_OPT_DIFFUSION, 1)
+    assert e.value.code == 3  # VC_ERR_LAYOUT
+    with pytest.raises(B.VcError):
+        c.set_option(B.VC_OPT_DIFFUSION, 2)
+    d = B.Cipher(0, synth.key_for_seed(0, 42), 8, 8, 3, 4)
+    d.set_option(B.VC_OPT_DIFFUSION, 1)
+    assert d.get_option(B.VC_OPT_DIFFUSION) == 1
+    x = torch.zeros((1, 8, 8, 3), dtype=torch.uint8, device="cuda")
+    batcher = B.Batcher()
+    with pytest.raises(B.VcError) as e:
+        batcher.submit([(d, 0, x, torch.empty_like(x), 1)])
+    assert e.value.code == 9  # VC_ERR_UNSUPPORTED
+    batcher.close()
+    c.close()
+    d.close()
 
 
 @pytest.mark.parametrize("tile_rows", [1, 4, 8, 16])
