@@ -15,8 +15,11 @@ extern "C" {
 #endif
 
 /* out[i] = the cipher's sine of t[i] (the reading of "sin" in Eq. 1 / Eq. 6:
- * Cody-Waite reduction by pi/2, Taylor polynomials by Horner), n doubles each. */
-int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream);
+ * Cody-Waite reduction by pi/2, Taylor polynomials by Horner), n doubles each;
+ * variant 0 = every reduction step on the binary64 pipe, 1 = the rounding,
+ * floor and t - k*PIO2_HI on the integer pipes (must give the same bits).
+ * VC_ERR_ARG for n < 0, null pointers with n > 0, or another variant. */
+int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, int32_t variant, void* stream);
 
 /* out[i] = one PLCM step F(x[i], p[i]) (Eq. 5); variant 0 = binary64 pipe,
  * 1 = integer-pipe evaluation (must give the same bits). */

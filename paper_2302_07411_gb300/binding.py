@@ -77,7 +77,7 @@ def lib():
             "enc_profile_read": (C.c_int, [p, p, p]),
             "vc_strerror": (C.c_char_p, [C.c_int]),
             "vc_last_error": (C.c_char_p, []),
-            "vc_dbg_csin": (C.c_int, [p, p, i64, p]),
+            "vc_dbg_csin": (C.c_int, [p, p, i64, i32, p]),
             "vc_dbg_plcm": (C.c_int, [p, p, p, i64, i32, p]),
             "enc_set_option": (C.c_int, [p, i32, i64]),
             "enc_get_option": (C.c_int, [p, i32, C.POINTER(C.c_int64)]),
@@ -211,8 +211,8 @@ def enc_destroy(ctx) -> None:
     lib().enc_destroy(ctx)
 
 
-def vc_dbg_csin(d_t, d_out, stream=None) -> None:
-    _check(lib().vc_dbg_csin(_dptr(d_t), _dptr(d_out), d_t.numel(), _stream(stream)), "vc_dbg_csin")
+def vc_dbg_csin(d_t, d_out, variant: int = 1, stream=None) -> None:
+    _check(lib().vc_dbg_csin(_dptr(d_t), _dptr(d_out), d_t.numel(), variant, _stream(stream)), "vc_dbg_csin")
 
 
 def vc_dbg_plcm(d_x, d_p, d_out, variant: int = 0, stream=None) -> None:

@@ -1067,9 +1067,9 @@ void enc_destroy(vc_ctx* c) {
 
 // ---- diagnostics (include/vcrypt_debug.h) ----
 
-int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, void* stream) {
-  if (n < 0 || (n > 0 && (!d_t || !d_out))) return VC_ERR_ARG;
-  VC_CUDA(vc::launch_dbg_csin(d_t, d_out, n, (cudaStream_t)stream));
+int vc_dbg_csin(const double* d_t, double* d_out, int64_t n, int32_t variant, void* stream) {
+  if (n < 0 || (n > 0 && (!d_t || !d_out)) || variant < 0 || variant > 1) return VC_ERR_ARG;
+  VC_CUDA(vc::launch_dbg_csin(d_t, d_out, n, variant, (cudaStream_t)stream));
   return VC_OK;
 }
 

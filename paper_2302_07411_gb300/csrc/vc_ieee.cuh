@@ -38,6 +38,11 @@ __device__ __forceinline__ int ieee_clz64(uint64_t v) { return __clzll((long lon
 __device__ __forceinline__ int lz64_hi(uint64_t v) {
   return 158 - (int)(__float_as_uint(__uint2float_rz((uint32_t)(v >> 32))) >> 23);
 }
+// Number of significant bits of v (floor(log2 v) + 1) by the same conversion;
+// v = 0 gives -126.
+__device__ __forceinline__ int ieee_bitlen32(uint32_t v) {
+  return (int)(__float_as_uint(__uint2float_rz(v)) >> 23) - 126;
+}
 #else
 inline uint64_t ieee_bits(double v) {
   uint64_t b;
@@ -52,6 +57,7 @@ inline double ieee_double(uint64_t b) {
 inline uint64_t ieee_mulhi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 inline int ieee_clz64(uint64_t v) { return v ? __builtin_clzll(v) : 64; }
 inline int lz64_hi(uint64_t v) { return __builtin_clz((uint32_t)(v >> 32)); }
+inline int ieee_bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : -126; }
 #endif
 
 constexpr uint64_t kMant52 = (1ull << 52) - 1;
@@ -265,6 +271,78 @@ __host__ __device__ __forceinline__ double one_minus_int(double x, bool& ok) {
   const int e = 1022 - (53 - L);
   ok = (ex == 1022) && (y != 0);
   return ieee_double(((uint64_t)e << 52) | (m & kMant52));
+}
+
+// ---- argument reduction of the cipher's sine on the integer pipes ----------
+// The sine reduces t by k pi/2 with k = floor(RN(RN(t 2/pi) + 1/2)) and
+// r = RN(RN(t - k HI) - RN(k LO)), HI = pi/2 to 33 bits (Cody-Waite).  Two of
+// those steps have exact integer forms: the rounding of u + 1/2 followed by
+// the floor, and t - k HI (k HI is exact, and so is the difference formed in
+// fixed point below).  Both return the values the binary64 operations return,
+// with five binary64 operations and conversions fewer per sine (the binary64
+// pipe is the scarce one when many chains share the SMs) but a longer
+// dependency chain (25 to 35 integer instructions against four binary64
+// operations).
+
+// floor(RN(u + 1/2)) from the bits of the binary64 u.  ok = false when
+// |u| >= 256 or u is not finite (the caller uses the binary64 operations).
+__host__ __device__ __forceinline__ int round_half_floor_int(uint64_t ub, bool& ok) {
+  const int eu = (int)((ub >> 52) & 0x7FF);
+  ok = eu <= 1030;
+  const bool neg = (ub >> 63) != 0;
+  const uint64_t mu = (ub & kMant52) | (1ull << 52);
+  const uint64_t U = mu << ((eu - 1021) & 15);  // |u| 2^54 when 1/4 <= |u| < 256 (below 2^62)
+  const uint64_t h = 1ull << 53;                 // 1/2 in units of 2^-54
+  const bool sneg = neg && U > h;                // u + 1/2 < 0
+  const uint64_t A = neg ? (sneg ? U - h : h - U) : U + h;  // |u + 1/2| 2^54, exact
+  // RN to 53 significant bits: d = dropped bits (0 when A < 2^53)
+  int d = 32 + ieee_bitlen32((uint32_t)(A >> 32)) - 53;
+  d = d < 0 ? 0 : d;
+  const uint64_t half = (1ull << d) >> 1;
+  const uint64_t inc = d ? half - 1 + ((A >> d) & 1) : 0;  // ties to even
+  const uint64_t Ar = ((A + inc) >> d) << d;
+  const int fl = sneg ? -(int)((Ar + ((1ull << 54) - 1)) >> 54) : (int)(Ar >> 54);
+  // |u| < 1/4: u + 1/2 lies in (1/4, 3/4) and so does its rounding: floor 0
+  return eu < 1021 ? 0 : fl;
+}
+
+// Bits of RN(t - k H) for H = hm 2^-32 (hm below 2^34), from the bits of the
+// binary64 t: t and k H are both multiples of 2^-53 when |t| >= 1/2, so their
+// difference is formed exactly as an integer in units of 2^-53 and rounded
+// once to 53 significant bits.  ok = false unless 1/2 <= |t| < 512 and
+// |k| <= 256 (the caller uses the binary64 operations).
+__host__ __device__ __forceinline__ uint64_t sub_kh_bits(uint64_t tb, int k, uint64_t hm, bool& ok) {
+  const int et = (int)((tb >> 52) & 0x7FF);
+  ok = et >= 1022 && et <= 1031 && k >= -256 && k <= 256;
+  const uint64_t T = ((tb & kMant52) | (1ull << 52)) << ((et - 1022) & 15);  // |t| 2^53, below 2^62
+  const uint64_t ak = (uint64_t)(k < 0 ? -k : k) & 511;
+  const uint64_t KH = (ak * hm) << 21;                                         // |k| H 2^53
+  const uint64_t sT = (tb >> 63) ? 0ull - T : T;
+  const uint64_t sK = k < 0 ? 0ull - KH : KH;
+  const uint64_t D = sT - sK;  // two's complement of (t - k H) 2^53; |.| < 2^63 in range
+  const bool dneg = (int64_t)D < 0;
+  const uint64_t A = dneg ? 0ull - D : D;
+  const uint32_t ahi = (uint32_t)(A >> 32);
+  const int b = ahi ? 32 + ieee_bitlen32(ahi) : ieee_bitlen32((uint32_t)A);  // significant bits of A
+  const int d = b > 53 ? b - 53 : 0;
+  const uint64_t half = (1ull << d) >> 1;
+  const uint64_t inc = d ? half - 1 + ((A >> d) & 1) : 0;  // ties to even
+  uint64_t M = (A + inc) >> d;
+  const bool carry = (M >> 53) != 0;  // rounded up to the next power of two
+  M = carry ? (M >> 1) : M;
+  M = b < 53 ? (A << ((53 - b) & 63)) : M;
+  const uint64_t e = (uint64_t)(b + 969 + (carry ? 1 : 0));  // biased exponent of A 2^-53
+  const uint64_t bits = ((uint64_t)dneg << 63) | (e << 52) | (M & kMant52);
+  return A == 0 ? 0ull : bits;  // t = k H exactly: +0
+}
+
+// Bits of the binary64 value of the integer k, |k| < 2^24.
+__host__ __device__ __forceinline__ uint64_t small_int_bits(int k) {
+  const uint32_t a = (uint32_t)(k < 0 ? -k : k);
+  const int b = ieee_bitlen32(a);
+  const uint64_t m = ((uint64_t)a << ((53 - b) & 63)) & kMant52;
+  const uint64_t bits = ((uint64_t)(k < 0) << 63) | ((uint64_t)(1022 + b) << 52) | m;
+  return a == 0 ? 0ull : bits;
 }
 
 }  // namespace vc

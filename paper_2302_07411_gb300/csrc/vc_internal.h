@@ -137,7 +137,7 @@ cudaError_t batch_ctas_per_sm(size_t smem, int* ctas);
 cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st);
 
 // Diagnostics: the chaotic primitives applied elementwise.
-cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st);
+cudaError_t launch_dbg_csin(const double* t, double* out, long long n, int variant, cudaStream_t st);
 cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant,
                             cudaStream_t st);
 cudaError_t launch_dbg_lasm(const double* xymu, double* out, long long n, cudaStream_t st);

@@ -545,7 +545,10 @@ __device__ __forceinline__ uint8_t* ks_frame(uint8_t* ks, const Layout& L, int f
   return ks + (long long)slot * L.rounds * L.Npad;
 }
 
-template <int KIND, bool FX>
+// SINE_B64: the 2DLASM sines with the all-binary64 reduction (shorter chain,
+// for kernels that hold whole SMs); otherwise the integer-assisted reduction
+// (fewer binary64 operations, for chains that share the SMs).
+template <int KIND, bool FX, bool SINE_B64 = false>
 __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb, const Chains& ch, int nframes,
                                               uint8_t* ks, const int i, const int side, int cap = 0, int slot0 = 0) {
   if (i >= L.n) return;  // both lanes of a pair leave together
@@ -593,7 +596,7 @@ __device__ __forceinline__ void ks_pair_chain(const Layout& L, const Tables& tb,
     return own48 ^ __shfl_xor_sync(pmask, own48, 1);
   };
   auto lasm_next = [&](uint64_t& vx, uint64_t& vy) {
-    lasm_step(x, y, pm);
+    lasm_step<SINE_B64>(x, y, pm);
     const uint64_t ox = mant48(x), oy = mant48(y);
     vx = ox ^ __shfl_xor_sync(pmask, ox, 1);
     vy = oy ^ __shfl_xor_sync(pmask, oy, 1);
@@ -904,7 +907,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128) k_ks_pair_sm(Layout L, Tables tb, Chains ch, int nframes, uint8_t* ks, int cap,
                                                     int slot0) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  ks_pair_chain<KIND, false>(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
+  ks_pair_chain<KIND, false, true>(L, tb, ch, nframes, ks, gt >> 1, gt & 1, cap, slot0);
 }
 
 static int reserve_smem_bytes() {
@@ -2012,9 +2015,9 @@ cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchSh
 // Diagnostics
 // =============================================================================
 
-__global__ void k_dbg_csin(const double* t, double* out, long long n) {
+__global__ void k_dbg_csin(const double* t, double* out, long long n, int variant) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = csin(t[i]);
+  if (i < n) out[i] = variant ? csin(t[i]) : csin_b64(t[i]);
 }
 __global__ void k_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2033,9 +2036,9 @@ __global__ void k_dbg_lasm(const double* xymu, double* out, long long n) {
   }
 }
 
-cudaError_t launch_dbg_csin(const double* t, double* out, long long n, cudaStream_t st) {
+cudaError_t launch_dbg_csin(const double* t, double* out, long long n, int variant, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_dbg_csin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, out, n);
+  k_dbg_csin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, out, n, variant);
   return cudaGetLastError();
 }
 cudaError_t launch_dbg_plcm(const double* x, const double* p, double* out, long long n, int variant,

@@ -21,6 +21,7 @@ static constexpr double kTwoPi = 0x1.921fb54442d18p+2;    // nearest double to 2
 static constexpr double kTwoOverPi = 0x1.45f306dc9c883p-1; // nearest double to 2/pi
 static constexpr double kPio2Hi = 0x1.921fb544p+0;
 static constexpr double kPio2Lo = 0x1.0b4611a626331p-34;
+static_assert(kPio2Hi == 0x1921fb544p-32, "the 33-bit head of pi/2 as an integer times 2^-32");
 
 // (-1)^k / (2k+1)!  and  (-1)^k / (2k)!, k = 1..8: each a quotient of exactly
 // representable integers, rounded once by the compiler's constant folding.
@@ -48,10 +49,7 @@ static constexpr double kCos8 = VC_S(8, 20922789888000.0);
 // coefficient set by quadrant instead of branching, so a warp whose lanes sit
 // in different quadrants still evaluates one polynomial.  (1*r^2 == r^2
 // exactly, so the cosine is the same binary64 value as 1 + r^2*C(r^2).)
-__device__ __forceinline__ double csin(double t) {
-  const double kd = floor(__dadd_rn(__dmul_rn(t, kTwoOverPi), 0.5));
-  const double r = __dsub_rn(__dsub_rn(t, __dmul_rn(kd, kPio2Hi)), __dmul_rn(kd, kPio2Lo));
-  const long long k = __double2ll_rz(kd);
+__device__ __forceinline__ double csin_poly(double r, long long k) {
   const int quad = (int)(k & 3);  // two's complement: the mathematical k mod 4
   const bool c = (quad & 1) != 0;
   const double r2 = __dmul_rn(r, r);
@@ -66,6 +64,31 @@ __device__ __forceinline__ double csin(double t) {
   const double a = c ? 1.0 : r;
   const double v = __dadd_rn(a, __dmul_rn(__dmul_rn(a, r2), s));
   return (quad & 2) ? -v : v;
+}
+
+// The reduction with every step on the binary64 pipe: the shortest dependency
+// chain (used where few chains run per SM and latency binds).
+__device__ __forceinline__ double csin_b64(double t) {
+  const double kd = floor(__dadd_rn(__dmul_rn(t, kTwoOverPi), 0.5));
+  const double r = __dsub_rn(__dsub_rn(t, __dmul_rn(kd, kPio2Hi)), __dmul_rn(kd, kPio2Lo));
+  return csin_poly(r, __double2ll_rz(kd));
+}
+
+// The same values with the rounding and floor of u + 1/2 and the exact
+// t - k*PIO2_HI on the integer pipes (vc_ieee.cuh): five binary64 operations
+// and conversions fewer per sine, for kernels where many chains share the
+// SMs' binary64 pipes; arguments outside the integer forms' range
+// (|t| >= 2^8 pi/2) take csin_b64.
+__device__ __forceinline__ double csin(double t) {
+  constexpr uint64_t kPio2HiM = 0x1921fb544ull;  // kPio2Hi = kPio2HiM 2^-32
+  const double u = __dmul_rn(t, kTwoOverPi);
+  bool ok1 = false, ok2 = false;
+  const int k = round_half_floor_int(ieee_bits(u), ok1);
+  const uint64_t db = sub_kh_bits(ieee_bits(t), k, kPio2HiM, ok2);
+  if (!ok1 || (k != 0 && !ok2)) return csin_b64(t);
+  const double d = k == 0 ? t : ieee_double(db);
+  const double r = __dsub_rn(d, __dmul_rn(ieee_double(small_int_bits(k)), kPio2Lo));
+  return csin_poly(r, k);
 }
 
 // ---- PLCM, Eq. 5 ------------------------------------------------------------
@@ -123,9 +146,13 @@ __device__ __forceinline__ double logistic_step(double x, double r) {
 
 // ---- 2DLASM, Eq. 6 ----------------------------------------------------------
 // pm = RN(pi * mu).  x' = csin(((pm*(y+3))*x)*(1-x)); y' uses the new x'.
+// SINE_B64 selects the all-binary64 reduction of the sine (same values).
+template <bool SINE_B64 = false>
 __device__ __forceinline__ void lasm_step(double& x, double& y, double pm) {
-  const double xn = csin(__dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(y, 3.0)), x), __dsub_rn(1.0, x)));
-  const double yn = csin(__dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(xn, 3.0)), y), __dsub_rn(1.0, y)));
+  const double tx = __dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(y, 3.0)), x), __dsub_rn(1.0, x));
+  const double xn = SINE_B64 ? csin_b64(tx) : csin(tx);
+  const double ty = __dmul_rn(__dmul_rn(__dmul_rn(pm, __dadd_rn(xn, 3.0)), y), __dsub_rn(1.0, y));
+  const double yn = SINE_B64 ? csin_b64(ty) : csin(ty);
   x = xn;
   y = yn;
 }

@@ -123,9 +123,79 @@ int main(int argc, char** argv) {
       bad_plcm++;
     }
   }
+  // argument reduction of the cipher's sine: k = floor(RN(u + 1/2)) and
+  // RN(t - k*HI) against the host's binary64 operations, and the binary64
+  // value of a small integer
+  const double HI = 0x1.921fb544p+0;
+  const double TWO_OVER_PI = 0x1.45f306dc9c883p-1;
+  long long bad_kr = 0, fb_kr = 0, checked_kr = 0, bad_skh = 0, fb_skh = 0, checked_skh = 0, bad_int = 0;
+  for (long long i = 0; i < n; i++) {
+    double u;
+    switch (i & 7) {
+      case 0: u = 600.0 * (U(g) - 0.5); break;
+      case 1: u = 40.0 * (U(g) - 0.5); break;
+      case 2: {  // within a few units in the last place of a half-integer
+        const double m = (double)((long long)(g() % 521) - 260) + 0.5;
+        u = from_bits(to_bits(m) + (g() % 7) - 3);
+        break;
+      }
+      case 3: u = std::ldexp(U(g) - 0.5, -(int)(g() % 80)); break;
+      case 4: u = from_bits(g()); break;  // any bit pattern (ok must exclude the unsupported ones)
+      case 5: u = (double)((long long)(g() % 601) - 300) * 0.5; break;  // exact halves and integers
+      case 6: u = 0.5 - std::ldexp(1.0, -(int)(50 + g() % 6)); break;  // just below 1/2
+      default: u = -0.5 - std::ldexp(1.0, -(int)(50 + g() % 6)) * (double)(g() % 3); break;
+    }
+    bool ok = false;
+    const int k = vc::round_half_floor_int(to_bits(u), ok);
+    if (!ok) {
+      fb_kr++;
+    } else {
+      checked_kr++;
+      const double want = std::floor(u + 0.5);
+      if ((double)k != want) {
+        if (bad_kr < 5) printf("kround u=%a got %d want %a\n", u, k, want);
+        bad_kr++;
+      }
+    }
+    // t near k pi/2 (the sine's arguments), at a multiple of HI, or anywhere
+    double t;
+    switch ((i >> 3) & 3) {
+      case 0: t = 1200.0 * (U(g) - 0.5); break;
+      case 1: t = 50.0 * (U(g) - 0.5); break;
+      case 2: {
+        const double kk = (double)((long long)(g() % 513) - 256);
+        t = from_bits(to_bits(kk * HI) + (g() % 9) - 4);
+        break;
+      }
+      default: t = (double)((long long)(g() % 513) - 256) * HI; break;
+    }
+    const double kd = std::floor(t * TWO_OVER_PI + 0.5);
+    const int kt = (int)kd;
+    if (std::fabs(kd) <= 256.0) {
+      bool ok2 = false;
+      const uint64_t got = vc::sub_kh_bits(to_bits(t), kt, 0x1921fb544ull, ok2);
+      if (!ok2) {
+        fb_skh++;
+      } else {
+        checked_skh++;
+        const double want = t - kd * HI;
+        if (got != to_bits(want)) {
+          if (bad_skh < 5) printf("t-kHI t=%a k=%d got %a want %a\n", t, kt, from_bits(got), want);
+          bad_skh++;
+        }
+      }
+    }
+    const int ki = (int)(g() % (1u << 21)) - (1 << 20);
+    if (vc::small_int_bits(ki) != to_bits((double)ki)) bad_int++;
+  }
+  for (int ki = -300; ki <= 300; ki++)
+    if (vc::small_int_bits(ki) != to_bits((double)ki)) bad_int++;
+  printf("kround checked %lld fallback %lld mismatches %lld\n", checked_kr, fb_kr, bad_kr);
+  printf("t-kHI checked %lld fallback %lld mismatches %lld\n", checked_skh, fb_skh, bad_skh);
+  printf("small_int mismatches %lld\n", bad_int);
   printf("plcm_fx checked %lld fallback %lld mismatches %lld\n", checked_plcm, fb_plcm, bad_plcm);
   printf("div checked %lld fallback %lld mismatches %lld\n", checked_div, fb_div, bad_div);
   printf("sub checked %lld fallback %lld mismatches %lld\n", checked_sub, fb_sub, bad_sub);
   printf("one_minus mismatches %lld\n", bad_om);
-  return (bad_div || bad_sub || bad_om || bad_plcm) ? 1 : 0;
+  return (bad_div || bad_sub || bad_om || bad_plcm || bad_kr || bad_skh || bad_int) ? 1 : 0;
 }

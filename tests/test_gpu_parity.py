@@ -35,19 +35,23 @@ def host(t):
 
 # --------------------------------------------------------------------- stages
 
-def test_csin_bitwise(B, orc):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_csin_bitwise(B, orc, variant):
+    """The cipher's sine == oracle, its reduction all on the binary64 pipe (0)
+    or with the rounding, floor and t - k*PIO2_HI on the integer pipes (1)."""
     rng = np.random.default_rng(100)
     t = np.concatenate([rng.uniform(0, 2 * np.pi, 200000), rng.uniform(0, np.pi, 100000),
                         np.array([0.0, 1e-300, np.pi / 4, np.pi / 2, np.pi, 2 * np.pi, 6.283185307179586])])
     out = torch.empty(t.size, dtype=torch.float64, device="cuda")
-    B.vc_dbg_csin(dev(t), out)
+    B.vc_dbg_csin(dev(t), out, variant)
     got = host(out)
     idx = rng.choice(t.size, 20000, replace=False)
     exp = np.array([orc.csin(float(v)) for v in t[idx]])
     assert np.array_equal(got[idx].view(np.uint64), exp.view(np.uint64))
 
 
-def test_csin_reduction_edges(B, orc):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_csin_reduction_edges(B, orc, variant):
     """Arguments where the reduction decides, every one against the oracle:
     u = t*2/pi within a few ulp of a half-integer (the rounding of u + 1/2 and
     its floor pick the quadrant), t within a few ulp of a multiple of PIO2_HI
@@ -64,10 +68,30 @@ def test_csin_reduction_edges(B, orc):
                         rng.uniform(-24.0, 3.0, 50000), -rng.uniform(0, 2 * np.pi, 10000),
                         np.array([-0.0, -1e-300, 400.0, -400.0, 402.1, 1e6, -1e6])])
     out = torch.empty(t.size, dtype=torch.float64, device="cuda")
-    B.vc_dbg_csin(dev(t), out)
+    B.vc_dbg_csin(dev(t), out, variant)
     got = host(out)
     exp = np.array([orc.csin(float(v)) for v in t])
     assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def test_csin_integer_reduction_equals_binary64_at_scale(B):
+    """2^26 arguments per batch, 4 batches over the ranges the cipher uses (the
+    2DLASM argument range, [0, 2 pi), near zero, and wide enough to reach the
+    fallback): both reductions return the same bits, non-finite inputs too."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(8)
+    n = 1 << 26
+    for batch in range(4):
+        u = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+        t = [27.0 * u - 24.0, 2 * np.pi * u, (u - 0.5) * 1e-3, (u - 0.5) * 2000.0][batch]
+        if batch == 3:
+            t[:3] = torch.tensor([float("inf"), float("-inf"), float("nan")], dtype=torch.float64)
+        a = torch.empty_like(t)
+        b = torch.empty_like(t)
+        B.vc_dbg_csin(t, a, 0)
+        B.vc_dbg_csin(t, b, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(a.view(torch.int64), b.view(torch.int64))
 
 
 @pytest.mark.parametrize("variant", [0, 1])

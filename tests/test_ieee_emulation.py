@@ -1,7 +1,9 @@
 """The integer-pipe binary64 routines of the CUDA library (csrc/vc_ieee.cuh:
-division by a constant, subtraction, 1 - x) compiled as host code and compared
-with the host CPU's IEEE-754 round-to-nearest-even arithmetic on millions of
-operands (PLCM-like and arbitrary normal ranges, near-ties of subtraction)."""
+division by a constant, subtraction, 1 - x, the PLCM step, and the sine's
+argument reduction: floor(RN(u + 1/2)), RN(t - k*PIO2_HI) and small integers
+as binary64) compiled as host code and compared with the host CPU's IEEE-754
+round-to-nearest-even arithmetic on millions of operands (PLCM-like and
+arbitrary normal ranges, near-ties, half-integers, multiples of PIO2_HI)."""
 from __future__ import annotations
 
 import os
@@ -22,4 +24,4 @@ def test_integer_binary64_matches_hardware(tmp_path):
                            "-o", exe, os.path.join(ROOT, "tests", "ieee_emulation_check.cu")])
     out = subprocess.run([exe, "3000000"], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout
-    assert "div checked" in out.stdout and "mismatches 0" in out.stdout
+    assert "div checked" in out.stdout and "kround checked" in out.stdout and "t-kHI checked" in out.stdout
