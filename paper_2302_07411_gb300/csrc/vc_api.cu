@@ -381,17 +381,23 @@ int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint
   const uint8_t* ksb = c->d_ks[b] + (long long)f_off * ks_stride;
   const int* kmod = c->d_kmod[b] + (long long)f_off * L.H;
   const int r = L.rounds;
-  if (c->diff_pc) {  // per-channel chains: two kernels per round through d_buf[0]
-    StageMark rounds_mark(c, st, 2, 2 * r);
+  if (c->diff_pc) {  // per-channel chains: one kernel per round, alternating buffers
+    StageMark rounds_mark(c, st, 2, r);
+    const bool bounce = (r == 1) && (in == out);  // a round cannot write over its own input
+    uint8_t* final_out = bounce ? c->d_buf[0] : out;
+    const long long final_stride = bounce ? L.Npad : out_stride;
     for (int step = 0; step < r; step++) {
-      const uint8_t* src = step == 0 ? in : c->d_buf[1];
+      const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
       const long long ss = step == 0 ? in_stride : L.Npad;
-      uint8_t* dst = step == r - 1 ? out : c->d_buf[1];
-      const long long ds = step == r - 1 ? out_stride : L.Npad;
+      uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
+      const long long ds = step == r - 1 ? final_stride : L.Npad;
       const int j = dir == 0 ? step : r - 1 - step;
-      VC_CUDA(vc::launch_pc_round(dir == 0, L, tb, src, ss, c->d_buf[0], dst, ds, ksb + (long long)j * L.Npad,
-                                  ks_stride, kmod, nf, st));
+      VC_CUDA(vc::launch_pc_round(dir == 0, L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
+                                  nf, st));
     }
+    if (bounce)
+      VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
+                                cudaMemcpyDeviceToDevice, st));
     return VC_OK;
   }
   StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));

@@ -125,12 +125,12 @@ cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long
 cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
                              int nframes, cudaStream_t st);
-// One round of the per-channel diffusion variant: encrypt = Eq. 1 into tmp
-// (Npad stride) then Eq. 3 per channel into out; decrypt = Eq. 4 per channel
-// into tmp then Eq. 2 into out.  in may equal out; tmp may not alias either.
+// One round of the per-channel diffusion variant: encrypt = Eq. 1 and Eq. 3
+// per channel, decrypt = Eq. 4 per channel and Eq. 2, each one kernel.  in and
+// out must not overlap.
 cudaError_t launch_pc_round(bool encrypt, const Layout& L, Tables tb, const uint8_t* in, long long in_stride,
-                            uint8_t* tmp, uint8_t* out, long long out_stride, const uint8_t* ks_round,
-                            long long ks_stride, const int* kmod, int nframes, cudaStream_t st);
+                            uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
+                            const int* kmod, int nframes, cudaStream_t st);
 size_t round_smem_bytes(const Layout& L);
 cudaError_t prepare_batch_kernels(size_t smem);
 cudaError_t batch_ctas_per_sm(size_t smem, int* ctas);

@@ -1660,12 +1660,13 @@ cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long
 
 // =============================================================================
 // Per-channel diffusion (the alternative reading of Eq. 3 / Eq. 4: one chain
-// per colour channel instead of one over the subframe's bytes).  Each round is
-// two kernels: Eq. 1 as a gather into a frame buffer, then one warp per
-// subframe that scans its C channel chains at once, a pixel's C bytes packed
-// in one 32-bit word (XOR and the mod-256 sums act byte by byte).  Decryption
-// is elementwise (Eq. 4; a subframe's first pixel recomputes the seed pixel of
-// the next subframe from the ciphertext), then the inverse gather (Eq. 2).
+// per colour channel instead of one over the subframe's bytes).  One kernel
+// per round: encryption runs one warp per subframe that gathers its confused
+// pixels (Eq. 1) and scans its C channel chains at once, a pixel's C bytes
+// packed in one 32-bit word (XOR and the mod-256 sums act byte by byte);
+// decryption is elementwise (Eq. 4; a subframe's first pixel recomputes the
+// seed pixel of the next subframe from the ciphertext) fused with the inverse
+// gather (Eq. 2).
 // =============================================================================
 
 template <int C>
@@ -1692,36 +1693,35 @@ __device__ __forceinline__ uint32_t vsub4(uint32_t a, uint32_t b) {
   return ((a | 0x80808080u) - (b & 0x7F7F7F7Fu)) ^ ((a ^ ~b) & 0x80808080u);
 }
 
-// Eq. 1: Y[alpha][beta] = X[a][o], o = (beta - k(alpha)) mod W, a = (alpha - o) mod H.
-template <int C>
-__global__ void k_pc_confuse(Layout L, const uint8_t* X, long long xs, uint8_t* Y, long long ys, const int* kmod) {
-  const long long pp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pp >= L.P) return;
-  const int f = blockIdx.y;
-  const int alpha = (int)(pp / L.W), beta = (int)(pp - (long long)alpha * L.W);
-  int o = beta - __ldg(&kmod[(long long)f * L.H + alpha]);
+// Source pixel of confused pixel p (Eq. 1): Y[alpha][beta] = X[a][o] with
+// o = (beta - k(alpha)) mod W and a = (alpha - o) mod H.
+__device__ __forceinline__ long long pc_source(const Layout& L, const int* km, int p) {
+  const int alpha = p / L.W, beta = p - alpha * L.W;
+  int o = beta - __ldg(&km[alpha]);
   if (o < 0) o += L.W;
-  const int a = mod_h(alpha - o, L.H);
-  store_px<C>(Y + f * ys, pp, load_px<C>(X + f * xs, (long long)a * L.W + o));
+  return (long long)mod_h(alpha - o, L.H) * L.W + o;
 }
 
-// Eq. 3 per channel: warp w of the grid diffuses subframe w, 8 pixels per lane
-// and step; the lanes' XOR totals are scanned with shuffles and the running
-// value carries to the next step.  The seed is the C bytes of the last pixel
-// of subframe (i+1) mod n of Y.
+// Eq. 1 and Eq. 3 per channel in one pass: warp w of the grid diffuses
+// subframe w, gathering each confused pixel from the previous round's output
+// as it goes (8 pixels per lane and step); the lanes' XOR totals are scanned
+// with shuffles and the running value carries to the next step.  The seed is
+// the confused value of the last pixel of subframe (i+1) mod n.  X and Xo
+// must not overlap (other warps still gather from X).
 template <int C>
-__global__ void __launch_bounds__(128) k_pc_diffuse(Layout L, Tables tb, const uint8_t* Y, long long ys,
-                                                    const uint8_t* ks, long long ks_stride, uint8_t* Xo,
-                                                    long long xs) {
+__global__ void __launch_bounds__(128) k_pc_enc_round(Layout L, Tables tb, const uint8_t* X, long long xs,
+                                                      const uint8_t* ks, long long ks_stride, const int* kmod,
+                                                      uint8_t* Xo, long long os) {
   const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (i >= L.n) return;  // whole warps
   const int lane = threadIdx.x & 31, f = blockIdx.y;
-  const uint8_t* y = Y + f * ys;
+  const uint8_t* x = X + f * xs;
   const uint8_t* b = ks + f * ks_stride;
-  uint8_t* out = Xo + f * xs;
+  const int* km = kmod + (long long)f * L.H;
+  uint8_t* out = Xo + f * os;
   const int p0 = tb.pi[i], p1 = tb.pi[i + 1];
   const int nxt = i + 1 == L.n ? 0 : i + 1;
-  uint32_t carry = load_px<C>(y, tb.pi[nxt + 1] - 1);
+  uint32_t carry = load_px<C>(x, pc_source(L, km, tb.pi[nxt + 1] - 1));
   constexpr int K = 8;
   for (int base = p0; base < p1; base += 32 * K) {  // the same trip count in every lane
     const int q0 = base + lane * K;
@@ -1731,7 +1731,7 @@ __global__ void __launch_bounds__(128) k_pc_diffuse(Layout L, Tables tb, const u
     for (int k = 0; k < K; k++) {
       const int p = q0 + k;
       if (p < p1) {
-        const uint32_t yy = load_px<C>(y, p), bb = load_px<C>(b, p);
+        const uint32_t yy = load_px<C>(x, pc_source(L, km, p)), bb = load_px<C>(b, p);
         acc ^= bb ^ vadd4(yy, bb);
       }
       pre[k] = acc;
@@ -1752,72 +1752,60 @@ __global__ void __launch_bounds__(128) k_pc_diffuse(Layout L, Tables tb, const u
   }
 }
 
-// Eq. 4 per channel, one thread per pixel: Y_p = (b xor c_p xor c_{p-1}) - b;
-// a subframe's first pixel uses the seed pixel s (the last pixel of subframe
-// (i+1) mod n, never a first pixel since every subframe holds 2 pixels or
-// more), itself recovered as (b_s xor c_s xor c_{s-1}) - b_s.
+// Eq. 4 per channel and Eq. 2 in one pass, one thread per output pixel (a, o):
+// it reads confused pixel q = ((a + o) mod H, (o + k) mod W) and recovers it
+// as (b xor c_q xor c_{q-1}) - b, or for a subframe's first pixel with the
+// seed pixel s (the last pixel of subframe (i+1) mod n, never a first pixel
+// since every subframe holds 2 pixels or more) recovered the same way.
+// Xc and X must not overlap.
 template <int C>
-__global__ void k_pc_undiffuse(Layout L, Tables tb, const uint8_t* Xc, long long xs, const uint8_t* ks,
-                               long long ks_stride, uint8_t* Y, long long ys) {
+__global__ void k_pc_dec_round(Layout L, Tables tb, const uint8_t* Xc, long long xs, const uint8_t* ks,
+                               long long ks_stride, const int* kmod, uint8_t* X, long long os) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.P) return;
   const int f = blockIdx.y;
   const uint8_t* c = Xc + f * xs;
   const uint8_t* b = ks + f * ks_stride;
-  const int i = starts_before(L, (int)p + 1) - 1;  // the subframe holding pixel p
-  const uint32_t bb = load_px<C>(b, p), cc = load_px<C>(c, p);
+  const int a = (int)(p / L.W), o = (int)(p - (long long)a * L.W);
+  const int alpha = mod_h(a + o, L.H);
+  int beta = o + __ldg(&kmod[(long long)f * L.H + alpha]);
+  if (beta >= L.W) beta -= L.W;
+  const int q = alpha * L.W + beta;
+  const int i = starts_before(L, q + 1) - 1;  // the subframe holding pixel q
+  const uint32_t bb = load_px<C>(b, q), cc = load_px<C>(c, q);
   uint32_t prev;
-  if (p > tb.pi[i]) {
-    prev = load_px<C>(c, p - 1);
+  if (q > tb.pi[i]) {
+    prev = load_px<C>(c, q - 1);
   } else {
     const int nxt = i + 1 == L.n ? 0 : i + 1;
     const long long sp = tb.pi[nxt + 1] - 1;
     const uint32_t bs = load_px<C>(b, sp);
     prev = vsub4(bs ^ load_px<C>(c, sp) ^ load_px<C>(c, sp - 1), bs);
   }
-  store_px<C>(Y + f * ys, p, vsub4(bb ^ cc ^ prev, bb));
-}
-
-// Eq. 2: X[a][o] = Y[(a + o) mod H][(o + k(alpha)) mod W].
-template <int C>
-__global__ void k_pc_unconfuse(Layout L, const uint8_t* Y, long long ys, uint8_t* X, long long xs, const int* kmod) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.P) return;
-  const int f = blockIdx.y;
-  const int a = (int)(p / L.W), o = (int)(p - (long long)a * L.W);
-  const int alpha = mod_h(a + o, L.H);
-  int beta = o + __ldg(&kmod[(long long)f * L.H + alpha]);
-  if (beta >= L.W) beta -= L.W;
-  store_px<C>(X + f * xs, p, load_px<C>(Y + f * ys, (long long)alpha * L.W + beta));
+  store_px<C>(X + f * os, p, vsub4(bb ^ cc ^ prev, bb));
 }
 
 template <int C>
-cudaError_t pc_round_c(bool enc, const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* tmp,
-                       uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
-                       const int* kmod, int nframes, cudaStream_t st) {
-  const dim3 px((unsigned)((L.P + 255) / 256), (unsigned)nframes);
-  if (enc) {
-    k_pc_confuse<C><<<px, 256, 0, st>>>(L, in, in_stride, tmp, L.Npad, kmod);
-    k_pc_diffuse<C><<<dim3((unsigned)((L.n + 3) / 4), (unsigned)nframes), 128, 0, st>>>(L, tb, tmp, L.Npad, ks_round,
-                                                                                         ks_stride, out, out_stride);
-  } else {
-    k_pc_undiffuse<C><<<px, 256, 0, st>>>(L, tb, in, in_stride, ks_round, ks_stride, tmp, L.Npad);
-    k_pc_unconfuse<C><<<px, 256, 0, st>>>(L, tmp, L.Npad, out, out_stride, kmod);
-  }
+cudaError_t pc_round_c(bool enc, const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
+                       long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
+                       int nframes, cudaStream_t st) {
+  if (enc)
+    k_pc_enc_round<C><<<dim3((unsigned)((L.n + 3) / 4), (unsigned)nframes), 128, 0, st>>>(
+        L, tb, in, in_stride, ks_round, ks_stride, kmod, out, out_stride);
+  else
+    k_pc_dec_round<C><<<dim3((unsigned)((L.P + 255) / 256), (unsigned)nframes), 256, 0, st>>>(
+        L, tb, in, in_stride, ks_round, ks_stride, kmod, out, out_stride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pc_round(bool encrypt, const Layout& L, Tables tb, const uint8_t* in, long long in_stride,
-                            uint8_t* tmp, uint8_t* out, long long out_stride, const uint8_t* ks_round,
-                            long long ks_stride, const int* kmod, int nframes, cudaStream_t st) {
+                            uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
+                            const int* kmod, int nframes, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
   switch (L.C) {
-    case 1: return pc_round_c<1>(encrypt, L, tb, in, in_stride, tmp, out, out_stride, ks_round, ks_stride, kmod,
-                                 nframes, st);
-    case 3: return pc_round_c<3>(encrypt, L, tb, in, in_stride, tmp, out, out_stride, ks_round, ks_stride, kmod,
-                                 nframes, st);
-    case 4: return pc_round_c<4>(encrypt, L, tb, in, in_stride, tmp, out, out_stride, ks_round, ks_stride, kmod,
-                                 nframes, st);
+    case 1: return pc_round_c<1>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
+    case 3: return pc_round_c<3>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
+    case 4: return pc_round_c<4>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
   }
   return cudaErrorInvalidValue;
 }
