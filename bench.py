@@ -235,7 +235,7 @@ def serving_capacity() -> dict:
     p = serve.capacity("perframe", 768, 768, counts=(2, 4, 8, 16, 24, 32, 48, 64), seconds=2.5)
     # the same with PLCM streams only (2DLASM keystream is binary64-bound and
     # about eight times the work of PLCM per frame)
-    bp = serve.capacity("batch", 768, 768, counts=(256, 320, 384, 448, 512), seconds=3.0, kinds=(0,))
+    bp = serve.capacity("batch", 768, 768, counts=(256, 384, 512, 640, 768), seconds=3.0, kinds=(0,))
     out["batched_streams"] = b["max_streams"]
     out["per_frame_streams"] = p["max_streams"]
     out["batched_streams_plcm_only"] = bp["max_streams"]
