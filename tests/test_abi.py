@@ -67,3 +67,36 @@ def test_binding_refuses_cpu_tensors():
 
     with pytest.raises(ValueError):
         B._dptr(torch.zeros(4, dtype=torch.uint8))
+
+
+def header_defines():
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            for m in re.finditer(r"^#define\s+(VC_[A-Z0-9_]+)\s+(-?\d+)\b", open(os.path.join(ROOT, "include", h)).read(),
+                                 flags=re.M):
+                out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_the_headers():
+    """Every VC_* constant the Python binding exposes has the value the C
+    headers define (maps, options, batch options, status codes)."""
+    from paper_2302_07411_gb300 import binding as B
+
+    defs = header_defines()
+    names = [n for n in dir(B) if n.startswith("VC_") and isinstance(getattr(B, n), int)]
+    assert {"VC_PLCM", "VC_2DLASM", "VC_LOGISTIC", "VC_OPT_DIFFUSION"} <= set(names)
+    for n in names:
+        assert n in defs, f"{n} is not defined in include/*.h"
+        assert getattr(B, n) == defs[n], (n, getattr(B, n), defs[n])
+
+
+def test_bench_maps_are_the_library_maps():
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    defs = header_defines()
+    assert bench.MAP_KIND == {"plcm": defs["VC_PLCM"], "2dlasm": defs["VC_2DLASM"], "logistic": defs["VC_LOGISTIC"]}
