@@ -70,7 +70,8 @@ typedef struct {
 typedef struct vc_ctx vc_ctx;
 
 /* Create a cipher context for one video stream on the current CUDA device.
- * Validates the key (Eq. 5 / Eq. 6 ranges) and the layout, allocates the
+ * Validates the key (the ranges of its map: Eq. 5, Eq. 6, or the logistic
+ * map's) and the layout, allocates the
  * device-resident chaotic state, and runs the key schedule of Alg. 1 (PRBG_m
  * keyed by K -> the parameters P_m of every PRBG_a^i) on the device
  * (synchronously).  Limits: H, W <= 16384, N = H*W*C < 2^31, n <= H*W, every
@@ -80,7 +81,8 @@ typedef struct vc_ctx vc_ctx;
 int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out);
 
 /* Encrypt nframes >= 0 consecutive frames of the stream (Alg. 1: per frame
- * s_c from PRBG_m; Alg. 2: r rounds of Eq. 1 then Eq. 3).  d_in and d_out are
+ * s_c from PRBG_m; Alg. 2: r rounds of Eq. 1 then Eq. 3, with the diffusion
+ * chains VC_OPT_DIFFUSION selects).  d_in and d_out are
  * device buffers of nframes*N bytes; d_in == d_out (in place) is allowed,
  * other overlap is not.  Advances the stream by nframes frames.  Errors:
  * VC_ERR_ARG, VC_ERR_CUDA. */
