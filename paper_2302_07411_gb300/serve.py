@@ -277,6 +277,80 @@ def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0
             "max_streams": best, "runs": runs}
 
 
+def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2) -> dict:
+    """Ragged batches against one call per frame.  nstreams streams, each with
+    its own key, resolutions cycling 480^2, 576^2, 768^2 and 1920x1080
+    (n = ceil(H/4)), maps and directions alternating, one frame per stream per
+    tick.  Batched: one vc_batch_submit per tick (one graph replay; keystream,
+    rounds and fix-up of every stream inside it).  Per frame: encrypt_frames /
+    decrypt_frames per stream, each stream on its own CUDA stream.  Device time
+    per tick by CUDA events after `warm` ticks; the outputs of the two forms
+    are compared byte for byte after the last tick."""
+    import torch
+
+    import synth
+
+    res = [(480, 480), (576, 576), (768, 768), (1080, 1920)]
+    specs = []
+    for s_ in range(nstreams):
+        H, W = res[s_ % len(res)]
+        kind, direction = (s_ // 4) % 2, (s_ // 8) % 2
+        specs.append((kind, direction, synth.key_for_seed(kind, 900 + s_), H, W, subframes_for(H)))
+    frames = {}
+    for (_, _, _, H, W, _) in specs:
+        if (H, W) not in frames:
+            frames[(H, W)] = torch.from_numpy(synth.uniform_frames(1, H, W, 3, seed=H + W)).cuda()
+    batched = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
+    single = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
+    out_b = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
+    out_s = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
+    streams = [torch.cuda.Stream() for _ in specs]
+    main = torch.cuda.current_stream()
+    batcher = B.Batcher(graph=True)
+
+    def tick_batched():
+        batcher.submit([(c, sp[1], frames[(sp[3], sp[4])], out_b[j], 1) for j, (c, sp) in enumerate(zip(batched, specs))],
+                       stream=main)
+
+    def tick_single():
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for j, (c, sp) in enumerate(zip(single, specs)):
+            st = streams[j]
+            st.wait_event(ev)
+            x = frames[(sp[3], sp[4])]
+            if sp[1] == 0:
+                c.encrypt(x, out_s[j], stream=st)
+            else:
+                c.decrypt(x, out_s[j], stream=st)
+        for st in streams:
+            main.wait_stream(st)
+
+    def timed(fn):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for _ in range(ticks):
+            fn()
+        b.record(main)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / ticks
+
+    ms_b = timed(tick_batched)
+    ms_s = timed(tick_single)
+    same = all(torch.equal(x, y) for x, y in zip(out_b, out_s))
+    px = sum(H * W for (_, _, _, H, W, _) in specs)
+    batcher.close()
+    for c in batched + single:
+        c.close()
+    return {"streams": nstreams, "resolutions": ["480x480", "576x576", "768x768", "1080x1920"],
+            "batched_ms_per_tick": round(ms_b, 3), "per_frame_ms_per_tick": round(ms_s, 3),
+            "batched_mpixel_s": round(px / ms_b / 1e3, 1), "per_frame_mpixel_s": round(px / ms_s / 1e3, 1),
+            "outputs_equal": bool(same)}
+
+
 def main():
     import argparse
     import json
@@ -298,11 +372,17 @@ def main():
     ap.add_argument("--size", type=int, nargs=2, default=[768, 768])
     ap.add_argument("--seconds", type=float, default=4.0)
     ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--batch-mix", type=int, default=0, metavar="N",
+                    help="instead: N streams of mixed resolutions, one batch per tick against one call per frame")
+    ap.add_argument("--ticks", type=int, default=6, help="timed ticks of --batch-mix")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     from . import build
 
     build.build()
+    if a.batch_mix:
+        print(json.dumps(batch_mix(a.batch_mix, ticks=a.ticks)))
+        return
     modes = ["batch", "perframe"] if a.mode == "both" else [a.mode]
     out = {}
     for mode in modes:
