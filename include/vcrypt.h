@@ -94,6 +94,19 @@ int encrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nfr
  * frame for frame. */
 int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
 
+/* encrypt_frames / decrypt_frames on frames frame_pitch bytes apart (the
+ * frame_pitch of the boundary the cipher's inputs suggest, Alg. 1: a video V
+ * of frames; e.g. frames inside a larger per-frame record, or rows of a
+ * buffer pool).  frame_pitch = 0 means N (packed, as encrypt_frames);
+ * otherwise frame_pitch >= N, any alignment, and the same pitch applies to
+ * d_in and d_out (d_in == d_out allowed).  Only the N bytes at the start of
+ * each frame slot are read or written.  Errors: those of encrypt_frames,
+ * VC_ERR_ARG for 0 < frame_pitch < N. */
+int encrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, size_t frame_pitch,
+                           void* stream);
+int decrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, size_t frame_pitch,
+                           void* stream);
+
 /* encrypt_frames / decrypt_frames on HOST buffers: copies h_in to the device,
  * runs the cipher, copies the result to h_out, in chunks that overlap copies
  * with compute; returns after the result is in h_out (synchronous).  direction
@@ -126,6 +139,11 @@ int crypt_frames_host(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8
  *    other streams without ordering between them) race on it.  Keep them on
  *    one stream or synchronise between them.  No byte of the array needs to
  *    start at zero: a call writes everything it reads.
+ *  - On a context whose previous encrypt_frames call generated keystream
+ *    ahead (VC_OPT_RUNAHEAD_CALLS), the call first undoes that run-ahead,
+ *    which waits on the host for the context's internal keystream stream.
+ *    Callers that must never wait can turn VC_OPT_RUNAHEAD_CALLS off, or use
+ *    this entry point alone on the context.
  * Errors: VC_ERR_ARG, VC_ERR_UNSUPPORTED (frame too large), VC_ERR_CUDA. */
 int encrypt_frames_static(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream);
 

@@ -34,6 +34,15 @@ int vc_dbg_lasm(const double* d_xymu, double* d_out, int64_t n, void* stream);
  * that round, Eq. 3), d_sc the frames' confusion seeds s_c (Alg. 1). */
 int vc_dbg_keystream(vc_ctx* ctx, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, void* stream);
 
+/* The passes the next encrypt_frames / decrypt_frames call of nframes >= 1
+ * frames on this context would run: plan[0 .. min(n, cap) - 1] receives their
+ * frame counts in order, info4 = {n passes, 1 if the first pass takes frames
+ * whose keystream the previous call generated ahead, frames of keystream the
+ * call would generate ahead for the next one at its end (0: none), warps per
+ * SM-holding keystream CTA (0: the keystream shares all SMs)}.  Reads the
+ * context only.  Errors: VC_ERR_ARG. */
+int vc_dbg_call_plan(const vc_ctx* ctx, int32_t nframes, int32_t* plan, int32_t cap, int32_t* info4);
+
 /* Internal geometry, for tests: {rows per tile, tiles per frame, padded frame
  * stride, N, P, scratch frames allocated, frames per pass, round-kernel shared
  * memory bytes}. */

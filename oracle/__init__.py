@@ -72,6 +72,7 @@ def lib():
             "orc_ctx_size": (C.c_size_t, [i32]),
             "orc_ctx_init": (i32, [p, i32, p, i32, i32, i32, i32, i32]),
             "orc_sub_params": (None, [p, i32, p]),
+            "orc_set_sub_params": (None, [p, i32, p]),
             "orc_next_sc": (i64, [p]),
             "orc_ktable": (None, [i32, i64, p]),
             "orc_confuse": (None, [i32, i32, i32, p, p, p]),
@@ -287,6 +288,13 @@ class OracleCipher:
         out = np.zeros(6, dtype=np.float64)
         lib().orc_sub_params(self.ptr, i, _ptr(out))
         return out
+
+    def set_sub_params(self, i: int, params) -> None:
+        """Test hook: restart subframe i's PRBG (Alg. 2) from these map
+        parameters, e.g. an orbit a test can compute exactly."""
+        prm = np.zeros(6, dtype=np.float64)
+        prm[: len(params)] = params
+        lib().orc_set_sub_params(self.ptr, i, _ptr(prm))
 
     def _run(self, fn, frames: np.ndarray) -> np.ndarray:
         frames = np.ascontiguousarray(frames, dtype=np.uint8)

@@ -337,6 +337,14 @@ void orc_sub_params(const orc_ctx* c, int i, double* out6) {
   memcpy(out6, c->sub[i].s, 6 * sizeof(double));
 }
 
+/* Test hook: restart PRBG_a^i of Alg. 2 from the given map parameters (its
+ * next output byte comes from x_1 of the new orbit).  Lets a test put every
+ * subframe on an orbit it can compute exactly by other means (the PLCM at
+ * p = 1/4 on dyadic x0), so a whole frame follows from closed forms. */
+void orc_set_sub_params(orc_ctx* c, int i, const double* params6) {
+  orc_prbg_init(&c->sub[i], c->sub[i].kind, params6);
+}
+
 /* Alg. 1: one confusion seed per frame, a positive integer */
 int64_t orc_next_sc(orc_ctx* c) { return 1 + (int64_t)(next_group(&c->main) % 65536u); }
 

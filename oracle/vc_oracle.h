@@ -51,6 +51,7 @@ int orc_layout_valid(int H, int W, int C, int n, int rounds);
 size_t orc_ctx_size(int n);
 int orc_ctx_init(orc_ctx* c, int kind, const double* key, int H, int W, int C, int n, int rounds);
 void orc_sub_params(const orc_ctx* c, int i, double* out6);
+void orc_set_sub_params(orc_ctx* c, int i, const double* params6);
 int64_t orc_next_sc(orc_ctx* c);
 void orc_ktable(int H, int64_t sc, int64_t* k);
 void orc_confuse(int H, int W, int C, const int64_t* k, const uint8_t* X, uint8_t* Y);

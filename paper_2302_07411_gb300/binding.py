@@ -59,6 +59,9 @@ def lib():
             "encrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "decrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "crypt_frames_host": (C.c_int, [p, i32, p, p, i32, p]),
+            "encrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
+            "decrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
+            "vc_dbg_call_plan": (C.c_int, [p, i32, p, i32, p]),
             "encrypt_frames_static": (C.c_int, [p, p, p, i32, p]),
             "vc_batcher_create": (C.c_int, [p]),
             "vc_batch_submit": (C.c_int, [p, p, i32, p]),
@@ -130,6 +133,13 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _dbase(t):
+    """Base address of a CUDA tensor that may be a strided view (pitched frames)."""
+    if t.device.type != "cuda":
+        raise ValueError("expected a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
 def _hptr(a):
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
@@ -157,6 +167,17 @@ def encrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
 
 def decrypt_frames(ctx, d_in, d_out, nframes: int, stream=None) -> None:
     _check(lib().decrypt_frames(ctx, _dptr(d_in), _dptr(d_out), nframes, _stream(stream)), "decrypt_frames")
+
+
+def encrypt_frames_pitched(ctx, d_in, d_out, nframes: int, frame_pitch: int, stream=None) -> None:
+    """encrypt_frames on frames frame_pitch bytes apart (0 = packed)."""
+    _check(lib().encrypt_frames_pitched(ctx, _dbase(d_in), _dbase(d_out), nframes,
+                                        frame_pitch, _stream(stream)), "encrypt_frames_pitched")
+
+
+def decrypt_frames_pitched(ctx, d_in, d_out, nframes: int, frame_pitch: int, stream=None) -> None:
+    _check(lib().decrypt_frames_pitched(ctx, _dbase(d_in), _dbase(d_out), nframes,
+                                        frame_pitch, _stream(stream)), "decrypt_frames_pitched")
 
 
 def encrypt_frames_static(ctx, d_in, d_out, nframes: int, stream=None) -> None:
@@ -236,6 +257,16 @@ def vc_dbg_lasm(d_xymu, d_out, stream=None) -> None:
 
 def vc_dbg_keystream(ctx, d_ks, d_sc, nframes: int, stream=None) -> None:
     _check(lib().vc_dbg_keystream(ctx, _dptr(d_ks), _dptr(d_sc), nframes, _stream(stream)), "vc_dbg_keystream")
+
+
+def vc_dbg_call_plan(ctx, nframes: int) -> dict:
+    """The passes the next call of nframes frames would run (diagnostic)."""
+    cap = 4096
+    plan = (C.c_int32 * cap)()
+    info = (C.c_int32 * 4)()
+    _check(lib().vc_dbg_call_plan(ctx, nframes, plan, cap, info), "vc_dbg_call_plan")
+    return {"passes": list(plan[: min(info[0], cap)]), "first_runahead": bool(info[1]),
+            "runahead_next": info[2], "ks_sm_warps": info[3]}
 
 
 def vc_dbg_layout(ctx) -> dict:

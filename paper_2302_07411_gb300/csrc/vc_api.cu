@@ -583,8 +583,10 @@ int enter(vc_ctx* c, cudaStream_t st) {
   return VC_OK;
 }
 
-int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nframes, void* stream) {
-  if (!c || nframes < 0 || (nframes > 0 && (!d_in || !d_out))) {
+// pitch: bytes from one frame to the next in d_in and d_out (>= N).
+int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nframes, void* stream,
+                 long long pitch) {
+  if (!c || nframes < 0 || (nframes > 0 && (!d_in || !d_out)) || pitch < c->L.N) {
     set_err("invalid argument");
     return VC_ERR_ARG;
   }
@@ -595,7 +597,7 @@ int crypt_device(vc_ctx* c, int dir, const uint8_t* d_in, uint8_t* d_out, int nf
   if (rc) return rc;
   rc = enter(c, st);
   if (rc) return rc;
-  const long long N = c->L.N;
+  const long long N = pitch;
   std::vector<int> plan;
   bool first_spec = false;
   int next_first = 0;
@@ -725,11 +727,25 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
 }
 
 int encrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream) {
-  return crypt_device(ctx, 0, d_in, d_out, nframes, stream);
+  return crypt_device(ctx, 0, d_in, d_out, nframes, stream, ctx ? ctx->L.N : 0);
 }
 
 int decrypt_frames(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, void* stream) {
-  return crypt_device(ctx, 1, d_in, d_out, nframes, stream);
+  return crypt_device(ctx, 1, d_in, d_out, nframes, stream, ctx ? ctx->L.N : 0);
+}
+
+int encrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, size_t frame_pitch,
+                           void* stream) {
+  if (!ctx) return VC_ERR_ARG;
+  const long long pitch = frame_pitch == 0 ? ctx->L.N : (frame_pitch > ((size_t)1 << 40) ? -1 : (long long)frame_pitch);
+  return crypt_device(ctx, 0, d_in, d_out, nframes, stream, pitch);
+}
+
+int decrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int32_t nframes, size_t frame_pitch,
+                           void* stream) {
+  if (!ctx) return VC_ERR_ARG;
+  const long long pitch = frame_pitch == 0 ? ctx->L.N : (frame_pitch > ((size_t)1 << 40) ? -1 : (long long)frame_pitch);
+  return crypt_device(ctx, 1, d_in, d_out, nframes, stream, pitch);
 }
 
 // Host staging buffers for passes of up to `frames` frames.
@@ -1116,6 +1132,20 @@ int vc_dbg_keystream(vc_ctx* c, uint8_t* d_ks, int64_t* d_sc, int32_t nframes, v
   c->frame += nframes;
   c->produced = c->frame;
   c->produced_done = c->frame;
+  return VC_OK;
+}
+
+int vc_dbg_call_plan(const vc_ctx* c, int32_t nframes, int32_t* plan, int32_t cap, int32_t* info4) {
+  if (!c || nframes < 1 || !info4 || cap < 0 || (cap > 0 && !plan)) return VC_ERR_ARG;
+  std::vector<int> p;
+  bool first_spec = false;
+  int next_first = 0;
+  call_plan(c, nframes, pass_frames(c, nframes), p, &first_spec, &next_first);
+  for (int k = 0; k < (int)p.size() && k < cap; k++) plan[k] = p[k];
+  info4[0] = (int32_t)p.size();
+  info4[1] = first_spec ? 1 : 0;
+  info4[2] = (c->overlap && c->spec_enabled) ? next_first : 0;
+  info4[3] = ks_warps_in_use(c);
   return VC_OK;
 }
 

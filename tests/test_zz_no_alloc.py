@@ -48,8 +48,38 @@ def test_static_scratch_matches_allocating_path_two_calls(B, kind, H, W, n):
         b.sync()
         assert torch.equal(ya, yb), f"call {call}: {(ya != yb).sum().item()} bytes differ"
     assert a.frame_index == b.frame_index == 8
+    # the property the entry point exists for: the context allocated no scratch
+    assert a.layout_info()["cap"] == 0
     a.close()
     b.close()
+
+
+def test_static_calls_interleaved_with_encrypt_frames(B):
+    """One context alternating encrypt_frames (which generates the next call's
+    first pass of keystream ahead) and encrypt_frames_static (which first undoes
+    that run-ahead) gives the bytes of encrypt_frames alone, call for call."""
+    key = synth.key_for_seed(0, 80)
+    H, W, n = 96, 128, 7
+    X = synth.uniform_frames(24, H, W, 3, seed=81)
+    mixed = B.Cipher(0, key, H, W, 3, n, 5)
+    plain = B.Cipher(0, key, H, W, 3, n, 5)
+    assert mixed.get_option(B.VC_OPT_RUNAHEAD_CALLS) == 1
+    d = torch.from_numpy(X).cuda()
+    for call, static in enumerate([False, True, False, False, True, True]):
+        part = d[4 * call: 4 * call + 4].contiguous()
+        ym = torch.empty_like(part)
+        yp = torch.empty_like(part)
+        if static:
+            B.encrypt_frames_static(mixed.ctx, part, ym, 4)
+        else:
+            B.encrypt_frames(mixed.ctx, part, ym, 4)
+        B.encrypt_frames(plain.ctx, part, yp, 4)
+        mixed.sync()
+        plain.sync()
+        assert torch.equal(ym, yp), f"call {call} (static={static}): {(ym != yp).sum().item()} bytes differ"
+    assert mixed.frame_index == plain.frame_index == 24
+    mixed.close()
+    plain.close()
 
 
 def test_static_scratch_rejects_frames_beyond_its_size(B):
