@@ -35,13 +35,26 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# k_ks_plcm_fx_sm: warp instructions per iterate and lane (ncu) and the
-# dependency chain of one iterate in cycles (clock64 probe of plcm_fx_step)
-PLCM_INSTR_PER_ITER = 113.0
-PLCM_ITER_CYCLES = 251.0
-# its DRAM read + write bytes per frame of keystream (ncu, 40-frame launch at
-# 768x768x3, n = 4096): scaled to the bench's launches by their frames
+# binary64 operations per map iterate, as the method specifies the iterate
+# (fixed by the equations and the sine reading, not by any kernel's code):
+#  PLCM, Eq. 5: one comparison, up to two additions/subtractions (1 - x and
+#    x - p) and one division, the division counted as the seven fused
+#    multiply-adds of a Newton-Raphson division with a final correction step
+#    (Markstein's sequence) -> 10;
+#  logistic map: two products and one difference -> 3;
+#  2DLASM, Eq. 6: two sines of the cipher's csin (Cody-Waite reduction, 7
+#    operations; degree-17 / degree-16 Taylor polynomial by Horner without
+#    fused multiply-adds, 18) and five products and sums per coordinate
+#    -> 2 x 25 + 10 = 60.
+FP64_OPS_PER_ITER = {"plcm": 10.0, "logistic": 3.0, "2dlasm": 60.0}
+# map iterates per 6 keystream bytes: two PLCM or logistic maps (6 bytes each,
+# XORed); a 2DLASM pair emits 12 bytes per iterate of its two maps
+ITERS_PER_BYTE = {"plcm": 2.0 / 6.0, "logistic": 2.0 / 6.0, "2dlasm": 2.0 / 12.0}
+# DRAM read + write bytes per frame of keystream of k_ks_plcm_fx_sm (ncu,
+# 40-frame launch at 768x768x3, n = 4096; profiles/k_ks_plcm_fx_sm_*): scaled
+# to the bench's launches by their frames
 PLCM_KS_DRAM_BYTES_PER_FRAME = (365_568 + 297_627_904) / 40
+SWEEP_N = (16, 64, 256, 1024, 4096)
 
 MAP_KIND = {"plcm": 0, "2dlasm": 1, "logistic": 2}  # VC_PLCM, VC_2DLASM, VC_LOGISTIC
 METRIC = "5-round enc Mpixel/s"
@@ -73,6 +86,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-serving", action="store_true", help="skip the 24 FPS serving-capacity leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the subframe-count sweep (n = 16 .. 4096)")
     return ap.parse_args()
 
 
@@ -249,6 +263,50 @@ def serving_capacity() -> dict:
     return out
 
 
+def subframe_sweep(a, X, d_in, d_out, kind, key, stream, clock_hz, step_cycles, at_n):
+    """The subframe-count sweep on the same clip (n = 16 .. 4096; Sec. 3 and
+    Sec. 6 vary the thread count, one subframe per thread): Mpixel/s, the
+    keystream and rounds stage times per 240-frame step, and the ceiling that
+    2n dependent PLCM chains set (2n chains x clock / cycles per step, over 5
+    map iterates per pixel).  n = a.n reuses the main measurement."""
+    import torch
+
+    from paper_2302_07411_gb300 import binding as B
+
+    F, H, W, Cc = a.frames, a.size, a.size, 3
+    rows = []
+    for n in SWEEP_N:
+        if n == a.n:
+            ms, ks_ms, rd_ms = at_n
+        else:
+            c = B.Cipher(kind, key, H, W, Cc, n, a.rounds)
+            steps = 1 if n <= 64 else 3
+            for _ in range(1):
+                c.encrypt(d_in, d_out, stream=stream)
+            torch.cuda.synchronize()
+            c.sync()
+            B.enc_profile_enable(c.ctx, True)
+            B.enc_profile_read(c.ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                c.encrypt(d_in, d_out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            pr = B.enc_profile_read(c.ctx)
+            ks_ms = pr["keystream"]["ms"] / steps
+            rd_ms = pr["rounds"]["ms"] / steps
+            c.close()
+        px = F * H * W
+        ceiling = 2 * n * clock_hz / step_cycles / 5.0 / 1e6  # Mpixel/s: 5 PLCM iterates per pixel
+        rows.append({"n": n, "mpixel_s": round(px / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
+                     "keystream_ms": round(ks_ms, 3), "rounds_ms": round(rd_ms, 3),
+                     "chain_ceiling_mpixel_s": round(ceiling, 2),
+                     "frac_of_chain_ceiling": round(px / (ms * 1e-3) / 1e6 / ceiling, 4)})
+    return rows
+
+
 def run_ours(a) -> None:
     import numpy as np
     import torch
@@ -362,55 +420,65 @@ def run_ours(a) -> None:
     if rank != 0:
         return
 
-    # ---- roofline of the dominant kernel (keystream) and the split
+    # ---- roofline of the dominant kernel (the keystream) against fixed bounds
     peaks = load_peaks()
+    probes = B.vc_dbg_peaks(stream)  # measured on this GPU in this run
     ks_launches = max(1, prof["keystream"]["launches"])
     ks_ms_step = prof["keystream"]["ms"] / max(1, a.steps)  # summed keystream launch time per step
     ks_ms = prof["keystream"]["ms"] / ks_launches            # per launch
     rd_ms = prof["rounds"]["ms"] / max(1, a.steps)
     sc_ms = prof["schedule"]["ms"] / max(1, a.steps)
-    if a.map != "2dlasm":
-        iters = F * (a.rounds * N) / 6.0 * 2  # two map iterations per 6 keystream bytes (PLCM, logistic)
-    else:
-        iters = F * (a.rounds * N) / 12.0 * 2  # two 2DLASM iterations per 12 keystream bytes
+    iters = F * a.rounds * N * ITERS_PER_BYTE[a.map]  # map iterates per step
     achieved_iter = iters / (ks_ms_step * 1e-3)
-    clock = 2.07e9  # maximum SM clock (Hz)
+    clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    fp64_ops = probes["fp64_ops_per_s"]
+    fp64_bound = fp64_ops / FP64_OPS_PER_ITER[a.map]
+    hbm = peaks.get("hbm_gbs")
+    alg_bytes = 2 * N * F  # plaintext read once + ciphertext written once
+    hbm_achieved = alg_bytes / (ms * 1e-3) / 1e9
+    frac_hbm = hbm_achieved / hbm if hbm else None
+    lat = None
     if a.map == "plcm":
-        # integer-pipe kernel: issue ceiling = 152 SMs x 4 schedulers x 1 warp
-        # instruction per clock x 32 lanes / warp instructions per iterate and lane
-        # (ncu count for k_ks_plcm_fx_sm at this workload, profiles/)
-        instr_per_iter = PLCM_INSTR_PER_ITER
-        peak_iter = 152 * 4 * clock * 32 / instr_per_iter
-        basis = (f"integer issue: 152 SM x 4 schedulers x 2.07 GHz x 32 lanes / {instr_per_iter:.0f} "
-                 f"instructions per iterate")
-        # what binds at this chain count: 2n chains, each one dependent iterate
-        # after another (PLCM_ITER_CYCLES: one iterate's dependency chain, clock64 probe)
+        # 2n independent chains, each one dependent iterate after another: the
+        # measured cycles of one PLCM step on its dependency chain
         chains = 2 * a.n
-        lat = {"chains": chains, "cycles_per_iterate": PLCM_ITER_CYCLES,
-               "ceiling": round(chains * clock / PLCM_ITER_CYCLES / 1e9, 4),
-               "frac": round(achieved_iter / (chains * clock / PLCM_ITER_CYCLES), 4)}
-    else:
-        # binary64 kernel: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz over ~60 binary64
-        # instructions per 2DLASM iterate (two csin of a degree-17/16 Horner chain),
-        # 3 per logistic iterate (two products and a difference)
-        fp64_per_iter = 60.0 if a.map == "2dlasm" else 3.0
-        peak_iter = 152 * 2 * clock / fp64_per_iter
-        basis = f"FP64 pipe: 152 SM x 2/clk x 2.07 GHz / {fp64_per_iter:.0f} FP64 instr per map iteration"
-        lat = None
+        cyc = probes["plcm_step_cycles"]
+        ceiling = chains * clock_hz / cyc
+        lat = {"chains": chains, "cycles_per_iterate": round(cyc, 1), "ceiling": round(ceiling / 1e9, 4),
+               "frac": round(achieved_iter / ceiling, 4),
+               "basis": "2n chains x median SM clock / cycles of one dependent PLCM step (clock64 probe, this run)"}
     per_launch = ks_launches // max(1, a.steps)
     traffic = None
     if a.map == "plcm" and a.size == 768 and a.n == 4096 and a.rounds == 5:
         traffic = round(PLCM_KS_DRAM_BYTES_PER_FRAME * F / per_launch)
-    roofline = {"bound": "alu", "kernel": {"plcm": "k_ks_plcm_fx_sm", "2dlasm": "k_ks_pair_sm<2DLASM>",
-                                           "logistic": "k_ks_pair_sm<logistic>"}[a.map],
-                "unit": "Giter/s", "achieved": round(achieved_iter / 1e9, 4), "peak": round(peak_iter / 1e9, 4),
-                "frac": round(achieved_iter / peak_iter, 4), "traffic": traffic, "peak_basis": basis,
-                "latency_bound": lat, "launch_ms": round(ks_ms, 3), "launches_per_step": per_launch}
-    hbm = peaks.get("hbm_gbs")
-    alg_bytes = 2 * N * F  # plaintext read once + ciphertext written once
+    roofline = {"bound": "alu", "pipe": "binary64",
+                "kernel": {"plcm": "k_ks_plcm_fx_sm", "2dlasm": "k_ks_pair_sm<2DLASM>",
+                           "logistic": "k_ks_pair_sm<logistic>"}[a.map],
+                "unit": "Giter/s", "achieved": round(achieved_iter / 1e9, 4), "peak": round(fp64_bound / 1e9, 4),
+                "frac": round(achieved_iter / fp64_bound, 4), "traffic": traffic,
+                "traffic_basis": "scaled from the 40-frame ncu capture (DRAM bytes per frame x frames per launch)"
+                                 if traffic else None,
+                "peak_basis": (f"measured binary64 FMA rate ({fp64_ops / 1e9:.1f} G/s, this run) / "
+                               f"{FP64_OPS_PER_ITER[a.map]:.0f} binary64 operations per map iterate of the method"),
+                "frac_fp64": round(achieved_iter / fp64_bound, 4),
+                "frac_hbm": round(frac_hbm, 5) if frac_hbm is not None else None,
+                "frac_latency": lat["frac"] if lat else None,
+                "hbm": {"achieved_gbs": round(hbm_achieved, 2), "peak_gbs": hbm,
+                        "basis": "6 B/pixel (plaintext read + ciphertext written) / ms_per_step, of measured copy BW"},
+                "latency_bound": lat,
+                "measured": {"fp64_gops": round(fp64_ops / 1e9, 2), "imad_gops": round(probes["imad_ops_per_s"] / 1e9, 1),
+                             "plcm_step_cycles": round(probes["plcm_step_cycles"], 1)},
+                "launch_ms": round(ks_ms, 3), "launches_per_step": per_launch}
+    rounds_bytes = 3 * N * F * a.rounds  # per round: read X and the keystream, write Y
     split = {"keystream_ms": round(ks_ms_step, 3), "rounds_ms": round(rd_ms, 3), "schedule_ms": round(sc_ms, 3),
              "overlapped": not a.no_overlap,
+             "rounds_alg_gbs": round(rounds_bytes / (rd_ms * 1e-3) / 1e9, 1) if rd_ms > 0 else None,
              "hbm_bound_ms": round(alg_bytes / (hbm * 1e9) * 1e3, 4) if hbm else None}
+
+    sweep = None
+    if not a.no_sweep and world == 1 and a.size == 768 and a.map == "plcm":
+        sweep = subframe_sweep(a, X, d_in, d_out, kind, key, stream, clock_hz, probes["plcm_step_cycles"],
+                               (ms, ks_ms_step, rd_ms))
 
     cpu = None
     if not a.no_cpu_baseline:
@@ -428,7 +496,7 @@ def run_ours(a) -> None:
             "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+u8", "data": "synthetic", "config": config(a, world),
             "roofline": roofline, "split": split, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "serving": serving,
+            "sweep": sweep, "serving": serving,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
     ciph.close()

@@ -191,10 +191,18 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  *                      A job may then ask for at most A frames, and a stream
  *                      with keystream produced ahead accepts no single-stream
  *                      calls or checkpoint (VC_ERR_SEQUENCE).  0 (default): off.
+ * VC_BOPT_SINE:        the sine reduction of 2DLASM chains whose keystream a
+ *                      batch generates (Eq. 6, both forms give the same bits):
+ *                      1 all on the binary64 pipe (the shorter dependency
+ *                      chain), 0 with the rounding, floor and t - k pi/2 on the
+ *                      integer pipes (fewer binary64 operations), -1 (default)
+ *                      chooses per batch: 1 while the batch's 2DLASM chains
+ *                      fill at most about 3.5 warps per SM, else 0.
  * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
 #define VC_BOPT_RUNAHEAD 3
+#define VC_BOPT_SINE 4
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
@@ -220,7 +228,10 @@ void vc_batcher_destroy(vc_batcher* b);
  * (frame k arrives at t_arrival + k / fps seconds after the server's
  * creation) and, in batch mode, whose keystream run-ahead is on the device,
  * and submits them as one ragged batch (mode 0) or as one encrypt_frames /
- * decrypt_frames call per frame (mode 1, for comparison).  Per-frame latency =
+ * decrypt_frames call per frame (mode 1, for comparison: each stream's calls
+ * on its own CUDA stream, created by vc_server_add, so that different
+ * streams' calls run concurrently; a frame completes when its stream's calls
+ * of the tick do).  Per-frame latency =
  * device completion time (CUDA event) - arrival time.  All calls are on the
  * host thread that drives the loop.
  *
@@ -297,9 +308,11 @@ int enc_sync_status(vc_ctx* ctx);
  *                  the caller's stream (the keystream does not depend on the
  *                  frames); 0 runs everything on the caller's stream.
  * VC_OPT_TILE_ROWS: frame rows per tile of the round kernels, a power of two
- *                  1..32 (capped by the 96 KB shared-memory tile budget);
- *                  0 (default) takes the largest that fits.  Reading it back
- *                  gives the rows in use.
+ *                  1..32 (capped so that a tile's shared memory -- one 32-bit
+ *                  slot per pixel for C = 3 and 4, a byte for C = 1, plus the
+ *                  tile's keystream when rows are whole 16-byte pieces -- stays
+ *                  within 192 KB); 0 (default) takes the largest whose tile
+ *                  stays within 64 KB.  Reading it back gives the rows in use.
  * VC_OPT_KS_SM_WARPS: -1..4.  k > 0 runs the keystream of each pass in CTAs
  *                  of k warps that each occupy a whole SM (they claim all of
  *                  its shared memory), on an internal stream of the device's

@@ -48,6 +48,21 @@ int vc_dbg_call_plan(const vc_ctx* ctx, int32_t nframes, int32_t* plan, int32_t 
  * memory bytes}. */
 int vc_dbg_layout(const vc_ctx* ctx, int32_t* out8);
 
+/* Measured denominators of the keystream roofline, timed with CUDA events on
+ * the current device (synchronous; each call takes a few milliseconds and
+ * allocates a small scratch buffer):
+ *  vc_dbg_fp64_peak: binary64 fused multiply-adds per second over all SMs
+ *    (independent chains; one FMA counted as one operation);
+ *  vc_dbg_imad_peak: 32-bit integer multiply-adds per second over all SMs;
+ *  vc_dbg_plcm_latency: clock64 cycles per PLCM step (Eq. 5, integer-pipe
+ *    form) along one dependent chain of `iters` steps (rounded up to a multiple
+ *    of 4, run four to a loop pass as the keystream kernel runs them) from x0
+ *    with parameter p (x0 in (0, 1), p in (0, 1/2)).
+ * Errors: VC_ERR_ARG, VC_ERR_OOM, VC_ERR_CUDA. */
+int vc_dbg_fp64_peak(double* ops_per_s, void* stream);
+int vc_dbg_imad_peak(double* ops_per_s, void* stream);
+int vc_dbg_plcm_latency(double x0, double p, int32_t iters, double* cycles_per_step, void* stream);
+
 /* Since the last read (then reset): host milliseconds a vc_server spent per
  * part of its ticks (ms6[0..3]: frame clocks, readiness and job building;
  * prefetch of starved streams; the submission; the completion event), the

@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvcrypt.so")
-SOURCES = ["vc_kernels.cu", "vc_api.cu", "vc_server.cu", "vc_stats.cu"]
-HEADERS = ["vc_internal.h", "vc_maps.cuh"]
+SOURCES = ["vc_kernels.cu", "vc_api.cu", "vc_server.cu", "vc_stats.cu", "vc_peaks.cu"]
+HEADERS = ["vc_internal.h", "vc_maps.cuh", "vc_ieee.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]

@@ -39,7 +39,10 @@ void set_err(const char* fmt, ...) {
     }                                                                                      \
   } while (0)
 
-constexpr size_t kTileBudget = 96 * 1024;  // bytes of one row-band tile in shared memory
+// bytes of one row-band tile in shared memory (its pixel slots and, when staged,
+// its keystream): small enough that several CTAs share an SM
+constexpr size_t kTileBudget = 64 * 1024;
+constexpr size_t kTileHardCap = 192 * 1024;  // rows asked for explicitly (VC_OPT_TILE_ROWS) may use up to this
 constexpr uint32_t kStateMagic = 0x56435354u;  // "VCST"
 constexpr uint32_t kStateVersion = 1;
 
@@ -76,10 +79,15 @@ int make_layout(const vc_layout& l, Layout* L, int tile_rows_max = 0) {
   if ((long long)l.channels * (P / l.n_subframes) < 2) return VC_ERR_LAYOUT;  // every subframe >= 2 bytes
   const long long rowb = (long long)l.width * l.channels;
   if (rowb > vc::kMaxRowBytes) return VC_ERR_LAYOUT;
+  // a tile row in shared memory: its pixel slots, and its keystream when rows are whole 16-byte pieces
+  const long long zrow = vc::tile_row_bytes(l.width, l.channels) + ((rowb & 15) == 0 ? rowb : 0);
+  const size_t cap = tile_rows_max > 0 ? kTileHardCap : kTileBudget;
   int T = tile_rows_max > 0 ? tile_rows_max : 32;
-  while (T > 1 && (size_t)T * rowb > kTileBudget) T >>= 1;
+  while (T > 1 && (size_t)T * zrow > cap) T >>= 1;
+  if ((size_t)T * zrow > kTileHardCap) return VC_ERR_LAYOUT;
   const int NT = (l.height + T - 1) / T;
   if (NT > vc::kMaxTiles) return VC_ERR_LAYOUT;
+  const int R = T >= 8 ? T / 8 : 1;
   L->H = l.height;
   L->W = l.width;
   L->C = l.channels;
@@ -90,6 +98,10 @@ int make_layout(const vc_layout& l, Layout* L, int tile_rows_max = 0) {
   L->Npad = (N + 255) & ~255LL;
   L->T = T;
   L->NT = NT;
+  L->R = R;
+  L->lgR = R == 1 ? 0 : (R == 2 ? 1 : (R == 4 ? 2 : 3));
+  L->NS = (l.height + R - 1) / R;
+  L->ZS = vc::tile_row_stride(l.width, l.channels);
   // a window of m pixels holds at most floor(m n / P) + 1 subframe starts
   const long long tile_starts = (long long)T * l.width * l.n_subframes / P + 2;
   L->SC = tile_starts <= vc::kMaxSeedSlots ? (int)((tile_starts + 15) & ~15LL) : 0;
@@ -228,7 +240,7 @@ int ensure_scratch(vc_ctx* c, int frames) {
     ok = cudaMalloc(&c->d_ks[b], F * L.rounds * L.Npad) == cudaSuccess &&
          cudaMalloc(&c->d_sc[b], F * sizeof(long long)) == cudaSuccess &&
          cudaMalloc(&c->d_kmod[b], F * L.H * sizeof(int)) == cudaSuccess &&
-         cudaMalloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && cudaMalloc(&c->d_agg[b], F * L.NT + 16) == cudaSuccess;
+         cudaMalloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && cudaMalloc(&c->d_agg[b], F * L.NS + 16) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -665,7 +677,7 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
   bool ok = cudaMalloc(&c->d_pi, sizeof(int) * (n + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_sbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
             cudaMalloc(&c->d_srank, sizeof(int) * nwords) == cudaSuccess &&
-            cudaMalloc(&c->d_fixlim, sizeof(int) * L.NT) == cudaSuccess &&
+            cudaMalloc(&c->d_fixlim, sizeof(int) * L.NS) == cudaSuccess &&
             cudaMalloc(&c->d_main, sizeof(vc::MainPrbg)) == cudaSuccess &&
             cudaMalloc(&c->d_st, sizeof(double) * c->state_words() * n) == cudaSuccess &&
             cudaMalloc(&c->d_par, sizeof(double) * c->par_words() * n) == cudaSuccess &&
@@ -1011,7 +1023,7 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (rs) return rs;
       sync_all(c);
       int* fl = nullptr;
-      if (cudaMalloc(&fl, sizeof(int) * L2.NT) != cudaSuccess) {
+      if (cudaMalloc(&fl, sizeof(int) * L2.NS) != cudaSuccess) {
         cudaGetLastError();
         set_err("tile table allocation failed");
         return VC_ERR_OOM;
@@ -1214,7 +1226,7 @@ size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Static-scratch bytes one frame of a pass needs.
 size_t static_bytes_per_frame(const Layout& L) {
   return round256((size_t)L.rounds * L.Npad) + 2 * round256((size_t)L.Npad) + round256((size_t)L.H * sizeof(int)) +
-         round256(sizeof(long long)) + 2 * round256((size_t)L.NT);
+         round256(sizeof(long long)) + 2 * round256((size_t)L.NS);
 }
 
 }  // namespace
@@ -1275,7 +1287,7 @@ extern "C" int encrypt_frames_static(vc_ctx* c, const uint8_t* d_in, uint8_t* d_
     p += round256((size_t)nf * sizeof(long long));
     uint8_t* agg[2];
     agg[0] = p;
-    p += round256((size_t)nf * L.NT);
+    p += round256((size_t)nf * L.NS);
     agg[1] = p;
 
     const uint8_t* in = d_in + f0 * N;
@@ -1337,6 +1349,7 @@ struct vc_batcher {
   bool use_graph = true;
   int ctas_per_sm = 0;
   int runahead = 0;  // frames of keystream kept ahead per stream (0 = off)
+  int sine = -1;     // 2DLASM sine reduction in the batch keystream: -1 by load, 0 integer-assisted, 1 binary64
   cudaStream_t cap_stream = nullptr;
   std::map<size_t, int> ctas_for_smem;  // round-kernel CTAs per SM by shared-memory size (queried once)
 };
@@ -1397,7 +1410,7 @@ int grow_lane(BatchLane& l, int need) {
 }
 
 size_t job_scratch_bytes(const Layout& L, int nf, bool with_keystream) {
-  size_t b = 2 * round256((size_t)nf * L.Npad) + 2 * round256((size_t)nf * L.NT);
+  size_t b = 2 * round256((size_t)nf * L.Npad) + 2 * round256((size_t)nf * L.NS);
   if (with_keystream)
     b += round256((size_t)nf * L.rounds * L.Npad) + round256((size_t)nf * L.H * sizeof(int)) +
          round256((size_t)nf * sizeof(long long));
@@ -1607,6 +1620,10 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
       if (value < 0 || value > 64) return VC_ERR_ARG;
       b->runahead = (int)value;
       return VC_OK;
+    case VC_BOPT_SINE:
+      if (value < -1 || value > 1) return VC_ERR_ARG;
+      b->sine = (int)value;
+      return VC_OK;
   }
   return VC_ERR_ARG;
 }
@@ -1750,9 +1767,9 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     d.buf[1] = p;
     p += round256((size_t)nf * L.Npad);
     d.agg[0] = p;
-    p += round256((size_t)nf * L.NT);
+    p += round256((size_t)nf * L.NS);
     d.agg[1] = p;
-    p += round256((size_t)nf * L.NT);
+    p += round256((size_t)nf * L.NS);
     d.warp_base = warps;
     d.tile_base = tiles;
     d.kmod_base = kmods;
@@ -1765,6 +1782,18 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     const size_t sm = vc::round_smem_bytes(L);
     if (sm > smem) smem = sm;
     hj[k] = d;
+  }
+  // 2DLASM chains of this batch's keystream: the all-binary64 sine reduction
+  // (the shorter dependency chain) while their warps leave the SMs' binary64
+  // pipes unsaturated -- about 3.5 warps of 2DLASM chains fill one SM's pipe
+  // -- else the integer-assisted one (fewer binary64 operations); both give
+  // the same bits
+  {
+    int lasm_warps = 0;
+    for (int k = 0; k < nj; k++)
+      if (hj[k].mode == 0 && hj[k].kind == VC_2DLASM) lasm_warps += (hj[k].L.n + 15) / 16;
+    const int b64 = b->sine >= 0 ? b->sine : (2 * lasm_warps <= 7 * b->sms ? 1 : 0);
+    for (int k = 0; k < nj; k++) hj[k].sine_b64 = (hj[k].kind == VC_2DLASM) ? b64 : 0;
   }
   rc = launch_lane(b, b->cons, nj, warps, tiles, kmods, rounds, smem, st, vbeg, vend, variants);
   if (rc) return rc;

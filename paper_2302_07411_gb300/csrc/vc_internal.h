@@ -32,14 +32,33 @@ struct Layout {
   int T;              // rows per tile of the round kernels (power of two <= 32)
   int NT;             // tiles per frame = ceil(H / T)
   int SC;             // shared-memory seed slots per tile (>= the subframe starts in any tile; 0: none)
+  // The diffusion of a tile runs in sub-tiles of R rows, one warp each (T / R
+  // <= 8 of them per tile); a sub-tile's bytes before its first subframe start
+  // stay relative to the chain value at the end of the previous sub-tile until
+  // the next round (or the fix-up) reads them.
+  int R, lgR;         // rows per sub-tile, a power of two: max(1, T / 8); lgR = log2(R)
+  int NS;             // sub-tiles per frame = ceil(H / R)
+  int ZS;             // stride of a tile row in shared memory: 32-bit pixel slots (C = 3, 4) or bytes (C = 1)
 };
+
+// Bytes of one tile row in shared memory: a 32-bit word per pixel for C = 3
+// and 4, with one extra word after every 32 pixels (column o in slot
+// o + o / 32, which spreads the lanes of a warp over the banks), the row
+// stride even so that consecutive rows start on different banks; one byte per
+// pixel for C = 1.
+__host__ __device__ inline int tile_row_stride(int W, int C) {
+  return C == 1 ? W : ((W + (W >> 5) + 2) & ~1);
+}
+__host__ __device__ inline long long tile_row_bytes(int W, int C) {
+  return C == 1 ? (long long)W : 4LL * tile_row_stride(W, C);
+}
 
 // Read-only per-layout tables built on the device at init.
 struct Tables {
   const int* pi;          // [n+1] first pixel of each subframe, pi[n] = P
   const uint32_t* sbits;  // [P/32 + 1] bit p set <=> pixel p starts a subframe
   const int* srank;       // [P/32 + 1] number of subframe starts before bit-word w
-  const int* fixlim;      // [NT] first subframe-start byte at or after the tile's first byte (or the tile end)
+  const int* fixlim;      // [NS] first subframe-start byte at or after the sub-tile's first byte (or its end)
 };
 
 // Device-resident chaotic state of the n assistant PRBGs (Alg. 2).
@@ -68,7 +87,8 @@ struct JobDesc {
   Tables tb;
   Chains ch;
   MainPrbg* main;
-  int kind, dir, nframes, pad0;
+  int kind, dir, nframes;
+  int sine_b64;             // 2DLASM keystream: 1 = the all-binary64 sine reduction (shorter chain), 0 = integer-assisted
   const uint8_t* in;
   uint8_t* out;
   uint8_t* ks;
@@ -131,7 +151,7 @@ cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long
 cudaError_t launch_pc_round(bool encrypt, const Layout& L, Tables tb, const uint8_t* in, long long in_stride,
                             uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
                             const int* kmod, int nframes, cudaStream_t st);
-size_t round_smem_bytes(const Layout& L);
+size_t round_smem_bytes(const Layout& L);  // encryption round CTA (the largest of the round kernels)
 cudaError_t prepare_batch_kernels(size_t smem);
 cudaError_t batch_ctas_per_sm(size_t smem, int* ctas);
 cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st);

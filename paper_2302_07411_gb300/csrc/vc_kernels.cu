@@ -76,14 +76,15 @@ __global__ void k_tables_rank(Layout L, int* srank, int nwords) {
   }
 }
 
-// fixlim[t] = first subframe-start byte >= the tile's first byte, capped at the
-// tile's end: the smallest i with pi_i >= x0 is ceil(x0 n / P).
+// fixlim[s] = first subframe-start byte >= the first byte of sub-tile s (rows
+// [s R, (s + 1) R)), capped at its end: the smallest i with pi_i >= x0 is
+// ceil(x0 n / P).
 __global__ void k_tables_fixlim(Layout L, int* fixlim) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < L.NT) {
-    const long long x0 = (long long)t * L.T * L.W;
+  if (t < L.NS) {
+    const long long x0 = (long long)t * L.R * L.W;
     const long long istar = (x0 * L.n + L.P - 1) / L.P;
-    const int rows_end = min(L.H, (t + 1) * L.T);
+    const int rows_end = min(L.H, (t + 1) * L.R);
     long long fl = (long long)rows_end * L.W * L.C;
     if (istar < L.n) {
       const long long ps = (istar * L.P) / L.n;
@@ -100,7 +101,7 @@ cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* 
   k_tables_pi<<<(L.n + 1 + 255) / 256, 256, 0, st>>>(L, pi);
   k_tables_bits<<<(L.n + 255) / 256, 256, 0, st>>>(L, pi, sbits);
   k_tables_rank<<<(nwords + 255) / 256, 256, 0, st>>>(L, srank, nwords);
-  k_tables_fixlim<<<(L.NT + 255) / 256, 256, 0, st>>>(L, fixlim);
+  k_tables_fixlim<<<(L.NS + 255) / 256, 256, 0, st>>>(L, fixlim);
   return cudaGetLastError();
 }
 
@@ -990,15 +991,18 @@ cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains
 // the row rotation Y[alpha][beta] = Z[alpha][(beta - k(alpha)) mod W].  Source
 // row a contributes the contiguous columns o = (alpha - a) mod H (+ m H), one
 // per output row, so the gather reads T consecutive pixels per source row into
-// shared memory.  The tile's bytes are then diffused in raster order as a
+// shared memory (one 32-bit slot per pixel for C = 3 and 4, see
+// tile_row_stride).  The tile's bytes are then diffused in raster order as a
 // segmented XOR scan: c_q = c_{q-1} xor d_q with d_q = b xor (y_q + b), reset to
 // s_d xor d_q at every subframe start (Eq. 3 with the seed of Alg. 2).
 //
-// Chains that enter the tile from the previous tile are left relative to the
-// tile's first byte: bytes q < fixlim[t] hold c_q xor c(end of tile t-1).  The
-// tile's value at its last byte is written to agg_out; the next round (or
-// k_enc_fixup after the last round) scans these per-tile values and applies
-// the missing prefix while reading.  No CTA waits on another.
+// Each warp diffuses one sub-tile (R rows) on its own: 16 bytes per lane, a
+// warp-shuffle scan per 512 bytes and a running carry, with no barrier.  The
+// bytes of a sub-tile before its first subframe start are left relative to its
+// first byte: bytes q < fixlim[s] hold c_q xor c(end of sub-tile s-1).  The
+// value at the sub-tile's last byte is written to agg_out; the next round (or
+// k_enc_fixup after the last round) scans these per-sub-tile values and applies
+// the missing prefix while reading.  No CTA or warp waits on another.
 
 // Segmented-scan element: bit 8 = "a subframe start lies in the span",
 // bits 0..7 = XOR value (relative to the span's start if no start).
@@ -1016,44 +1020,48 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
   return x;
 }
 
-// s_carry[t] = true ciphertext byte at the last byte of tile t-1 (warp 0).
-__device__ void tile_carries(const Layout& L, const Tables& tb, const uint8_t* agg, uint8_t* s_carry) {
-  const int lane = threadIdx.x & 31;
-  uint32_t run = 0;
-  const int rowb = L.W * L.C;
-  for (int base = 0; base < L.NT; base += 32) {
-    const int t = base + lane;
-    uint32_t x = 0;
-    if (t < L.NT) {
-      const int tend = min(L.H, (t + 1) * L.T) * rowb;
-      const bool flag = __ldg(&tb.fixlim[t]) < tend;
-      x = (flag ? 0x100u : 0u) | (uint32_t)agg[t];
-    }
-    x = seg_combine(run, warp_incl_scan(x));
-    if (t + 1 < L.NT) s_carry[t + 1] = (uint8_t)x;
-    run = __shfl_sync(0xFFFFFFFFu, x, 31);
-  }
-  if (lane == 0) s_carry[0] = 0;
+// s_carry[s] = true ciphertext byte at the last byte of sub-tile s-1, for all
+// NS sub-tiles of the frame, by every warp of the block: warp w scans its
+// share [s0, s1) of the aggregates relative to the share's start, the shares'
+// totals (s_tot, one word per warp) then give each share its incoming value,
+// which the entries before the share's first subframe start still miss.  Ends
+// with a barrier; every thread of the block must call it.
+__device__ __forceinline__ bool sub_flag(const Layout& L, const Tables& tb, int s, int rowb) {
+  return __ldg(&tb.fixlim[s]) < min(L.H, (s + 1) * L.R) * rowb;  // a subframe starts in sub-tile s
 }
 
-// Exclusive block-wide segmented scan; *total = inclusive total of the block.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total, uint32_t* s_warp) {
+__device__ void sub_carries(const Layout& L, const Tables& tb, const uint8_t* agg, uint8_t* s_carry,
+                            uint32_t* s_tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t inc = warp_incl_scan(x);
-  if (lane == 31) s_warp[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t v = lane < nw ? s_warp[lane] : 0u;
-    v = warp_incl_scan(v);
-    if (lane < nw) s_warp[lane] = v;
+  const int rowb = L.W * L.C;
+  const int share = (((L.NS + nw - 1) / nw) + 31) & ~31;
+  const int s0 = min(L.NS, warp * share), s1 = min(L.NS, s0 + share);
+  uint32_t run = 0;
+  for (int base = s0; base < s1; base += 32) {
+    const int s = base + lane;
+    uint32_t x = 0;
+    if (s < s1) x = (sub_flag(L, tb, s, rowb) ? 0x100u : 0u) | (uint32_t)agg[s];
+    x = seg_combine(run, warp_incl_scan(x));
+    if (s < s1 && s + 1 < L.NS) s_carry[s + 1] = (uint8_t)x;
+    run = __shfl_sync(0xFFFFFFFFu, x, 31);
   }
+  if (lane == 0) s_tot[warp] = run;
   __syncthreads();
-  const uint32_t wpre = warp > 0 ? s_warp[warp - 1] : 0u;
-  uint32_t lex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
-  if (lane == 0) lex = 0;
-  *total = s_warp[nw - 1];
+  uint32_t in = 0;  // value at the end of sub-tile s0 - 1
+  for (int k = 0; k < warp; k++) in = seg_combine(in, s_tot[k]);
+  if ((in & 0xFFu) != 0) {
+    for (int base = s0; base < s1; base += 32) {
+      const int s = base + lane;
+      const bool flag = s < s1 && sub_flag(L, tb, s, rowb);
+      const uint32_t fl = __ballot_sync(0xFFFFFFFFu, flag);
+      // entries whose share holds no start at or before them are relative
+      const bool rel = s < s1 && (fl & (0xFFFFFFFFu >> (31 - lane))) == 0;
+      if (rel && s + 1 < L.NS) s_carry[s + 1] ^= (uint8_t)(in & 0xFFu);
+      if (fl != 0) break;  // every later entry of the share is absolute
+    }
+  }
+  if (threadIdx.x == 0) s_carry[0] = 0;
   __syncthreads();
-  return seg_combine(wpre, lex);
 }
 
 __device__ __forceinline__ int mod_h(int v, int H) {
@@ -1080,6 +1088,127 @@ __device__ __forceinline__ uint32_t vadd4(uint32_t a, uint32_t b) {
 // Byte 3 of w in all four bytes.
 __device__ __forceinline__ uint32_t bcast3(uint32_t w) { return __byte_perm(w, 0u, 0x3333u); }
 
+// A byte repeated over the C bytes of a pixel word.
+template <int C>
+__device__ __forceinline__ uint32_t rep_px(uint32_t b) {
+  return C == 1 ? b : (C == 3 ? b * 0x010101u : b * 0x01010101u);
+}
+
+// Shared-memory slot of pixel (tile row tt, column o): a word index for C = 3
+// and 4 (one word per pixel, a skipped word after every 32), a byte index for
+// C = 1.
+template <int C>
+__device__ __forceinline__ int zslot(const Layout& L, int tt, int o) {
+  return C == 1 ? tt * L.ZS + o : tt * L.ZS + o + (o >> 5);
+}
+
+template <int C>
+__device__ __forceinline__ void store_z(uint8_t* Z, int slot, uint32_t v) {
+  if (C == 1)
+    Z[slot] = (uint8_t)v;
+  else
+    reinterpret_cast<uint32_t*>(Z)[slot] = v;
+}
+
+// Byte ch of pixel (tt, o) of the tile in shared memory.
+template <int C>
+__device__ __forceinline__ uint8_t z_byte(const Layout& L, const uint8_t* Z, int tt, int o, int ch) {
+  return C == 1 ? Z[zslot<1>(L, tt, o)] : Z[4 * zslot<C>(L, tt, o) + ch];
+}
+
+// The C bytes of the pixel at byte qx of frame X as the low bytes of a word
+// (the rest zero).  aligned: X is 4-byte aligned, so the aligned words that
+// hold the pixel lie in the frame whenever qx + 8 <= N; otherwise byte loads.
+template <int C>
+__device__ __forceinline__ uint32_t load_px_g(const uint8_t* X, int qx, bool aligned, int N) {
+  if (C == 4 && aligned) return __ldg(reinterpret_cast<const uint32_t*>(X + qx));
+  if (C == 3 && aligned && qx + 8 <= N) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(X + (qx & ~3));
+    const uint32_t w0 = __ldg(w);
+    const uint32_t w1 = (qx & 3) >= 2 ? __ldg(w + 1) : 0u;
+    return __funnelshift_r(w0, w1, (uint32_t)(qx & 3) * 8u) & 0xFFFFFFu;
+  }
+  uint32_t v = 0;
+#pragma unroll
+  for (int c = 0; c < C; c++) v |= (uint32_t)__ldg(X + qx + c) << (8 * c);
+  return v;
+}
+
+// Packed bytes zs .. zs + 15 of tile row tt (columns taken cyclically mod W,
+// as the row rotation of Eq. 1 reads them) as four words, byte 0 lowest.
+// C = 1 needs zs + 16 <= W or W a multiple of 4 (the caller checks).
+template <int C>
+__device__ __forceinline__ void z_row16(const Layout& L, const uint8_t* Z, int tt, int zs, uint32_t& y0,
+                                        uint32_t& y1, uint32_t& y2, uint32_t& y3) {
+  const uint32_t* Zw = reinterpret_cast<const uint32_t*>(Z);
+  if (C == 4) {  // zs is a multiple of 4: four whole pixels
+    uint32_t w[4];
+    const int p = zs >> 2;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      int q = p + i;
+      if (q >= L.W) q -= L.W;
+      w[i] = Zw[zslot<4>(L, tt, q)];
+    }
+    y0 = w[0];
+    y1 = w[1];
+    y2 = w[2];
+    y3 = w[3];
+  } else if (C == 3) {  // six pixels cover bytes zs .. zs + 15 (zs = 3 p + ph)
+    const int p = zs / 3, ph = zs - 3 * p;
+    uint32_t w[6];
+    const int base = tt * L.ZS;
+    if (p + 5 < L.W) {
+      const int s0 = base + p + (p >> 5), lo = p & 31;
+#pragma unroll
+      for (int i = 0; i < 6; i++) w[i] = Zw[s0 + i + ((lo + i) >> 5)];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        int q = p + i;
+        if (q >= L.W) q -= L.W;
+        w[i] = Zw[base + q + (q >> 5)];
+      }
+    }
+    // the six 3-byte pixels as 18 consecutive bytes (k4 holds bytes 16, 17)
+    const uint32_t k0 = __byte_perm(w[0], w[1], 0x4210u);
+    const uint32_t k1 = __byte_perm(w[1], w[2], 0x5421u);
+    const uint32_t k2 = __byte_perm(w[2], w[3], 0x6542u);
+    const uint32_t k3 = __byte_perm(w[4], w[5], 0x4210u);
+    const uint32_t k4 = __byte_perm(w[5], 0u, 0x4421u);
+    const uint32_t sh = 8u * (uint32_t)ph;
+    y0 = __funnelshift_r(k0, k1, sh);
+    y1 = __funnelshift_r(k1, k2, sh);
+    y2 = __funnelshift_r(k2, k3, sh);
+    y3 = __funnelshift_r(k3, k4, sh);
+  } else {  // bytes; the five words wrap word-wise at the row end when W is whole words
+    uint32_t z0, z1, z2, z3, z4, sh;
+    if (zs + 16 <= L.W) {
+      const int za = tt * L.ZS + zs;
+      const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
+      sh = (uint32_t)(za & 3) * 8u;
+      z0 = zw[0];
+      z1 = zw[1];
+      z2 = zw[2];
+      z3 = zw[3];
+      z4 = zw[4];
+    } else {
+      const uint32_t* zr = reinterpret_cast<const uint32_t*>(Z + tt * L.ZS);
+      const int rw = L.W >> 2, wi = zs >> 2;
+      sh = (uint32_t)(zs & 3) * 8u;
+      z0 = zr[wi];
+      z1 = zr[wi + 1 < rw ? wi + 1 : wi + 1 - rw];
+      z2 = zr[wi + 2 < rw ? wi + 2 : wi + 2 - rw];
+      z3 = zr[wi + 3 < rw ? wi + 3 : wi + 3 - rw];
+      z4 = zr[wi + 4 < rw ? wi + 4 : wi + 4 - rw];
+    }
+    y0 = __funnelshift_r(z0, z1, sh);
+    y1 = __funnelshift_r(z1, z2, sh);
+    y2 = __funnelshift_r(z2, z3, sh);
+    y3 = __funnelshift_r(z3, z4, sh);
+  }
+}
+
 struct RoundArgs {
   Layout L;
   Tables tb;
@@ -1094,8 +1223,43 @@ struct RoundArgs {
   uint8_t* agg_out;
 };
 
+// Dynamic shared memory of an encryption round CTA:
+// [tile Z, 16-aligned][the tile's keystream, T W C bytes when rows are whole
+// 16-byte pieces, else none][sub-tile carries, NS bytes rounded to 16]
+// [share totals, 32 words][row shifts, 32 ints][the tile's subframe-start bit
+// words][subframe seeds, SC bytes].  A decryption round uses the tile alone.
+struct RoundSmem {
+  int ks, carry, tot, kmod, sbits, seed, total;
+  bool ks_staged;
+};
+__host__ __device__ inline RoundSmem round_smem(const Layout& L) {
+  RoundSmem m;
+  const int rowb = L.W * L.C;
+  m.ks = (int)(((long long)L.T * tile_row_bytes(L.W, L.C) + 15) & ~15LL);
+  m.ks_staged = (rowb & 15) == 0;
+  m.carry = m.ks + (m.ks_staged ? L.T * rowb : 0);
+  m.tot = m.carry + ((L.NS + 15) & ~15);
+  m.kmod = m.tot + 32 * (int)sizeof(uint32_t);
+  m.sbits = m.kmod + 32 * (int)sizeof(int);
+  m.seed = m.sbits + 4 * (((L.T * L.W) >> 5) + 4);
+  m.total = m.seed + L.SC;
+  return m;
+}
+
+size_t round_smem_bytes(const Layout& L) { return (size_t)round_smem(L).total; }
+size_t dec_smem_bytes(const Layout& L) { return (size_t)(((long long)L.T * tile_row_bytes(L.W, L.C) + 15) & ~15LL); }
+
+// 16-byte global -> shared copy that completes asynchronously (cp.async, L2
+// only); cp_async_wait_all() waits for this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Byte qb of the current round's confused frame Y, read through Eq. 1 from
-// the previous round's output X (with the pending tile prefixes applied).
+// the previous round's output X (with the pending sub-tile prefixes applied).
 template <int C>
 __device__ __forceinline__ uint8_t enc_y_at(const Layout& L, const Tables& tb, const uint8_t* X, const int* kmod,
                                             const uint8_t* s_carry, bool fix, int qb) {
@@ -1107,10 +1271,291 @@ __device__ __forceinline__ uint8_t enc_y_at(const Layout& L, const Tables& tb, c
   const int qx = (a * L.W + o) * C + ch;
   uint8_t x = X[qx];
   if (fix) {
-    const int ta = a / L.T;
-    if (qx < __ldg(&tb.fixlim[ta])) x ^= s_carry[ta];
+    const int sa = a >> L.lgR;
+    if (qx < __ldg(&tb.fixlim[sa])) x ^= s_carry[sa];
   }
   return x;
+}
+
+// Gather of the tile Z for C = 3 and 4 (T >= 4): each lane moves a run of
+// four consecutive pixels of one source row (T / 4 lanes per source row), as
+// four aligned 32-bit loads shifted into place and four 32-bit slot stores.
+// Runs that wrap at H, leave the frame's columns or its bytes go pixel by
+// pixel.  Z[tt][o] = X[(a0 + tt - o) mod H][o] as in the per-pixel gather.
+template <int C>
+__device__ __forceinline__ void gather_runs(const Layout& L, const Tables& tb, const uint8_t* X, uint8_t* Z,
+                                            const uint8_t* s_carry, const bool fix, const int a0, const int Te,
+                                            const bool aligned) {
+  constexpr int PR = 4;  // pixels per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int LS = L.T / PR;  // lanes per source row
+  const int rpw = 32 / LS;  // source rows per warp pass
+  const int tt0 = (lane % LS) * PR;
+  const int sub = lane / LS;
+  const int astep = nw * rpw;
+  const int MC = (L.W + L.H - 1) / L.H;
+  uint32_t* Zw = reinterpret_cast<uint32_t*>(Z);
+  constexpr int U = 4;  // source rows in flight per lane
+  if (tt0 >= Te) return;
+  const bool whole = tt0 + PR <= Te;
+  for (int m = 0; m < MC; m++) {
+    const int mo = m * L.H;
+    for (int a = warp * rpw + sub; a < L.H; a += U * astep) {
+      uint32_t w0[U], w1[U], w2[U], w3[U];
+      int ov[U], qv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int au = a + u * astep;
+        int o = a0 + tt0 - au;
+        if (o < 0) o += L.H;
+        // the run's columns o .. o + 3 are consecutive, inside the frame and
+        // its aligned words inside the frame's bytes
+        const int qx = (au * L.W + o + mo) * C;
+        const bool fast = aligned && whole && au < L.H && o + PR <= L.H && o + mo + PR <= L.W &&
+                          (qx & ~3) + 16 <= L.N;
+        ov[u] = au < L.H ? o + mo : -1;
+        qv[u] = fast ? qx : -1;
+        w0[u] = w1[u] = w2[u] = w3[u] = 0u;
+        if (fast) {
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(X + (qx & ~3));
+          w0[u] = __ldg(src);
+          w1[u] = __ldg(src + 1);
+          w2[u] = __ldg(src + 2);
+          if (C == 4 || (qx & 3) != 0) w3[u] = __ldg(src + 3);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (ov[u] < 0) continue;
+        const int au = a + u * astep;
+        const int sa = au >> L.lgR;
+        const int lim = fix ? __ldg(&tb.fixlim[sa]) : 0;
+        const uint32_t cy = fix ? rep_px<C>(s_carry[sa]) : 0u;
+        if (qv[u] >= 0) {
+          const int qx = qv[u];
+          const uint32_t sh = (uint32_t)(qx & 3) * 8u;
+          const uint32_t u0 = __funnelshift_r(w0[u], w1[u], sh), u1 = __funnelshift_r(w1[u], w2[u], sh);
+          const uint32_t u2 = __funnelshift_r(w2[u], w3[u], sh), u3 = __funnelshift_r(w3[u], 0u, sh);
+          uint32_t px[PR];
+          if (C == 4) {
+            px[0] = u0;
+            px[1] = u1;
+            px[2] = u2;
+            px[3] = u3;
+          } else {  // bytes 0-2, 3-5, 6-8, 9-11 of the run
+            px[0] = u0 & 0xFFFFFFu;
+            px[1] = __byte_perm(u0, u1, 0x0543u) & 0xFFFFFFu;
+            px[2] = __byte_perm(u1, u2, 0x0432u) & 0xFFFFFFu;
+            px[3] = u2 >> 8;
+          }
+#pragma unroll
+          for (int j = 0; j < PR; j++) {
+            uint32_t x = px[j];
+            if (fix && qx + j * C < lim) x ^= cy;  // subframe starts are pixel-aligned
+            Zw[zslot<C>(L, tt0 + j, ov[u] + j)] = x;
+          }
+        } else {
+          // pixel by pixel: each tile row tt of the run has its own column
+#pragma unroll
+          for (int j = 0; j < PR; j++) {
+            const int tt = tt0 + j;
+            if (tt >= Te) break;
+            int o = a0 + tt - au;
+            if (o < 0) o += L.H;
+            o += mo;
+            if (o >= L.W) continue;
+            const int qx = (au * L.W + o) * C;
+            uint32_t x = load_px_g<C>(X, qx, aligned, L.N);
+            if (fix && qx < lim) x ^= cy;
+            Zw[zslot<C>(L, tt, o)] = x;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Diffusion of one warp's sub-tile (rows r0 .. r1 - 1) in chunks of 16
+// pixels (16 C bytes) per lane, for C = 3 and 4 with W a multiple of 16 and
+// the tile's keystream in shared memory (s_ks, tile byte offsets).  A chunk
+// never crosses a row and, since the row rotation of Eq. 1 moves whole
+// pixels, its source bytes in Z start at a pixel: sixteen slot loads packed
+// into 4 C words.  The subframe starts of a chunk are 16 consecutive bits of
+// one start-bit word.  Chunks with more than one start (or, without seed
+// slots, any start) go byte by byte.
+// c ? a : b, opaque to the compiler, so that a loop of selections over an
+// unrolled register array stays in registers (an index would move the array
+// to local memory).
+__device__ __forceinline__ uint32_t sel_u32(bool c, uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("{\n .reg .pred p;\n setp.ne.u32 p, %3, 0;\n selp.b32 %0, %1, %2, p;\n}" : "=r"(r) : "r"(a), "r"(b),
+      "r"((uint32_t)c));
+  return r;
+}
+
+// Seed of the subframe starting at pixel pix (the rare many-starts path of
+// diffuse_px16).
+template <int C>
+__device__ __forceinline__ uint8_t px16_seed(const RoundArgs& A, int pix, const uint32_t* s_sbits, int wlo,
+                                          const uint8_t* s_seed, int s_lo, bool seeded, const uint8_t* X,
+                                          const int* kmod, const uint8_t* s_carry, bool fix) {
+  const Layout& L = A.L;
+  const int wq = pix >> 5;
+  const int s = __ldg(&A.tb.srank[wq]) + __popc(s_sbits[wq - wlo] & ((1u << (pix & 31)) - 1u));
+  if (seeded) return s_seed[s - s_lo];
+  const int nx = (s + 1 == L.n) ? 0 : s + 1;
+  return enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, C * __ldg(&A.tb.pi[nx + 1]) - 1);
+}
+
+template <int C>
+__device__ __forceinline__ void diffuse_px16(const RoundArgs& A, const int f, const uint8_t* Z, const uint8_t* s_ks,
+                                             const int* s_kmod, const uint32_t* s_sbits, const int wlo,
+                                             const uint8_t* s_seed, const int s_lo, const bool seeded,
+                                             const uint8_t* X, const int* kmod, const uint8_t* s_carry,
+                                             const bool fix, uint8_t* Out, const int a0, const int r0,
+                                             const int r1) {
+  constexpr int NW = 4 * C;  // words per chunk
+  constexpr int CB = 16 * C;  // bytes per chunk
+  const Layout& L = A.L;
+  const int lane = threadIdx.x & 31;
+  const int rowb = L.W * C;
+  const int cpr = L.W >> 4;  // chunks per row
+  const int nchunks = (r1 - r0) * cpr;
+  const int tstart = a0 * rowb;
+  const bool out_vec = ((reinterpret_cast<uintptr_t>(Out)) & 15) == 0;
+  const uint32_t* Zw = reinterpret_cast<const uint32_t*>(Z);
+  uint32_t run = 0;
+  for (int cb = 0; cb < nchunks; cb += 32) {
+    const int c = cb + lane;
+    uint32_t pre[NW];
+#pragma unroll
+    for (int i = 0; i < NW; i++) pre[i] = 0u;
+    int fse = CB;
+    uint32_t agg = 0;
+    int q0 = 0;
+    if (c < nchunks) {
+      const int rl = (c >= cpr ? 1 : 0) + (c >= 2 * cpr ? 1 : 0) + (c >= 3 * cpr ? 1 : 0);  // R <= 4
+      const int p0 = (c - rl * cpr) << 4;  // first output pixel of the chunk in its row
+      const int tt0 = r0 - a0 + rl;
+      q0 = (r0 + rl) * rowb + p0 * C;  // first byte of the chunk in the frame
+      int ps = p0 - s_kmod[tt0];       // first source pixel in the tile row (0 <= k < W)
+      if (ps < 0) ps += L.W;
+      const uint32_t* ksw = reinterpret_cast<const uint32_t*>(s_ks + (q0 - tstart));
+      const int zb = tt0 * L.ZS;
+      const bool contig = ps + 15 < L.W;  // the sixteen source pixels do not wrap at the row end
+      const int s0 = zb + ps + (ps >> 5), lo = ps & 31;
+      // slot of source pixel i (0..15) of the chunk
+      auto slot = [&](int i) -> int {
+        if (contig) return s0 + i + ((lo + i) >> 5);
+        int q = ps + i;
+        if (q >= L.W) q -= L.W;
+        return zb + q + (q >> 5);
+      };
+      // packed word i (0..NW-1) of the chunk's source bytes, from its pixel slots
+      auto yword = [&](int i) -> uint32_t {
+        if (C == 4) return Zw[slot(i)];
+        const int g = i / 3, r = i - 3 * g;  // word r of four 3-byte pixels 4g .. 4g + 3
+        const uint32_t wa = Zw[slot(4 * g + r)], wb = Zw[slot(4 * g + r + 1)];
+        return __byte_perm(wa, wb, r == 0 ? 0x4210u : (r == 1 ? 0x5421u : 0x6542u));
+      };
+      const int pix0 = (r0 + rl) * L.W + p0;  // a multiple of 16
+      const uint32_t sw = (s_sbits[(pix0 >> 5) - wlo] >> (pix0 & 16)) & 0xFFFFu;
+      const int nst = __popc(sw);
+      if (nst == 0 || (nst == 1 && seeded)) {
+        // d = b xor (y + b) per byte, its prefix XOR inside each word, then across words
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+          const uint32_t kk = ksw[i];
+          uint32_t d = kk ^ vadd4(yword(i), kk);
+          d ^= d << 8;
+          d ^= d << 16;
+          if (i > 0) d ^= bcast3(pre[i - 1]);
+          pre[i] = d;
+        }
+        if (nst == 1) {
+          // byte kb starts subframe s: from kb on the chain is seed ^ d_kb ^ ..,
+          // i.e. the chunk prefix xor (seed ^ prefix at kb - 1)
+          const int b = __ffs(sw) - 1;
+          const int kb = C * b;
+          const int wq = pix0 >> 5;
+          const int s = __ldg(&A.tb.srank[wq]) + __popc(s_sbits[wq - wlo] & ((1u << ((pix0 & 16) + b)) - 1u));
+          uint32_t pk = 0;
+          if (kb > 0) {
+            const int km = kb - 1;
+            uint32_t t = 0;
+#pragma unroll
+            for (int i = 0; i < NW; i++) t = sel_u32(i == (km >> 2), pre[i], t);
+            pk = (t >> (8 * (km & 3))) & 0xFFu;
+          }
+          const uint32_t V = ((uint32_t)s_seed[s - s_lo] ^ pk) * 0x01010101u;
+#pragma unroll
+          for (int i = 0; i < NW; i++) pre[i] ^= V & mask_from(kb, 4 * i);
+          fse = kb;
+          agg = 0x100u | (pre[NW - 1] >> 24);
+        } else {
+          agg = pre[NW - 1] >> 24;
+        }
+      } else {
+        // several starts in the chunk: byte by byte
+        uint32_t v = 0;
+        bool has = false;
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+          const uint32_t yw = yword(i), kw = ksw[i];
+          uint32_t o = 0;
+#pragma unroll
+          for (int bi = 0; bi < 4; bi++) {
+            const int kb = 4 * i + bi;
+            const uint8_t yb = (uint8_t)(yw >> (8 * bi));
+            const uint8_t bb = (uint8_t)(kw >> (8 * bi));
+            const uint8_t d = bb ^ (uint8_t)(yb + bb);
+            if (kb % C == 0 && ((sw >> (kb / C)) & 1u)) {
+              v = (uint32_t)(px16_seed<C>(A, pix0 + kb / C, s_sbits, wlo, s_seed, s_lo, seeded, X, kmod, s_carry,
+                                          fix) ^ d);
+              if (!has) {
+                has = true;
+                fse = kb;
+              }
+            } else {
+              v ^= d;
+            }
+            o |= (v & 0xFFu) << (8 * bi);
+          }
+          pre[i] = o;
+        }
+        agg = (has ? 0x100u : 0u) | (v & 0xFFu);
+      }
+    }
+    // warp-wide segmented scan of the chunks' values, then the running carry
+    const uint32_t incl = warp_incl_scan(agg);
+    uint32_t excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = 0;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t E = seg_combine(run, excl);
+    run = seg_combine(run, total);
+    if (c < nchunks) {
+      const uint32_t evx4 = (E & 0xFFu) * 0x01010101u;
+      if (fse == CB) {
+#pragma unroll
+        for (int i = 0; i < NW; i++) pre[i] ^= evx4;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NW; i++) pre[i] ^= evx4 & ~mask_from(fse, 4 * i);  // bytes before fse miss E
+      }
+      if (out_vec) {
+        uint4* o4 = reinterpret_cast<uint4*>(Out + q0);
+#pragma unroll
+        for (int i = 0; i < NW / 4; i++) o4[i] = make_uint4(pre[4 * i], pre[4 * i + 1], pre[4 * i + 2], pre[4 * i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+#pragma unroll
+          for (int bi = 0; bi < 4; bi++) Out[q0 + 4 * i + bi] = (uint8_t)(pre[i] >> (8 * bi));
+        }
+      }
+    }
+  }
+  if (lane == 0) A.agg_out[(long long)f * L.NS + (r0 >> L.lgR)] = (uint8_t)run;
 }
 
 template <int C>
@@ -1119,11 +1564,14 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   const int rowb = L.W * C;
   const int a0 = t * L.T;
   const int Te = min(L.T, L.H - a0);
+  const RoundSmem sm = round_smem(L);
   uint8_t* Z = smem;
-  uint8_t* s_carry = smem + (((size_t)L.T * rowb + 15) & ~(size_t)15);
-  int* s_kmod = reinterpret_cast<int*>(s_carry + ((L.NT + 15) & ~15));
-  uint32_t* s_warp = reinterpret_cast<uint32_t*>(s_kmod + 32);
-  uint8_t* s_seed = reinterpret_cast<uint8_t*>(s_warp + 32);
+  uint8_t* s_carry = smem + sm.carry;
+  uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + sm.tot);
+  int* s_kmod = reinterpret_cast<int*>(smem + sm.kmod);
+  uint32_t* s_sbits = reinterpret_cast<uint32_t*>(smem + sm.sbits);
+  uint8_t* s_seed = smem + sm.seed;
+  const uint8_t* s_ks = smem + sm.ks;
 
   const uint8_t* X = A.in + f * A.in_stride;
   uint8_t* Out = A.out + f * A.out_stride;
@@ -1133,9 +1581,22 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   // subframes s_lo .. s_hi - 1 start in this tile's pixels
   const int s_lo = starts_before(L, a0 * L.W), s_hi = starts_before(L, (a0 + Te) * L.W);
   const bool seeded = L.SC > 0;
+  // start-bit words wlo .. wlo + nsw - 1 cover the tile's pixels and one word more
+  const int wlo = (a0 * L.W) >> 5;
+  const int nsw = ((((a0 + Te) * L.W - 1) >> 5) + 1) - wlo + 1;
 
-  if (fix && threadIdx.x < 32) tile_carries(L, A.tb, A.agg_in + (long long)f * L.NT, s_carry);
+  // the tile's keystream (bytes [tstart, tstart + Te W C) of the round) into
+  // shared memory, in flight while the carries, seeds and gather run
+  const int tstart = a0 * rowb;
+  const bool ks_staged = sm.ks_staged && ((reinterpret_cast<uintptr_t>(KS + tstart) & 15) == 0);
+  if (ks_staged) {
+    const int n16 = (Te * rowb) >> 4;
+    for (int k = threadIdx.x; k < n16; k += blockDim.x) cp_async16(smem + sm.ks + 16 * k, KS + tstart + 16 * k);
+    cp_async_commit();
+  }
+  if (fix) sub_carries(L, A.tb, A.agg_in + (long long)f * L.NS, s_carry, s_tot);
   if (threadIdx.x < Te) s_kmod[threadIdx.x] = kmod[a0 + threadIdx.x];
+  for (int k = threadIdx.x; k < nsw; k += blockDim.x) s_sbits[k] = __ldg(&A.tb.sbits[wlo + k]);
   __syncthreads();
 
   // ---- seeds (Eq. 3 with the seed of reading R9) of the subframes starting
@@ -1150,129 +1611,113 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   }
 
   // ---- gather: Z[tt][o] = X[(a0 + tt - o) mod H][o] -------------------------
-  {
+  if constexpr (C == 3 || C == 4) {
+    if (L.T >= 4) gather_runs<C>(L, A.tb, X, Z, s_carry, fix, a0, Te, (reinterpret_cast<uintptr_t>(X) & 3) == 0);
+  }
+  if (C == 1 || L.T < 4) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int rpw = 32 / L.T;  // source rows per warp pass
     const int tt = lane & (L.T - 1);
     const int sub = lane / L.T;
     const int astep = nw * rpw;
-    if (L.W <= L.H && tt < Te) {
-      // one column per source row: 8 rows per iteration keep 8C loads in flight
-      for (int a = warp * rpw + sub; a < L.H; a += 8 * astep) {
-        uint8_t v[8][C];
-        int zo[8];
+    const int MC = (L.W + L.H - 1) / L.H;  // columns o, o + H, ... of a source row per tile row
+    const bool aligned = (reinterpret_cast<uintptr_t>(X) & 3) == 0;
+    constexpr int U = 8;  // source rows in flight per lane
+    if (tt < Te) {
+      for (int m = 0; m < MC; m++) {
+        const int mo = m * L.H;
+        for (int a = warp * rpw + sub; a < L.H; a += U * astep) {
+          uint32_t v[U];
+          int zo[U];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const int au = a + u * astep;
-          int o = a0 + tt - au;
-          if (o < 0) o += L.H;
-          zo[u] = (au < L.H && o < L.W) ? o : -1;
-          if (zo[u] >= 0) {
-            const int qx = (au * L.W + o) * C;
-#pragma unroll
-            for (int c = 0; c < C; c++) v[u][c] = X[qx + c];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          if (zo[u] < 0) continue;
-          const int au = a + u * astep;
-          uint8_t m = 0;
-          if (fix) {
-            const int ta = au / L.T;
-            if ((au * L.W + zo[u]) * C < __ldg(&A.tb.fixlim[ta])) m = s_carry[ta];  // starts are pixel-aligned
+          for (int u = 0; u < U; u++) {
+            const int au = a + u * astep;
+            int o = a0 + tt - au;
+            if (o < 0) o += L.H;
+            o += mo;
+            zo[u] = (au < L.H && o < L.W) ? o : -1;
+            v[u] = zo[u] >= 0 ? load_px_g<C>(X, (au * L.W + o) * C, aligned, L.N) : 0u;
           }
 #pragma unroll
-          for (int c = 0; c < C; c++) Z[tt * rowb + zo[u] * C + c] = v[u][c] ^ m;
-        }
-      }
-    } else if (tt < Te) {
-      for (int a = warp * rpw + sub; a < L.H; a += astep) {
-        int o = a0 + tt - a;
-        if (o < 0) o += L.H;
-        const int ta = a / L.T;
-        const int lim = fix ? __ldg(&A.tb.fixlim[ta]) : 0;
-        const uint8_t cy = fix ? s_carry[ta] : 0;
-        for (; o < L.W; o += L.H) {
-          const int qx = (a * L.W + o) * C;
-          const uint8_t m = (qx < lim) ? cy : 0;  // subframe starts are pixel-aligned
-#pragma unroll
-          for (int c = 0; c < C; c++) Z[tt * rowb + o * C + c] = X[qx + c] ^ m;
+          for (int u = 0; u < U; u++) {
+            if (zo[u] < 0) continue;
+            uint32_t x = v[u];
+            if (fix) {
+              const int au = a + u * astep;
+              const int sa = au >> L.lgR;
+              // subframe starts are pixel-aligned: the whole pixel is on one side of fixlim
+              if ((au * L.W + zo[u]) * C < __ldg(&A.tb.fixlim[sa])) x ^= rep_px<C>(s_carry[sa]);
+            }
+            store_z<C>(Z, zslot<C>(L, tt, zo[u]), x);
+          }
         }
       }
     }
   }
+  if (ks_staged) cp_async_wait_all();
   __syncthreads();
 
-  // ---- diffusion over the tile's bytes, 16-byte chunks per thread ----------
-  const int tstart = a0 * rowb;
-  const int tend = tstart + Te * rowb;
-  const int base16 = tstart & ~15;
-  const int nchunks = (tend - base16 + 15) >> 4;
+  // ---- diffusion of this warp's sub-tile, 16-byte chunks per lane ------------
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int WPT = L.T >> L.lgR;  // sub-tiles per tile
+  const int r0 = a0 + warp * L.R;
+  if (warp >= WPT || r0 >= a0 + Te) return;
+  const int r1 = min(r0 + L.R, a0 + Te);
+  if constexpr (C == 3 || C == 4) {
+    if (ks_staged && (L.W & 15) == 0) {
+      diffuse_px16<C>(A, f, Z, s_ks, s_kmod, s_sbits, wlo, s_seed, s_lo, seeded, X, kmod, s_carry, fix, Out, a0, r0,
+                      r1);
+      return;
+    }
+  }
+  const int ws = r0 * rowb, we = r1 * rowb;
+  const int base16 = ws & ~15;
+  const int nchunks = (we - base16 + 15) >> 4;
   const bool out_vec = ((reinterpret_cast<uintptr_t>(Out)) & 15) == 0;
   uint32_t run = 0;
-  // keystream of the thread's next full chunk, loaded one iteration ahead
+  // keystream of the lane's next full chunk (shared memory when staged, else
+  // global memory one iteration ahead)
   auto ks_full = [&](int cc) -> uint4 {
     const int s0 = base16 + 16 * cc;
-    if (cc < nchunks && s0 >= tstart && s0 + 16 <= tend) return *reinterpret_cast<const uint4*>(KS + s0);
+    if (cc < nchunks && s0 >= ws && s0 + 16 <= we)
+      return ks_staged ? *reinterpret_cast<const uint4*>(s_ks + (s0 - tstart))
+                       : *reinterpret_cast<const uint4*>(KS + s0);
     return make_uint4(0u, 0u, 0u, 0u);
   };
-  uint4 kv_next = ks_full(threadIdx.x);
-  for (int cb = 0; cb < nchunks; cb += blockDim.x) {
-    const int c = cb + threadIdx.x;
+  uint4 kv_next = ks_full(lane);
+  for (int cb = 0; cb < nchunks; cb += 32) {
+    const int c = cb + lane;
     const uint4 kv = kv_next;
-    kv_next = ks_full(c + blockDim.x);
+    kv_next = ks_full(c + 32);
     int cs = base16 + 16 * c, ce = cs + 16;
-    if (cs < tstart) cs = tstart;
-    if (ce > tend) ce = tend;
+    if (cs < ws) cs = ws;
+    if (ce > we) ce = we;
     const int len = (c < nchunks && ce > cs) ? ce - cs : 0;
     uint32_t pre[4] = {0u, 0u, 0u, 0u};
     int fse = 16;
     uint32_t agg = 0;
     bool fast = false;
     if (len == 16 && (cs & 15) == 0) {
-      // fast path: the chunk lies in one row, its rotated source bytes do not
-      // wrap (or the row is whole words, so they wrap word-wise), and at most
-      // one subframe starts inside it (its seed is in shared memory)
-      const int off = cs - tstart;
-      const int tt0 = off / rowb;
-      const int e0 = off - tt0 * rowb;
+      // fast path: the chunk lies in one row (for C = 1: its rotated source
+      // bytes do not wrap, or the row is whole words) and at most one subframe
+      // starts inside it (its seed is in shared memory)
+      const int rloc = cs - ws;  // < R rows (R <= 4)
+      const int rl = (rloc >= rowb ? 1 : 0) + (rloc >= 2 * rowb ? 1 : 0) + (rloc >= 3 * rowb ? 1 : 0);
+      const int tt0 = r0 - a0 + rl;
+      const int e0 = rloc - rl * rowb;
       int zs = e0 - s_kmod[tt0] * C;
       if (zs < 0) zs += rowb;
-      const bool nowrap = zs + 16 <= rowb;
-      if (e0 + 16 <= rowb && (nowrap || (rowb & 3) == 0)) {
+      if (e0 + 16 <= rowb && (C != 1 || zs + 16 <= rowb || (rowb & 3) == 0)) {
         const int pfirst = (cs + C - 1) / C, plast = (cs + 15) / C;
         const int wq = pfirst >> 5;
-        const uint64_t win = (uint64_t)__ldg(&A.tb.sbits[wq]) | ((uint64_t)__ldg(&A.tb.sbits[wq + 1]) << 32);
-        const int rk = __ldg(&A.tb.srank[wq]);
+        const uint64_t win = (uint64_t)s_sbits[wq - wlo] | ((uint64_t)s_sbits[wq - wlo + 1] << 32);
         const int lb = pfirst - (wq << 5), hb = plast - (wq << 5);
         const uint64_t sw = win & ((2ull << hb) - 1ull) & ~((1ull << lb) - 1ull);
         const int nst = __popcll(sw);
         if (nst == 0 || (nst == 1 && seeded)) {
           fast = true;
-          uint32_t z0, z1, z2, z3, z4;
-          uint32_t sh;
-          if (nowrap) {
-            const int za = tt0 * rowb + zs;
-            const uint32_t* zw = reinterpret_cast<const uint32_t*>(Z + (za & ~3));
-            sh = (uint32_t)(za & 3) * 8u;
-            z0 = zw[0];
-            z1 = zw[1];
-            z2 = zw[2];
-            z3 = zw[3];
-            z4 = zw[4];
-          } else {  // whole-word row: the five words wrap around its end
-            const uint32_t* zr = reinterpret_cast<const uint32_t*>(Z + tt0 * rowb);
-            const int rw = rowb >> 2, wi = zs >> 2;
-            sh = (uint32_t)(zs & 3) * 8u;
-            z0 = zr[wi];
-            z1 = zr[wi + 1 < rw ? wi + 1 : wi + 1 - rw];
-            z2 = zr[wi + 2 < rw ? wi + 2 : wi + 2 - rw];
-            z3 = zr[wi + 3 < rw ? wi + 3 : wi + 3 - rw];
-            z4 = zr[wi + 4 < rw ? wi + 4 : wi + 4 - rw];
-          }
-          const uint32_t y0 = __funnelshift_r(z0, z1, sh), y1 = __funnelshift_r(z1, z2, sh);
-          const uint32_t y2 = __funnelshift_r(z2, z3, sh), y3 = __funnelshift_r(z3, z4, sh);
+          uint32_t y0, y1, y2, y3;
+          z_row16<C>(L, Z, tt0, zs, y0, y1, y2, y3);
           uint32_t d0 = kv.x ^ vadd4(y0, kv.x), d1 = kv.y ^ vadd4(y1, kv.y);
           uint32_t d2 = kv.z ^ vadd4(y2, kv.z), d3 = kv.w ^ vadd4(y3, kv.w);
           d0 ^= d0 << 8;
@@ -1292,7 +1737,7 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
             // k still miss the incoming prefix
             const int b = __ffsll((long long)sw) - 1;
             const int k = C * ((wq << 5) + b) - cs;
-            const int s = rk + __popcll(win & ((1ull << b) - 1ull));
+            const int s = __ldg(&A.tb.srank[wq]) + __popcll(win & ((1ull << b) - 1ull));
             uint32_t pk = 0;
             if (k > 0) {
               const int km = k - 1;
@@ -1318,15 +1763,8 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
     }
     if (len > 0 && !fast) {
       uint8_t kb[16];
-      if (len == 16 && (cs & 15) == 0) {
-        const uint4 v = *reinterpret_cast<const uint4*>(KS + cs);
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < 16; k++) kb[k] = (uint8_t)(wv[k >> 2] >> (8 * (k & 3)));
-      } else {
-#pragma unroll
-        for (int k = 0; k < 16; k++) kb[k] = k < len ? KS[cs + k] : 0;
-      }
+      for (int k = 0; k < 16; k++) kb[k] = k < len ? (ks_staged ? s_ks[cs - tstart + k] : KS[cs + k]) : 0;
       const int off = cs - tstart;
       int tt = off / rowb;
       int e = off - tt * rowb;
@@ -1336,13 +1774,13 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
       if (zo < 0) zo += L.W;
       const int pix0 = cs / C;
       const int w0 = pix0 >> 5;
-      const uint64_t win = (uint64_t)__ldg(&A.tb.sbits[w0]) | ((uint64_t)__ldg(&A.tb.sbits[w0 + 1]) << 32);
+      const uint64_t win = (uint64_t)s_sbits[w0 - wlo] | ((uint64_t)s_sbits[w0 - wlo + 1] << 32);
       uint32_t v = 0;
       bool has = false;
 #pragma unroll
       for (int k = 0; k < 16; k++) {
         if (k < len) {
-          const uint8_t y = Z[tt * rowb + zo * C + ch];
+          const uint8_t y = z_byte<C>(L, Z, tt, zo, ch);
           const uint8_t b = kb[k];
           const uint8_t d = b ^ (uint8_t)(y + b);
           bool st = false;
@@ -1353,7 +1791,7 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
           }
           if (st) {
             const int wq = pix >> 5;
-            const int s = __ldg(&A.tb.srank[wq]) + __popc(__ldg(&A.tb.sbits[wq]) & ((1u << (pix & 31)) - 1u));
+            const int s = __ldg(&A.tb.srank[wq]) + __popc(s_sbits[wq - wlo] & ((1u << (pix & 31)) - 1u));
             uint8_t sd;
             if (seeded) {
               sd = s_seed[s - s_lo];
@@ -1387,13 +1825,15 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
       }
       agg = (has ? 0x100u : 0u) | (v & 0xFFu);
     }
-    uint32_t total;
-    const uint32_t excl = block_excl_scan(agg, &total, s_warp);
+    // warp-wide segmented scan of the chunks' values, then the running carry
+    const uint32_t incl = warp_incl_scan(agg);
+    uint32_t excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = 0;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t E = seg_combine(run, excl);
     run = seg_combine(run, total);
     if (len > 0) {
-      const uint32_t ev = E & 0xFFu;
-      const uint32_t evx4 = ev * 0x01010101u;
+      const uint32_t evx4 = (E & 0xFFu) * 0x01010101u;
 #pragma unroll
       for (int w4 = 0; w4 < 4; w4++) pre[w4] ^= evx4 & ~mask_from(fse, 4 * w4);  // bytes before fse miss E
       if (len == 16 && (cs & 15) == 0 && out_vec) {
@@ -1405,20 +1845,13 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
       }
     }
   }
-  if (threadIdx.x == 0) A.agg_out[(long long)f * L.NT + t] = (uint8_t)run;
+  if (lane == 0) A.agg_out[(long long)f * L.NS + (r0 >> L.lgR)] = (uint8_t)run;
 }
 
 template <int C>
-__global__ void __launch_bounds__(kRoundThreads) k_enc_round(RoundArgs A) {
+__global__ void __launch_bounds__(kRoundThreads, 4) k_enc_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   enc_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
-}
-
-// [Z tile, 16-aligned][tile carries, NT bytes rounded to 16][row shifts, 32 ints][scan, 32 words]
-// [subframe seeds, SC bytes]
-size_t round_smem_bytes(const Layout& L) {
-  return (((size_t)L.T * L.W * L.C + 15) & ~(size_t)15) + ((L.NT + 15) & ~15) + 32 * sizeof(int) +
-         32 * sizeof(uint32_t) + (size_t)L.SC;
 }
 
 template <int C>
@@ -1444,54 +1877,65 @@ cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long
   return cudaErrorInvalidValue;
 }
 
-// After the last round: apply each tile's missing prefix in place.
+// Shared memory of the fix-up: the carries (NS bytes, rounded to 16) and the
+// carry scan's share totals (32 words).
+__host__ __device__ inline int fixup_smem_bytes(const Layout& L) { return ((L.NS + 15) & ~15) + 32 * 4; }
+
+// After the last round: apply each sub-tile's missing prefix in place (one warp
+// per sub-tile of tile t).
 __device__ __forceinline__ void enc_fixup_tile(const Layout& L, const Tables& tb, uint8_t* out, long long out_stride,
-                                               const uint8_t* agg, const int f, const int t, uint8_t* s_carry) {
-  if (threadIdx.x < 32) tile_carries(L, tb, agg + (long long)f * L.NT, s_carry);
-  __syncthreads();
-  if (t == 0) return;
+                                               const uint8_t* agg, const int f, const int t, uint8_t* smem) {
+  uint8_t* s_carry = smem;
+  sub_carries(L, tb, agg + (long long)f * L.NS, s_carry, reinterpret_cast<uint32_t*>(smem + ((L.NS + 15) & ~15)));
   const int rowb = L.W * L.C;
-  const int tstart = t * L.T * rowb;
-  const int lim = __ldg(&tb.fixlim[t]);
-  if (lim <= tstart) return;
   uint8_t* O = out + f * out_stride;
-  const uint8_t cy = s_carry[t];
-  const uint32_t c4 = cy * 0x01010101u;
-  // head bytes up to 16-byte alignment, aligned body, tail bytes
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(O + tstart);
-  int head = (int)((16 - (addr & 15)) & 15);
-  if (head > lim - tstart) head = lim - tstart;
-  for (int k = threadIdx.x; k < head; k += blockDim.x) O[tstart + k] ^= cy;
-  const int body0 = tstart + head;
-  const int nvec = (lim - body0) >> 4;
-  uint4* V = reinterpret_cast<uint4*>(O + body0);
-  for (int k = threadIdx.x; k < nvec; k += blockDim.x) {
-    uint4 v = V[k];
-    v.x ^= c4; v.y ^= c4; v.z ^= c4; v.w ^= c4;
-    V[k] = v;
+  const int lane = threadIdx.x & 31;
+  const int WPT = L.T >> L.lgR;
+  for (int w = threadIdx.x >> 5; w < WPT; w += blockDim.x >> 5) {
+    const int s = t * WPT + w;
+    if (s == 0 || s >= L.NS) continue;
+    const int sstart = s * L.R * rowb;
+    const int lim = __ldg(&tb.fixlim[s]);
+    if (lim <= sstart) continue;
+    const uint8_t cy = s_carry[s];
+    const uint32_t c4 = cy * 0x01010101u;
+    // head bytes up to 16-byte alignment, aligned body, tail bytes
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(O + sstart);
+    int head = (int)((16 - (addr & 15)) & 15);
+    if (head > lim - sstart) head = lim - sstart;
+    if (lane < head) O[sstart + lane] ^= cy;
+    const int body0 = sstart + head;
+    const int nvec = (lim - body0) >> 4;
+    uint4* V = reinterpret_cast<uint4*>(O + body0);
+    for (int k = lane; k < nvec; k += 32) {
+      uint4 v = V[k];
+      v.x ^= c4;
+      v.y ^= c4;
+      v.z ^= c4;
+      v.w ^= c4;
+      V[k] = v;
+    }
+    for (int k = body0 + nvec * 16 + lane; k < lim; k += 32) O[k] ^= cy;
   }
-  for (int k = body0 + nvec * 16 + threadIdx.x; k < lim; k += blockDim.x) O[k] ^= cy;
 }
 
 __global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb, uint8_t* out, long long out_stride,
                                                              const uint8_t* agg) {
-  __shared__ uint8_t s_carry[kMaxTiles];
-  enc_fixup_tile(L, tb, out, out_stride, agg, blockIdx.y, blockIdx.x, s_carry);
+  extern __shared__ __align__(16) uint8_t smem[];
+  enc_fixup_tile(L, tb, out, out_stride, agg, blockIdx.y, blockIdx.x, smem);
 }
 
 cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
                              int nframes, cudaStream_t st) {
   if (nframes <= 0) return cudaSuccess;
+  const int smem = fixup_smem_bytes(L);
+  cudaError_t e = allow_smem(k_enc_fixup, smem);
+  if (e != cudaSuccess) return e;
   dim3 grid(L.NT, nframes);
-  k_enc_fixup<<<grid, kRoundThreads, 0, st>>>(L, tb, out, out_stride, agg);
+  k_enc_fixup<<<grid, kRoundThreads, smem, st>>>(L, tb, out, out_stride, agg);
   return cudaGetLastError();
 }
 
-// Decryption round (Eq. 4 then Eq. 2), one CTA per (row-band tile of the
-// OUTPUT frame X, frame).  X[a][o] = Y[(a + o) mod H][(o + k(alpha)) mod W], and
-// Y is elementwise in the ciphertext C of the round: y_q = (b xor c_q xor c_{q-1}) - b,
-// with c_{q-1} replaced at a subframe start by the seed y of the last byte of
-// the next subframe (itself a non-first byte, so computable the same way).
 // Byte-wise a - b mod 256 in each of the eight bytes of a word.
 __device__ __forceinline__ uint64_t vsub8(uint64_t a, uint64_t b) {
   constexpr uint64_t Hb = 0x8080808080808080ull;
@@ -1503,12 +1947,13 @@ __device__ __forceinline__ uint64_t vsub8(uint64_t a, uint64_t b) {
 // beta = (o + k(alpha)) mod W, where y_q = ((b ^ c_q ^ c_{q-1}) - b) mod 256 and,
 // at a subframe start, c_{q-1} is replaced by the seed: the decrypted byte at
 // the end of the next subframe (reading R10; never itself a start, S_i >= 2).
-// Band row tt takes one pixel from every ciphertext row, so the lanes of a
-// warp read runs of consecutive pixels of a row.  Four rows are handled per
-// iteration in phases (row shifts, then ciphertext and
-// keystream words, then the result) so that a lane keeps several rows of
-// loads in flight instead of one dependent round trip per row.
-template <int C>
+// Band row tt takes one pixel from every ciphertext row (o = alpha - a0 - tt
+// mod H, + m H), so the lanes of a warp read runs of consecutive pixels of a
+// row.  Eight rows are handled per iteration in phases (row shifts, then
+// ciphertext, keystream and start-bit words, then the result) so that a lane
+// keeps several rows of loads in flight; each decrypted pixel is one 32-bit
+// shared-memory slot (C = 3, 4), packed into bytes when the band is written.
+template <int C, int U = 4>
 __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
   const Layout& L = A.L;
   const int rowb = L.W * C;
@@ -1525,7 +1970,9 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   const int tt = lane & (L.T - 1);
   const int sub = lane / L.T;
   const int astep = nw * rpw;
-  auto decrypt_pixel = [&](int pix, int o, uint32_t sw) {
+  const uint32_t pmask = C == 4 ? 0xFFFFFFFFu : ((1u << (8 * C)) - 1u);
+  // the decrypted pixel at pixel index pix of the round's input, byte by byte
+  auto decrypt_pixel = [&](int pix, uint32_t sw) -> uint32_t {
     const int qb = pix * C;
     uint8_t prev;
     if ((sw >> (pix & 31)) & 1u) {  // subframe start: the seed
@@ -1537,107 +1984,132 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
     } else {
       prev = Cin[qb - 1];
     }
-    uint8_t* dst = Xt + tt * rowb + o * C;
+    uint32_t v = 0;
 #pragma unroll
     for (int c = 0; c < C; c++) {
       const uint8_t cq = Cin[qb + c];
       const uint8_t b = KS[qb + c];
-      dst[c] = (uint8_t)((uint8_t)(b ^ cq ^ prev) - b);
+      v |= (uint32_t)(uint8_t)((uint8_t)(b ^ cq ^ prev) - b) << (8 * c);
       prev = cq;
     }
+    return v;
   };
   // ciphertext bytes q-1 .. q+C-1 and keystream bytes q .. q+C-1 of a pixel as
   // two aligned words each (frame bases 4-byte aligned, away from the frame
   // ends); bytes one by one otherwise
   const bool words = ((reinterpret_cast<uintptr_t>(Cin) | reinterpret_cast<uintptr_t>(KS)) & 3) == 0;
-  if (L.W <= L.H) {
-    // one pixel per ciphertext row and band row, U rows per iteration
-    constexpr int U = 4;
-    for (int alpha = warp * rpw + sub; alpha < L.H; alpha += U * astep) {
-      int pix[U], ov[U];
-      uint32_t c0[U], c1[U], k0[U], k1[U], sw[U];
+  const int MC = (L.W + L.H - 1) / L.H;
+  if (tt < Te) {
+    for (int m = 0; m < MC; m++) {
+      const int mo = m * L.H;
+      for (int alpha = warp * rpw + sub; alpha < L.H; alpha += U * astep) {
+        int pix[U], ov[U];
+        uint32_t c0[U], c1[U], k0[U], k1[U], sw[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int al = alpha + u * astep;
-        int o = al - (a0 + tt);
-        if (o < 0) o += L.H;
-        ov[u] = (tt < Te && al < L.H && o < L.W) ? o : -1;
-        int beta = 0;
-        if (ov[u] >= 0) {
-          beta = o + __ldg(&kmod[al]);
-          if (beta >= L.W) beta -= L.W;
+        for (int u = 0; u < U; u++) {
+          const int al = alpha + u * astep;
+          int o = al - (a0 + tt);
+          if (o < 0) o += L.H;
+          o += mo;
+          ov[u] = (al < L.H && o < L.W) ? o : -1;
+          int beta = 0;
+          if (ov[u] >= 0) {
+            beta = o + __ldg(&kmod[al]);
+            if (beta >= L.W) beta -= L.W;
+          }
+          pix[u] = al * L.W + beta;
         }
-        pix[u] = al * L.W + beta;
-      }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int qb = pix[u] * C;
-        sw[u] = ov[u] >= 0 ? __ldg(&A.tb.sbits[pix[u] >> 5]) : 0u;  // start bits, with the data
-        if (ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
-          const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - 1) & ~3));
-          const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
-          c0[u] = __ldg(cw);
-          c1[u] = __ldg(cw + 1);
-          k0[u] = __ldg(kw);
-          k1[u] = __ldg(kw + 1);
-        } else {
-          c0[u] = c1[u] = k0[u] = k1[u] = 0;
+        for (int u = 0; u < U; u++) {
+          const int qb = pix[u] * C;
+          sw[u] = ov[u] >= 0 ? __ldg(&A.tb.sbits[pix[u] >> 5]) : 0u;  // start bits, with the data
+          if (ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
+            const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - 1) & ~3));
+            const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
+            c0[u] = __ldg(cw);
+            c1[u] = __ldg(cw + 1);
+            k0[u] = __ldg(kw);
+            k1[u] = __ldg(kw + 1);
+          } else {
+            c0[u] = c1[u] = k0[u] = k1[u] = 0;
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (ov[u] < 0) continue;
-        const int p = pix[u], qb = p * C;
-        if (((sw[u] >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
-          decrypt_pixel(p, ov[u], sw[u]);
-          continue;
+        for (int u = 0; u < U; u++) {
+          if (ov[u] < 0) continue;
+          const int p = pix[u], qb = p * C;
+          uint32_t y;
+          if (((sw[u] >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
+            y = decrypt_pixel(p, sw[u]);
+          } else {
+            const uint64_t c = ((uint64_t)c1[u] << 32 | c0[u]) >> (8 * ((qb - 1) & 3));
+            const uint64_t b = ((uint64_t)k1[u] << 32 | k0[u]) >> (8 * (qb & 3));
+            y = (uint32_t)vsub8(b ^ (c >> 8) ^ c, b) & pmask;
+          }
+          store_z<C>(Xt, zslot<C>(L, tt, ov[u]), y);
         }
-        const uint64_t c = ((uint64_t)c1[u] << 32 | c0[u]) >> (8 * ((qb - 1) & 3));
-        const uint64_t b = ((uint64_t)k1[u] << 32 | k0[u]) >> (8 * (qb & 3));
-        const uint64_t y = vsub8(b ^ (c >> 8) ^ c, b);
-        uint8_t* dst = Xt + tt * rowb + ov[u] * C;
-#pragma unroll
-        for (int k = 0; k < C; k++) dst[k] = (uint8_t)(y >> (8 * k));
-      }
-    }
-  } else {
-    for (int alpha = warp * rpw + sub; alpha < L.H; alpha += astep) {
-      if (tt >= Te) continue;
-      int o = alpha - (a0 + tt);
-      if (o < 0) o += L.H;
-      const int km = __ldg(&kmod[alpha]);
-      for (; o < L.W; o += L.H) {
-        int beta = o + km;
-        if (beta >= L.W) beta -= L.W;
-        const int pix = alpha * L.W + beta;
-        decrypt_pixel(pix, o, __ldg(&A.tb.sbits[pix >> 5]));
       }
     }
   }
   __syncthreads();
-  // write the tile's rows (contiguous bytes)
+  // write the band's rows (contiguous bytes of the output frame)
   const int tstart = a0 * rowb;
   const int nb = Te * rowb;
   uint8_t* dstg = Out + tstart;
-  if ((reinterpret_cast<uintptr_t>(dstg) & 15) == 0) {
-    const int nvec = nb >> 4;
-    for (int k = threadIdx.x; k < nvec; k += blockDim.x)
-      reinterpret_cast<uint4*>(dstg)[k] = reinterpret_cast<const uint4*>(Xt)[k];
-    for (int k = nvec * 16 + threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
-  } else {
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
+  if (C == 1) {
+    if ((reinterpret_cast<uintptr_t>(dstg) & 15) == 0) {
+      const int nvec = nb >> 4;
+      for (int k = threadIdx.x; k < nvec; k += blockDim.x)
+        reinterpret_cast<uint4*>(dstg)[k] = reinterpret_cast<const uint4*>(Xt)[k];
+      for (int k = nvec * 16 + threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
+    } else {
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) dstg[k] = Xt[k];
+    }
+    return;
+  }
+  // 16-byte chunks at 16-byte frame offsets: whole chunks inside one row are
+  // packed from six (C = 3) or four (C = 4) pixel slots, the others byte by byte
+  const bool out_vec = (reinterpret_cast<uintptr_t>(Out) & 15) == 0;
+  const int base16 = tstart & ~15;
+  const int tend = tstart + nb;
+  const int nchunks = (tend - base16 + 15) >> 4;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    int cs = base16 + 16 * c, ce = cs + 16;
+    if (cs < tstart) cs = tstart;
+    if (ce > tend) ce = tend;
+    const int off = cs - tstart;
+    const int r = off / rowb;
+    const int e0 = off - r * rowb;
+    if (ce - cs == 16 && (cs & 15) == 0 && e0 + 16 <= rowb) {
+      uint32_t y0, y1, y2, y3;
+      z_row16<C>(L, Xt, r, e0, y0, y1, y2, y3);
+      if (out_vec) {
+        *reinterpret_cast<uint4*>(Out + cs) = make_uint4(y0, y1, y2, y3);
+      } else {
+        const uint32_t yw[4] = {y0, y1, y2, y3};
+#pragma unroll
+        for (int k = 0; k < 16; k++) Out[cs + k] = (uint8_t)(yw[k >> 2] >> (8 * (k & 3)));
+      }
+    } else {
+      for (int q = cs; q < ce; q++) {
+        const int oq = q - tstart;
+        const int rr = oq / rowb, e = oq - rr * rowb;
+        const int px = e / C;
+        Out[q] = z_byte<C>(L, Xt, rr, px, e - px * C);
+      }
+    }
   }
 }
 
 template <int C>
-__global__ void __launch_bounds__(kRoundThreads) k_dec_round(RoundArgs A) {
+__global__ void __launch_bounds__(kRoundThreads, 4) k_dec_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   dec_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
 }
 
 template <int C>
 static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
-  const size_t smem = round_smem_bytes(A.L);
+  const size_t smem = dec_smem_bytes(A.L);
   cudaError_t e = allow_smem(k_dec_round<C>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(A.L.NT, nframes);
@@ -1866,6 +2338,8 @@ __global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHd
     ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
   else if (d.kind == 2)
     ks_pair_chain<2, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+  else if (d.sine_b64)
+    ks_pair_chain<1, false, true>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
   else
     ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
 }
@@ -1888,8 +2362,8 @@ __device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step
   A.ks = d.ks + (long long)slot * r * L.Npad + (long long)jr * L.Npad;
   A.ks_stride = 0;
   A.kmod = d.kmod + (long long)slot * L.H;
-  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] + (long long)f * L.NT : nullptr;
-  A.agg_out = d.dir == 0 ? d.agg[step & 1] + (long long)f * L.NT : nullptr;
+  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] + (long long)f * L.NS : nullptr;
+  A.agg_out = d.dir == 0 ? d.agg[step & 1] + (long long)f * L.NS : nullptr;
   return A;
 }
 

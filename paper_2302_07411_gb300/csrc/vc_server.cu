@@ -6,7 +6,8 @@
 // each tick it takes, for every stream, the frames that have arrived by its
 // frame clock and whose keystream run-ahead is ready, and submits them as one
 // ragged batch (vc_batch_submit: one launch per phase over all streams), or,
-// for comparison, as one encrypt_frames / decrypt_frames call per frame.
+// for comparison, as one encrypt_frames / decrypt_frames call per frame, each
+// stream on its own CUDA stream so that different streams' calls overlap.
 // Completion is timed with CUDA events against an event recorded at creation,
 // so per-frame latency = device completion time - arrival time.
 #include <cuda_runtime.h>
@@ -34,6 +35,10 @@ struct SrvStream {
   double fps = 24.0, t_arr = 0.0;
   int64_t total = 0, next = 0, done = 0;
   bool active = false;
+  // one-call-per-frame mode: the stream's own CUDA stream, so that the calls
+  // of different streams run concurrently, and the event that joins it back
+  cudaStream_t cs = nullptr;
+  cudaEvent_t join = nullptr;
 };
 
 struct SrvFrame {
@@ -44,8 +49,12 @@ struct SrvFrame {
 
 struct SrvTick {
   cudaEvent_t ev0 = nullptr;  // before the submission
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;   // after all of the tick's work
   std::vector<SrvFrame> frames;
+  // one-call-per-frame mode: the completion event of each stream's calls and
+  // the end of its frames in `frames` (each frame is timed by its own stream)
+  std::vector<cudaEvent_t> job_ev;
+  std::vector<size_t> job_end;
   size_t taken = 0;  // frames already returned by a partial drain
 };
 
@@ -137,6 +146,11 @@ int vc_server_add(vc_server* s, vc_ctx* ctx, int32_t direction, int64_t frame_by
     vc_ctx* c = ctx;
     int rc = vc_batch_prefetch(s->b, &c, 1);  // keystream of its first frames now
     if (rc) return rc;
+  } else if (cudaStreamCreateWithFlags(&t.cs, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (t.cs) cudaStreamDestroy(t.cs);
+    return VC_ERR_CUDA;
   }
   s->streams.push_back(t);
   *id = (int32_t)(s->streams.size() - 1);
@@ -207,15 +221,31 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
     int rc = vc_batch_submit(s->b, s->jobs.data(), (int32_t)s->jobs.size(), s->st);
     if (rc) return rc;
   } else {
+    // each stream's calls on its own CUDA stream (after the tick's start),
+    // timed by an event there, then joined back into the server's stream
+    size_t fend = 0;
     for (size_t q = 0; q < s->jobs.size(); q++) {
       const vc_job& j = s->jobs[q];
-      const long long N = s->streams[s->job_stream[q]].N;
+      SrvStream& t = s->streams[s->job_stream[q]];
+      if (cudaStreamWaitEvent(t.cs, tick.ev0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return VC_ERR_CUDA;
+      }
       for (int k = 0; k < j.nframes; k++) {
-        const uint8_t* in = j.d_in + (size_t)k * N;
-        uint8_t* out = j.d_out + (size_t)k * N;
-        int rc = j.direction == 0 ? encrypt_frames(j.ctx, in, out, 1, s->st) : decrypt_frames(j.ctx, in, out, 1, s->st);
+        const uint8_t* in = j.d_in + (size_t)k * t.N;
+        uint8_t* out = j.d_out + (size_t)k * t.N;
+        int rc = j.direction == 0 ? encrypt_frames(j.ctx, in, out, 1, t.cs) : decrypt_frames(j.ctx, in, out, 1, t.cs);
         if (rc) return rc;
       }
+      cudaEvent_t e = srv_event(s);
+      if (!e || cudaEventRecord(e, t.cs) != cudaSuccess || cudaEventRecord(t.join, t.cs) != cudaSuccess ||
+          cudaStreamWaitEvent(s->st, t.join, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return VC_ERR_CUDA;
+      }
+      fend += (size_t)j.nframes;
+      tick.job_ev.push_back(e);
+      tick.job_end.push_back(fend);
     }
   }
   s->host_ms[2] += ms_since(t_start);
@@ -247,18 +277,27 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
       s->gpu_ticks++;
     }
     const double done_s = ms / 1e3;
+    size_t q = 0;  // the job (stream) of frame tk.taken in one-call-per-frame mode
     while (tk.taken < tk.frames.size() && n < cap) {
+      double fdone = done_s;
+      if (!tk.job_ev.empty()) {
+        while (q + 1 < tk.job_end.size() && tk.job_end[q] <= tk.taken) q++;
+        float jm = 0.f;
+        if (cudaEventElapsedTime(&jm, s->t0, tk.job_ev[q]) != cudaSuccess) return VC_ERR_CUDA;
+        fdone = jm / 1e3;
+      }
       const SrvFrame& f = tk.frames[tk.taken++];
       ids[n] = f.id;
       frames[n] = f.frame;
       arrival_s[n] = f.arrival;
-      latency_ms[n] = (done_s - f.arrival) * 1e3;
+      latency_ms[n] = (fdone - f.arrival) * 1e3;
       s->streams[f.id].done++;
       n++;
     }
     if (tk.taken == tk.frames.size()) {
       s->ev_pool.push_back(tk.ev);
       if (tk.ev0) s->ev_pool.push_back(tk.ev0);
+      for (cudaEvent_t e : tk.job_ev) s->ev_pool.push_back(e);
       s->inflight.pop_front();
     }
   }
@@ -285,6 +324,15 @@ int vc_server_remove(vc_server* s, int32_t id) {
   }
   t.active = false;
   t.ctx = nullptr;
+  if (t.cs) {
+    cudaStreamSynchronize(t.cs);
+    cudaStreamDestroy(t.cs);
+    t.cs = nullptr;
+  }
+  if (t.join) {
+    cudaEventDestroy(t.join);
+    t.join = nullptr;
+  }
   return VC_OK;
 }
 
@@ -311,6 +359,14 @@ void vc_server_destroy(vc_server* s) {
   for (SrvTick& tk : s->inflight) {
     if (tk.ev) cudaEventDestroy(tk.ev);
     if (tk.ev0) cudaEventDestroy(tk.ev0);
+    for (cudaEvent_t e : tk.job_ev) cudaEventDestroy(e);
+  }
+  for (SrvStream& t : s->streams) {
+    if (t.cs) {
+      cudaStreamSynchronize(t.cs);
+      cudaStreamDestroy(t.cs);
+    }
+    if (t.join) cudaEventDestroy(t.join);
   }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->t0) cudaEventDestroy(s->t0);

@@ -67,6 +67,35 @@ def test_batch_equals_solo_runs(B, graph, runahead):
     batcher.close()
 
 
+@pytest.mark.parametrize("sine", [0, 1, -1])
+def test_batch_sine_forms_equal_solo_runs(B, sine):
+    """VC_BOPT_SINE: the 2DLASM chains of a batch's keystream with the
+    all-binary64 sine reduction (1), the integer-assisted one (0) or the
+    per-batch choice (-1) give the bytes of the streams run alone."""
+    shapes = [(1, 40, 40, 3, 4, 0), (1, 72, 64, 3, 18, 1), (0, 48, 64, 3, 12, 0), (1, 30, 50, 4, 7, 0)]
+    batcher = B.Batcher(graph=True)
+    B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SINE, sine)
+    mixed = [B.Cipher(k, synth.key_for_seed(k, 800 + i), H, W, C, n) for i, (k, H, W, C, n, d) in enumerate(shapes)]
+    solo = [B.Cipher(k, synth.key_for_seed(k, 800 + i), H, W, C, n) for i, (k, H, W, C, n, d) in enumerate(shapes)]
+    for tick in range(2):
+        jobs, outs, refs = [], [], []
+        for i, (k, H, W, C, n, d) in enumerate(shapes):
+            x = torch.from_numpy(synth.uniform_frames(2, H, W, C, seed=810 + 10 * tick + i)).cuda()
+            y = torch.empty_like(x)
+            jobs.append((mixed[i], d, x, y, 2))
+            outs.append(y)
+            refs.append(solo[i].encrypt(x) if d == 0 else solo[i].decrypt(x))
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for i in range(len(shapes)):
+            assert torch.equal(outs[i], refs[i]), f"tick {tick}, stream {i}"
+    with pytest.raises(B.VcError):
+        B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SINE, 2)
+    for c in mixed + solo:
+        c.close()
+    batcher.close()
+
+
 def test_batch_round_trip_and_mixing_with_single_calls(B, orc):
     """Encrypt in a batch, continue the same contexts with single-stream calls,
     then decrypt everything in a batch; the oracle agrees on the ciphertext."""
