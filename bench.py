@@ -237,19 +237,25 @@ def load_peaks() -> dict:
 
 
 def serving_capacity() -> dict:
-    """Concurrent 24 FPS 768x768x3 streams (half encrypt / half decrypt,
-    alternating PLCM / 2DLASM, n = 192; and PLCM only) the serving loop sustains with
-    steady-state p99 per-frame latency under 41.7 ms: continuous batching (one
-    graph replay per 4 ms tick, keystream run-ahead) vs one launch sequence
-    per frame."""
+    """Serving (continuous batching, one graph replay per 4 ms tick, keystream
+    run-ahead) against one call per frame (each stream on its own CUDA
+    stream), two workloads:
+
+    * capacity: the largest number of concurrent 24 FPS 768x768x3 streams
+      (half encrypt / half decrypt, alternating PLCM / 2DLASM, n = 192; and
+      PLCM only) whose steady-state p99 per-frame latency stays under 41.7 ms;
+    * mixed: 256 streams arriving as a Poisson process (64/s), 480^2 ...
+      3840x2160, 24/30/60 FPS, half 2DLASM, half decrypt, admitted by HBM
+      budget and compute-aware admission (calibrated device rates), with the
+      admitted streams' steady p99 and first-frame p99."""
     from paper_2302_07411_gb300 import serve
 
     out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
-    b = serve.capacity("batch", 768, 768, counts=(16, 32, 64, 96, 128, 160, 192, 224, 256, 288, 320), seconds=3.0)
-    p = serve.capacity("perframe", 768, 768, counts=(2, 4, 8, 16, 24, 32, 48, 64), seconds=2.5)
+    b = serve.capacity("batch", 768, 768, counts=(128, 192, 224, 256, 288, 320), seconds=3.0)
+    p = serve.capacity("perframe", 768, 768, counts=(32, 64, 96, 128, 160, 192, 224, 256), seconds=2.5)
     # the same with PLCM streams only (2DLASM keystream is binary64-bound and
     # about eight times the work of PLCM per frame)
-    bp = serve.capacity("batch", 768, 768, counts=(256, 384, 512, 640, 768), seconds=3.0, kinds=(0,))
+    bp = serve.capacity("batch", 768, 768, counts=(512, 640, 768, 896), seconds=3.0, kinds=(0,))
     out["batched_streams"] = b["max_streams"]
     out["per_frame_streams"] = p["max_streams"]
     out["batched_streams_plcm_only"] = bp["max_streams"]
@@ -260,15 +266,52 @@ def serving_capacity() -> dict:
                                                   "fps", "tick_host_p50_ms", "tick_host_p99_ms")} for r in b["runs"]]
     out["per_frame_runs"] = [{k: r.get(k) for k in ("streams", "steady_p50_ms", "steady_p99_ms", "fps")}
                              for r in p["runs"]]
+    rates = serve.calibrate()
+    keep = ("load_target", "admitted", "rejected", "rejected_load", "rejected_chain", "frames", "fps", "steady_p50_ms",
+            "steady_p99_ms", "first_frame_p99_ms", "peak_concurrent_streams")
+    mixed = {"calibration": rates}
+    for mode in ("batch", "perframe"):
+        r = serve.serve_mixed(mode, rates=rates)
+        mixed[mode] = {"admitted_within_budget": r["admitted_within_budget"], "load_target": r["load_target"],
+                       "runs": [{k: x.get(k) for k in keep} for x in r["runs"]]}
+    mixed["workload"] = "256 Poisson streams (64/s), 480^2..3840x2160, 24/30/60 FPS, half 2DLASM, half decrypt"
+    out["mixed"] = mixed
     return out
+
+
+def kernel_chain_cycles(a, kind, key, stream) -> float:
+    """Cycles per map iterate of the keystream kernel when its chains run
+    alone: one frame of 768x768x3 with n = 16 (32 chains = one warp) in the
+    bench's keystream kernel (SM-holding CTAs), timed with CUDA events."""
+    import torch
+
+    from paper_2302_07411_gb300 import binding as B
+
+    n, H = 16, 768
+    N = H * H * 3
+    c = B.Cipher(kind, key, H, H, 3, n, a.rounds)
+    c.set_option(B.VC_OPT_OVERLAP, 1)
+    ks = torch.empty(a.rounds * N, dtype=torch.uint8, device="cuda")
+    sc = torch.empty(1, dtype=torch.int64, device="cuda")
+    B.vc_dbg_keystream(c.ctx, ks, sc, 1, stream=stream)  # warm-up, scratch
+    torch.cuda.synchronize()
+    B.enc_profile_enable(c.ctx, True)
+    B.enc_profile_read(c.ctx)
+    B.vc_dbg_keystream(c.ctx, ks, sc, 1, stream=stream)
+    torch.cuda.synchronize()
+    ms = B.enc_profile_read(c.ctx)["keystream"]["ms"]
+    c.close()
+    iters_per_chain = a.rounds * (N / n) * ITERS_PER_BYTE[a.map] / 2
+    return ms * 1e-3 * 2.07e9 / iters_per_chain
 
 
 def subframe_sweep(a, X, d_in, d_out, kind, key, stream, clock_hz, step_cycles, at_n):
     """The subframe-count sweep on the same clip (n = 16 .. 4096; Sec. 3 and
     Sec. 6 vary the thread count, one subframe per thread): Mpixel/s, the
     keystream and rounds stage times per 240-frame step, and the ceiling that
-    2n dependent PLCM chains set (2n chains x clock / cycles per step, over 5
-    map iterates per pixel).  n = a.n reuses the main measurement."""
+    2n dependent PLCM chains set (2n chains x clock / the kernel's cycles per
+    iterate with one warp of chains, over 5 map iterates per pixel).  n = a.n
+    reuses the main measurement."""
     import torch
 
     from paper_2302_07411_gb300 import binding as B
@@ -423,6 +466,8 @@ def run_ours(a) -> None:
     # ---- roofline of the dominant kernel (the keystream) against fixed bounds
     peaks = load_peaks()
     probes = B.vc_dbg_peaks(stream)  # measured on this GPU in this run
+    if a.map == "plcm":
+        probes["kernel_iter_cycles"] = kernel_chain_cycles(a, kind, key, stream)
     ks_launches = max(1, prof["keystream"]["launches"])
     ks_ms_step = prof["keystream"]["ms"] / max(1, a.steps)  # summed keystream launch time per step
     ks_ms = prof["keystream"]["ms"] / ks_launches            # per launch
@@ -439,14 +484,17 @@ def run_ours(a) -> None:
     frac_hbm = hbm_achieved / hbm if hbm else None
     lat = None
     if a.map == "plcm":
-        # 2n independent chains, each one dependent iterate after another: the
-        # measured cycles of one PLCM step on its dependency chain
+        # 2n independent chains, each one dependent iterate after another, at
+        # the cycles per iterate the same keystream kernel takes when its
+        # chains run alone (one warp on the GPU, timed in this run)
         chains = 2 * a.n
-        cyc = probes["plcm_step_cycles"]
+        cyc = probes["kernel_iter_cycles"]
         ceiling = chains * clock_hz / cyc
         lat = {"chains": chains, "cycles_per_iterate": round(cyc, 1), "ceiling": round(ceiling / 1e9, 4),
                "frac": round(achieved_iter / ceiling, 4),
-               "basis": "2n chains x median SM clock / cycles of one dependent PLCM step (clock64 probe, this run)"}
+               "probe_step_cycles": round(probes["plcm_step_cycles"], 1),
+               "basis": ("2n chains x median SM clock / cycles per iterate of the keystream kernel with one "
+                         "warp of chains on the GPU (768x768x3, n = 16, one frame, this run)")}
     per_launch = ks_launches // max(1, a.steps)
     traffic = None
     if a.map == "plcm" and a.size == 768 and a.n == 4096 and a.rounds == 5:
@@ -477,7 +525,7 @@ def run_ours(a) -> None:
 
     sweep = None
     if not a.no_sweep and world == 1 and a.size == 768 and a.map == "plcm":
-        sweep = subframe_sweep(a, X, d_in, d_out, kind, key, stream, clock_hz, probes["plcm_step_cycles"],
+        sweep = subframe_sweep(a, X, d_in, d_out, kind, key, stream, clock_hz, probes["kernel_iter_cycles"],
                                (ms, ks_ms_step, rd_ms))
 
     cpu = None

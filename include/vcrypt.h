@@ -198,11 +198,22 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  *                      integer pipes (fewer binary64 operations), -1 (default)
  *                      chooses per batch: 1 while the batch's 2DLASM chains
  *                      fill at most about 3.5 warps per SM, else 0.
+ * VC_BOPT_SPLIT:       batches with the keystream inside (run-ahead off):
+ *                      jobs whose serial chains take much longer than the
+ *                      others' go to a second lane on an internal stream --
+ *                      their keystream in CTAs that each hold a whole SM,
+ *                      their rounds behind it -- while the other jobs run
+ *                      beside them (the results are the same).  -1 (default)
+ *                      automatic: the jobs whose chains take at least half
+ *                      the longest, when that one is long (about 2 ms) and
+ *                      they are at most three quarters of the jobs; 1 split
+ *                      whenever the jobs' chains differ; 0 never.
  * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
 #define VC_BOPT_RUNAHEAD 3
 #define VC_BOPT_SINE 4
+#define VC_BOPT_SPLIT 5
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
@@ -312,7 +323,7 @@ int enc_sync_status(vc_ctx* ctx);
  *                  slot per pixel for C = 3 and 4, a byte for C = 1, plus the
  *                  tile's keystream when rows are whole 16-byte pieces -- stays
  *                  within 192 KB); 0 (default) takes the largest whose tile
- *                  stays within 64 KB.  Reading it back gives the rows in use.
+ *                  stays within 110 KB.  Reading it back gives the rows in use.
  * VC_OPT_KS_SM_WARPS: -1..4.  k > 0 runs the keystream of each pass in CTAs
  *                  of k warps that each occupy a whole SM (they claim all of
  *                  its shared memory), on an internal stream of the device's
@@ -323,7 +334,11 @@ int enc_sync_status(vc_ctx* ctx);
  *                  overlapping: PLCM 4 warps (one per SM sub-partition) if
  *                  those CTAs fill at most half of the SMs; 2DLASM (bound by
  *                  the SM's binary64 pipe) 2 warps if at least an eighth of
- *                  the SMs stay free, else as PLCM; otherwise 0.
+ *                  the SMs stay free, else as PLCM; otherwise 0.  The
+ *                  keystream a batcher produces ahead (VC_BOPT_RUNAHEAD) for
+ *                  this context holds SMs only when k > 0 is set explicitly
+ *                  (else one-warp CTAs share the SMs: many streams' chains
+ *                  pack the pipes better).
  * VC_OPT_RUNAHEAD_CALLS: 1 (default) with overlap: at the end of a call the
  *                  keystream of the next call's first pass is generated on the
  *                  internal stream, so it overlaps this call's last rounds; the

@@ -43,6 +43,10 @@ int vc_dbg_keystream(vc_ctx* ctx, uint8_t* d_ks, int64_t* d_sc, int32_t nframes,
  * context only.  Errors: VC_ERR_ARG. */
 int vc_dbg_call_plan(const vc_ctx* ctx, int32_t nframes, int32_t* plan, int32_t cap, int32_t* info4);
 
+/* Jobs of the batcher's last batch that ran in its long-chain lane
+ * (VC_BOPT_SPLIT; 0: none), or -VC_ERR_ARG. */
+int vc_dbg_batch_split(const vc_batcher* b);
+
 /* Internal geometry, for tests: {rows per tile, tiles per frame, padded frame
  * stride, N, P, scratch frames allocated, frames per pass, round-kernel shared
  * memory bytes}. */

@@ -114,6 +114,51 @@ def apply_stream(cipher: B.Cipher, options: dict) -> None:
     cipher.set_option(B.VC_OPT_KS_SM_WARPS, int(options.get("ks_sm_warps", -1)))
 
 
+def tune_rounds(kind: int, H: int, W: int, C: int, n: int, rounds: int = 5, frames: int = 4,
+                use_cache: bool = True) -> dict:
+    """Best rows per round-kernel tile (VC_OPT_TILE_ROWS: the block shape and
+    shared-memory staging depth of the confusion gather) for this shape class,
+    by the rounds' device time alone (stage events, keystream not
+    overlapped), over tile heights 4 .. 32 and the automatic choice.
+    Returns {"options": {"tile_rows": T}, "rounds_ms": t, "trials": [...]}."""
+    import torch
+
+    key = f"rounds|{_gpu_name()}|{kind}|{H}x{W}x{C}|n{n}|r{rounds}|f{frames}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    rng = np.random.default_rng(2)
+    x = torch.from_numpy(rng.integers(0, 256, (frames, H, W, C), dtype=np.uint8)).cuda()
+    y = torch.empty_like(x)
+    trials = []
+    for tile in (0, 4, 8, 16, 32):
+        c = B.Cipher(kind, _KEYS[kind], H, W, C, n, rounds)
+        c.set_option(B.VC_OPT_OVERLAP, 0)
+        try:
+            c.set_option(B.VC_OPT_TILE_ROWS, tile)
+        except B.VcError:  # the tile does not fit in shared memory
+            c.close()
+            continue
+        used = c.get_option(B.VC_OPT_TILE_ROWS)
+        c.encrypt(x, y)
+        torch.cuda.synchronize()
+        B.enc_profile_enable(c.ctx, True)
+        B.enc_profile_read(c.ctx)
+        for _ in range(2):
+            c.encrypt(x, y)
+        torch.cuda.synchronize()
+        ms = B.enc_profile_read(c.ctx)["rounds"]["ms"] / 2
+        trials.append({"tile_rows": tile, "rows_used": used, "rounds_ms": round(ms, 4)})
+        c.close()
+    best = min(trials, key=lambda t: t["rounds_ms"])
+    out = {"options": {"tile_rows": best["tile_rows"]}, "rows_used": best["rows_used"],
+           "rounds_ms": best["rounds_ms"], "trials": trials}
+    cache = _load()
+    cache[key] = out
+    _store(cache)
+    return out
+
+
 def tune_batch(layouts, frames_per_job: int = 1, use_cache: bool = True) -> dict:
     """Best persistent-grid CTAs per SM and tile rows for a batch made of one
     job per entry of `layouts` ((kind, H, W, C, n) tuples, encrypting)."""

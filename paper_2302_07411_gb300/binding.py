@@ -20,7 +20,7 @@ VC_OK = 0
 VC_PLCM, VC_2DLASM, VC_LOGISTIC = 0, 1, 2
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS, VC_OPT_KS_SM_WARPS = 1, 2, 3, 4, 5, 6
 VC_OPT_RUNAHEAD_CALLS, VC_OPT_DIFFUSION = 7, 8
-VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD, VC_BOPT_SINE = 1, 2, 3, 4
+VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD, VC_BOPT_SINE, VC_BOPT_SPLIT = 1, 2, 3, 4, 5
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
 
@@ -62,6 +62,7 @@ def lib():
             "encrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
             "decrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
             "vc_dbg_call_plan": (C.c_int, [p, i32, p, i32, p]),
+            "vc_dbg_batch_split": (C.c_int, [p]),
             "vc_dbg_fp64_peak": (C.c_int, [C.POINTER(C.c_double), p]),
             "vc_dbg_imad_peak": (C.c_int, [C.POINTER(C.c_double), p]),
             "vc_dbg_plcm_latency": (C.c_int, [C.c_double, C.c_double, i32, C.POINTER(C.c_double), p]),

@@ -40,8 +40,9 @@ void set_err(const char* fmt, ...) {
   } while (0)
 
 // bytes of one row-band tile in shared memory (its pixel slots and, when staged,
-// its keystream): small enough that several CTAs share an SM
-constexpr size_t kTileBudget = 64 * 1024;
+// its keystream): two CTAs share an SM (deeper tiles measured faster than four
+// shallower CTAs per SM, and they contend less with a concurrent keystream)
+constexpr size_t kTileBudget = 110 * 1024;
 constexpr size_t kTileHardCap = 192 * 1024;  // rows asked for explicitly (VC_OPT_TILE_ROWS) may use up to this
 constexpr uint32_t kStateMagic = 0x56435354u;  // "VCST"
 constexpr uint32_t kStateVersion = 1;
@@ -210,6 +211,19 @@ void sync_all(vc_ctx* c) {
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
+
+}  // namespace
+
+void vc::ctx_release_stream(vc_ctx* c, cudaStream_t s) {
+  if (!c || !s) return;
+  cudaStreamSynchronize(s);
+  if (c->last == s) {
+    // later calls order themselves after the internal streams, not after s
+    c->last = nullptr;
+  }
+}
+
+namespace {
 
 void free_scratch(vc_ctx* c) {
   for (int b = 0; b < 2; b++) {
@@ -1350,6 +1364,11 @@ struct vc_batcher {
   int ctas_per_sm = 0;
   int runahead = 0;  // frames of keystream kept ahead per stream (0 = off)
   int sine = -1;     // 2DLASM sine reduction in the batch keystream: -1 by load, 0 integer-assisted, 1 binary64
+  int split = -1;    // long-chain lane: -1 automatic, 0 never, 1 whenever the jobs differ
+  int last_split = 0;  // jobs the last batch ran in the long-chain lane
+  BatchLane cons_long;  // the long-chain lane (its own staging and graphs)
+  cudaStream_t side = nullptr;  // the long-chain lane's stream
+  cudaEvent_t fork = nullptr, join = nullptr, long_up = nullptr;
   cudaStream_t cap_stream = nullptr;
   std::map<size_t, int> ctas_for_smem;  // round-kernel CTAs per SM by shared-memory size (queried once)
 };
@@ -1488,8 +1507,12 @@ int produce(vc_ctx* c, int64_t target) {
   const int nf = (int)(target - c->produced);
   const int slot0 = (int)(c->produced % c->ring_cap);
   VC_CUDA(vc::launch_frame_schedule(c->L, c->d_main, nf, c->ring_sc, c->ring_kmod, ks, c->ring_cap, slot0));
+  // one-warp CTAs sharing the SMs (many streams' chains pack the pipes),
+  // unless VC_OPT_KS_SM_WARPS was set explicitly: then CTAs of that many warps
+  // that hold whole SMs (for a stream whose serial chains would otherwise
+  // miss its frame period)
   VC_CUDA(vc::launch_keystream(c->kind, c->L, c->tables(), c->chains(), nf, c->ring_ks, c->plcm_int, ks, c->ring_cap,
-                               slot0));
+                               slot0, c->ks_sm_warps > 0 ? c->ks_sm_warps : 0));
   const int i = (int)(c->nprod % vc_ctx::kProdEv);
   VC_CUDA(cudaEventRecord(c->ev_prod[i], ks));
   c->prod_upto[i] = target;
@@ -1510,8 +1533,11 @@ vc::JobDesc base_desc(vc_ctx* c) {
 
 // Stage `nj` descriptors (already in l.h_jobs[l.cur]) and launch them on st:
 // a captured graph per shape, or plain launches.
+// uploaded != nullptr: plain launches (no graph), with `uploaded` recorded on
+// st between the descriptor upload and the kernels.
 int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int kmods, int rounds, size_t smem,
-                cudaStream_t st, const int* vbeg, const int* vend, int variants) {
+                cudaStream_t st, const int* vbeg, const int* vend, int variants, int ks_sm_warps,
+                cudaEvent_t uploaded = nullptr) {
   vc::JobDesc* hj = l.h_jobs[l.cur];
   vc::BatchHdr* hh = l.h_hdr[l.cur];
   hh->njobs = nj;
@@ -1524,6 +1550,7 @@ int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int k
   }
   vc::BatchShape sh;
   sh.variants = variants;
+  sh.ks_sm_warps = ks_sm_warps;
   sh.jobs_cap = bucket(nj, 64);
   if (sh.jobs_cap > l.jobs_cap) sh.jobs_cap = l.jobs_cap;
   sh.warps_cap = bucket(warps, 64);
@@ -1549,9 +1576,9 @@ int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int k
     sh.grid = b->sms * ctas;
   }
   const size_t jobs_bytes = sizeof(vc::JobDesc) * (size_t)sh.jobs_cap;
-  if (b->use_graph) {
+  if (b->use_graph && !uploaded) {
     const auto key = std::make_tuple(sh.jobs_cap, sh.warps_cap, sh.kmod_cap, sh.rounds, sh.grid, sh.smem, l.cur,
-                                     sh.variants);
+                                     sh.variants * 8 + sh.ks_sm_warps);
     auto it = l.graphs.find(key);
     if (it == l.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1574,6 +1601,7 @@ int launch_lane(vc_batcher* b, BatchLane& l, int nj, int warps, int tiles, int k
   } else {
     VC_CUDA(cudaMemcpyAsync(l.d_hdr, hh, sizeof(vc::BatchHdr), cudaMemcpyHostToDevice, st));
     VC_CUDA(cudaMemcpyAsync(l.d_jobs, hj, jobs_bytes, cudaMemcpyHostToDevice, st));
+    if (uploaded) VC_CUDA(cudaEventRecord(uploaded, st));
     VC_CUDA(vc::launch_batch(l.d_jobs, l.d_hdr, sh, st));
   }
   VC_CUDA(cudaEventRecord(l.staged[l.cur], st));
@@ -1592,8 +1620,15 @@ int vc_batcher_create(vc_batcher** out) {
   if (!b) return VC_ERR_OOM;
   cudaGetDevice(&b->dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
-  bool ok = init_lane(b->cons) == VC_OK && grow_lane(b->cons, 64) == VC_OK &&
-            cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  bool ok = init_lane(b->cons) == VC_OK && grow_lane(b->cons, 64) == VC_OK && init_lane(b->cons_long) == VC_OK &&
+            grow_lane(b->cons_long, 64) == VC_OK &&
+            cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_greatest) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->long_up, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     vc_batcher_destroy(b);
@@ -1615,6 +1650,7 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
       if (value < 0 || value > 32) return VC_ERR_ARG;
       b->ctas_per_sm = (int)value;
       drop_graphs(b->cons);
+      drop_graphs(b->cons_long);
       return VC_OK;
     case VC_BOPT_RUNAHEAD:
       if (value < 0 || value > 64) return VC_ERR_ARG;
@@ -1624,9 +1660,150 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return VC_ERR_ARG;
       b->sine = (int)value;
       return VC_OK;
+    case VC_BOPT_SPLIT:
+      if (value < -1 || value > 1) return VC_ERR_ARG;
+      b->split = (int)value;
+      return VC_OK;
   }
   return VC_ERR_ARG;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Descriptors of one lane of a batch and its launch geometry.
+struct LaneFill {
+  int nj = 0, warps = 0, tiles = 0, kmods = 0, rounds = 0, variants = 0;
+  size_t smem = 4096;  // at least the fix-up's carries
+  int vbeg[vc::kBatchVariants] = {}, vend[vc::kBatchVariants] = {};
+};
+
+// Serial steps of one map chain of a job (its longest subframe) times the
+// cycles of one step, for choosing which jobs bound a batch with the
+// keystream inline (PLCM and logistic: one iterate per 6 bytes of a map;
+// 2DLASM: one step per 12 bytes of a pair).
+double job_chain_cycles(const vc_job& J) {
+  const Layout& L = J.ctx->L;
+  const double smax = (double)L.C * (double)((L.P + L.n - 1) / L.n);
+  const double bytes = (double)J.nframes * L.rounds * smax;
+  const int kind = J.ctx->kind;
+  const double steps = kind == VC_2DLASM ? bytes / 12.0 : bytes / 6.0;
+  const double cyc = kind == VC_2DLASM ? 3400.0 : (kind == VC_LOGISTIC ? 370.0 : 290.0);
+  return steps * cyc;
+}
+
+// lane_of[k] = 1 for the jobs that go to the long-chain lane.  Automatic
+// (VC_BOPT_SPLIT -1): the jobs whose chains take at least half the longest,
+// when the longest takes over 2 ms at 2 GHz, the others are at least a
+// quarter of the batch's jobs, and the long jobs' warps fit on half the SMs
+// in two-warp CTAs; 1: the same without the size conditions.
+bool split_long_jobs(const vc_batcher* b, const vc_job* jobs, const std::vector<int>& live, std::vector<int>& lane_of) {
+  const int nj = (int)live.size();
+  if (b->split == 0 || nj < 2) return false;
+  double tmax = 0;
+  std::vector<double> t((size_t)nj);
+  for (int k = 0; k < nj; k++) {
+    t[k] = job_chain_cycles(jobs[live[k]]);
+    tmax = std::max(tmax, t[k]);
+  }
+  int nlong = 0, lwarps = 0;
+  for (int k = 0; k < nj; k++) {
+    lane_of[k] = t[k] >= 0.5 * tmax ? 1 : 0;
+    if (lane_of[k]) {
+      nlong++;
+      lwarps += (jobs[live[k]].ctx->L.n + 15) / 16;
+    }
+  }
+  if (nlong == nj) {  // all alike: nothing bounds the batch alone
+    if (b->split != 1) return false;
+    for (int k = 0; k < nj; k++) lane_of[k] = 0;
+    int kmax = 0;
+    for (int k = 1; k < nj; k++)
+      if (t[k] > t[kmax]) kmax = k;
+    lane_of[kmax] = 1;
+    return true;
+  }
+  if (b->split == 1) return true;
+  const bool ok = tmax > 4e6 && 4 * (nj - nlong) >= nj && lwarps <= b->sms;
+  if (!ok) std::fill(lane_of.begin(), lane_of.end(), 0);
+  return ok;
+}
+
+// Descriptors of the jobs live[k] with lane_of[k] == which into lane l's
+// staging, their scratch taken from the pool at *pp.
+void fill_lane(vc_batcher* b, BatchLane& l, const vc_job* jobs, const std::vector<int>& live,
+               const std::vector<int>& lane_of, int which, int A, uint8_t** pp, LaneFill& F) {
+  vc::JobDesc* hj = l.h_jobs[l.cur];
+  uint8_t* p = *pp;
+  for (int k = 0; k < (int)live.size(); k++) {
+    if (lane_of[k] != which) continue;
+    const vc_job& J = jobs[live[k]];
+    vc_ctx* c = J.ctx;
+    const Layout& L = c->L;
+    const int nf = J.nframes;
+    const int v = vc::batch_variant(J.direction, L.C);
+    if (!(F.variants & (1 << v))) F.vbeg[v] = F.tiles;
+    F.variants |= 1 << v;
+    F.vend[v] = F.tiles + nf * L.NT;
+    vc::JobDesc d = base_desc(c);
+    d.dir = J.direction;
+    d.nframes = nf;
+    d.in = J.d_in;
+    d.out = J.d_out;
+    if (A > 0) {
+      d.mode = 1;
+      d.ks = c->ring_ks;
+      d.sc = c->ring_sc;
+      d.kmod = c->ring_kmod;
+      d.ring_cap = c->ring_cap;
+      d.ring_slot0 = (int)(c->frame % c->ring_cap);
+    } else {
+      d.mode = 0;
+      d.ks = p;
+      p += round256((size_t)nf * L.rounds * L.Npad);
+      d.kmod = reinterpret_cast<int*>(p);
+      p += round256((size_t)nf * L.H * sizeof(int));
+      d.sc = reinterpret_cast<long long*>(p);
+      p += round256((size_t)nf * sizeof(long long));
+    }
+    d.buf[0] = p;
+    p += round256((size_t)nf * L.Npad);
+    d.buf[1] = p;
+    p += round256((size_t)nf * L.Npad);
+    d.agg[0] = p;
+    p += round256((size_t)nf * L.NS);
+    d.agg[1] = p;
+    p += round256((size_t)nf * L.NS);
+    d.warp_base = F.warps;
+    d.tile_base = F.tiles;
+    d.kmod_base = F.kmods;
+    if (d.mode == 0) {
+      F.warps += (L.n + 15) / 16;
+      F.kmods += nf * L.H;
+    }
+    F.tiles += nf * L.NT;
+    if (L.rounds > F.rounds) F.rounds = L.rounds;
+    const size_t sm = vc::round_smem_bytes(L);
+    if (sm > F.smem) F.smem = sm;
+    hj[F.nj++] = d;
+  }
+  // 2DLASM chains of the lane's keystream: the all-binary64 sine reduction
+  // (the shorter dependency chain) on SMs they hold, and while their warps
+  // leave the SMs' binary64 pipes unsaturated -- about 3.5 warps of 2DLASM
+  // chains fill one SM's pipe -- else the integer-assisted one (fewer
+  // binary64 operations); both give the same bits
+  int lasm_warps = 0;
+  for (int k = 0; k < F.nj; k++)
+    if (hj[k].mode == 0 && hj[k].kind == VC_2DLASM) lasm_warps += (hj[k].L.n + 15) / 16;
+  const int b64 = b->sine >= 0 ? b->sine : ((which == 1 || 2 * lasm_warps <= 7 * b->sms) ? 1 : 0);
+  for (int k = 0; k < F.nj; k++) hj[k].sine_b64 = (hj[k].kind == VC_2DLASM) ? b64 : 0;
+  *pp = p;
+}
+
+}  // namespace
+
+extern "C" {
 
 int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stream) {
   vc::NvtxRange range("vc.batch");
@@ -1687,6 +1864,8 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
   }
   rc = grow_lane(b->cons, nj);
   if (rc) return rc;
+  rc = grow_lane(b->cons_long, nj);
+  if (rc) return rc;
   if (pool_need > b->pool_cap) {
     cudaDeviceSynchronize();
     cudaFree(b->d_pool);
@@ -1725,78 +1904,35 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
   }
 
   // ---- the batch: the rounds of every job (and the keystream when inline) ----
-  VC_CUDA(cudaEventSynchronize(b->cons.staged[b->cons.cur]));
-  vc::JobDesc* hj = b->cons.h_jobs[b->cons.cur];
+  // With the keystream inline, jobs whose chains are much longer than the
+  // rest (they bound the batch) may go to a second lane on a side stream:
+  // their keystream in CTAs that hold whole SMs, their rounds behind it,
+  // while the other jobs' keystream and rounds run beside them.
+  std::vector<int> lane_of((size_t)nj, 0);
+  const bool split = A == 0 && split_long_jobs(b, jobs, live, lane_of);
   uint8_t* p = b->d_pool;
-  int warps = 0, tiles = 0, kmods = 0, rounds = 0, variants = 0;
-  int vbeg[vc::kBatchVariants], vend[vc::kBatchVariants];
-  for (int v = 0; v < vc::kBatchVariants; v++) vbeg[v] = vend[v] = 0;
-  size_t smem = 4096;  // the fix-up needs one byte per tile
-  for (int k = 0; k < nj; k++) {
-    const vc_job& J = jobs[live[k]];
-    vc_ctx* c = J.ctx;
-    const Layout& L = c->L;
-    const int nf = J.nframes;
-    const int v = vc::batch_variant(J.direction, L.C);
-    if (!(variants & (1 << v))) vbeg[v] = tiles;
-    variants |= 1 << v;
-    vend[v] = tiles + nf * L.NT;
-    vc::JobDesc d = base_desc(c);
-    d.dir = J.direction;
-    d.nframes = nf;
-    d.in = J.d_in;
-    d.out = J.d_out;
-    if (A > 0) {
-      d.mode = 1;
-      d.ks = c->ring_ks;
-      d.sc = c->ring_sc;
-      d.kmod = c->ring_kmod;
-      d.ring_cap = c->ring_cap;
-      d.ring_slot0 = (int)(c->frame % c->ring_cap);
-    } else {
-      d.mode = 0;
-      d.ks = p;
-      p += round256((size_t)nf * L.rounds * L.Npad);
-      d.kmod = reinterpret_cast<int*>(p);
-      p += round256((size_t)nf * L.H * sizeof(int));
-      d.sc = reinterpret_cast<long long*>(p);
-      p += round256((size_t)nf * sizeof(long long));
-    }
-    d.buf[0] = p;
-    p += round256((size_t)nf * L.Npad);
-    d.buf[1] = p;
-    p += round256((size_t)nf * L.Npad);
-    d.agg[0] = p;
-    p += round256((size_t)nf * L.NS);
-    d.agg[1] = p;
-    p += round256((size_t)nf * L.NS);
-    d.warp_base = warps;
-    d.tile_base = tiles;
-    d.kmod_base = kmods;
-    if (d.mode == 0) {
-      warps += (L.n + 15) / 16;
-      kmods += nf * L.H;
-    }
-    tiles += nf * L.NT;
-    if (L.rounds > rounds) rounds = L.rounds;
-    const size_t sm = vc::round_smem_bytes(L);
-    if (sm > smem) smem = sm;
-    hj[k] = d;
+  LaneFill F0, F1;
+  VC_CUDA(cudaEventSynchronize(b->cons.staged[b->cons.cur]));
+  fill_lane(b, b->cons, jobs, live, lane_of, 0, A, &p, F0);
+  if (split) {
+    VC_CUDA(cudaEventSynchronize(b->cons_long.staged[b->cons_long.cur]));
+    fill_lane(b, b->cons_long, jobs, live, lane_of, 1, A, &p, F1);
+    // the long lane first, on a stream of the highest priority: its CTAs need
+    // empty SMs, so they must reach the GPU before the short lane's CTAs
+    // spread over every SM; the short lane waits for its descriptor upload
+    VC_CUDA(cudaEventRecord(b->fork, st));
+    VC_CUDA(cudaStreamWaitEvent(b->side, b->fork, 0));
+    rc = launch_lane(b, b->cons_long, F1.nj, F1.warps, F1.tiles, F1.kmods, F1.rounds, F1.smem, b->side, F1.vbeg,
+                     F1.vend, F1.variants, 2, b->long_up);
+    if (rc) return rc;
+    VC_CUDA(cudaEventRecord(b->join, b->side));
+    VC_CUDA(cudaStreamWaitEvent(st, b->long_up, 0));
   }
-  // 2DLASM chains of this batch's keystream: the all-binary64 sine reduction
-  // (the shorter dependency chain) while their warps leave the SMs' binary64
-  // pipes unsaturated -- about 3.5 warps of 2DLASM chains fill one SM's pipe
-  // -- else the integer-assisted one (fewer binary64 operations); both give
-  // the same bits
-  {
-    int lasm_warps = 0;
-    for (int k = 0; k < nj; k++)
-      if (hj[k].mode == 0 && hj[k].kind == VC_2DLASM) lasm_warps += (hj[k].L.n + 15) / 16;
-    const int b64 = b->sine >= 0 ? b->sine : (2 * lasm_warps <= 7 * b->sms ? 1 : 0);
-    for (int k = 0; k < nj; k++) hj[k].sine_b64 = (hj[k].kind == VC_2DLASM) ? b64 : 0;
-  }
-  rc = launch_lane(b, b->cons, nj, warps, tiles, kmods, rounds, smem, st, vbeg, vend, variants);
+  rc = launch_lane(b, b->cons, F0.nj, F0.warps, F0.tiles, F0.kmods, F0.rounds, F0.smem, st, F0.vbeg, F0.vend,
+                   F0.variants, 0);
   if (rc) return rc;
+  if (split) VC_CUDA(cudaStreamWaitEvent(st, b->join, 0));
+  b->last_split = split ? F1.nj : 0;
   for (int k = 0; k < nj; k++) {
     const vc_job& J = jobs[live[k]];
     vc_ctx* c = J.ctx;
@@ -1866,12 +2002,19 @@ int vc_batch_ready(vc_batcher* b, const vc_ctx* c, int32_t nframes) {
   return cc->produced_done >= cc->frame + nframes ? 1 : 0;
 }
 
+int vc_dbg_batch_split(const vc_batcher* b) { return b ? b->last_split : -VC_ERR_ARG; }
+
 void vc_batcher_destroy(vc_batcher* b) {
   if (!b) return;
   cudaDeviceSynchronize();
   free_lane(b->cons);
+  free_lane(b->cons_long);
   cudaFree(b->d_pool);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->long_up) cudaEventDestroy(b->long_up);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 

@@ -117,9 +117,20 @@ struct BatchHdr {
 // rounds = 0 launches the keystream phases only.
 struct BatchShape {
   int jobs_cap, warps_cap, kmod_cap, rounds, grid;
-  int variants;  // bit v set: a round kernel of variant v is launched
+  int variants;     // bit v set: a round kernel of variant v is launched
+  int ks_sm_warps;  // > 0: the keystream in CTAs of this many warps that each hold a whole SM; 0: one-warp CTAs
   size_t smem;
 };
+
+}  // namespace vc
+
+struct vc_ctx;
+namespace vc {
+
+// For a caller inside the library that is about to destroy CUDA stream `s`:
+// waits for the context's work on `s` and makes the context forget `s` as
+// the stream of its last call (vc_api.cu).
+void ctx_release_stream(vc_ctx* c, cudaStream_t s);
 
 // Launchers (vc_kernels.cu).  All enqueue on `st` and return the launch error.
 cudaError_t launch_build_tables(const Layout& L, int* pi, uint32_t* sbits, int* srank, int* fixlim, cudaStream_t st);

@@ -2344,6 +2344,28 @@ __global__ void __launch_bounds__(32) k_batch_ks(const JobDesc* J, const BatchHd
     ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
 }
 
+// The same over CTAs of W warps that each hold a whole SM (their dynamic shared
+// memory is claimed, not used): for the batch's long chains, which bound the
+// batch and lose issue slots when other chains or round CTAs share their SM.
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_batch_ks_sm(const JobDesc* J, const BatchHdr* hdr) {
+  const int w = blockIdx.x * W + (threadIdx.x >> 5);
+  if (w >= hdr->total_warps) return;
+  const int lane = threadIdx.x & 31;
+  const int j = find_job(J, hdr->njobs, w, [](const JobDesc& d) { return d.warp_base; });
+  const JobDesc& d = J[j];
+  const int i = (w - d.warp_base) * 16 + (lane >> 1);
+  const int side = lane & 1;
+  if (d.kind == 0)
+    ks_plcm_fx_chain(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+  else if (d.kind == 2)
+    ks_pair_chain<2, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+  else if (d.sine_b64)
+    ks_pair_chain<1, false, true>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+  else
+    ks_pair_chain<1, false>(d.L, d.tb, d.ch, d.nframes, d.ks, i, side, d.ring_cap, d.ring_slot0);
+}
+
 // Round `step` of frame f of a job (job rounds may differ): encryption applies
 // round `step`, decryption round r - 1 - step; the buffers alternate as in a
 // single-stream pass.  Every pointer is offset to frame f.
@@ -2458,7 +2480,14 @@ cudaError_t batch_ctas_per_sm(size_t smem, int* ctas) {
 cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st) {
   k_batch_sc<<<(sh.jobs_cap + 31) / 32, 32, 0, st>>>(jobs, hdr);
   k_batch_kmod<<<(sh.kmod_cap + 255) / 256, 256, 0, st>>>(jobs, hdr);
-  k_batch_ks<<<sh.warps_cap, 32, 0, st>>>(jobs, hdr);
+  if (sh.ks_sm_warps > 0) {
+    const int smem = reserve_smem_bytes();
+    cudaError_t e = allow_smem(k_batch_ks_sm<2>, smem);
+    if (e != cudaSuccess) return e;
+    k_batch_ks_sm<2><<<(sh.warps_cap + 1) / 2, 64, smem, st>>>(jobs, hdr);
+  } else {
+    k_batch_ks<<<sh.warps_cap, 32, 0, st>>>(jobs, hdr);
+  }
   if (sh.rounds > 0) {
     for (int step = 0; step < sh.rounds; step++) {
       if (sh.variants & (1 << 0)) k_batch_round<0, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);

@@ -322,13 +322,13 @@ int vc_server_remove(vc_server* s, int32_t id) {
           break;
         }
   }
-  t.active = false;
-  t.ctx = nullptr;
   if (t.cs) {
-    cudaStreamSynchronize(t.cs);
+    vc::ctx_release_stream(t.ctx, t.cs);  // the context must not keep the stream as its last one
     cudaStreamDestroy(t.cs);
     t.cs = nullptr;
   }
+  t.active = false;
+  t.ctx = nullptr;
   if (t.join) {
     cudaEventDestroy(t.join);
     t.join = nullptr;
@@ -363,7 +363,7 @@ void vc_server_destroy(vc_server* s) {
   }
   for (SrvStream& t : s->streams) {
     if (t.cs) {
-      cudaStreamSynchronize(t.cs);
+      vc::ctx_release_stream(t.ctx, t.cs);
       cudaStreamDestroy(t.cs);
     }
     if (t.join) cudaEventDestroy(t.join);

@@ -34,58 +34,172 @@ def subframes_for(H: int) -> int:
     return max(1, math.ceil(H / 4))
 
 
-@dataclass
-class Stream:
-    spec: dict
-    cipher: B.Cipher
-    out: object                      # device ring of output frames
-    bytes: int
-    frames_total: int = 0
-    sid: int = -1                    # handle in the native server
+# warps per SM-holding keystream CTA by map: PLCM and logistic chains are
+# latency-bound (one warp per scheduler), 2DLASM chains share the SM's
+# binary64 pipe (two warps)
+HOLD_WARPS = {0: 4, 1: 2, 2: 4}
+
+# map iterates per keystream byte: a PLCM or logistic pair emits 6 bytes per
+# iterate of each of its two maps (Sec. 3), a 2DLASM pair 12 bytes per step
+# of its two maps (Eq. 6: x then y)
+ITERS_PER_BYTE = {0: 2.0 / 6.0, 1: 2.0 / 12.0, 2: 2.0 / 6.0}
 
 
-@dataclass
-class ServeResult:
-    mode: str
-    latencies_ms: list = field(default_factory=list)
-    arrivals_s: list = field(default_factory=list)   # frame arrival time of each latency sample
-    first_frame_ms: list = field(default_factory=list)  # per stream: latency of its first frame
-    frames: int = 0
-    admitted: int = 0
-    rejected: int = 0
-    failed: int = 0        # admitted streams whose context could not be created (error kept in `errors`)
-    errors: list = field(default_factory=list)
-    peak_streams: int = 0
-    wall_s: float = 0.0
-    ticks: int = 0
-    tick_host_ms: list = field(default_factory=list)  # host time of each loop iteration that submitted work
-    native_ms: dict = field(default_factory=dict)      # host ms per part of the native ticks
+def calibrate(kinds=(0, 1), use_cache: bool = True) -> dict:
+    """Device rates that compute-aware admission charges streams against,
+    measured on this GPU (CUDA events) and cached per GPU name:
 
-    def summary(self, steady_after_s: float | None = None) -> dict:
-        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        out = {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
-               "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-               "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
-               "failed": self.failed, "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
-        if self.first_frame_ms:
-            out["first_frame_p99_ms"] = round(float(np.percentile(self.first_frame_ms, 99)), 3)
-        if self.tick_host_ms:
-            out["tick_host_p50_ms"] = round(float(np.percentile(self.tick_host_ms, 50)), 3)
-            out["tick_host_p99_ms"] = round(float(np.percentile(self.tick_host_ms, 99)), 3)
-        if self.native_ms.get("ticks"):
-            t = self.native_ms["ticks"]
-            out["native_tick_ms"] = {k: round(v / t, 4) for k, v in self.native_ms.items()
-                                     if k not in ("ticks", "gpu_ms_per_tick")}
-            out["gpu_ms_per_tick"] = round(self.native_ms.get("gpu_ms_per_tick", 0.0), 4)
-        if steady_after_s is not None:
-            arr = np.array(self.arrivals_s)
-            sel = lat[arr >= steady_after_s] if len(arr) == len(lat) else lat
-            if sel.size:
-                out["steady_after_s"] = steady_after_s
-                out["steady_frames"] = int(sel.size)
-                out["steady_p50_ms"] = round(float(np.percentile(sel, 50)), 3)
-                out["steady_p99_ms"] = round(float(np.percentile(sel, 99)), 3)
-        return out
+    * ks_iter_per_s[kind]: map iterates per second of the keystream under
+      serving load -- many streams' productions at once, each on its own CUDA
+      stream in the kernel productions use (one-warp CTAs sharing the SMs):
+      128 PLCM or 48 2DLASM streams of 768x768x3 with n = 192, one frame each;
+    * chain_s_per_iter[kind]: the seconds one chain needs per iterate under
+      that load (the serial limit of a single stream's chains);
+    * rounds_px_per_s: pixels per second of the five rounds (1920x1080x3,
+      n = 270, 8 frames, keystream not overlapped)."""
+    import torch
+
+    from . import autotune
+
+    key = f"serve-calibration-v3|{autotune._gpu_name()}|{','.join(map(str, kinds))}"
+    cache = autotune._load() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    out = {"ks_iter_per_s": {}, "chain_s_per_iter": {}, "chain_s_per_iter_held": {},
+           "sms": torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count}
+    H, W, C = 768, 768, 3
+    n = subframes_for(H)
+    N = H * W * C
+    keys = {0: [0.31, 0.21, 0.62, 0.37], 1: [0.31, 0.6, 0.62], 2: [0.31, 3.95, 0.62, 3.99]}
+    main = torch.cuda.current_stream()
+    for kind in kinds:
+        K = 48 if kind == 1 else 128
+        ciphers, bufs, streams = [], [], []
+        for i in range(K):
+            c = B.Cipher(kind, keys[kind], H, W, C, n, 5)
+            c.set_option(B.VC_OPT_OVERLAP, 0)
+            c.set_option(B.VC_OPT_KS_SM_WARPS, 0)
+            ciphers.append(c)
+            bufs.append((torch.empty(5 * N, dtype=torch.uint8, device="cuda"),
+                         torch.empty(1, dtype=torch.int64, device="cuda")))
+            streams.append(torch.cuda.Stream())
+
+        def produce_all():
+            ev = torch.cuda.Event()
+            ev.record(main)
+            for c, (ks, sc), st in zip(ciphers, bufs, streams):
+                st.wait_event(ev)
+                B.vc_dbg_keystream(c.ctx, ks, sc, 1, stream=st)
+            for st in streams:
+                main.wait_stream(st)
+
+        produce_all()  # warm-up (scratch allocation)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        produce_all()
+        e1.record(main)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        for c in ciphers:
+            c.close()
+        per_chain = 5 * (N / n) * ITERS_PER_BYTE[kind] / 2  # iterates of one map chain per frame
+        out["ks_iter_per_s"][str(kind)] = K * 2 * n * per_chain / sec
+        out["chain_s_per_iter"][str(kind)] = sec / per_chain
+        # one stream alone in CTAs that hold whole SMs (HOLD_WARPS warps each)
+        c = B.Cipher(kind, keys[kind], H, W, C, n, 5)
+        c.set_option(B.VC_OPT_KS_SM_WARPS, HOLD_WARPS[kind])
+        ks, sc = bufs[0]
+        B.vc_dbg_keystream(c.ctx, ks, sc, 1)
+        torch.cuda.synchronize()
+        B.enc_profile_enable(c.ctx, True)
+        B.enc_profile_read(c.ctx)
+        B.vc_dbg_keystream(c.ctx, ks, sc, 1)
+        torch.cuda.synchronize()
+        out["chain_s_per_iter_held"][str(kind)] = B.enc_profile_read(c.ctx)["keystream"]["ms"] * 1e-3 / per_chain
+        c.close()
+    Hr, Wr = 1080, 1920
+    x = torch.zeros((8, Hr, Wr, 3), dtype=torch.uint8, device="cuda")
+    c = B.Cipher(0, keys[0], Hr, Wr, 3, subframes_for(Hr), 5)
+    c.set_option(B.VC_OPT_OVERLAP, 0)
+    c.encrypt(x, x)
+    torch.cuda.synchronize()
+    B.enc_profile_enable(c.ctx, True)
+    B.enc_profile_read(c.ctx)
+    c.encrypt(x, x)
+    torch.cuda.synchronize()
+    prof = B.enc_profile_read(c.ctx)
+    c.close()
+    out["rounds_px_per_s"] = 8 * Hr * Wr / (prof["rounds"]["ms"] * 1e-3)
+    cache = autotune._load()
+    cache[key] = out
+    autotune._store(cache)
+    return out
+
+
+class ComputeBudget:
+    """Compute-aware admission and keystream placement.  A stream whose own
+    chains, sharing the SMs under load, would be busy more than `hold_above`
+    of its frame period gets its keystream in CTAs that hold whole SMs
+    (VC_OPT_KS_SM_WARPS); it is refused when even there one chain's iterates
+    per frame times the calibrated seconds per iterate, times the frame rate,
+    exceed `chain_busy_max` (a chain is serial; its frames' keystream is
+    produced ahead).  Each admitted stream is charged the fraction of the
+    device it keeps busy -- its keystream iterates per second over the
+    calibrated rate of its map (held: its SMs' share of the device), plus its
+    pixels per second over the rounds' rate -- against `target`."""
+
+    def __init__(self, rates: dict, target: float = 0.8, chain_busy_max: float = 0.6, hold_above: float = 0.5):
+        self.rates, self.target = rates, target
+        self.chain_busy_max, self.hold_above = chain_busy_max, hold_above
+        self.used = 0.0
+
+    def plan(self, spec: dict) -> dict:
+        H, W, C, kind, fps = spec["H"], spec["W"], spec["C"], spec["kind"], float(spec["fps"])
+        P = H * W
+        n = subframes_for(H)
+        S = P * C / n  # bytes per subframe
+        it_chain = 5 * S * ITERS_PER_BYTE[kind] / 2  # iterates of one map chain per frame
+        k = str(kind)
+        busy = fps * it_chain * self.rates["chain_s_per_iter"][k]
+        hold = 0
+        ks_load = fps * 2 * n * it_chain / self.rates["ks_iter_per_s"][k]
+        if busy > self.hold_above and "chain_s_per_iter_held" in self.rates:
+            hold = HOLD_WARPS[kind]
+            busy = fps * it_chain * self.rates["chain_s_per_iter_held"][k]
+            ctas = -(-2 * n // (32 * hold))
+            ks_load = ctas * busy / float(self.rates.get("sms", 152))
+        return {"load": ks_load + fps * P / self.rates["rounds_px_per_s"], "busy": busy, "hold": hold}
+
+    def cost(self, spec: dict) -> tuple[float, float]:
+        p = self.plan(spec)
+        return p["load"], p["busy"]
+
+    def admit(self, spec: dict) -> tuple[bool, float, str]:
+        p = self.plan(spec)
+        if p["busy"] > self.chain_busy_max:
+            return False, 0.0, "chain"
+        if self.used + p["load"] > self.target:
+            return False, 0.0, "load"
+        self.used += p["load"]
+        return True, p["load"], ""
+
+    def release(self, load: float) -> None:
+        self.used = max(0.0, self.used - load)
+
+
+def tune_shapes(requests) -> dict:
+    """The autotuner's choice (rows per round-kernel tile, by the rounds'
+    device time; cached per GPU) for every shape class (kind, H, W, C) of
+    the requests, with n = ceil(H/4): {(kind, H, W, C): {"tile_rows": T}}."""
+    from . import autotune
+
+    out = {}
+    for r in requests:
+        k = (r["kind"], r["H"], r["W"], r["C"])
+        if k not in out:
+            out[k] = autotune.tune_rounds(r["kind"], r["H"], r["W"], r["C"], subframes_for(r["H"]))["options"]
+    return out
 
 
 class Server:
@@ -93,10 +207,20 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 64 << 30, tick_ms: float = 4.0, mode: str = "batch",
                  max_frames_per_tick: int = 4, ring: int = 8, keep_outputs: bool = False,
-                 cipher_options: dict | None = None):
+                 cipher_options: dict | None = None, compute: ComputeBudget | None = None,
+                 setup_lead_s: float = 0.0, tuned: dict | None = None):
+        """compute: admission also charges each stream's device load (None:
+        HBM budget only).  setup_lead_s: a request is admitted this long
+        before its first frame arrives (the session's setup), so its context
+        and, when batching, its first frames' keystream exist by then.
+        tuned: per shape class (kind, H, W, C) the options the autotuner
+        chose (tune_shapes), applied to each stream's context."""
         import torch
 
         self.torch = torch
+        self.compute = compute
+        self.lead = setup_lead_s
+        self.tuned = dict(tuned or {})
         self.cipher_options = dict(cipher_options or {})  # enc_set_option values for every stream
         self.budget = hbm_budget_bytes
         self.tick = tick_ms / 1e3
@@ -118,6 +242,13 @@ class Server:
         ciph = B.Cipher(spec["kind"], spec["key"], H, W, C, subframes_for(H), 5)
         for opt, val in self.cipher_options.items():
             ciph.set_option(opt, val)
+        tuned = self.tuned.get((spec["kind"], H, W, C))
+        if tuned:
+            ciph.set_option(B.VC_OPT_TILE_ROWS, int(tuned.get("tile_rows", 0)))
+        if self.compute is not None:
+            hold = self.compute.plan(spec)["hold"]
+            if hold:
+                ciph.set_option(B.VC_OPT_KS_SM_WARPS, hold)
         out = torch.empty((self.ring, H, W, C), dtype=torch.uint8, device="cuda")
         return Stream(spec, ciph, out, fp, frames_total=max(1, int(spec["duration"] * spec["fps"])))
 
@@ -148,6 +279,7 @@ class Server:
         torch = self.torch
         res = ServeResult(self.mode)
         pending = deque(sorted(requests, key=lambda r: r["arrival"]))
+        lead = self.lead
         starting = deque()  # futures of streams whose context is being created
         active: dict[int, Stream] = {}
         used = 0
@@ -169,26 +301,38 @@ class Server:
             while True:
                 t_iter = time.perf_counter()
                 now = t_iter - t0
-                # admissions (HBM budget)
-                while pending and pending[0]["arrival"] <= now:
+                # admissions (HBM budget, then the compute budget)
+                while pending and pending[0]["arrival"] - lead <= now:
                     spec = pending.popleft()
                     fp = self.footprint(spec, self.ring, self.maxf)
                     if used + fp > self.budget:
                         res.rejected += 1
                         continue
+                    load = 0.0
+                    if self.compute is not None:
+                        ok, load, why = self.compute.admit(spec)
+                        if not ok:
+                            if why == "chain":
+                                res.rejected_chain += 1
+                            else:
+                                res.rejected_load += 1
+                            continue
                     used += fp
                     res.admitted += 1
                     # context creation (key schedule on the GPU) off the loop's thread
-                    starting.append((self.pool.submit(self._open, spec, fp), fp))
+                    starting.append((self.pool.submit(self._open, spec, fp), fp, load))
                 while starting and starting[0][0].done():
-                    fut, fp = starting.popleft()
+                    fut, fp, load = starting.popleft()
                     try:
                         st = fut.result()
                     except Exception as e:  # e.g. a key outside the valid ranges: this stream only
                         res.failed += 1
                         res.errors.append(f"{type(e).__name__}: {e}")
                         used -= fp
+                        if self.compute is not None:
+                            self.compute.release(load)
                         continue
+                    st.load = load
                     H, W, C = st.spec["H"], st.spec["W"], st.spec["C"]
                     st.sid = srv.add(st.cipher, st.spec["direction"], H * W * C, self.input_frames(H, W, C),
                                      self.maxf, st.out, self.ring, float(st.spec["fps"]), st.spec["arrival"],
@@ -205,6 +349,8 @@ class Server:
                     if now >= last_arrival and srv.stream_done(sid):
                         srv.remove(sid)
                         used -= st.bytes
+                        if self.compute is not None:
+                            self.compute.release(st.load)
                         del active[sid]
                         if self.keep:
                             self.finished.append(st)
@@ -277,7 +423,43 @@ def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0
             "max_streams": best, "runs": runs}
 
 
-def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2) -> dict:
+def serve_mixed(mode: str, nstreams: int = 256, rate_per_s: float = 64.0, seed: int = 5,
+                targets=(0.8, 0.55, 0.4, 0.25, 0.15), budget_ms: float = 1000.0 / 24.0,
+                hbm_budget_bytes: int = 160 << 30, setup_lead_s: float = 0.1, rates: dict | None = None,
+                steady_after_s: float = 1.5) -> dict:
+    """The mixed serving workload: nstreams requests arriving as a Poisson
+    process (rate_per_s), resolutions 480^2 ... 3840x2160, 24 / 30 / 60 FPS,
+    PLCM and 2DLASM alternating, half encrypt and half decrypt, n = ceil(H/4)
+    (synth.serving_workload).  Served with compute-aware admission at the
+    given load targets in turn, until the steady-state p99 per-frame latency of
+    the admitted streams is under budget_ms; every run is reported (admitted,
+    rejected by memory / device load / chain rate, p50 / p99, first-frame p99,
+    frames/s).  Requests are admitted setup_lead_s before their first frame."""
+    import synth
+
+    rates = rates or calibrate()
+    reqs = synth.serving_workload(nstreams, seed=seed, rate_per_s=rate_per_s)
+    tuned = tune_shapes(reqs)
+    runs, best = [], None
+    for t in targets:
+        srv = Server(hbm_budget_bytes=hbm_budget_bytes, mode=mode, compute=ComputeBudget(rates, target=t),
+                     setup_lead_s=setup_lead_s, tuned=tuned)
+        res = srv.run(reqs)
+        srv.close()
+        summ = res.summary(steady_after_s=steady_after_s)
+        summ["load_target"] = t
+        runs.append(summ)
+        if summ.get("steady_p99_ms", summ["p99_ms"]) < budget_ms:
+            best = summ
+            break
+    return {"mode": mode, "requests": nstreams, "rate_per_s": rate_per_s, "p99_budget_ms": round(budget_ms, 2),
+            "setup_lead_s": setup_lead_s,
+            "tuned": {f"{k[0]}:{k[1]}x{k[2]}x{k[3]}": v for k, v in tuned.items()},
+            "admitted_within_budget": best["admitted"] if best else 0,
+            "load_target": best["load_target"] if best else None, "runs": runs}
+
+
+def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2, split: int = -1) -> dict:
     """Ragged batches against one call per frame.  nstreams streams, each with
     its own key, resolutions cycling 480^2, 576^2, 768^2 and 1920x1080
     (n = ceil(H/4)), maps and directions alternating, one frame per stream per
@@ -300,13 +482,23 @@ def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2) -> dict:
     for (_, _, _, H, W, _) in specs:
         if (H, W) not in frames:
             frames[(H, W)] = torch.from_numpy(synth.uniform_frames(1, H, W, 3, seed=H + W)).cuda()
+    from . import autotune
+
+    # the autotuner's tile rows per shape class, the same for both forms
+    tuned = {}
+    for (k, d, key, H, W, n) in specs:
+        if (k, H, W) not in tuned:
+            tuned[(k, H, W)] = autotune.tune_rounds(k, H, W, 3, n)["options"]["tile_rows"]
     batched = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
     single = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
+    for c, (k, d, key, H, W, n) in zip(batched + single, specs + specs):
+        c.set_option(B.VC_OPT_TILE_ROWS, tuned[(k, H, W)])
     out_b = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
     out_s = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
     streams = [torch.cuda.Stream() for _ in specs]
     main = torch.cuda.current_stream()
     batcher = B.Batcher(graph=True)
+    B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SPLIT, split)
 
     def tick_batched():
         batcher.submit([(c, sp[1], frames[(sp[3], sp[4])], out_b[j], 1) for j, (c, sp) in enumerate(zip(batched, specs))],
@@ -339,6 +531,7 @@ def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2) -> dict:
         return a.elapsed_time(b) / ticks
 
     ms_b = timed(tick_batched)
+    long_jobs = B.lib().vc_dbg_batch_split(batcher.b)
     ms_s = timed(tick_single)
     same = all(torch.equal(x, y) for x, y in zip(out_b, out_s))
     px = sum(H * W for (_, _, _, H, W, _) in specs)
@@ -348,7 +541,8 @@ def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2) -> dict:
     return {"streams": nstreams, "resolutions": ["480x480", "576x576", "768x768", "1080x1920"],
             "batched_ms_per_tick": round(ms_b, 3), "per_frame_ms_per_tick": round(ms_s, 3),
             "batched_mpixel_s": round(px / ms_b / 1e3, 1), "per_frame_mpixel_s": round(px / ms_s / 1e3, 1),
-            "outputs_equal": bool(same)}
+            "outputs_equal": bool(same), "batch_long_lane_jobs": int(long_jobs),
+            "tuned_tile_rows": {f"{k}:{H}x{W}": v for (k, H, W), v in tuned.items()}}
 
 
 def main():
@@ -375,13 +569,21 @@ def main():
     ap.add_argument("--batch-mix", type=int, default=0, metavar="N",
                     help="instead: N streams of mixed resolutions, one batch per tick against one call per frame")
     ap.add_argument("--ticks", type=int, default=6, help="timed ticks of --batch-mix")
+    ap.add_argument("--split", type=int, default=-1, help="VC_BOPT_SPLIT of --batch-mix")
+    ap.add_argument("--mixed", action="store_true",
+                    help="instead: the mixed Poisson workload with compute-aware admission (both modes)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     from . import build
 
     build.build()
     if a.batch_mix:
-        print(json.dumps(batch_mix(a.batch_mix, ticks=a.ticks)))
+        print(json.dumps(batch_mix(a.batch_mix, ticks=a.ticks, split=a.split)))
+        return
+    if a.mixed:
+        rates = calibrate()
+        print(json.dumps({"calibration": rates, **{m: serve_mixed(m, nstreams=a.streams, rate_per_s=a.rate, rates=rates)
+                                                   for m in (["batch", "perframe"] if a.mode == "both" else [a.mode])}}))
         return
     modes = ["batch", "perframe"] if a.mode == "both" else [a.mode]
     out = {}

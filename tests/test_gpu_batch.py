@@ -96,6 +96,40 @@ def test_batch_sine_forms_equal_solo_runs(B, sine):
     batcher.close()
 
 
+@pytest.mark.parametrize("split", [1, -1, 0])
+def test_batch_long_chain_lane_equals_solo_runs(B, split):
+    """VC_BOPT_SPLIT: jobs whose chains are much longer than the rest (a large
+    2DLASM frame with few subframes beside small PLCM ones) run in the
+    batcher's second lane -- keystream in SM-holding CTAs on a side stream --
+    and every output equals the stream run alone, over consecutive batches."""
+    shapes = [(1, 96, 128, 3, 4, 0), (0, 32, 32, 3, 8, 0), (0, 40, 48, 3, 12, 1), (2, 24, 40, 3, 6, 0),
+              (0, 36, 36, 1, 9, 1), (1, 64, 48, 3, 2, 1)]
+    batcher = B.Batcher(graph=True)
+    B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SPLIT, split)
+    mixed = [B.Cipher(k, synth.key_for_seed(k, 820 + i), H, W, C, n) for i, (k, H, W, C, n, d) in enumerate(shapes)]
+    solo = [B.Cipher(k, synth.key_for_seed(k, 820 + i), H, W, C, n) for i, (k, H, W, C, n, d) in enumerate(shapes)]
+    for tick in range(3):
+        jobs, outs, refs = [], [], []
+        for i, (k, H, W, C, n, d) in enumerate(shapes):
+            x = torch.from_numpy(synth.uniform_frames(2, H, W, C, seed=830 + 10 * tick + i)).cuda()
+            y = torch.empty_like(x)
+            jobs.append((mixed[i], d, x, y, 2))
+            outs.append(y)
+            refs.append(solo[i].encrypt(x) if d == 0 else solo[i].decrypt(x))
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for i in range(len(shapes)):
+            assert torch.equal(outs[i], refs[i]), f"tick {tick}, stream {i}"
+        nlong = B.lib().vc_dbg_batch_split(batcher.b)
+        if split == 1:
+            assert nlong >= 1  # the two 2DLASM frames with 2 and 4 subframes
+        if split == 0:
+            assert nlong == 0
+    for c in mixed + solo:
+        c.close()
+    batcher.close()
+
+
 def test_batch_round_trip_and_mixing_with_single_calls(B, orc):
     """Encrypt in a batch, continue the same contexts with single-stream calls,
     then decrypt everything in a batch; the oracle agrees on the ciphertext."""
