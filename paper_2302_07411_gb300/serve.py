@@ -188,6 +188,63 @@ class ComputeBudget:
         self.used = max(0.0, self.used - load)
 
 
+@dataclass
+class Stream:
+    spec: dict
+    cipher: B.Cipher
+    out: object                      # device ring of output frames
+    bytes: int
+    frames_total: int = 0
+    sid: int = -1                    # handle in the native server
+    load: float = 0.0                # device fraction charged by the compute budget
+
+
+@dataclass
+class ServeResult:
+    mode: str
+    latencies_ms: list = field(default_factory=list)
+    arrivals_s: list = field(default_factory=list)   # frame arrival time of each latency sample
+    first_frame_ms: list = field(default_factory=list)  # per stream: latency of its first frame
+    frames: int = 0
+    admitted: int = 0
+    rejected: int = 0      # HBM budget
+    rejected_load: int = 0   # compute budget: the device is full
+    rejected_chain: int = 0  # compute budget: the stream's own chains cannot keep up
+    failed: int = 0        # admitted streams whose context could not be created (error kept in `errors`)
+    errors: list = field(default_factory=list)
+    peak_streams: int = 0
+    wall_s: float = 0.0
+    ticks: int = 0
+    tick_host_ms: list = field(default_factory=list)  # host time of each loop iteration that submitted work
+    native_ms: dict = field(default_factory=dict)      # host ms per part of the native ticks
+
+    def summary(self, steady_after_s: float | None = None) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        out = {"mode": self.mode, "frames": self.frames, "fps": round(self.frames / max(self.wall_s, 1e-9), 1),
+               "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+               "max_ms": round(float(lat.max()), 3), "admitted": self.admitted, "rejected": self.rejected,
+               "rejected_load": self.rejected_load, "rejected_chain": self.rejected_chain, "failed": self.failed, "peak_concurrent_streams": self.peak_streams, "ticks": self.ticks}
+        if self.first_frame_ms:
+            out["first_frame_p99_ms"] = round(float(np.percentile(self.first_frame_ms, 99)), 3)
+        if self.tick_host_ms:
+            out["tick_host_p50_ms"] = round(float(np.percentile(self.tick_host_ms, 50)), 3)
+            out["tick_host_p99_ms"] = round(float(np.percentile(self.tick_host_ms, 99)), 3)
+        if self.native_ms.get("ticks"):
+            t = self.native_ms["ticks"]
+            out["native_tick_ms"] = {k: round(v / t, 4) for k, v in self.native_ms.items()
+                                     if k not in ("ticks", "gpu_ms_per_tick")}
+            out["gpu_ms_per_tick"] = round(self.native_ms.get("gpu_ms_per_tick", 0.0), 4)
+        if steady_after_s is not None:
+            arr = np.array(self.arrivals_s)
+            sel = lat[arr >= steady_after_s] if len(arr) == len(lat) else lat
+            if sel.size:
+                out["steady_after_s"] = steady_after_s
+                out["steady_frames"] = int(sel.size)
+                out["steady_p50_ms"] = round(float(np.percentile(sel, 50)), 3)
+                out["steady_p99_ms"] = round(float(np.percentile(sel, 99)), 3)
+        return out
+
+
 def tune_shapes(requests) -> dict:
     """The autotuner's choice (rows per round-kernel tile, by the rounds'
     device time; cached per GPU) for every shape class (kind, H, W, C) of

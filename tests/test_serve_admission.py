@@ -75,3 +75,14 @@ def test_long_chains_get_sm_holding_keystream():
     assert p["load"] == pytest.approx(ctas * p["busy"] / 152 + 24 * 1080 * 1920 / 40e9)
     q = b.plan(spec(0, 768, 768, 24))
     assert q["hold"] == 0 and q["busy"] == pytest.approx(24 * (5 * 9216 / 6) * 150e-9)
+
+
+def test_result_summary_without_gpu():
+    """The serving result's summary (latency percentiles, steady-state window,
+    admission counters) is host arithmetic."""
+    r = serve.ServeResult("batch", latencies_ms=[1.0, 2.0, 3.0, 50.0], arrivals_s=[0.1, 2.0, 2.5, 3.0],
+                          first_frame_ms=[1.0], frames=4, admitted=2, rejected_chain=1, wall_s=2.0)
+    s = r.summary(steady_after_s=1.5)
+    assert s["frames"] == 4 and s["fps"] == 2.0 and s["admitted"] == 2 and s["rejected_chain"] == 1
+    assert s["steady_frames"] == 3 and s["steady_p50_ms"] == 3.0
+    assert s["first_frame_p99_ms"] == 1.0
