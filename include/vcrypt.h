@@ -208,12 +208,19 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  *                      the longest, when that one is long (about 2 ms) and
  *                      they are at most three quarters of the jobs; 1 split
  *                      whenever the jobs' chains differ; 0 never.
+ * VC_BOPT_KS_PLACE:    where the keystream produced ahead (VC_BOPT_RUNAHEAD)
+ *                      runs: 0 (default) one-warp CTAs sharing the SMs with
+ *                      other work; 1 as the context's own calls place it
+ *                      (VC_OPT_KS_SM_WARPS, -1 automatic: CTAs that hold
+ *                      whole SMs when they leave enough SMs free).  A context
+ *                      with VC_OPT_KS_SM_WARPS > 0 holds SMs in both.
  * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
 #define VC_BOPT_RUNAHEAD 3
 #define VC_BOPT_SINE 4
 #define VC_BOPT_SPLIT 5
+#define VC_BOPT_KS_PLACE 6
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
@@ -278,6 +285,10 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
 int vc_server_stream_done(const vc_server* s, int32_t id);
 int vc_server_remove(vc_server* s, int32_t id);
 int32_t vc_server_inflight(const vc_server* s);
+/* vc_server_set_option: a batcher option (VC_BOPT_*) of a batching server
+ * (mode 0); the run-ahead is the server's max_frames_per_tick and cannot be
+ * set.  Errors: VC_ERR_ARG (mode 1, VC_BOPT_RUNAHEAD, bad option or value). */
+int vc_server_set_option(vc_server* s, int32_t option, int64_t value);
 void vc_server_destroy(vc_server* s);
 
 /* Size in bytes of a checkpoint of the context's stream state (chaotic map
@@ -427,8 +438,18 @@ int vc_stats_local_entropy(const uint8_t* d_frames, int32_t nframes, int32_t hei
 int vc_stats_npcr_uaci(const uint8_t* d_a, const uint8_t* d_b, int32_t nframes, int32_t height, int32_t width,
                        int32_t channels, uint64_t* d_sums, double* d_npcr, double* d_uaci, void* stream);
 
-/* Release the context and its device memory (synchronises its stream). */
+/* Release the context and its device memory.  enc_destroy first waits for
+ * the context's work (its internal streams and the stream of its last call);
+ * when it returns, nothing of the context runs any more.
+ * enc_destroy_async does not wait: the device memory goes back to the
+ * library's stream-ordered pool after the work enqueued so far, and the host
+ * object is freed at once.  The caller keeps the buffers that this work reads
+ * or writes (its frames) alive until that work is complete (e.g. an event on
+ * the stream of the last call).  A context whose keystream was generated
+ * ahead (run-ahead) may still be running that keystream when this returns; it
+ * touches only the context's own memory.  Both accept NULL. */
 void enc_destroy(vc_ctx* ctx);
+void enc_destroy_async(vc_ctx* ctx);
 
 /* Human-readable text of a status code; last CUDA error text of this thread. */
 const char* vc_strerror(int code);

@@ -75,6 +75,19 @@ int vc_dbg_plcm_latency(double x0, double p, int32_t iters, double* cycles_per_s
  * Errors: VC_ERR_ARG. */
 int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks);
 
+/* Latency records of a vc_server, for splitting per-frame latency into the
+ * wait before submission (frame clock, keystream readiness, tick cadence) and
+ * the device time after it.  vc_dbg_server_record: enable != 0 starts keeping
+ * a record per drained frame and per drained tick (0 stops and frees them).
+ * vc_dbg_server_take: moves up to cap records into out, 4 doubles each, and
+ * sets *n to their number: which = 0 frames (stream id, arrival, submission,
+ * completion), which = 1 ticks (submission, device start, device end, frame
+ * count); times in seconds on the server's clock (vc_server_tick's `now`;
+ * device times by CUDA events against the creation event).
+ * Errors: VC_ERR_ARG. */
+int vc_dbg_server_record(vc_server* s, int32_t enable);
+int vc_dbg_server_take(vc_server* s, int32_t which, int32_t cap, double* out, int32_t* n);
+
 #ifdef __cplusplus
 }
 #endif

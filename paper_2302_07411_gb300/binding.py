@@ -20,7 +20,7 @@ VC_OK = 0
 VC_PLCM, VC_2DLASM, VC_LOGISTIC = 0, 1, 2
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS, VC_OPT_KS_SM_WARPS = 1, 2, 3, 4, 5, 6
 VC_OPT_RUNAHEAD_CALLS, VC_OPT_DIFFUSION = 7, 8
-VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD, VC_BOPT_SINE, VC_BOPT_SPLIT = 1, 2, 3, 4, 5
+VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD, VC_BOPT_SINE, VC_BOPT_SPLIT, VC_BOPT_KS_PLACE = 1, 2, 3, 4, 5, 6
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}
 
@@ -80,6 +80,7 @@ def lib():
             "enc_sync_status": (C.c_int, [p]),
             "enc_set_chunk": (C.c_int, [p, i32]),
             "enc_destroy": (None, [p]),
+            "enc_destroy_async": (None, [p]),
             "enc_profile_enable": (C.c_int, [p, i32]),
             "enc_profile_read": (C.c_int, [p, p, p]),
             "vc_strerror": (C.c_char_p, [C.c_int]),
@@ -99,8 +100,11 @@ def lib():
             "vc_server_stream_done": (C.c_int, [p, i32]),
             "vc_server_remove": (C.c_int, [p, i32]),
             "vc_server_inflight": (i32, [p]),
+            "vc_server_set_option": (C.c_int, [p, i32, i64]),
             "vc_server_destroy": (None, [p]),
             "vc_dbg_server_stats": (C.c_int, [p, p, p]),
+            "vc_dbg_server_record": (C.c_int, [p, i32]),
+            "vc_dbg_server_take": (C.c_int, [p, i32, i32, p, p]),
             "vc_stats_histogram": (C.c_int, [p, i32, i32, i32, i32, p, p, p, p, p]),
             "vc_stats_correlation": (C.c_int, [p, i32, i32, i32, i32, i32, p, i64, p, p, p]),
             "vc_stats_local_entropy": (C.c_int, [p, i32, i32, i32, i32, i32, p, i32, i32, p, p, p]),
@@ -236,6 +240,10 @@ def enc_destroy(ctx) -> None:
     lib().enc_destroy(ctx)
 
 
+def enc_destroy_async(ctx) -> None:
+    lib().enc_destroy_async(ctx)
+
+
 def vc_dbg_csin(d_t, d_out, variant: int = 1, stream=None) -> None:
     _check(lib().vc_dbg_csin(_dptr(d_t), _dptr(d_out), d_t.numel(), variant, _stream(stream)), "vc_dbg_csin")
 
@@ -353,9 +361,12 @@ class Cipher:
     def layout_info(self) -> dict:
         return vc_dbg_layout(self.ctx)
 
-    def close(self) -> None:
+    def close(self, wait: bool = True) -> None:
+        """Release the context: after its work (wait), or with its memory given
+        back in stream order after that work (enc_destroy_async: the caller
+        keeps the frames that work uses alive until it is complete)."""
         if getattr(self, "ctx", None):
-            enc_destroy(self.ctx)
+            (enc_destroy if wait else enc_destroy_async)(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -486,6 +497,10 @@ class NativeServer:
     def inflight(self) -> int:
         return lib().vc_server_inflight(self.s)
 
+    def set_option(self, option: int, value: int) -> None:
+        """A batcher option (VC_BOPT_*) of a batching server."""
+        _check(lib().vc_server_set_option(self.s, option, value), "vc_server_set_option")
+
     def host_stats(self) -> dict:
         """Host ms per part of the ticks since the last call (vc_dbg_server_stats)."""
         ms = (C.c_double * 6)()
@@ -493,6 +508,27 @@ class NativeServer:
         _check(lib().vc_dbg_server_stats(self.s, ms, C.byref(t)), "vc_dbg_server_stats")
         return {"ticks": t.value, "clocks_ms": ms[0], "prefetch_ms": ms[1], "submit_ms": ms[2], "event_ms": ms[3],
                 "gpu_ms_per_tick": ms[4] / ms[5] if ms[5] else 0.0}
+
+    def record(self, enable: bool = True) -> None:
+        """Keep per-frame and per-tick latency records (vc_dbg_server_record)."""
+        _check(lib().vc_dbg_server_record(self.s, 1 if enable else 0), "vc_dbg_server_record")
+
+    def take_records(self):
+        """(frames [k, 4]: stream, arrival, submission, completion; ticks [m, 4]:
+        submission, device start, device end, frame count), seconds."""
+        np = self._np
+        out = []
+        for which in (0, 1):
+            parts = []
+            while True:
+                buf = np.empty((4096, 4), dtype=np.float64)
+                n = C.c_int32()
+                _check(lib().vc_dbg_server_take(self.s, which, 4096, buf.ctypes.data, C.byref(n)), "vc_dbg_server_take")
+                parts.append(buf[:n.value].copy())
+                if n.value < 4096:
+                    break
+            out.append(np.concatenate(parts))
+        return tuple(out)
 
     def close(self) -> None:
         if getattr(self, "s", None):

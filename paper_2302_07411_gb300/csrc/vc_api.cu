@@ -47,6 +47,79 @@ constexpr size_t kTileHardCap = 192 * 1024;  // rows asked for explicitly (VC_OP
 constexpr uint32_t kStateMagic = 0x56435354u;  // "VCST"
 constexpr uint32_t kStateVersion = 1;
 
+// ---- device memory: a stream-ordered pool of the library's own per device.
+// A buffer is taken from it at once (its allocation stream carries nothing
+// else) and given back in stream order after the work that used it, so that
+// releasing a context's or a batcher's memory never waits for the device (a
+// plain cudaFree waits for all of it, e.g. for other streams' long keystream
+// chains).  The pool keeps its memory mapped between uses and never makes an
+// allocation wait for another stream's work.
+constexpr int kMaxPoolDevices = 64;
+struct DevPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t st = nullptr;
+};
+std::mutex g_pool_mu;
+DevPool g_pool[kMaxPoolDevices];
+
+cudaError_t dev_pool(DevPool** out) {  // under g_pool_mu
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  DevPool& d = g_pool[dev];
+  if (!d.pool) {
+    cudaMemPoolProps pr{};
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.handleTypes = cudaMemHandleTypeNone;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &pr);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ull;
+    int no = 0;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
+    cudaStream_t st = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    d.pool = p;
+    d.st = st;
+  }
+  *out = &d;
+  return cudaSuccess;
+}
+
+// bytes of device memory, usable on every stream when this returns
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  *p = nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  DevPool* d = nullptr;
+  cudaError_t e = dev_pool(&d);
+  void* v = nullptr;
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&v, bytes ? bytes : 1, d->pool, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  if (e == cudaSuccess) *p = static_cast<T*>(v);
+  return e;
+}
+
+// p (may be null) back to the pool once the work enqueued on `after` so far is
+// complete (after == nullptr: at once, for memory no work has used)
+void dev_free(void* p, cudaStream_t after) {
+  if (!p) return;
+  if (!after) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    DevPool* d = nullptr;
+    if (dev_pool(&d) == cudaSuccess) after = d->st;
+  }
+  cudaFreeAsync(p, after);
+}
+
 bool key_valid(const vc_key& k) {
   if (k.kind == VC_PLCM) {
     for (int i = 0; i < 4; i += 2)
@@ -149,6 +222,7 @@ struct vc_ctx {
   cudaEvent_t ev_rd[2] = {};   // rounds reading buffer b done
   cudaEvent_t ev_entry = nullptr;
   cudaEvent_t ev_batch = nullptr;  // recorded after a batch that used this context
+  cudaEvent_t ev_free = nullptr;   // joins the other streams into ks_stream before a free
   bool batch_pending = false;
   // keystream run-ahead ring of the batcher: frame f's keystream, s_c and shift
   // table live in slot f mod ring_cap; `produced` frames exist (the chaotic
@@ -157,10 +231,13 @@ struct vc_ctx {
   long long* ring_sc = nullptr;
   int* ring_kmod = nullptr;
   int ring_cap = 0;
+  // per ring slot: recorded after the batch that read it, so that a production
+  // overwriting the slot waits for that batch and for no later one
+  std::vector<cudaEvent_t> ev_slot;
   int64_t produced = 0;
-  // productions of the ring run on ks_stream; the last four are tracked so
+  // productions of the ring run on ks_stream; the last eight are tracked so
   // that readiness can be polled without blocking
-  static constexpr int kProdEv = 4;
+  static constexpr int kProdEv = 8;
   cudaEvent_t ev_prod[kProdEv] = {};
   int64_t prod_upto[kProdEv] = {};
   int64_t nprod = 0;
@@ -212,6 +289,19 @@ void sync_all(vc_ctx* c) {
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
 
+// ks_stream after everything enqueued so far on the context's other streams
+// (its buffers are given back to the pool there, in stream order).
+cudaStream_t ctx_join(vc_ctx* c) {
+  cudaStream_t ks = c->ks_stream;
+  if (!ks || !c->ev_free) {  // a context whose creation failed part-way: nothing of it ran
+    sync_all(c);
+    return nullptr;
+  }
+  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream})
+    if (o && o != ks && cudaEventRecord(c->ev_free, o) == cudaSuccess) cudaStreamWaitEvent(ks, c->ev_free, 0);
+  return ks;
+}
+
 }  // namespace
 
 void vc::ctx_release_stream(vc_ctx* c, cudaStream_t s) {
@@ -225,13 +315,14 @@ void vc::ctx_release_stream(vc_ctx* c, cudaStream_t s) {
 
 namespace {
 
-void free_scratch(vc_ctx* c) {
+// the pass scratch back to the pool after the work enqueued on `after`
+void free_scratch(vc_ctx* c, cudaStream_t after) {
   for (int b = 0; b < 2; b++) {
-    cudaFree(c->d_ks[b]);
-    cudaFree(c->d_sc[b]);
-    cudaFree(c->d_kmod[b]);
-    cudaFree(c->d_buf[b]);
-    cudaFree(c->d_agg[b]);
+    dev_free(c->d_ks[b], after);
+    dev_free(c->d_sc[b], after);
+    dev_free(c->d_kmod[b], after);
+    dev_free(c->d_buf[b], after);
+    dev_free(c->d_agg[b], after);
     c->d_ks[b] = c->d_buf[b] = c->d_agg[b] = nullptr;
     c->d_sc[b] = nullptr;
     c->d_kmod[b] = nullptr;
@@ -245,20 +336,19 @@ int ensure_scratch(vc_ctx* c, int frames) {
   if (frames <= c->cap) return VC_OK;
   int rc = spec_rollback(c);
   if (rc) return rc;
-  sync_all(c);
-  free_scratch(c);
+  free_scratch(c, ctx_join(c));  // after the passes that used it
   const Layout& L = c->L;
   const size_t F = (size_t)frames;
   bool ok = true;
   for (int b = 0; b < 2 && ok; b++) {
-    ok = cudaMalloc(&c->d_ks[b], F * L.rounds * L.Npad) == cudaSuccess &&
-         cudaMalloc(&c->d_sc[b], F * sizeof(long long)) == cudaSuccess &&
-         cudaMalloc(&c->d_kmod[b], F * L.H * sizeof(int)) == cudaSuccess &&
-         cudaMalloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && cudaMalloc(&c->d_agg[b], F * L.NS + 16) == cudaSuccess;
+    ok = dev_alloc(&c->d_ks[b], F * L.rounds * L.Npad) == cudaSuccess &&
+         dev_alloc(&c->d_sc[b], F * sizeof(long long)) == cudaSuccess &&
+         dev_alloc(&c->d_kmod[b], F * L.H * sizeof(int)) == cudaSuccess &&
+         dev_alloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && dev_alloc(&c->d_agg[b], F * L.NS + 16) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
-    free_scratch(c);
+    free_scratch(c, nullptr);
     set_err("cudaMalloc of %d frames of scratch failed", frames);
     return VC_ERR_OOM;
   }
@@ -495,7 +585,7 @@ int spec_issue(vc_ctx* c, int nf) {
       c->produced != c->frame)
     return VC_OK;
   if (!c->d_snap) {
-    if (cudaMalloc(&c->d_snap, snap_bytes(c)) != cudaSuccess) {
+    if (dev_alloc(&c->d_snap, snap_bytes(c)) != cudaSuccess) {
       cudaGetLastError();
       c->d_snap = nullptr;
       return VC_OK;  // no run-ahead without room for the snapshot
@@ -688,15 +778,15 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
   cudaGetDevice(&c->dev);
   const int n = L.n;
   const int nwords = L.P / 32 + 2;
-  bool ok = cudaMalloc(&c->d_pi, sizeof(int) * (n + 1)) == cudaSuccess &&
-            cudaMalloc(&c->d_sbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
-            cudaMalloc(&c->d_srank, sizeof(int) * nwords) == cudaSuccess &&
-            cudaMalloc(&c->d_fixlim, sizeof(int) * L.NS) == cudaSuccess &&
-            cudaMalloc(&c->d_main, sizeof(vc::MainPrbg)) == cudaSuccess &&
-            cudaMalloc(&c->d_st, sizeof(double) * c->state_words() * n) == cudaSuccess &&
-            cudaMalloc(&c->d_par, sizeof(double) * c->par_words() * n) == cudaSuccess &&
-            cudaMalloc(&c->d_carry, sizeof(uint64_t) * 2 * n) == cudaSuccess &&
-            cudaMalloc(&c->d_carry_len, sizeof(int) * n) == cudaSuccess;
+  bool ok = dev_alloc(&c->d_pi, sizeof(int) * (n + 1)) == cudaSuccess &&
+            dev_alloc(&c->d_sbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
+            dev_alloc(&c->d_srank, sizeof(int) * nwords) == cudaSuccess &&
+            dev_alloc(&c->d_fixlim, sizeof(int) * L.NS) == cudaSuccess &&
+            dev_alloc(&c->d_main, sizeof(vc::MainPrbg)) == cudaSuccess &&
+            dev_alloc(&c->d_st, sizeof(double) * c->state_words() * n) == cudaSuccess &&
+            dev_alloc(&c->d_par, sizeof(double) * c->par_words() * n) == cudaSuccess &&
+            dev_alloc(&c->d_carry, sizeof(uint64_t) * 2 * n) == cudaSuccess &&
+            dev_alloc(&c->d_carry_len, sizeof(int) * n) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     enc_destroy(c);
@@ -721,10 +811,10 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
       cudaEventCreateWithFlags(&c->ev_rd[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_batch, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_prod[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_prod[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_prod[2], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_prod[3], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming) != cudaSuccess ||
+      !std::all_of(std::begin(c->ev_prod), std::end(c->ev_prod), [](cudaEvent_t& e) {
+        return cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      })) {
     enc_destroy(c);
     set_err("stream/event creation failed");
     return VC_ERR_CUDA;
@@ -777,16 +867,15 @@ int decrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int
 // Host staging buffers for passes of up to `frames` frames.
 int ensure_io(vc_ctx* c, int frames) {
   if (c->io_cap >= frames) return VC_OK;
-  cudaStreamSynchronize(c->copy_stream);
-  if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
+  cudaStream_t after = ctx_join(c);
   for (auto& b : c->d_io) {
-    cudaFree(b);
+    dev_free(b, after);
     b = nullptr;
   }
   c->io_cap = 0;
   const size_t N = (size_t)c->L.N;
   for (auto& b : c->d_io) {
-    if (cudaMalloc(&b, (size_t)frames * N) != cudaSuccess) {
+    if (dev_alloc(&b, (size_t)frames * N) != cudaSuccess) {
       cudaGetLastError();
       set_err("staging allocation failed");
       return VC_ERR_OOM;
@@ -1037,7 +1126,7 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (rs) return rs;
       sync_all(c);
       int* fl = nullptr;
-      if (cudaMalloc(&fl, sizeof(int) * L2.NS) != cudaSuccess) {
+      if (dev_alloc(&fl, sizeof(int) * L2.NS) != cudaSuccess) {
         cudaGetLastError();
         set_err("tile table allocation failed");
         return VC_ERR_OOM;
@@ -1045,9 +1134,9 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       // the partition tables other than the tile limits do not depend on the tile shape
       VC_CUDA(vc::launch_build_tables(L2, c->d_pi, c->d_sbits, c->d_srank, fl, c->copy_stream));
       VC_CUDA(cudaStreamSynchronize(c->copy_stream));
-      cudaFree(c->d_fixlim);
+      dev_free(c->d_fixlim, nullptr);  // the context's streams are idle
       c->d_fixlim = fl;
-      free_scratch(c);
+      free_scratch(c, nullptr);
       c->L = L2;
       c->tile_rows = (int)value;
       return VC_OK;
@@ -1072,20 +1161,22 @@ int enc_get_option(const vc_ctx* c, int32_t option, int64_t* value) {
   return VC_ERR_ARG;
 }
 
-void enc_destroy(vc_ctx* c) {
+namespace {
+
+// Releases the context; wait: first wait for its work (enc_destroy), else
+// give its memory back in stream order after that work (enc_destroy_async).
+void destroy_ctx(vc_ctx* c, bool wait) {
   if (!c) return;
-  sync_all(c);
-  free_scratch(c);
-  for (auto b : c->d_io) cudaFree(b);
-  cudaFree(c->d_pi);
-  cudaFree(c->d_sbits);
-  cudaFree(c->d_srank);
-  cudaFree(c->d_fixlim);
-  cudaFree(c->d_main);
-  cudaFree(c->d_st);
-  cudaFree(c->d_par);
-  cudaFree(c->d_carry);
-  cudaFree(c->d_carry_len);
+  if (wait) sync_all(c);
+  cudaStream_t after = ctx_join(c);
+  if (wait) after = nullptr;
+  free_scratch(c, after);
+  for (auto b : c->d_io) dev_free(b, after);
+  for (void* b : {(void*)c->d_pi, (void*)c->d_sbits, (void*)c->d_srank, (void*)c->d_fixlim, (void*)c->d_main,
+                  (void*)c->d_st, (void*)c->d_par, (void*)c->d_carry, (void*)c->d_carry_len, (void*)c->ring_ks,
+                  (void*)c->ring_sc, (void*)c->ring_kmod, (void*)c->d_snap})
+    dev_free(b, after);
+  // events and streams: their resources are released once pending work is done
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_io)
@@ -1102,16 +1193,19 @@ void enc_destroy(vc_ctx* c) {
     if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
     if (c->ev_rd[b]) cudaEventDestroy(c->ev_rd[b]);
   }
-  if (c->ev_entry) cudaEventDestroy(c->ev_entry);
-  if (c->ev_batch) cudaEventDestroy(c->ev_batch);
+  for (cudaEvent_t e : {c->ev_entry, c->ev_batch, c->ev_free})
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_slot) cudaEventDestroy(e);
   for (int i = 0; i < vc_ctx::kProdEv; i++)
     if (c->ev_prod[i]) cudaEventDestroy(c->ev_prod[i]);
-  cudaFree(c->ring_ks);
-  cudaFree(c->ring_sc);
-  cudaFree(c->ring_kmod);
-  cudaFree(c->d_snap);
   delete c;
 }
+
+}  // namespace
+
+void enc_destroy(vc_ctx* c) { destroy_ctx(c, true); }
+
+void enc_destroy_async(vc_ctx* c) { destroy_ctx(c, false); }
 
 // ---- diagnostics (include/vcrypt_debug.h) ----
 
@@ -1351,6 +1445,7 @@ struct BatchLane {
   cudaEvent_t staged[2] = {nullptr, nullptr};
   int cur = 0;
   std::map<std::tuple<int, int, int, int, int, size_t, int, int>, cudaGraphExec_t> graphs;
+  std::vector<void*> retired_host;  // outgrown pinned staging, freed with the lane (its copies may be in flight)
 };
 
 }  // namespace
@@ -1366,9 +1461,11 @@ struct vc_batcher {
   int sine = -1;     // 2DLASM sine reduction in the batch keystream: -1 by load, 0 integer-assisted, 1 binary64
   int split = -1;    // long-chain lane: -1 automatic, 0 never, 1 whenever the jobs differ
   int last_split = 0;  // jobs the last batch ran in the long-chain lane
+  int ks_place = 0;    // run-ahead productions: 0 shared SMs, 1 as the context's own calls place them
   BatchLane cons_long;  // the long-chain lane (its own staging and graphs)
   cudaStream_t side = nullptr;  // the long-chain lane's stream
   cudaEvent_t fork = nullptr, join = nullptr, long_up = nullptr;
+  cudaEvent_t done = nullptr;  // the end of the last batch, on its stream
   cudaStream_t cap_stream = nullptr;
   std::map<size_t, int> ctas_for_smem;  // round-kernel CTAs per SM by shared-memory size (queried once)
 };
@@ -1386,20 +1483,21 @@ void drop_graphs(BatchLane& l) {
   l.graphs.clear();
 }
 
-void free_lane(BatchLane& l) {
+void free_lane(BatchLane& l) {  // the device is idle
   drop_graphs(l);
-  cudaFree(l.d_jobs);
-  cudaFree(l.d_hdr);
+  dev_free(l.d_jobs, nullptr);
+  dev_free(l.d_hdr, nullptr);
   for (int i = 0; i < 2; i++) {
     cudaFreeHost(l.h_jobs[i]);
     cudaFreeHost(l.h_hdr[i]);
     if (l.staged[i]) cudaEventDestroy(l.staged[i]);
   }
+  for (void* h : l.retired_host) cudaFreeHost(h);
   l = BatchLane();
 }
 
 int init_lane(BatchLane& l) {
-  bool ok = cudaMalloc(&l.d_hdr, sizeof(vc::BatchHdr)) == cudaSuccess &&
+  bool ok = dev_alloc(&l.d_hdr, sizeof(vc::BatchHdr)) == cudaSuccess &&
             cudaMallocHost(&l.h_hdr[0], sizeof(vc::BatchHdr)) == cudaSuccess &&
             cudaMallocHost(&l.h_hdr[1], sizeof(vc::BatchHdr)) == cudaSuccess &&
             cudaEventCreateWithFlags(&l.staged[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -1407,17 +1505,20 @@ int init_lane(BatchLane& l) {
   return ok ? VC_OK : VC_ERR_OOM;
 }
 
-int grow_lane(BatchLane& l, int need) {
+// Descriptors for `need` jobs.  The old device array goes back to the pool
+// after the work enqueued on `after` (the batches that read it); the old
+// pinned staging is kept until the lane is freed.
+int grow_lane(BatchLane& l, int need, cudaStream_t after) {
   if (need <= l.jobs_cap) return VC_OK;
   const int cap = bucket(need, 64);
-  cudaDeviceSynchronize();
-  drop_graphs(l);  // the descriptor address is a kernel argument of the captured graphs
-  cudaFree(l.d_jobs);
-  for (int i = 0; i < 2; i++) cudaFreeHost(l.h_jobs[i]);
+  drop_graphs(l);  // the descriptor address is a kernel argument of the captured graphs (in flight: freed when done)
+  dev_free(l.d_jobs, after);
+  for (int i = 0; i < 2; i++)
+    if (l.h_jobs[i]) l.retired_host.push_back(l.h_jobs[i]);
   l.d_jobs = nullptr;
   l.h_jobs[0] = l.h_jobs[1] = nullptr;
   l.jobs_cap = 0;
-  if (cudaMalloc(&l.d_jobs, sizeof(vc::JobDesc) * cap) != cudaSuccess ||
+  if (dev_alloc(&l.d_jobs, sizeof(vc::JobDesc) * cap) != cudaSuccess ||
       cudaMallocHost(&l.h_jobs[0], sizeof(vc::JobDesc) * cap) != cudaSuccess ||
       cudaMallocHost(&l.h_jobs[1], sizeof(vc::JobDesc) * cap) != cudaSuccess) {
     cudaGetLastError();
@@ -1442,22 +1543,30 @@ int ensure_ring(vc_ctx* c, int cap) {
     set_err("cannot grow a keystream ring that holds frames");
     return VC_ERR_SEQUENCE;
   }
-  sync_all(c);
-  cudaFree(c->ring_ks);
-  cudaFree(c->ring_sc);
-  cudaFree(c->ring_kmod);
+  cudaStream_t after = ctx_join(c);  // after the productions and batches that used it
+  dev_free(c->ring_ks, after);
+  dev_free(c->ring_sc, after);
+  dev_free(c->ring_kmod, after);
   c->ring_ks = nullptr;
   c->ring_sc = nullptr;
   c->ring_kmod = nullptr;
   c->ring_cap = 0;
   const Layout& L = c->L;
-  if (cudaMalloc(&c->ring_ks, (size_t)cap * L.rounds * L.Npad) != cudaSuccess ||
-      cudaMalloc(&c->ring_sc, (size_t)cap * sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&c->ring_kmod, (size_t)cap * L.H * sizeof(int)) != cudaSuccess) {
+  if (dev_alloc(&c->ring_ks, (size_t)cap * L.rounds * L.Npad) != cudaSuccess ||
+      dev_alloc(&c->ring_sc, (size_t)cap * sizeof(long long)) != cudaSuccess ||
+      dev_alloc(&c->ring_kmod, (size_t)cap * L.H * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     set_err("keystream ring allocation failed");
     return VC_ERR_OOM;
   }
+  for (cudaEvent_t e : c->ev_slot) cudaEventDestroy(e);
+  c->ev_slot.assign((size_t)cap, nullptr);
+  for (auto& e : c->ev_slot)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("ring event creation failed");
+      return VC_ERR_CUDA;
+    }
   c->ring_cap = cap;
   return VC_OK;
 }
@@ -1484,9 +1593,21 @@ bool production_busy(vc_ctx* c) {
   return cudaEventQuery(c->ev_prod[(c->nprod - 1) % vc_ctx::kProdEv]) == cudaErrorNotReady;
 }
 
+// Productions not known complete (after a non-blocking poll).
+int productions_in_flight(vc_ctx* c) {
+  if (poll_production(c) != VC_OK) return vc_ctx::kProdEv;
+  int n = 0;
+  for (int64_t k = std::max<int64_t>(0, c->nprod - vc_ctx::kProdEv); k < c->nprod; k++)
+    if (c->prod_upto[k % vc_ctx::kProdEv] > c->produced_done) n++;
+  return n;
+}
+
 // Produce frames [produced, target) of the stream's keystream into its ring on
 // its own internal stream, after the batch that last read the ring's slots.
-int produce(vc_ctx* c, int64_t target) {
+// place: 0 one-warp CTAs sharing the SMs, 1 the placement of the context's own
+// calls (VC_OPT_KS_SM_WARPS); an explicit VC_OPT_KS_SM_WARPS > 0 holds SMs in
+// both.
+int produce(vc_ctx* c, int64_t target, int place) {
   if (c->produced >= target) return VC_OK;
   vc::NvtxRange range("vc.keystream");
   cudaStream_t ks = c->ks_stream;
@@ -1494,7 +1615,9 @@ int produce(vc_ctx* c, int64_t target) {
     VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
     VC_CUDA(cudaStreamWaitEvent(ks, c->ev_entry, 0));
   }
-  VC_CUDA(cudaStreamWaitEvent(ks, c->ev_batch, 0));
+  // the slots about to be overwritten: after the batches that read them (a slot
+  // no batch has read yet has an event never recorded: no wait)
+  for (int64_t f = c->produced; f < target; f++) VC_CUDA(cudaStreamWaitEvent(ks, c->ev_slot[f % c->ring_cap], 0));
   // at most kProdEv productions in flight (their events are tracked); the
   // oldest is normally long done, this only blocks if it is not
   if (c->nprod >= vc_ctx::kProdEv) {
@@ -1512,7 +1635,7 @@ int produce(vc_ctx* c, int64_t target) {
   // that hold whole SMs (for a stream whose serial chains would otherwise
   // miss its frame period)
   VC_CUDA(vc::launch_keystream(c->kind, c->L, c->tables(), c->chains(), nf, c->ring_ks, c->plcm_int, ks, c->ring_cap,
-                               slot0, c->ks_sm_warps > 0 ? c->ks_sm_warps : 0));
+                               slot0, c->ks_sm_warps > 0 ? c->ks_sm_warps : (place == 1 ? ks_warps_in_use(c) : 0)));
   const int i = (int)(c->nprod % vc_ctx::kProdEv);
   VC_CUDA(cudaEventRecord(c->ev_prod[i], ks));
   c->prod_upto[i] = target;
@@ -1622,8 +1745,9 @@ int vc_batcher_create(vc_batcher** out) {
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-  bool ok = init_lane(b->cons) == VC_OK && grow_lane(b->cons, 64) == VC_OK && init_lane(b->cons_long) == VC_OK &&
-            grow_lane(b->cons_long, 64) == VC_OK &&
+  bool ok = init_lane(b->cons) == VC_OK && grow_lane(b->cons, 64, nullptr) == VC_OK &&
+            init_lane(b->cons_long) == VC_OK && grow_lane(b->cons_long, 64, nullptr) == VC_OK &&
+            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess &&
             cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_greatest) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->long_up, cudaEventDisableTiming) == cudaSuccess &&
@@ -1663,6 +1787,10 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
     case VC_BOPT_SPLIT:
       if (value < -1 || value > 1) return VC_ERR_ARG;
       b->split = (int)value;
+      return VC_OK;
+    case VC_BOPT_KS_PLACE:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      b->ks_place = (int)value;
       return VC_OK;
   }
   return VC_ERR_ARG;
@@ -1716,8 +1844,8 @@ bool split_long_jobs(const vc_batcher* b, const vc_job* jobs, const std::vector<
     }
   }
   if (nlong == nj) {  // all alike: nothing bounds the batch alone
-    if (b->split != 1) return false;
     for (int k = 0; k < nj; k++) lane_of[k] = 0;
+    if (b->split != 1) return false;
     int kmax = 0;
     for (int k = 1; k < nj; k++)
       if (t[k] > t[kmax]) kmax = k;
@@ -1862,17 +1990,19 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     rc = spec_rollback(jobs[live[k]].ctx);
     if (rc) return rc;
   }
-  rc = grow_lane(b->cons, nj);
+  // what the last batch used goes back to the pool after it (st waits for its end)
+  if (nj > b->cons.jobs_cap || nj > b->cons_long.jobs_cap || pool_need > b->pool_cap)
+    VC_CUDA(cudaStreamWaitEvent(st, b->done, 0));
+  rc = grow_lane(b->cons, nj, st);
   if (rc) return rc;
-  rc = grow_lane(b->cons_long, nj);
+  rc = grow_lane(b->cons_long, nj, st);
   if (rc) return rc;
   if (pool_need > b->pool_cap) {
-    cudaDeviceSynchronize();
-    cudaFree(b->d_pool);
+    dev_free(b->d_pool, st);
     b->d_pool = nullptr;
     b->pool_cap = 0;
     const size_t cap = pool_need + pool_need / 4;
-    if (cudaMalloc(&b->d_pool, cap) != cudaSuccess) {
+    if (dev_alloc(&b->d_pool, cap) != cudaSuccess) {
       cudaGetLastError();
       set_err("batch scratch pool of %zu bytes failed", cap);
       return VC_ERR_OOM;
@@ -1893,7 +2023,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       rc = ensure_ring(c, 2 * A + 1);
       if (rc) return rc;
       if (c->produced < c->frame + J.nframes) {
-        rc = produce(c, c->frame + J.nframes + A);
+        rc = produce(c, c->frame + J.nframes + A, b->ks_place);
         if (rc) return rc;
       }
       rc = poll_production(c);
@@ -1932,10 +2062,14 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
                    F0.variants, 0);
   if (rc) return rc;
   if (split) VC_CUDA(cudaStreamWaitEvent(st, b->join, 0));
+  VC_CUDA(cudaEventRecord(b->done, st));
   b->last_split = split ? F1.nj : 0;
   for (int k = 0; k < nj; k++) {
     const vc_job& J = jobs[live[k]];
     vc_ctx* c = J.ctx;
+    if (A > 0)
+      for (int64_t f = c->frame; f < c->frame + J.nframes; f++)
+        VC_CUDA(cudaEventRecord(c->ev_slot[f % c->ring_cap], st));
     c->frame += J.nframes;
     if (A == 0) {
       c->produced = c->frame;
@@ -1946,12 +2080,13 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     c->batch_pending = true;
   }
   // ---- top-ups: each stream's keystream back to A frames ahead, on its own
-  // internal stream, coalesced (not while its previous production runs) ----
+  // internal stream, queued behind the productions still running there (so
+  // that a long chain never idles between frames), a few at most ----
   if (A > 0) {
     for (int k = 0; k < nj; k++) {
       vc_ctx* c = jobs[live[k]].ctx;
-      if (c->produced >= c->frame + A || production_busy(c)) continue;
-      rc = produce(c, c->frame + A);
+      if (c->produced >= c->frame + A || productions_in_flight(c) >= vc_ctx::kProdEv / 2) continue;
+      rc = produce(c, c->frame + A, b->ks_place);
       if (rc) return rc;
     }
   }
@@ -1981,12 +2116,12 @@ int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
     // nothing (coalesced, like the top-ups)
     bool issued = false;
     if (c->produced < c->frame + 1) {
-      rc = produce(c, c->frame + 1);
+      rc = produce(c, c->frame + 1, b->ks_place);
       if (rc) return rc;
       issued = true;
     }
     if (c->produced < c->frame + A && (issued || !production_busy(c))) {
-      rc = produce(c, c->frame + A);
+      rc = produce(c, c->frame + A, b->ks_place);
       if (rc) return rc;
     }
   }
@@ -2009,7 +2144,8 @@ void vc_batcher_destroy(vc_batcher* b) {
   cudaDeviceSynchronize();
   free_lane(b->cons);
   free_lane(b->cons_long);
-  cudaFree(b->d_pool);
+  dev_free(b->d_pool, nullptr);
+  if (b->done) cudaEventDestroy(b->done);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->fork) cudaEventDestroy(b->fork);

@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <deque>
 #include <vector>
 
@@ -45,6 +46,7 @@ struct SrvFrame {
   int32_t id;
   int64_t frame;
   double arrival;
+  double submitted;  // host time of the tick that submitted it
 };
 
 struct SrvTick {
@@ -56,6 +58,7 @@ struct SrvTick {
   std::vector<cudaEvent_t> job_ev;
   std::vector<size_t> job_end;
   size_t taken = 0;  // frames already returned by a partial drain
+  double now = 0.0;  // host time of the submission
 };
 
 }  // namespace
@@ -76,6 +79,11 @@ struct vc_server {
   int64_t host_ticks = 0;
   double gpu_ms = 0;  // device time from a tick's first enqueued work to its completion, summed
   int64_t gpu_ticks = 0;
+  // latency records (vc_dbg_server_record): per frame (stream, arrival,
+  // submission, completion), per tick (submission, device start, device end,
+  // frames), seconds since creation
+  bool rec = false;
+  std::vector<double> rec_frames, rec_ticks;
 };
 
 namespace {
@@ -200,7 +208,7 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
     j.nframes = (int32_t)m;
     s->jobs.push_back(j);
     s->job_stream.push_back((int32_t)i);
-    for (int64_t k = 0; k < m; k++) tick.frames.push_back(SrvFrame{(int32_t)i, t.next + k, t.t_arr + (t.next + k) / t.fps});
+    for (int64_t k = 0; k < m; k++) tick.frames.push_back(SrvFrame{(int32_t)i, t.next + k, t.t_arr + (t.next + k) / t.fps, now});
     t.next += m;
   }
   s->host_ms[0] += ms_since(t_start);
@@ -257,6 +265,7 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
   }
   s->host_ms[3] += ms_since(t_start);
   if (frames_submitted) *frames_submitted = (int32_t)tick.frames.size();
+  tick.now = now;
   s->inflight.push_back(std::move(tick));
   return VC_OK;
 }
@@ -275,6 +284,10 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
     if (tk.taken == 0 && tk.ev0 && cudaEventElapsedTime(&dur, tk.ev0, tk.ev) == cudaSuccess) {
       s->gpu_ms += dur;
       s->gpu_ticks++;
+      if (s->rec) {
+        const double t = tk.now, e = ms / 1e3;
+        s->rec_ticks.insert(s->rec_ticks.end(), {t, e - dur / 1e3, e, (double)tk.frames.size()});
+      }
     }
     const double done_s = ms / 1e3;
     size_t q = 0;  // the job (stream) of frame tk.taken in one-call-per-frame mode
@@ -291,6 +304,7 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
       frames[n] = f.frame;
       arrival_s[n] = f.arrival;
       latency_ms[n] = (fdone - f.arrival) * 1e3;
+      if (s->rec) s->rec_frames.insert(s->rec_frames.end(), {(double)f.id, f.arrival, f.submitted, fdone});
       s->streams[f.id].done++;
       n++;
     }
@@ -338,6 +352,11 @@ int vc_server_remove(vc_server* s, int32_t id) {
 
 int32_t vc_server_inflight(const vc_server* s) { return s ? (int32_t)s->inflight.size() : 0; }
 
+int vc_server_set_option(vc_server* s, int32_t option, int64_t value) {
+  if (!s || s->mode != 0 || !s->b || option == VC_BOPT_RUNAHEAD) return VC_ERR_ARG;
+  return vc_batcher_set_option(s->b, option, value);
+}
+
 int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks) {
   if (!s || !ms6 || !ticks) return VC_ERR_ARG;
   for (int k = 0; k < 4; k++) {
@@ -350,6 +369,26 @@ int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks) {
   s->gpu_ticks = 0;
   *ticks = s->host_ticks;
   s->host_ticks = 0;
+  return VC_OK;
+}
+
+int vc_dbg_server_record(vc_server* s, int32_t enable) {
+  if (!s) return VC_ERR_ARG;
+  s->rec = enable != 0;
+  if (!s->rec) {
+    s->rec_frames.clear();
+    s->rec_ticks.clear();
+  }
+  return VC_OK;
+}
+
+int vc_dbg_server_take(vc_server* s, int32_t which, int32_t cap, double* out, int32_t* n) {
+  if (!s || !n || (which != 0 && which != 1) || cap < 0 || (cap > 0 && !out)) return VC_ERR_ARG;
+  std::vector<double>& v = which == 0 ? s->rec_frames : s->rec_ticks;
+  const size_t k = std::min<size_t>((size_t)cap, v.size() / 4);
+  std::copy(v.begin(), v.begin() + 4 * k, out);
+  v.erase(v.begin(), v.begin() + 4 * k);
+  *n = (int32_t)k;
   return VC_OK;
 }
 

@@ -217,6 +217,29 @@ class ServeResult:
     ticks: int = 0
     tick_host_ms: list = field(default_factory=list)  # host time of each loop iteration that submitted work
     native_ms: dict = field(default_factory=dict)      # host ms per part of the native ticks
+    frame_records: object = None  # [k, 4]: stream, arrival, submission, completion (s), when recorded
+    tick_records: object = None   # [m, 4]: submission, device start, device end (s), frames
+
+    def latency_split(self, steady_after_s: float = 0.0) -> dict:
+        """Per-frame latency split at the submission (frames arriving after
+        steady_after_s): the wait from arrival to the tick that submitted the
+        frame (frame clock, keystream readiness, tick cadence) and the device
+        time from that tick to completion; per tick, the device time and the
+        delay from submission to the device starting it."""
+        if self.frame_records is None or not len(self.frame_records):
+            return {}
+        fr = self.frame_records[self.frame_records[:, 1] >= steady_after_s]
+        tk = self.tick_records
+        q = lambda a, p: round(float(np.percentile(a, p)) * 1e3, 3) if len(a) else None
+        wait, dev = fr[:, 2] - fr[:, 1], fr[:, 3] - fr[:, 2]
+        out = {"frames": int(len(fr)), "wait_p50_ms": q(wait, 50), "wait_p99_ms": q(wait, 99),
+               "device_p50_ms": q(dev, 50), "device_p99_ms": q(dev, 99)}
+        if tk is not None and len(tk):
+            tk = tk[tk[:, 0] >= steady_after_s]
+            out.update({"ticks": int(len(tk)), "tick_device_p50_ms": q(tk[:, 2] - tk[:, 1], 50),
+                        "tick_device_p99_ms": q(tk[:, 2] - tk[:, 1], 99),
+                        "tick_queue_p99_ms": q(tk[:, 1] - tk[:, 0], 99)})
+        return out
 
     def summary(self, steady_after_s: float | None = None) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
@@ -265,13 +288,18 @@ class Server:
     def __init__(self, hbm_budget_bytes: int = 64 << 30, tick_ms: float = 4.0, mode: str = "batch",
                  max_frames_per_tick: int = 4, ring: int = 8, keep_outputs: bool = False,
                  cipher_options: dict | None = None, compute: ComputeBudget | None = None,
-                 setup_lead_s: float = 0.0, tuned: dict | None = None):
+                 setup_lead_s: float = 0.0, tuned: dict | None = None, record: bool = False,
+                 server_options: dict | None = None, priority: int = 0):
         """compute: admission also charges each stream's device load (None:
         HBM budget only).  setup_lead_s: a request is admitted this long
         before its first frame arrives (the session's setup), so its context
         and, when batching, its first frames' keystream exist by then.
         tuned: per shape class (kind, H, W, C) the options the autotuner
-        chose (tune_shapes), applied to each stream's context."""
+        chose (tune_shapes), applied to each stream's context.  record: keep
+        per-frame and per-tick latency records (ServeResult.latency_split).
+        server_options: batcher options (VC_BOPT_*) of a batching server.
+        priority: of the server's CUDA stream (torch's convention: lower is
+        more urgent)."""
         import torch
 
         self.torch = torch
@@ -284,13 +312,15 @@ class Server:
         self.mode = mode
         self.maxf = max_frames_per_tick
         self.ring = ring
-        self.stream = torch.cuda.Stream()
+        self.server_options = dict(server_options or {})
+        self.stream = torch.cuda.Stream(priority=priority)
 
         self.inputs = {}  # (H, W, C) -> device frames reused as input content
         from concurrent.futures import ThreadPoolExecutor
 
         self.pool = ThreadPoolExecutor(max_workers=2)
         self.keep = keep_outputs
+        self.record = record
         self.finished: list[Stream] = []  # kept when keep_outputs (tests)
 
     def _open(self, spec: dict, fp: int) -> Stream:
@@ -342,6 +372,11 @@ class Server:
         used = 0
         torch.cuda.synchronize()
         srv = B.NativeServer(0 if self.mode == "batch" else 1, self.maxf, self.stream)
+        if self.record:
+            srv.record(True)
+        if self.mode == "batch":
+            for opt, val in self.server_options.items():
+                srv.set_option(opt, val)
         t0 = time.perf_counter()  # the server's time origin was just recorded
         end_time = horizon_s if horizon_s is not None else max(
             (r["arrival"] + r["duration"] for r in requests), default=0.0)
@@ -412,7 +447,7 @@ class Server:
                         if self.keep:
                             self.finished.append(st)
                         else:
-                            st.cipher.close()
+                            st.cipher.close(wait=False)  # its frames are done; run-ahead keystream may still run
                 if not pending and not active and not starting and srv.inflight() == 0:
                     break
                 if now > end_time + 5.0:  # safety: stop a run that cannot keep up
@@ -423,6 +458,8 @@ class Server:
         finally:
             res.wall_s = time.perf_counter() - t0
             res.native_ms = srv.host_stats()
+            if self.record:
+                res.frame_records, res.tick_records = srv.take_records()
             for st in active.values():
                 if self.keep:
                     self.finished.append(st)
@@ -483,7 +520,7 @@ def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0
 def serve_mixed(mode: str, nstreams: int = 256, rate_per_s: float = 64.0, seed: int = 5,
                 targets=(0.8, 0.55, 0.4, 0.25, 0.15), budget_ms: float = 1000.0 / 24.0,
                 hbm_budget_bytes: int = 160 << 30, setup_lead_s: float = 0.1, rates: dict | None = None,
-                steady_after_s: float = 1.5) -> dict:
+                steady_after_s: float = 1.5, server_kw: dict | None = None) -> dict:
     """The mixed serving workload: nstreams requests arriving as a Poisson
     process (rate_per_s), resolutions 480^2 ... 3840x2160, 24 / 30 / 60 FPS,
     PLCM and 2DLASM alternating, half encrypt and half decrypt, n = ceil(H/4)
@@ -500,11 +537,12 @@ def serve_mixed(mode: str, nstreams: int = 256, rate_per_s: float = 64.0, seed: 
     runs, best = [], None
     for t in targets:
         srv = Server(hbm_budget_bytes=hbm_budget_bytes, mode=mode, compute=ComputeBudget(rates, target=t),
-                     setup_lead_s=setup_lead_s, tuned=tuned)
+                     setup_lead_s=setup_lead_s, tuned=tuned, record=True, **(server_kw or {}))
         res = srv.run(reqs)
         srv.close()
         summ = res.summary(steady_after_s=steady_after_s)
         summ["load_target"] = t
+        summ["split"] = res.latency_split(steady_after_s)
         runs.append(summ)
         if summ.get("steady_p99_ms", summ["p99_ms"]) < budget_ms:
             best = summ
@@ -516,15 +554,27 @@ def serve_mixed(mode: str, nstreams: int = 256, rate_per_s: float = 64.0, seed: 
             "load_target": best["load_target"] if best else None, "runs": runs}
 
 
-def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2, split: int = -1) -> dict:
+def batch_mix(nstreams: int = 64, ticks: int = 8, warm: int = 3, split: int = -1, rates: dict | None = None) -> dict:
     """Ragged batches against one call per frame.  nstreams streams, each with
     its own key, resolutions cycling 480^2, 576^2, 768^2 and 1920x1080
     (n = ceil(H/4)), maps and directions alternating, one frame per stream per
-    tick.  Batched: one vc_batch_submit per tick (one graph replay; keystream,
-    rounds and fix-up of every stream inside it).  Per frame: encrypt_frames /
-    decrypt_frames per stream, each stream on its own CUDA stream.  Device time
-    per tick by CUDA events after `warm` ticks; the outputs of the two forms
-    are compared byte for byte after the last tick."""
+    tick.  Four forms, each on its own contexts:
+
+    * batched_inline: one vc_batch_submit per tick with the keystream inside
+      it (one graph replay: schedule, keystream, rounds, fix-up of every
+      stream; long chains in the second lane per `split`);
+    * batched_runahead: one vc_batch_submit per tick of rounds only, each
+      stream's keystream produced one frame ahead on its own internal stream
+      (SM-holding CTAs for the streams whose chains the compute budget says
+      need them at 24 FPS);
+    * per_frame: encrypt_frames / decrypt_frames per stream, each on its own
+      CUDA stream, the next call's keystream generated ahead (the default);
+    * per_frame_inline: the same without that run-ahead.
+
+    Time per tick = host wall time over `ticks` ticks between two device-wide
+    synchronisations after `warm` ticks, so that keystream generated ahead on
+    the contexts' internal streams is counted in the tick that issued it.  The
+    outputs of the last tick are compared byte for byte across the forms."""
     import torch
 
     import synth
@@ -541,64 +591,93 @@ def batch_mix(nstreams: int = 64, ticks: int = 6, warm: int = 2, split: int = -1
             frames[(H, W)] = torch.from_numpy(synth.uniform_frames(1, H, W, 3, seed=H + W)).cuda()
     from . import autotune
 
-    # the autotuner's tile rows per shape class, the same for both forms
+    # the autotuner's tile rows per shape class, the same for every form
     tuned = {}
     for (k, d, key, H, W, n) in specs:
         if (k, H, W) not in tuned:
             tuned[(k, H, W)] = autotune.tune_rounds(k, H, W, 3, n)["options"]["tile_rows"]
-    batched = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
-    single = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
-    for c, (k, d, key, H, W, n) in zip(batched + single, specs + specs):
-        c.set_option(B.VC_OPT_TILE_ROWS, tuned[(k, H, W)])
-    out_b = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
-    out_s = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
-    streams = [torch.cuda.Stream() for _ in specs]
+    budget = ComputeBudget(rates or calibrate())
+    hold = {(k, H, W): budget.plan({"kind": k, "H": H, "W": W, "C": 3, "fps": 24})["hold"]
+            for (k, H, W) in tuned}
+
+    def contexts():
+        cs = [B.Cipher(k, key, H, W, 3, n, 5) for (k, d, key, H, W, n) in specs]
+        for c, (k, d, key, H, W, n) in zip(cs, specs):
+            c.set_option(B.VC_OPT_TILE_ROWS, tuned[(k, H, W)])
+        return cs
+
     main = torch.cuda.current_stream()
-    batcher = B.Batcher(graph=True)
-    B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SPLIT, split)
+    streams = [torch.cuda.Stream() for _ in specs]
 
-    def tick_batched():
-        batcher.submit([(c, sp[1], frames[(sp[3], sp[4])], out_b[j], 1) for j, (c, sp) in enumerate(zip(batched, specs))],
-                       stream=main)
+    def form_batched(runahead):
+        cs = contexts()
+        if runahead:
+            for c, (k, d, key, H, W, n) in zip(cs, specs):
+                if hold[(k, H, W)]:
+                    c.set_option(B.VC_OPT_KS_SM_WARPS, hold[(k, H, W)])
+        out = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
+        batcher = B.Batcher(graph=True, runahead=runahead)
+        B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SPLIT, split)
 
-    def tick_single():
-        ev = torch.cuda.Event()
-        ev.record(main)
-        for j, (c, sp) in enumerate(zip(single, specs)):
-            st = streams[j]
-            st.wait_event(ev)
-            x = frames[(sp[3], sp[4])]
-            if sp[1] == 0:
-                c.encrypt(x, out_s[j], stream=st)
-            else:
-                c.decrypt(x, out_s[j], stream=st)
-        for st in streams:
-            main.wait_stream(st)
+        def tick():
+            batcher.submit([(c, sp[1], frames[(sp[3], sp[4])], out[j], 1) for j, (c, sp) in enumerate(zip(cs, specs))],
+                           stream=main)
+        return cs, out, tick, batcher
+
+    def form_single(runahead):
+        cs = contexts()
+        if not runahead:
+            for c in cs:
+                c.set_option(B.VC_OPT_RUNAHEAD_CALLS, 0)
+        out = [torch.empty_like(frames[(H, W)]) for (_, _, _, H, W, _) in specs]
+
+        def tick():
+            ev = torch.cuda.Event()
+            ev.record(main)
+            for j, (c, sp) in enumerate(zip(cs, specs)):
+                st = streams[j]
+                st.wait_event(ev)
+                x = frames[(sp[3], sp[4])]
+                if sp[1] == 0:
+                    c.encrypt(x, out[j], stream=st)
+                else:
+                    c.decrypt(x, out[j], stream=st)
+            for st in streams:
+                main.wait_stream(st)
+        return cs, out, tick, None
 
     def timed(fn):
         for _ in range(warm):
             fn()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(main)
+        t0 = time.perf_counter()
         for _ in range(ticks):
             fn()
-        b.record(main)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / ticks
+        return (time.perf_counter() - t0) * 1e3 / ticks
 
-    ms_b = timed(tick_batched)
-    long_jobs = B.lib().vc_dbg_batch_split(batcher.b)
-    ms_s = timed(tick_single)
-    same = all(torch.equal(x, y) for x, y in zip(out_b, out_s))
+    ms, outs, long_jobs = {}, {}, 0
+    for name, make, arg in (("batched_inline", form_batched, 0), ("batched_runahead", form_batched, 1),
+                            ("per_frame", form_single, True), ("per_frame_inline", form_single, False)):
+        cs, out, tick, batcher = make(arg)
+        ms[name] = timed(tick)
+        if name == "batched_inline":
+            long_jobs = B.lib().vc_dbg_batch_split(batcher.b)
+        outs[name] = out
+        if batcher is not None:
+            batcher.close()
+        for c in cs:
+            c.close()
+    ref = outs["per_frame"]
+    same = {k: all(torch.equal(x, y) for x, y in zip(v, ref)) for k, v in outs.items()}
     px = sum(H * W for (_, _, _, H, W, _) in specs)
-    batcher.close()
-    for c in batched + single:
-        c.close()
     return {"streams": nstreams, "resolutions": ["480x480", "576x576", "768x768", "1080x1920"],
-            "batched_ms_per_tick": round(ms_b, 3), "per_frame_ms_per_tick": round(ms_s, 3),
-            "batched_mpixel_s": round(px / ms_b / 1e3, 1), "per_frame_mpixel_s": round(px / ms_s / 1e3, 1),
-            "outputs_equal": bool(same), "batch_long_lane_jobs": int(long_jobs),
+            "ticks": ticks, "timing": "host wall time between device-wide synchronisations",
+            "ms_per_tick": {k: round(v, 3) for k, v in ms.items()},
+            "mpixel_s": {k: round(px / v / 1e3, 1) for k, v in ms.items()},
+            "batched_ms_per_tick": round(ms["batched_inline"], 3), "per_frame_ms_per_tick": round(ms["per_frame"], 3),
+            "outputs_equal": bool(all(same.values())), "batch_long_lane_jobs": int(long_jobs),
+            "held_keystream": {f"{k}:{H}x{W}": v for (k, H, W), v in hold.items() if v},
             "tuned_tile_rows": {f"{k}:{H}x{W}": v for (k, H, W), v in tuned.items()}}
 
 
@@ -625,7 +704,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--batch-mix", type=int, default=0, metavar="N",
                     help="instead: N streams of mixed resolutions, one batch per tick against one call per frame")
-    ap.add_argument("--ticks", type=int, default=6, help="timed ticks of --batch-mix")
+    ap.add_argument("--ticks", type=int, default=8, help="timed ticks of --batch-mix")
     ap.add_argument("--split", type=int, default=-1, help="VC_BOPT_SPLIT of --batch-mix")
     ap.add_argument("--mixed", action="store_true",
                     help="instead: the mixed Poisson workload with compute-aware admission (both modes)")

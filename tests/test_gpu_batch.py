@@ -130,6 +130,36 @@ def test_batch_long_chain_lane_equals_solo_runs(B, split):
     batcher.close()
 
 
+@pytest.mark.parametrize("split", [-1, 0, 1])
+def test_batch_of_alike_jobs_equals_solo_runs(B, split):
+    """A batch whose jobs all have chains of the same length (one shape, one
+    map; keystream inline): whatever VC_BOPT_SPLIT says, every job runs (in
+    one lane, or with the longest in the second lane when forced) and equals
+    its stream run alone."""
+    shape = (1, 48, 64, 3, 6)
+    k, H, W, C, n = shape
+    batcher = B.Batcher(graph=True)
+    B.vc_batcher_set_option(batcher.b, B.VC_BOPT_SPLIT, split)
+    mixed = [B.Cipher(k, synth.key_for_seed(k, 840 + i), H, W, C, n) for i in range(4)]
+    solo = [B.Cipher(k, synth.key_for_seed(k, 840 + i), H, W, C, n) for i in range(4)]
+    for tick in range(2):
+        jobs, outs, refs = [], [], []
+        for i in range(4):
+            x = torch.from_numpy(synth.uniform_frames(1, H, W, C, seed=850 + 10 * tick + i)).cuda()
+            y = torch.full_like(x, 7)
+            jobs.append((mixed[i], i % 2, x, y, 1))
+            outs.append(y)
+            refs.append(solo[i].encrypt(x) if i % 2 == 0 else solo[i].decrypt(x))
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for i in range(4):
+            assert torch.equal(outs[i], refs[i]), f"tick {tick}, stream {i}"
+        assert B.lib().vc_dbg_batch_split(batcher.b) == (1 if split == 1 else 0)
+    for c in mixed + solo:
+        c.close()
+    batcher.close()
+
+
 def test_batch_round_trip_and_mixing_with_single_calls(B, orc):
     """Encrypt in a batch, continue the same contexts with single-stream calls,
     then decrypt everything in a batch; the oracle agrees on the ciphertext."""
