@@ -247,15 +247,18 @@ def serving_capacity() -> dict:
     * mixed: 256 streams arriving as a Poisson process (64/s), 480^2 ...
       3840x2160, 24/30/60 FPS, half 2DLASM, half decrypt, admitted by HBM
       budget and compute-aware admission (calibrated device rates), with the
-      admitted streams' steady p99 and first-frame p99."""
+      admitted streams' steady p99, first-frame p99 and the latency split at
+      submission (wait for the frame clock and keystream / device time);
+    * batch_mix: 64 streams of 480^2 ... 1920x1080, one frame each per tick,
+      as one ragged batch per tick against one call per frame."""
     from paper_2302_07411_gb300 import serve
 
     out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
-    b = serve.capacity("batch", 768, 768, counts=(128, 192, 224, 256, 288, 320), seconds=3.0)
-    p = serve.capacity("perframe", 768, 768, counts=(32, 64, 96, 128, 160, 192, 224, 256), seconds=2.5)
+    b = serve.capacity("batch", 768, 768, counts=(192, 256, 320, 352, 384, 448), seconds=3.0)
+    p = serve.capacity("perframe", 768, 768, counts=(64, 96, 128, 160, 192, 256), seconds=2.5)
     # the same with PLCM streams only (2DLASM keystream is binary64-bound and
     # about eight times the work of PLCM per frame)
-    bp = serve.capacity("batch", 768, 768, counts=(512, 640, 768, 896), seconds=3.0, kinds=(0,))
+    bp = serve.capacity("batch", 768, 768, counts=(640, 768, 896, 1024), seconds=3.0, kinds=(0,))
     out["batched_streams"] = b["max_streams"]
     out["per_frame_streams"] = p["max_streams"]
     out["batched_streams_plcm_only"] = bp["max_streams"]
@@ -273,9 +276,11 @@ def serving_capacity() -> dict:
     for mode in ("batch", "perframe"):
         r = serve.serve_mixed(mode, rates=rates)
         mixed[mode] = {"admitted_within_budget": r["admitted_within_budget"], "load_target": r["load_target"],
-                       "runs": [{k: x.get(k) for k in keep} for x in r["runs"]]}
+                       "runs": [dict({k: x.get(k) for k in keep}, latency_split=x.get("split")) for x in r["runs"]]}
     mixed["workload"] = "256 Poisson streams (64/s), 480^2..3840x2160, 24/30/60 FPS, half 2DLASM, half decrypt"
     out["mixed"] = mixed
+    # ragged batch against one call per frame, 64 streams of mixed resolutions
+    out["batch_mix"] = serve.batch_mix(64, rates=rates)
     return out
 
 

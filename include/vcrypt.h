@@ -214,6 +214,12 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  *                      (VC_OPT_KS_SM_WARPS, -1 automatic: CTAs that hold
  *                      whole SMs when they leave enough SMs free).  A context
  *                      with VC_OPT_KS_SM_WARPS > 0 holds SMs in both.
+ * VC_BOPT_KS_PRIORITY: the stream priority of the keystream produced ahead:
+ *                      0 (default) the device's highest (a chain that starts
+ *                      late delays every frame behind it), 1 its lowest (the
+ *                      batches' round kernels, on a stream of higher priority,
+ *                      take the SMs that free up first).  It applies to the
+ *                      streams whose first production comes after it is set.
  * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
@@ -221,6 +227,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
 #define VC_BOPT_SINE 4
 #define VC_BOPT_SPLIT 5
 #define VC_BOPT_KS_PLACE 6
+#define VC_BOPT_KS_PRIORITY 7
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
@@ -285,9 +292,14 @@ int vc_server_drain(vc_server* s, int32_t block, int32_t cap, int32_t* ids, int6
 int vc_server_stream_done(const vc_server* s, int32_t id);
 int vc_server_remove(vc_server* s, int32_t id);
 int32_t vc_server_inflight(const vc_server* s);
-/* vc_server_set_option: a batcher option (VC_BOPT_*) of a batching server
- * (mode 0); the run-ahead is the server's max_frames_per_tick and cannot be
- * set.  Errors: VC_ERR_ARG (mode 1, VC_BOPT_RUNAHEAD, bad option or value). */
+/* vc_server_set_option: an option of a batching server (mode 0): a batcher
+ * option (VC_BOPT_*; the run-ahead is the server's max_frames_per_tick and
+ * cannot be set), or VC_SOPT_QUEUED_TICKS: q > 0 submits a tick only while
+ * fewer than q earlier ticks wait for the device to start them (a tick that
+ * would queue deeper submits nothing, and its frames join the next, larger
+ * batch); 0 (default) submits every tick.  Errors: VC_ERR_ARG (mode 1,
+ * VC_BOPT_RUNAHEAD, bad option or value). */
+#define VC_SOPT_QUEUED_TICKS 100
 int vc_server_set_option(vc_server* s, int32_t option, int64_t value);
 void vc_server_destroy(vc_server* s);
 

@@ -234,6 +234,9 @@ struct vc_ctx {
   // per ring slot: recorded after the batch that read it, so that a production
   // overwriting the slot waits for that batch and for no later one
   std::vector<cudaEvent_t> ev_slot;
+  // the productions' stream (created with the ring, at the priority the
+  // batcher asks for: VC_BOPT_KS_PRIORITY)
+  cudaStream_t prod_stream = nullptr;
   int64_t produced = 0;
   // productions of the ring run on ks_stream; the last eight are tracked so
   // that readiness can be polled without blocking
@@ -285,6 +288,7 @@ namespace {
 void sync_all(vc_ctx* c) {
   if (c->last) cudaStreamSynchronize(c->last);
   if (c->ks_stream) cudaStreamSynchronize(c->ks_stream);
+  if (c->prod_stream) cudaStreamSynchronize(c->prod_stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
@@ -297,7 +301,7 @@ cudaStream_t ctx_join(vc_ctx* c) {
     sync_all(c);
     return nullptr;
   }
-  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream})
+  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream, c->prod_stream})
     if (o && o != ks && cudaEventRecord(c->ev_free, o) == cudaSuccess) cudaStreamWaitEvent(ks, c->ev_free, 0);
   return ks;
 }
@@ -1189,6 +1193,7 @@ void destroy_ctx(vc_ctx* c, bool wait) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
   if (c->ks_stream) cudaStreamDestroy(c->ks_stream);
+  if (c->prod_stream) cudaStreamDestroy(c->prod_stream);
   for (int b = 0; b < 2; b++) {
     if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
     if (c->ev_rd[b]) cudaEventDestroy(c->ev_rd[b]);
@@ -1462,6 +1467,7 @@ struct vc_batcher {
   int split = -1;    // long-chain lane: -1 automatic, 0 never, 1 whenever the jobs differ
   int last_split = 0;  // jobs the last batch ran in the long-chain lane
   int ks_place = 0;    // run-ahead productions: 0 shared SMs, 1 as the context's own calls place them
+  bool ks_low = false;  // run-ahead productions at the device's lowest stream priority (else its highest)
   BatchLane cons_long;  // the long-chain lane (its own staging and graphs)
   cudaStream_t side = nullptr;  // the long-chain lane's stream
   cudaEvent_t fork = nullptr, join = nullptr, long_up = nullptr;
@@ -1537,7 +1543,14 @@ size_t job_scratch_bytes(const Layout& L, int nf, bool with_keystream) {
   return b;
 }
 
-int ensure_ring(vc_ctx* c, int cap) {
+// A keystream ring of `cap` frame slots; the first one also makes the
+// productions' stream (low_priority: the device's lowest, else its highest).
+int ensure_ring(vc_ctx* c, int cap, bool low_priority) {
+  if (!c->prod_stream) {
+    int least = 0, greatest = 0;
+    VC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    VC_CUDA(cudaStreamCreateWithPriority(&c->prod_stream, cudaStreamNonBlocking, low_priority ? least : greatest));
+  }
   if (c->ring_cap >= cap) return VC_OK;
   if (c->ring_cap > 0 && c->produced != c->frame) {
     set_err("cannot grow a keystream ring that holds frames");
@@ -1610,10 +1623,13 @@ int productions_in_flight(vc_ctx* c) {
 int produce(vc_ctx* c, int64_t target, int place) {
   if (c->produced >= target) return VC_OK;
   vc::NvtxRange range("vc.keystream");
-  cudaStream_t ks = c->ks_stream;
-  if (c->produced == c->frame && c->last && !c->batch_pending) {  // single-stream work on this context first
-    VC_CUDA(cudaEventRecord(c->ev_entry, c->last));
-    VC_CUDA(cudaStreamWaitEvent(ks, c->ev_entry, 0));
+  cudaStream_t ks = c->prod_stream;
+  if (c->produced == c->frame && !c->batch_pending) {  // single-stream work on this context first
+    for (cudaStream_t o : {c->last, c->ks_stream})
+      if (o) {
+        VC_CUDA(cudaEventRecord(c->ev_entry, o));
+        VC_CUDA(cudaStreamWaitEvent(ks, c->ev_entry, 0));
+      }
   }
   // the slots about to be overwritten: after the batches that read them (a slot
   // no batch has read yet has an event never recorded: no wait)
@@ -1791,6 +1807,10 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
     case VC_BOPT_KS_PLACE:
       if (value != 0 && value != 1) return VC_ERR_ARG;
       b->ks_place = (int)value;
+      return VC_OK;
+    case VC_BOPT_KS_PRIORITY:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      b->ks_low = value == 1;
       return VC_OK;
   }
   return VC_ERR_ARG;
@@ -2020,7 +2040,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     if (A > 0) {
       // frames not produced yet are produced now (with the look-ahead); the
       // batch waits only if its frames are not known to be complete
-      rc = ensure_ring(c, 2 * A + 1);
+      rc = ensure_ring(c, 2 * A + 1, b->ks_low);
       if (rc) return rc;
       if (c->produced < c->frame + J.nframes) {
         rc = produce(c, c->frame + J.nframes + A, b->ks_place);
@@ -2109,7 +2129,7 @@ int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
     }
     int rc = spec_rollback(c);
     if (rc) return rc;
-    rc = ensure_ring(c, 2 * A + 1);
+    rc = ensure_ring(c, 2 * A + 1, b->ks_low);
     if (rc) return rc;
     // the next frame on its own (ready soonest), then the rest of the run-ahead
     // queued behind it; a repeated call while a production is in flight adds

@@ -84,6 +84,11 @@ struct vc_server {
   // frames), seconds since creation
   bool rec = false;
   std::vector<double> rec_frames, rec_ticks;
+  // batching: a tick is submitted only while fewer than this many submitted
+  // ticks wait for the device to start them (0: every tick); the frames of a
+  // skipped tick go into the next, larger batch
+  int max_queued = 0;
+  int64_t skipped = 0;
 };
 
 namespace {
@@ -174,6 +179,22 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
   s->starved.clear();
   auto t_start = std::chrono::steady_clock::now();
   s->host_ticks++;
+  if (s->mode == 0 && s->max_queued > 0) {
+    int queued = 0;
+    for (auto it = s->inflight.rbegin(); it != s->inflight.rend() && queued < s->max_queued; ++it) {
+      const cudaError_t e = cudaEventQuery(it->ev0);
+      if (e == cudaErrorNotReady) {
+        queued++;
+        continue;
+      }
+      if (e != cudaSuccess) return VC_ERR_CUDA;
+      break;  // earlier ticks started before this one
+    }
+    if (queued >= s->max_queued) {
+      s->skipped++;
+      return VC_OK;
+    }
+  }
   SrvTick tick;
   for (size_t i = 0; i < s->streams.size(); i++) {
     SrvStream& t = s->streams[i];
@@ -354,6 +375,11 @@ int32_t vc_server_inflight(const vc_server* s) { return s ? (int32_t)s->inflight
 
 int vc_server_set_option(vc_server* s, int32_t option, int64_t value) {
   if (!s || s->mode != 0 || !s->b || option == VC_BOPT_RUNAHEAD) return VC_ERR_ARG;
+  if (option == VC_SOPT_QUEUED_TICKS) {
+    if (value < 0 || value > 64) return VC_ERR_ARG;
+    s->max_queued = (int)value;
+    return VC_OK;
+  }
   return vc_batcher_set_option(s->b, option, value);
 }
 
