@@ -323,6 +323,15 @@ int64_t enc_frame_index(const vc_ctx* ctx);
  * by its device code or its asynchronous CUDA work (VC_OK if none); clears it. */
 int enc_sync_status(vc_ctx* ctx);
 
+/* Make `stream` wait, on the device (the host does not block), for all work
+ * the context has enqueued so far on its internal streams: the keystream
+ * generated ahead for the next call (VC_OPT_RUNAHEAD_CALLS), a batcher's
+ * productions, the copies of host-buffer calls.  An event recorded on
+ * `stream` afterwards therefore marks the end of everything the context's
+ * calls so far have set going (e.g. to time a run of calls).
+ * Errors: VC_ERR_ARG, VC_ERR_CUDA. */
+int enc_join(vc_ctx* ctx, void* stream);
+
 /* ---- tuning options (enc_set_option / enc_get_option) ----
  * VC_OPT_CHUNK:    frames per internal pass (same as enc_set_chunk), 1..65535.
  * VC_OPT_PLCM_INT: 1 (default) evaluates the PLCM division and subtraction of

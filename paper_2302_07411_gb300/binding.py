@@ -82,6 +82,7 @@ def lib():
             "enc_sync_status": (C.c_int, [p]),
             "enc_set_chunk": (C.c_int, [p, i32]),
             "enc_destroy": (None, [p]),
+            "enc_join": (C.c_int, [p, p]),
             "enc_destroy_async": (None, [p]),
             "enc_profile_enable": (C.c_int, [p, i32]),
             "enc_profile_read": (C.c_int, [p, p, p]),
@@ -236,6 +237,11 @@ def enc_profile_read(ctx) -> dict:
     _check(lib().enc_profile_read(ctx, ms, ln), "enc_profile_read")
     names = ("schedule", "keystream", "rounds")
     return {nm: {"ms": ms[i], "launches": ln[i]} for i, nm in enumerate(names)}
+
+
+def enc_join(ctx, stream=None) -> None:
+    """`stream` waits on the device for the context's internal streams."""
+    _check(lib().enc_join(ctx, _stream(stream)), "enc_join")
 
 
 def enc_destroy(ctx) -> None:

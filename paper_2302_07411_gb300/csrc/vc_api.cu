@@ -1029,11 +1029,23 @@ int enc_sync_status(vc_ctx* c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
   if (e == cudaSuccess && c->d2h_stream) e = cudaStreamSynchronize(c->d2h_stream);
   if (e == cudaSuccess && c->ks_stream) e = cudaStreamSynchronize(c->ks_stream);
+  if (e == cudaSuccess && c->prod_stream) e = cudaStreamSynchronize(c->prod_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_err("asynchronous CUDA error: %s", cudaGetErrorString(e));
     return VC_ERR_CUDA;
   }
+  return VC_OK;
+}
+
+int enc_join(vc_ctx* c, void* stream) {
+  if (!c) return VC_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (cudaStream_t o : {c->ks_stream, c->prod_stream, c->copy_stream, c->d2h_stream})
+    if (o && o != st) {
+      VC_CUDA(cudaEventRecord(c->ev_free, o));
+      VC_CUDA(cudaStreamWaitEvent(st, c->ev_free, 0));
+    }
   return VC_OK;
 }
 

@@ -58,6 +58,7 @@ def test_argument_validation_without_gpu(cudalib):
     assert L.enc_init(None, None, None) == 1
     assert L.encrypt_frames(None, None, None, 1, None) == 1
     assert L.enc_set_chunk(None, 4) == 1
+    assert L.enc_join(None, None) == 1
     assert L.enc_sync_status(None) == 1
 
 
