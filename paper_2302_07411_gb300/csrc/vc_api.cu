@@ -293,6 +293,17 @@ void sync_all(vc_ctx* c) {
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
 
+// The per-channel round CTA (word carries and seeds) fits the device's shared
+// memory per block.
+bool pc_smem_fits(const vc_ctx* c, const Layout* L2 = nullptr) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev) != cudaSuccess) {
+    cudaGetLastError();
+    optin = 48 * 1024;
+  }
+  return vc::round_smem_bytes(L2 ? *L2 : c->L, true) <= (size_t)optin;
+}
+
 // ks_stream after everything enqueued so far on the context's other streams
 // (its buffers are given back to the pool there, in stream order).
 cudaStream_t ctx_join(vc_ctx* c) {
@@ -348,7 +359,7 @@ int ensure_scratch(vc_ctx* c, int frames) {
     ok = dev_alloc(&c->d_ks[b], F * L.rounds * L.Npad) == cudaSuccess &&
          dev_alloc(&c->d_sc[b], F * sizeof(long long)) == cudaSuccess &&
          dev_alloc(&c->d_kmod[b], F * L.H * sizeof(int)) == cudaSuccess &&
-         dev_alloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && dev_alloc(&c->d_agg[b], F * L.NS + 16) == cudaSuccess;
+         dev_alloc(&c->d_buf[b], F * L.Npad) == cudaSuccess && dev_alloc(&c->d_agg[b], F * L.NS * 4 + 16) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -501,25 +512,7 @@ int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint
   const uint8_t* ksb = c->d_ks[b] + (long long)f_off * ks_stride;
   const int* kmod = c->d_kmod[b] + (long long)f_off * L.H;
   const int r = L.rounds;
-  if (c->diff_pc) {  // per-channel chains: one kernel per round, alternating buffers
-    StageMark rounds_mark(c, st, 2, r);
-    const bool bounce = (r == 1) && (in == out);  // a round cannot write over its own input
-    uint8_t* final_out = bounce ? c->d_buf[0] : out;
-    const long long final_stride = bounce ? L.Npad : out_stride;
-    for (int step = 0; step < r; step++) {
-      const uint8_t* src = step == 0 ? in : c->d_buf[(step - 1) & 1];
-      const long long ss = step == 0 ? in_stride : L.Npad;
-      uint8_t* dst = step == r - 1 ? final_out : c->d_buf[step & 1];
-      const long long ds = step == r - 1 ? final_stride : L.Npad;
-      const int j = dir == 0 ? step : r - 1 - step;
-      VC_CUDA(vc::launch_pc_round(dir == 0, L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
-                                  nf, st));
-    }
-    if (bounce)
-      VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
-                                cudaMemcpyDeviceToDevice, st));
-    return VC_OK;
-  }
+  const bool pc = c->diff_pc;  // per-channel chains (the same kernels, word carries)
   StageMark rounds_mark(c, st, 2, r + (dir == 0 ? 1 : 0));
   // with one round and in == out, the round cannot write its own input: go through a buffer
   const bool bounce = (r == 1) && (in == out);
@@ -533,13 +526,14 @@ int rounds_pass(vc_ctx* c, int dir, const uint8_t* in, long long in_stride, uint
     if (dir == 0) {
       const int j = step;
       VC_CUDA(vc::launch_enc_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod,
-                                   step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st));
+                                   step == 0 ? nullptr : c->d_agg[(step - 1) & 1], c->d_agg[step & 1], nf, st, pc));
     } else {
       const int j = r - 1 - step;
-      VC_CUDA(vc::launch_dec_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod, nf, st));
+      VC_CUDA(
+          vc::launch_dec_round(L, tb, src, ss, dst, ds, ksb + (long long)j * L.Npad, ks_stride, kmod, nf, st, pc));
     }
   }
-  if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st));
+  if (dir == 0) VC_CUDA(vc::launch_enc_fixup(L, tb, final_out, final_stride, c->d_agg[(r - 1) & 1], nf, st, pc));
   if (bounce)
     VC_CUDA(cudaMemcpy2DAsync(out, (size_t)out_stride, c->d_buf[0], (size_t)L.Npad, (size_t)L.N, (size_t)nf,
                               cudaMemcpyDeviceToDevice, st));
@@ -1111,6 +1105,11 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
         set_err("per-channel diffusion needs at least 2 pixels in every subframe");
         return VC_ERR_LAYOUT;
       }
+      if (value == 1 && !pc_smem_fits(c)) {
+        set_err("per-channel diffusion of this layout needs %zu bytes of shared memory per round CTA",
+                vc::round_smem_bytes(c->L, true));
+        return VC_ERR_LAYOUT;
+      }
       c->diff_pc = value == 1;
       return VC_OK;
     case VC_OPT_RUNAHEAD_CALLS: {
@@ -1138,6 +1137,11 @@ int enc_set_option(vc_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && (value < 1 || value > 32 || (value & (value - 1)))) return VC_ERR_ARG;
       Layout L2{};
       if (make_layout(c->user_layout, &L2, (int)value) != VC_OK) return VC_ERR_ARG;
+      if (c->diff_pc && !pc_smem_fits(c, &L2)) {
+        set_err("per-channel diffusion with %d tile rows needs %zu bytes of shared memory per round CTA", (int)value,
+                vc::round_smem_bytes(L2, true));
+        return VC_ERR_LAYOUT;
+      }
       int rs = spec_rollback(c);
       if (rs) return rs;
       sync_all(c);
@@ -1295,7 +1299,7 @@ int vc_dbg_layout(const vc_ctx* c, int32_t* out8) {
   out8[4] = c->L.P;
   out8[5] = c->cap;
   out8[6] = c->chunk > 0 ? c->chunk : pass_frames(c, 1 << 20);
-  out8[7] = (int32_t)vc::round_smem_bytes(c->L);
+  out8[7] = (int32_t)vc::round_smem_bytes(c->L, c->diff_pc);
   return VC_OK;
 }
 

@@ -148,21 +148,22 @@ cudaError_t launch_keystream(int kind, const Layout& L, Tables tb, Chains ch, in
                              int plcm_int, cudaStream_t st, int cap = 0, int slot0 = 0, int sm_warps = 0);
 cudaError_t launch_keystream_thread(int kind, const Layout& L, Tables tb, Chains ch, int nframes, uint8_t* ks,
                                     int plcm_int, cudaStream_t st);
+// The round kernels.  pc: per-channel diffusion chains (the alternative
+// reading of Eq. 3 / Eq. 4: byte ch of a pixel chains to byte ch of the
+// previous pixel, carries and aggregates one word per sub-tile) instead of one
+// chain over the subframe's bytes; with C = 1 the two are the same.  The
+// aggregate buffers hold NS bytes per frame (NS words with pc).  A round's
+// in and out must not overlap.
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
-                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st);
+                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st, bool pc = false);
 cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
-                             int nframes, cudaStream_t st);
+                             int nframes, cudaStream_t st, bool pc = false);
 cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
-                             int nframes, cudaStream_t st);
-// One round of the per-channel diffusion variant: encrypt = Eq. 1 and Eq. 3
-// per channel, decrypt = Eq. 4 per channel and Eq. 2, each one kernel.  in and
-// out must not overlap.
-cudaError_t launch_pc_round(bool encrypt, const Layout& L, Tables tb, const uint8_t* in, long long in_stride,
-                            uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
-                            const int* kmod, int nframes, cudaStream_t st);
-size_t round_smem_bytes(const Layout& L);  // encryption round CTA (the largest of the round kernels)
+                             int nframes, cudaStream_t st, bool pc = false);
+// encryption round CTA (the largest of the round kernels)
+size_t round_smem_bytes(const Layout& L, bool pc = false);
 cudaError_t prepare_batch_kernels(size_t smem);
 cudaError_t batch_ctas_per_sm(size_t smem, int* ctas);
 cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchShape& sh, cudaStream_t st);

@@ -1020,48 +1020,92 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
   return x;
 }
 
-// s_carry[s] = true ciphertext byte at the last byte of sub-tile s-1, for all
-// NS sub-tiles of the frame, by every warp of the block: warp w scans its
-// share [s0, s1) of the aggregates relative to the share's start, the shares'
-// totals (s_tot, one word per warp) then give each share its incoming value,
-// which the entries before the share's first subframe start still miss.  Ends
-// with a barrier; every thread of the block must call it.
+// Carries of the two diffusion readings: a byte per chain for R4 (one chain
+// over the subframe's bytes), a pixel word for R4' (one chain per channel,
+// the C bytes of a pixel side by side).  A scan element holds the XOR value
+// and, above it, the flag "a subframe start lies in the span".
+template <bool PC>
+struct CarryT {
+  using V = uint32_t;  // scan element: bit 8 flag, bits 0..7 value
+  using E = uint8_t;   // stored carry / aggregate
+  static constexpr V F = 0x100u, M = 0xFFu;
+};
+template <>
+struct CarryT<true> {
+  using V = uint64_t;  // bit 32 flag, bits 0..31 value
+  using E = uint32_t;
+  static constexpr V F = 1ull << 32, M = 0xFFFFFFFFull;
+};
+
+template <bool PC>
+__device__ __forceinline__ typename CarryT<PC>::V seg_comb(typename CarryT<PC>::V a, typename CarryT<PC>::V b) {
+  using T = CarryT<PC>;
+  return (b & T::F) ? b : ((a & T::F) | ((a ^ b) & T::M));
+}
+
+template <bool PC>
+__device__ __forceinline__ typename CarryT<PC>::V warp_scan_t(typename CarryT<PC>::V x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const typename CarryT<PC>::V o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x = seg_comb<PC>(o, x);
+  }
+  return x;
+}
+
+// s_carry[s] = true ciphertext value (R4: byte, R4': pixel word) at the end of
+// sub-tile s-1, for all NS sub-tiles of the frame, by every warp of the block:
+// warp w scans its share [s0, s1) of the aggregates relative to the share's
+// start, the shares' totals (s_tot, one element per warp) then give each share
+// its incoming value, which the entries before the share's first subframe
+// start still miss.  Ends with a barrier; every thread of the block must call
+// it.
 __device__ __forceinline__ bool sub_flag(const Layout& L, const Tables& tb, int s, int rowb) {
   return __ldg(&tb.fixlim[s]) < min(L.H, (s + 1) * L.R) * rowb;  // a subframe starts in sub-tile s
 }
 
-__device__ void sub_carries(const Layout& L, const Tables& tb, const uint8_t* agg, uint8_t* s_carry,
-                            uint32_t* s_tot) {
+template <bool PC>
+__device__ void sub_carries_t(const Layout& L, const Tables& tb, const typename CarryT<PC>::E* agg,
+                              typename CarryT<PC>::E* s_carry, typename CarryT<PC>::V* s_tot) {
+  using T = CarryT<PC>;
+  using V = typename T::V;
+  using E = typename T::E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int rowb = L.W * L.C;
   const int share = (((L.NS + nw - 1) / nw) + 31) & ~31;
   const int s0 = min(L.NS, warp * share), s1 = min(L.NS, s0 + share);
-  uint32_t run = 0;
+  V run = 0;
   for (int base = s0; base < s1; base += 32) {
     const int s = base + lane;
-    uint32_t x = 0;
-    if (s < s1) x = (sub_flag(L, tb, s, rowb) ? 0x100u : 0u) | (uint32_t)agg[s];
-    x = seg_combine(run, warp_incl_scan(x));
-    if (s < s1 && s + 1 < L.NS) s_carry[s + 1] = (uint8_t)x;
+    V x = 0;
+    if (s < s1) x = (sub_flag(L, tb, s, rowb) ? T::F : (V)0) | (V)agg[s];
+    x = seg_comb<PC>(run, warp_scan_t<PC>(x));
+    if (s < s1 && s + 1 < L.NS) s_carry[s + 1] = (E)x;
     run = __shfl_sync(0xFFFFFFFFu, x, 31);
   }
   if (lane == 0) s_tot[warp] = run;
   __syncthreads();
-  uint32_t in = 0;  // value at the end of sub-tile s0 - 1
-  for (int k = 0; k < warp; k++) in = seg_combine(in, s_tot[k]);
-  if ((in & 0xFFu) != 0) {
+  V in = 0;  // value at the end of sub-tile s0 - 1
+  for (int k = 0; k < warp; k++) in = seg_comb<PC>(in, s_tot[k]);
+  if ((in & T::M) != 0) {
     for (int base = s0; base < s1; base += 32) {
       const int s = base + lane;
       const bool flag = s < s1 && sub_flag(L, tb, s, rowb);
       const uint32_t fl = __ballot_sync(0xFFFFFFFFu, flag);
       // entries whose share holds no start at or before them are relative
       const bool rel = s < s1 && (fl & (0xFFFFFFFFu >> (31 - lane))) == 0;
-      if (rel && s + 1 < L.NS) s_carry[s + 1] ^= (uint8_t)(in & 0xFFu);
+      if (rel && s + 1 < L.NS) s_carry[s + 1] ^= (E)(in & T::M);
       if (fl != 0) break;  // every later entry of the share is absolute
     }
   }
   if (threadIdx.x == 0) s_carry[0] = 0;
   __syncthreads();
+}
+
+__device__ __forceinline__ void sub_carries(const Layout& L, const Tables& tb, const uint8_t* agg, uint8_t* s_carry,
+                                            uint32_t* s_tot) {
+  sub_carries_t<false>(L, tb, agg, s_carry, s_tot);
 }
 
 __device__ __forceinline__ int mod_h(int v, int H) {
@@ -1084,6 +1128,10 @@ __device__ __forceinline__ uint32_t mask_from(int k, int w0) {
 // Byte-wise a + b mod 256 in each of the four bytes of a word.
 __device__ __forceinline__ uint32_t vadd4(uint32_t a, uint32_t b) {
   return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
+}
+// Byte-wise a - b mod 256 in each of the four bytes of a word.
+__device__ __forceinline__ uint32_t vsub4(uint32_t a, uint32_t b) {
+  return ((a | 0x80808080u) - (b & 0x7F7F7F7Fu)) ^ ((a ^ ~b) & 0x80808080u);
 }
 // Byte 3 of w in all four bytes.
 __device__ __forceinline__ uint32_t bcast3(uint32_t w) { return __byte_perm(w, 0u, 0x3333u); }
@@ -1225,28 +1273,30 @@ struct RoundArgs {
 
 // Dynamic shared memory of an encryption round CTA:
 // [tile Z, 16-aligned][the tile's keystream, T W C bytes when rows are whole
-// 16-byte pieces, else none][sub-tile carries, NS bytes rounded to 16]
-// [share totals, 32 words][row shifts, 32 ints][the tile's subframe-start bit
-// words][subframe seeds, SC bytes].  A decryption round uses the tile alone.
+// 16-byte pieces, else none][sub-tile carries, NS bytes (per-channel chains:
+// NS words) rounded to 16][share totals, 32 scan elements][row shifts, 32
+// ints][the tile's subframe-start bit words][subframe seeds, SC bytes
+// (per-channel: SC words)].  A decryption round uses the tile alone.
 struct RoundSmem {
   int ks, carry, tot, kmod, sbits, seed, total;
   bool ks_staged;
 };
-__host__ __device__ inline RoundSmem round_smem(const Layout& L) {
+__host__ __device__ inline RoundSmem round_smem(const Layout& L, bool pc = false) {
   RoundSmem m;
   const int rowb = L.W * L.C;
+  const int w = pc ? 4 : 1;  // bytes per carry and per seed
   m.ks = (int)(((long long)L.T * tile_row_bytes(L.W, L.C) + 15) & ~15LL);
   m.ks_staged = (rowb & 15) == 0;
   m.carry = m.ks + (m.ks_staged ? L.T * rowb : 0);
-  m.tot = m.carry + ((L.NS + 15) & ~15);
-  m.kmod = m.tot + 32 * (int)sizeof(uint32_t);
+  m.tot = m.carry + ((w * L.NS + 15) & ~15);
+  m.kmod = m.tot + 32 * (pc ? 8 : 4);
   m.sbits = m.kmod + 32 * (int)sizeof(int);
   m.seed = m.sbits + 4 * (((L.T * L.W) >> 5) + 4);
-  m.total = m.seed + L.SC;
+  m.total = m.seed + w * L.SC;
   return m;
 }
 
-size_t round_smem_bytes(const Layout& L) { return (size_t)round_smem(L).total; }
+size_t round_smem_bytes(const Layout& L, bool pc) { return (size_t)round_smem(L, pc && L.C > 1).total; }
 size_t dec_smem_bytes(const Layout& L) { return (size_t)(((long long)L.T * tile_row_bytes(L.W, L.C) + 15) & ~15LL); }
 
 // 16-byte global -> shared copy that completes asynchronously (cp.async, L2
@@ -1277,12 +1327,34 @@ __device__ __forceinline__ uint8_t enc_y_at(const Layout& L, const Tables& tb, c
   return x;
 }
 
+// Pixel pp of the current round's confused frame Y as a word of C bytes (the
+// per-channel seeds), read through Eq. 1 from the previous round's output X
+// with the pending sub-tile word carries applied.
+template <int C>
+__device__ __forceinline__ uint32_t enc_ypx_at(const Layout& L, const Tables& tb, const uint8_t* X, const int* kmod,
+                                               const uint32_t* s_carry, bool fix, int pp) {
+  const int alpha = pp / L.W, beta = pp - alpha * L.W;
+  int o = beta - __ldg(&kmod[alpha]);
+  if (o < 0) o += L.W;
+  const int a = mod_h(alpha - o, L.H);
+  const int qx = (a * L.W + o) * C;
+  uint32_t x = 0;
+#pragma unroll
+  for (int c = 0; c < C; c++) x |= (uint32_t)X[qx + c] << (8 * c);
+  if (fix) {
+    const int sa = a >> L.lgR;
+    if (qx < __ldg(&tb.fixlim[sa])) x ^= s_carry[sa];
+  }
+  return x;
+}
+
 // Gather of the tile Z for C = 3 and 4 (T >= 4): each lane moves a run of
 // four consecutive pixels of one source row (T / 4 lanes per source row), as
 // four aligned 32-bit loads shifted into place and four 32-bit slot stores.
 // Runs that wrap at H, leave the frame's columns or its bytes go pixel by
 // pixel.  Z[tt][o] = X[(a0 + tt - o) mod H][o] as in the per-pixel gather.
-template <int C>
+// PC: the pending carries are pixel words (per-channel chains), else bytes.
+template <int C, bool PC = false>
 __device__ __forceinline__ void gather_runs(const Layout& L, const Tables& tb, const uint8_t* X, uint8_t* Z,
                                             const uint8_t* s_carry, const bool fix, const int a0, const int Te,
                                             const bool aligned) {
@@ -1330,7 +1402,8 @@ __device__ __forceinline__ void gather_runs(const Layout& L, const Tables& tb, c
         const int au = a + u * astep;
         const int sa = au >> L.lgR;
         const int lim = fix ? __ldg(&tb.fixlim[sa]) : 0;
-        const uint32_t cy = fix ? rep_px<C>(s_carry[sa]) : 0u;
+        const uint32_t cy =
+            fix ? (PC ? reinterpret_cast<const uint32_t*>(s_carry)[sa] : rep_px<C>(s_carry[sa])) : 0u;
         if (qv[u] >= 0) {
           const int qx = qv[u];
           const uint32_t sh = (uint32_t)(qx & 3) * 8u;
@@ -1558,13 +1631,269 @@ __device__ __forceinline__ void diffuse_px16(const RoundArgs& A, const int f, co
   if (lane == 0) A.agg_out[(long long)f * L.NS + (r0 >> L.lgR)] = (uint8_t)run;
 }
 
+// ---- per-channel chains (the alternative reading of Eq. 3: byte ch of pixel
+// p follows byte ch of pixel p - 1 of the subframe) --------------------------
+// The scan runs over pixel words: d_p = b_p xor (y_p + b_p) byte by byte, the
+// chain value c_p = c_{p-1} xor d_p, reset to seed xor d_p at a subframe start
+// (seed = the confused pixel at the end of the next subframe).  Sub-tile
+// carries and aggregates are pixel words; otherwise the tile, the lazy
+// carries and the fix-up are those of the byte chains.
+
+// Keystream bytes of pixel j (0..15) of a 16-pixel chunk held as 4 C packed
+// words kw (j a compile-time index).
 template <int C>
+__device__ __forceinline__ uint32_t chunk_px(const uint32_t* kw, int j) {
+  if (C == 4) return kw[j];
+  const int g = j >> 2, r = j & 3;
+  const uint32_t u0 = kw[3 * g], u1 = kw[3 * g + 1], u2 = kw[3 * g + 2];
+  return r == 0 ? (u0 & 0xFFFFFFu)
+                : (r == 1 ? (__byte_perm(u0, u1, 0x0543u) & 0xFFFFFFu)
+                          : (r == 2 ? (__byte_perm(u1, u2, 0x0432u) & 0xFFFFFFu) : (u2 >> 8)));
+}
+
+// Seed pixel of the subframe starting at pixel pix.
+template <int C>
+__device__ __forceinline__ uint32_t pc_seed_at(const RoundArgs& A, int pix, const uint32_t* s_sbits, int wlo,
+                                               const uint32_t* s_seed, int s_lo, bool seeded, const uint8_t* X,
+                                               const int* kmod, const uint32_t* s_carry, bool fix) {
+  const int wq = pix >> 5;
+  const int s = __ldg(&A.tb.srank[wq]) + __popc(s_sbits[wq - wlo] & ((1u << (pix & 31)) - 1u));
+  if (seeded) return s_seed[s - s_lo];
+  const int nx = (s + 1 == A.L.n) ? 0 : s + 1;
+  return enc_ypx_at<C>(A.L, A.tb, X, kmod, s_carry, fix, __ldg(&A.tb.pi[nx + 1]) - 1);
+}
+
+// The warp's sub-tile (rows r0 .. r1 - 1) in chunks of 16 pixels per lane,
+// for W a multiple of 16 with the tile's keystream in shared memory: sixteen
+// pixel slots and 4 C keystream words in, 4 C packed words out (16-byte
+// stores).  Chunks with more than one subframe start (or, without seed slots,
+// any) take their seeds one by one.
+template <int C>
+__device__ __forceinline__ void diffuse_pc16(const RoundArgs& A, const int f, const uint8_t* Z, const uint8_t* s_ks,
+                                             const int* s_kmod, const uint32_t* s_sbits, const int wlo,
+                                             const uint32_t* s_seed, const int s_lo, const bool seeded,
+                                             const uint8_t* X, const int* kmod, const uint32_t* s_carry,
+                                             const bool fix, uint8_t* Out, const int a0, const int r0,
+                                             const int r1) {
+  constexpr int NW = 4 * C;  // words per chunk
+  using T = CarryT<true>;
+  const Layout& L = A.L;
+  const int lane = threadIdx.x & 31;
+  const int rowb = L.W * C;
+  const int cpr = L.W >> 4;  // chunks per row
+  const int nchunks = (r1 - r0) * cpr;
+  const int tstart = a0 * rowb;
+  const bool out_vec = ((reinterpret_cast<uintptr_t>(Out)) & 15) == 0;
+  const uint32_t* Zw = reinterpret_cast<const uint32_t*>(Z);
+  uint64_t run = 0;
+  for (int cb = 0; cb < nchunks; cb += 32) {
+    const int c = cb + lane;
+    uint32_t px[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) px[j] = 0u;
+    int fse = 16;
+    uint64_t agg = 0;
+    int q0 = 0;
+    if (c < nchunks) {
+      const int rl = (c >= cpr ? 1 : 0) + (c >= 2 * cpr ? 1 : 0) + (c >= 3 * cpr ? 1 : 0);  // R <= 4
+      const int p0 = (c - rl * cpr) << 4;  // first output pixel of the chunk in its row
+      const int tt0 = r0 - a0 + rl;
+      q0 = (r0 + rl) * rowb + p0 * C;  // first byte of the chunk in the frame
+      int ps = p0 - s_kmod[tt0];       // first source pixel in the tile row
+      if (ps < 0) ps += L.W;
+      const uint32_t* ksw = reinterpret_cast<const uint32_t*>(s_ks + (q0 - tstart));
+      const int zb = tt0 * L.ZS;
+      const bool contig = ps + 15 < L.W;
+      const int s0 = zb + ps + (ps >> 5), lo = ps & 31;
+      auto slot = [&](int i) -> int {
+        if (contig) return s0 + i + ((lo + i) >> 5);
+        int q = ps + i;
+        if (q >= L.W) q -= L.W;
+        return zb + q + (q >> 5);
+      };
+      uint32_t kw[NW];
+#pragma unroll
+      for (int i = 0; i < NW; i++) kw[i] = ksw[i];
+      const int pix0 = (r0 + rl) * L.W + p0;  // a multiple of 16
+      const uint32_t sw = (s_sbits[(pix0 >> 5) - wlo] >> (pix0 & 16)) & 0xFFFFu;
+      const int nst = __popc(sw);
+      if (nst == 0 || (nst == 1 && seeded)) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const uint32_t b = chunk_px<C>(kw, j);
+          acc ^= b ^ vadd4(Zw[slot(j)], b);
+          px[j] = acc;
+        }
+        if (nst == 1) {
+          // pixel j0 starts subframe s: from j0 on the chain is seed ^ d_j0 ^ ..,
+          // i.e. the chunk prefix xor (seed ^ prefix at j0 - 1)
+          const int j0 = __ffs(sw) - 1;
+          const int wq = pix0 >> 5;
+          const int s = __ldg(&A.tb.srank[wq]) + __popc(s_sbits[wq - wlo] & ((1u << ((pix0 & 16) + j0)) - 1u));
+          uint32_t pk = 0;
+#pragma unroll
+          for (int j = 0; j < 15; j++) pk = sel_u32(j == j0 - 1, px[j], pk);
+          const uint32_t V = s_seed[s - s_lo] ^ pk;
+#pragma unroll
+          for (int j = 0; j < 16; j++) px[j] ^= sel_u32(j >= j0, V, 0u);
+          fse = j0;
+          agg = T::F | px[15];
+        } else {
+          agg = px[15];
+        }
+      } else {
+        uint32_t v = 0;
+        bool has = false;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const uint32_t b = chunk_px<C>(kw, j);
+          const uint32_t d = b ^ vadd4(Zw[slot(j)], b);
+          if ((sw >> j) & 1u) {
+            v = pc_seed_at<C>(A, pix0 + j, s_sbits, wlo, s_seed, s_lo, seeded, X, kmod, s_carry, fix) ^ d;
+            if (!has) {
+              has = true;
+              fse = j;
+            }
+          } else {
+            v ^= d;
+          }
+          px[j] = v;
+        }
+        agg = (has ? T::F : 0ull) | v;
+      }
+    }
+    // warp-wide segmented scan of the chunks' values, then the running carry
+    const uint64_t incl = warp_scan_t<true>(agg);
+    uint64_t excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = 0;
+    const uint64_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint64_t E = seg_comb<true>(run, excl);
+    run = seg_comb<true>(run, total);
+    if (c < nchunks) {
+      const uint32_t ev = (uint32_t)E;
+#pragma unroll
+      for (int j = 0; j < 16; j++) px[j] ^= sel_u32(j < fse, ev, 0u);  // pixels before fse miss E
+      uint32_t ow[NW];
+      if (C == 4) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) ow[j] = px[j];
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+          ow[3 * g] = px[4 * g] | (px[4 * g + 1] << 24);
+          ow[3 * g + 1] = (px[4 * g + 1] >> 8) | (px[4 * g + 2] << 16);
+          ow[3 * g + 2] = (px[4 * g + 2] >> 16) | (px[4 * g + 3] << 8);
+        }
+      }
+      if (out_vec) {
+        uint4* o4 = reinterpret_cast<uint4*>(Out + q0);
+#pragma unroll
+        for (int i = 0; i < NW / 4; i++) o4[i] = make_uint4(ow[4 * i], ow[4 * i + 1], ow[4 * i + 2], ow[4 * i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+#pragma unroll
+          for (int bi = 0; bi < 4; bi++) Out[q0 + 4 * i + bi] = (uint8_t)(ow[i] >> (8 * bi));
+        }
+      }
+    }
+  }
+  if (lane == 0) reinterpret_cast<uint32_t*>(A.agg_out)[(long long)f * L.NS + (r0 >> L.lgR)] = (uint32_t)run;
+}
+
+// Any other shape: 16 consecutive pixels of the sub-tile per lane, one pixel
+// at a time (slot, keystream bytes, start bit), bytes stored one by one.
+template <int C>
+__device__ __forceinline__ void diffuse_pc_any(const RoundArgs& A, const int f, const uint8_t* Z, const uint8_t* s_ks,
+                                               const bool ks_staged, const uint8_t* KS, const int* s_kmod,
+                                               const uint32_t* s_sbits, const int wlo, const uint32_t* s_seed,
+                                               const int s_lo, const bool seeded, const uint8_t* X, const int* kmod,
+                                               const uint32_t* s_carry, const bool fix, uint8_t* Out, const int a0,
+                                               const int r0, const int r1) {
+  using T = CarryT<true>;
+  const Layout& L = A.L;
+  const int lane = threadIdx.x & 31;
+  const int pbeg = r0 * L.W, pend = r1 * L.W;
+  const int tstart = a0 * L.W * C;
+  const int nchunks = (pend - pbeg + 15) >> 4;
+  const uint32_t* Zw = reinterpret_cast<const uint32_t*>(Z);
+  uint64_t run = 0;
+  for (int cb = 0; cb < nchunks; cb += 32) {
+    const int c = cb + lane;
+    const int q = pbeg + 16 * c;
+    const int len = c < nchunks ? min(16, pend - q) : 0;
+    uint32_t px[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) px[j] = 0u;
+    int fse = 16;
+    uint64_t agg = 0;
+    if (len > 0) {
+      int row = q / L.W;
+      int beta = q - row * L.W;
+      uint32_t v = 0;
+      bool has = false;
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        if (j < len) {
+          const int p = q + j;
+          const int tt = row - a0;
+          int zo = beta - s_kmod[tt];
+          if (zo < 0) zo += L.W;
+          const uint32_t y = Zw[zslot<C>(L, tt, zo)];
+          uint32_t b = 0;
+#pragma unroll
+          for (int ch = 0; ch < C; ch++)
+            b |= (uint32_t)(ks_staged ? s_ks[p * C - tstart + ch] : KS[p * C + ch]) << (8 * ch);
+          const uint32_t d = b ^ vadd4(y, b);
+          if ((s_sbits[(p >> 5) - wlo] >> (p & 31)) & 1u) {
+            v = pc_seed_at<C>(A, p, s_sbits, wlo, s_seed, s_lo, seeded, X, kmod, s_carry, fix) ^ d;
+            if (!has) {
+              has = true;
+              fse = j;
+            }
+          } else {
+            v ^= d;
+          }
+          px[j] = v;
+          if (++beta == L.W) {
+            beta = 0;
+            row++;
+          }
+        }
+      }
+      agg = (has ? T::F : 0ull) | v;
+    }
+    const uint64_t incl = warp_scan_t<true>(agg);
+    uint64_t excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = 0;
+    const uint64_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint64_t E = seg_comb<true>(run, excl);
+    run = seg_comb<true>(run, total);
+    if (len > 0) {
+      const uint32_t ev = (uint32_t)E;
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        if (j < len) {
+          const uint32_t o = px[j] ^ (j < fse ? ev : 0u);
+#pragma unroll
+          for (int ch = 0; ch < C; ch++) Out[(q + j) * C + ch] = (uint8_t)(o >> (8 * ch));
+        }
+      }
+    }
+  }
+  if (lane == 0) reinterpret_cast<uint32_t*>(A.agg_out)[(long long)f * L.NS + (r0 >> L.lgR)] = (uint32_t)run;
+}
+
+// PC: per-channel chains (C = 3 or 4), else chains over the subframe's bytes.
+template <int C, bool PC = false>
 __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
+  static_assert(!PC || C > 1, "per-channel chains with one channel are the byte chains");
   const Layout& L = A.L;
   const int rowb = L.W * C;
   const int a0 = t * L.T;
   const int Te = min(L.T, L.H - a0);
-  const RoundSmem sm = round_smem(L);
+  const RoundSmem sm = round_smem(L, PC);
   uint8_t* Z = smem;
   uint8_t* s_carry = smem + sm.carry;
   uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + sm.tot);
@@ -1594,7 +1923,15 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
     for (int k = threadIdx.x; k < n16; k += blockDim.x) cp_async16(smem + sm.ks + 16 * k, KS + tstart + 16 * k);
     cp_async_commit();
   }
-  if (fix) sub_carries(L, A.tb, A.agg_in + (long long)f * L.NS, s_carry, s_tot);
+  uint32_t* s_carry_w = reinterpret_cast<uint32_t*>(s_carry);
+  uint32_t* s_seed_w = reinterpret_cast<uint32_t*>(s_seed);
+  if (fix) {
+    if constexpr (PC)
+      sub_carries_t<true>(L, A.tb, reinterpret_cast<const uint32_t*>(A.agg_in) + (long long)f * L.NS, s_carry_w,
+                          reinterpret_cast<uint64_t*>(s_tot));
+    else
+      sub_carries(L, A.tb, A.agg_in + (long long)f * L.NS, s_carry, s_tot);
+  }
   if (threadIdx.x < Te) s_kmod[threadIdx.x] = kmod[a0 + threadIdx.x];
   for (int k = threadIdx.x; k < nsw; k += blockDim.x) s_sbits[k] = __ldg(&A.tb.sbits[wlo + k]);
   __syncthreads();
@@ -1606,13 +1943,17 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
     for (int k = threadIdx.x; k < s_hi - s_lo; k += blockDim.x) {
       const int s = s_lo + k;
       const int nx = (s + 1 == L.n) ? 0 : s + 1;
-      s_seed[k] = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, C * __ldg(&A.tb.pi[nx + 1]) - 1);
+      if constexpr (PC)
+        s_seed_w[k] = enc_ypx_at<C>(L, A.tb, X, kmod, s_carry_w, fix, __ldg(&A.tb.pi[nx + 1]) - 1);
+      else
+        s_seed[k] = enc_y_at<C>(L, A.tb, X, kmod, s_carry, fix, C * __ldg(&A.tb.pi[nx + 1]) - 1);
     }
   }
 
   // ---- gather: Z[tt][o] = X[(a0 + tt - o) mod H][o] -------------------------
   if constexpr (C == 3 || C == 4) {
-    if (L.T >= 4) gather_runs<C>(L, A.tb, X, Z, s_carry, fix, a0, Te, (reinterpret_cast<uintptr_t>(X) & 3) == 0);
+    if (L.T >= 4)
+      gather_runs<C, PC>(L, A.tb, X, Z, s_carry, fix, a0, Te, (reinterpret_cast<uintptr_t>(X) & 3) == 0);
   }
   if (C == 1 || L.T < 4) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1646,7 +1987,8 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
               const int au = a + u * astep;
               const int sa = au >> L.lgR;
               // subframe starts are pixel-aligned: the whole pixel is on one side of fixlim
-              if ((au * L.W + zo[u]) * C < __ldg(&A.tb.fixlim[sa])) x ^= rep_px<C>(s_carry[sa]);
+              if ((au * L.W + zo[u]) * C < __ldg(&A.tb.fixlim[sa]))
+                x ^= PC ? s_carry_w[sa] : rep_px<C>(s_carry[sa]);
             }
             store_z<C>(Z, zslot<C>(L, tt, zo[u]), x);
           }
@@ -1663,6 +2005,15 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   const int r0 = a0 + warp * L.R;
   if (warp >= WPT || r0 >= a0 + Te) return;
   const int r1 = min(r0 + L.R, a0 + Te);
+  if constexpr (PC) {
+    if (ks_staged && (L.W & 15) == 0)
+      diffuse_pc16<C>(A, f, Z, s_ks, s_kmod, s_sbits, wlo, s_seed_w, s_lo, seeded, X, kmod, s_carry_w, fix, Out, a0,
+                      r0, r1);
+    else
+      diffuse_pc_any<C>(A, f, Z, s_ks, ks_staged, KS, s_kmod, s_sbits, wlo, s_seed_w, s_lo, seeded, X, kmod,
+                        s_carry_w, fix, Out, a0, r0, r1);
+    return;
+  }
   if constexpr (C == 3 || C == 4) {
     if (ks_staged && (L.W & 15) == 0) {
       diffuse_px16<C>(A, f, Z, s_ks, s_kmod, s_sbits, wlo, s_seed, s_lo, seeded, X, kmod, s_carry, fix, Out, a0, r0,
@@ -1848,38 +2199,41 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
   if (lane == 0) A.agg_out[(long long)f * L.NS + (r0 >> L.lgR)] = (uint8_t)run;
 }
 
-template <int C>
+template <int C, bool PC>
 __global__ void __launch_bounds__(kRoundThreads, 4) k_enc_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
-  enc_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
+  enc_round_tile<C, PC>(A, blockIdx.y, blockIdx.x, smem);
 }
 
-template <int C>
+template <int C, bool PC>
 static cudaError_t enc_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
-  const size_t smem = round_smem_bytes(A.L);
-  cudaError_t e = allow_smem(k_enc_round<C>, (int)smem);
+  const size_t smem = round_smem_bytes(A.L, PC);
+  cudaError_t e = allow_smem(k_enc_round<C, PC>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(A.L.NT, nframes);
-  k_enc_round<C><<<grid, kRoundThreads, smem, st>>>(A);
+  k_enc_round<C, PC><<<grid, kRoundThreads, smem, st>>>(A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_enc_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
-                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st) {
+                             const uint8_t* agg_in, uint8_t* agg_out, int nframes, cudaStream_t st, bool pc) {
   if (nframes <= 0) return cudaSuccess;
   RoundArgs A{L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, agg_in, agg_out};
   switch (L.C) {
-    case 1: return enc_round_c<1>(A, nframes, st);
-    case 3: return enc_round_c<3>(A, nframes, st);
-    case 4: return enc_round_c<4>(A, nframes, st);
+    case 1: return enc_round_c<1, false>(A, nframes, st);
+    case 3: return pc ? enc_round_c<3, true>(A, nframes, st) : enc_round_c<3, false>(A, nframes, st);
+    case 4: return pc ? enc_round_c<4, true>(A, nframes, st) : enc_round_c<4, false>(A, nframes, st);
   }
   return cudaErrorInvalidValue;
 }
 
-// Shared memory of the fix-up: the carries (NS bytes, rounded to 16) and the
-// carry scan's share totals (32 words).
-__host__ __device__ inline int fixup_smem_bytes(const Layout& L) { return ((L.NS + 15) & ~15) + 32 * 4; }
+// Shared memory of the fix-up: the carries (NS bytes, or NS words for
+// per-channel chains, rounded to 16) and the carry scan's share totals (32
+// scan elements).
+__host__ __device__ inline int fixup_smem_bytes(const Layout& L, bool pc = false) {
+  return pc ? ((4 * L.NS + 15) & ~15) + 32 * 8 : ((L.NS + 15) & ~15) + 32 * 4;
+}
 
 // After the last round: apply each sub-tile's missing prefix in place (one warp
 // per sub-tile of tile t).
@@ -1919,20 +2273,56 @@ __device__ __forceinline__ void enc_fixup_tile(const Layout& L, const Tables& tb
   }
 }
 
+// The same for per-channel chains: the missing prefix is a pixel word, XORed
+// into the C bytes of every pixel before the sub-tile's first subframe start.
+__device__ __forceinline__ void enc_fixup_tile_pc(const Layout& L, const Tables& tb, uint8_t* out,
+                                                  long long out_stride, const uint8_t* agg, const int f, const int t,
+                                                  uint8_t* smem) {
+  uint32_t* s_carry = reinterpret_cast<uint32_t*>(smem);
+  sub_carries_t<true>(L, tb, reinterpret_cast<const uint32_t*>(agg) + (long long)f * L.NS, s_carry,
+                      reinterpret_cast<uint64_t*>(smem + ((4 * L.NS + 15) & ~15)));
+  const int C = L.C;
+  uint8_t* O = out + f * out_stride;
+  const int lane = threadIdx.x & 31;
+  const int WPT = L.T >> L.lgR;
+  for (int w = threadIdx.x >> 5; w < WPT; w += blockDim.x >> 5) {
+    const int s = t * WPT + w;
+    if (s == 0 || s >= L.NS) continue;
+    const int p0 = s * L.R * L.W;               // first pixel of the sub-tile
+    const int p1 = __ldg(&tb.fixlim[s]) / C;    // its first subframe start (pixel-aligned) or its end
+    const uint32_t cy = s_carry[s];
+    if (cy == 0u) continue;
+    for (int p = p0 + lane; p < p1; p += 32) {
+#pragma unroll 4
+      for (int ch = 0; ch < C; ch++) O[p * C + ch] ^= (uint8_t)(cy >> (8 * ch));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kRoundThreads) k_enc_fixup(Layout L, Tables tb, uint8_t* out, long long out_stride,
                                                              const uint8_t* agg) {
   extern __shared__ __align__(16) uint8_t smem[];
   enc_fixup_tile(L, tb, out, out_stride, agg, blockIdx.y, blockIdx.x, smem);
 }
 
+__global__ void __launch_bounds__(kRoundThreads) k_enc_fixup_pc(Layout L, Tables tb, uint8_t* out,
+                                                                long long out_stride, const uint8_t* agg) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  enc_fixup_tile_pc(L, tb, out, out_stride, agg, blockIdx.y, blockIdx.x, smem);
+}
+
 cudaError_t launch_enc_fixup(const Layout& L, Tables tb, uint8_t* out, long long out_stride, const uint8_t* agg,
-                             int nframes, cudaStream_t st) {
+                             int nframes, cudaStream_t st, bool pc) {
   if (nframes <= 0) return cudaSuccess;
-  const int smem = fixup_smem_bytes(L);
-  cudaError_t e = allow_smem(k_enc_fixup, smem);
+  pc = pc && L.C > 1;
+  const int smem = fixup_smem_bytes(L, pc);
+  cudaError_t e = pc ? allow_smem(k_enc_fixup_pc, smem) : allow_smem(k_enc_fixup, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(L.NT, nframes);
-  k_enc_fixup<<<grid, kRoundThreads, smem, st>>>(L, tb, out, out_stride, agg);
+  if (pc)
+    k_enc_fixup_pc<<<grid, kRoundThreads, smem, st>>>(L, tb, out, out_stride, agg);
+  else
+    k_enc_fixup<<<grid, kRoundThreads, smem, st>>>(L, tb, out, out_stride, agg);
   return cudaGetLastError();
 }
 
@@ -1953,8 +2343,11 @@ __device__ __forceinline__ uint64_t vsub8(uint64_t a, uint64_t b) {
 // ciphertext, keystream and start-bit words, then the result) so that a lane
 // keeps several rows of loads in flight; each decrypted pixel is one 32-bit
 // shared-memory slot (C = 3, 4), packed into bytes when the band is written.
-template <int C, int U = 4>
+// PC: per-channel chains (C = 3 or 4): c_{q-1} is then the same byte of the
+// previous pixel, and the seed the decrypted last pixel of the next subframe.
+template <int C, int U = 4, bool PC = false>
 __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
+  static_assert(!PC || C > 1, "per-channel chains with one channel are the byte chains");
   const Layout& L = A.L;
   const int rowb = L.W * C;
   const int a0 = t * L.T;
@@ -1972,8 +2365,28 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   const int astep = nw * rpw;
   const uint32_t pmask = C == 4 ? 0xFFFFFFFFu : ((1u << (8 * C)) - 1u);
   // the decrypted pixel at pixel index pix of the round's input, byte by byte
+  auto cpx = [&](const uint8_t* base, int pp) -> uint32_t {  // the C bytes of pixel pp
+    uint32_t v = 0;
+#pragma unroll
+    for (int c = 0; c < C; c++) v |= (uint32_t)base[pp * C + c] << (8 * c);
+    return v;
+  };
   auto decrypt_pixel = [&](int pix, uint32_t sw) -> uint32_t {
     const int qb = pix * C;
+    if constexpr (PC) {
+      uint32_t prev;
+      if ((sw >> (pix & 31)) & 1u) {  // subframe start: the seed pixel
+        const int s = __ldg(&A.tb.srank[pix >> 5]) + __popc(sw & ((1u << (pix & 31)) - 1u));
+        const int nx = (s + 1 == L.n) ? 0 : s + 1;
+        const int sp = __ldg(&A.tb.pi[nx + 1]) - 1;
+        const uint32_t bs = cpx(KS, sp);
+        prev = vsub4(bs ^ cpx(Cin, sp) ^ cpx(Cin, sp - 1), bs) & pmask;
+      } else {
+        prev = cpx(Cin, pix - 1);
+      }
+      const uint32_t b = cpx(KS, pix);
+      return vsub4(b ^ cpx(Cin, pix) ^ prev, b) & pmask;
+    }
     uint8_t prev;
     if ((sw >> (pix & 31)) & 1u) {  // subframe start: the seed
       const int s = __ldg(&A.tb.srank[pix >> 5]) + __popc(sw & ((1u << (pix & 31)) - 1u));
@@ -2004,7 +2417,7 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
       const int mo = m * L.H;
       for (int alpha = warp * rpw + sub; alpha < L.H; alpha += U * astep) {
         int pix[U], ov[U];
-        uint32_t c0[U], c1[U], k0[U], k1[U], sw[U];
+        uint32_t c0[U], c1[U], c2[U], k0[U], k1[U], sw[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const int al = alpha + u * astep;
@@ -2023,7 +2436,17 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
         for (int u = 0; u < U; u++) {
           const int qb = pix[u] * C;
           sw[u] = ov[u] >= 0 ? __ldg(&A.tb.sbits[pix[u] >> 5]) : 0u;  // start bits, with the data
-          if (ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
+          c2[u] = 0;
+          if (PC && ov[u] >= 0 && words && qb >= C && qb + 12 <= L.N) {
+            // ciphertext bytes qb - C .. qb + C - 1 (three words), keystream qb .. qb + C - 1
+            const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - C) & ~3));
+            const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
+            c0[u] = __ldg(cw);
+            c1[u] = __ldg(cw + 1);
+            c2[u] = C == 3 ? __ldg(cw + 2) : 0u;
+            k0[u] = __ldg(kw);
+            k1[u] = C == 3 ? __ldg(kw + 1) : 0u;
+          } else if (!PC && ov[u] >= 0 && words && qb >= 4 && qb + 8 <= L.N) {
             const uint32_t* cw = reinterpret_cast<const uint32_t*>(Cin + ((qb - 1) & ~3));
             const uint32_t* kw = reinterpret_cast<const uint32_t*>(KS + (qb & ~3));
             c0[u] = __ldg(cw);
@@ -2039,8 +2462,23 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
           if (ov[u] < 0) continue;
           const int p = pix[u], qb = p * C;
           uint32_t y;
-          if (((sw[u] >> (p & 31)) & 1u) || !(words && qb >= 4 && qb + 8 <= L.N)) {
+          const bool fast = PC ? (words && qb >= C && qb + 12 <= L.N) : (words && qb >= 4 && qb + 8 <= L.N);
+          if (((sw[u] >> (p & 31)) & 1u) || !fast) {
             y = decrypt_pixel(p, sw[u]);
+          } else if constexpr (PC) {
+            uint32_t prev, cur, b;
+            if (C == 4) {  // qb is a multiple of 4
+              prev = c0[u];
+              cur = c1[u];
+              b = k0[u];
+            } else {
+              const uint32_t sh = (uint32_t)((qb - 3) & 3) * 8u;
+              const uint32_t lo = __funnelshift_r(c0[u], c1[u], sh), hi = __funnelshift_r(c1[u], c2[u], sh);
+              prev = lo & 0xFFFFFFu;
+              cur = __byte_perm(lo, hi, 0x0543u) & 0xFFFFFFu;
+              b = __funnelshift_r(k0[u], k1[u], (uint32_t)(qb & 3) * 8u) & 0xFFFFFFu;
+            }
+            y = vsub4(b ^ cur ^ prev, b) & pmask;
           } else {
             const uint64_t c = ((uint64_t)c1[u] << 32 | c0[u]) >> (8 * ((qb - 1) & 3));
             const uint64_t b = ((uint64_t)k1[u] << 32 | k0[u]) >> (8 * (qb & 3));
@@ -2101,183 +2539,31 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   }
 }
 
-template <int C>
+template <int C, bool PC>
 __global__ void __launch_bounds__(kRoundThreads, 4) k_dec_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
-  dec_round_tile<C>(A, blockIdx.y, blockIdx.x, smem);
+  dec_round_tile<C, 4, PC>(A, blockIdx.y, blockIdx.x, smem);
 }
 
-template <int C>
+template <int C, bool PC>
 static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
   const size_t smem = dec_smem_bytes(A.L);
-  cudaError_t e = allow_smem(k_dec_round<C>, (int)smem);
+  cudaError_t e = allow_smem(k_dec_round<C, PC>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(A.L.NT, nframes);
-  k_dec_round<C><<<grid, kRoundThreads, smem, st>>>(A);
+  k_dec_round<C, PC><<<grid, kRoundThreads, smem, st>>>(A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dec_round(const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
                              long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
-                             int nframes, cudaStream_t st) {
+                             int nframes, cudaStream_t st, bool pc) {
   if (nframes <= 0) return cudaSuccess;
   RoundArgs A{L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nullptr, nullptr};
   switch (L.C) {
-    case 1: return dec_round_c<1>(A, nframes, st);
-    case 3: return dec_round_c<3>(A, nframes, st);
-    case 4: return dec_round_c<4>(A, nframes, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-// =============================================================================
-// Per-channel diffusion (the alternative reading of Eq. 3 / Eq. 4: one chain
-// per colour channel instead of one over the subframe's bytes).  One kernel
-// per round: encryption runs one warp per subframe that gathers its confused
-// pixels (Eq. 1) and scans its C channel chains at once, a pixel's C bytes
-// packed in one 32-bit word (XOR and the mod-256 sums act byte by byte);
-// decryption is elementwise (Eq. 4; a subframe's first pixel recomputes the
-// seed pixel of the next subframe from the ciphertext) fused with the inverse
-// gather (Eq. 2).
-// =============================================================================
-
-template <int C>
-__device__ __forceinline__ uint32_t load_px(const uint8_t* base, long long p) {
-  const uint8_t* a = base + p * C;
-  uint32_t v = a[0];
-  if (C > 1) v |= (uint32_t)a[1] << 8;
-  if (C > 2) v |= (uint32_t)a[2] << 16;
-  if (C > 3) v |= (uint32_t)a[3] << 24;
-  return v;
-}
-
-template <int C>
-__device__ __forceinline__ void store_px(uint8_t* base, long long p, uint32_t v) {
-  uint8_t* a = base + p * C;
-  a[0] = (uint8_t)v;
-  if (C > 1) a[1] = (uint8_t)(v >> 8);
-  if (C > 2) a[2] = (uint8_t)(v >> 16);
-  if (C > 3) a[3] = (uint8_t)(v >> 24);
-}
-
-// Byte-wise a - b mod 256 in each of the four bytes of a word.
-__device__ __forceinline__ uint32_t vsub4(uint32_t a, uint32_t b) {
-  return ((a | 0x80808080u) - (b & 0x7F7F7F7Fu)) ^ ((a ^ ~b) & 0x80808080u);
-}
-
-// Source pixel of confused pixel p (Eq. 1): Y[alpha][beta] = X[a][o] with
-// o = (beta - k(alpha)) mod W and a = (alpha - o) mod H.
-__device__ __forceinline__ long long pc_source(const Layout& L, const int* km, int p) {
-  const int alpha = p / L.W, beta = p - alpha * L.W;
-  int o = beta - __ldg(&km[alpha]);
-  if (o < 0) o += L.W;
-  return (long long)mod_h(alpha - o, L.H) * L.W + o;
-}
-
-// Eq. 1 and Eq. 3 per channel in one pass: warp w of the grid diffuses
-// subframe w, gathering each confused pixel from the previous round's output
-// as it goes (8 pixels per lane and step); the lanes' XOR totals are scanned
-// with shuffles and the running value carries to the next step.  The seed is
-// the confused value of the last pixel of subframe (i+1) mod n.  X and Xo
-// must not overlap (other warps still gather from X).
-template <int C>
-__global__ void __launch_bounds__(128) k_pc_enc_round(Layout L, Tables tb, const uint8_t* X, long long xs,
-                                                      const uint8_t* ks, long long ks_stride, const int* kmod,
-                                                      uint8_t* Xo, long long os) {
-  const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (i >= L.n) return;  // whole warps
-  const int lane = threadIdx.x & 31, f = blockIdx.y;
-  const uint8_t* x = X + f * xs;
-  const uint8_t* b = ks + f * ks_stride;
-  const int* km = kmod + (long long)f * L.H;
-  uint8_t* out = Xo + f * os;
-  const int p0 = tb.pi[i], p1 = tb.pi[i + 1];
-  const int nxt = i + 1 == L.n ? 0 : i + 1;
-  uint32_t carry = load_px<C>(x, pc_source(L, km, tb.pi[nxt + 1] - 1));
-  constexpr int K = 8;
-  for (int base = p0; base < p1; base += 32 * K) {  // the same trip count in every lane
-    const int q0 = base + lane * K;
-    uint32_t pre[K];
-    uint32_t acc = 0;
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      const int p = q0 + k;
-      if (p < p1) {
-        const uint32_t yy = load_px<C>(x, pc_source(L, km, p)), bb = load_px<C>(b, p);
-        acc ^= bb ^ vadd4(yy, bb);
-      }
-      pre[k] = acc;
-    }
-    uint32_t incl = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl ^= t;
-    }
-    const uint32_t head = carry ^ incl ^ acc;  // chain value before this lane's pixels
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      const int p = q0 + k;
-      if (p < p1) store_px<C>(out, p, head ^ pre[k]);
-    }
-    carry ^= __shfl_sync(0xFFFFFFFFu, incl, 31);
-  }
-}
-
-// Eq. 4 per channel and Eq. 2 in one pass, one thread per output pixel (a, o):
-// it reads confused pixel q = ((a + o) mod H, (o + k) mod W) and recovers it
-// as (b xor c_q xor c_{q-1}) - b, or for a subframe's first pixel with the
-// seed pixel s (the last pixel of subframe (i+1) mod n, never a first pixel
-// since every subframe holds 2 pixels or more) recovered the same way.
-// Xc and X must not overlap.
-template <int C>
-__global__ void k_pc_dec_round(Layout L, Tables tb, const uint8_t* Xc, long long xs, const uint8_t* ks,
-                               long long ks_stride, const int* kmod, uint8_t* X, long long os) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.P) return;
-  const int f = blockIdx.y;
-  const uint8_t* c = Xc + f * xs;
-  const uint8_t* b = ks + f * ks_stride;
-  const int a = (int)(p / L.W), o = (int)(p - (long long)a * L.W);
-  const int alpha = mod_h(a + o, L.H);
-  int beta = o + __ldg(&kmod[(long long)f * L.H + alpha]);
-  if (beta >= L.W) beta -= L.W;
-  const int q = alpha * L.W + beta;
-  const int i = starts_before(L, q + 1) - 1;  // the subframe holding pixel q
-  const uint32_t bb = load_px<C>(b, q), cc = load_px<C>(c, q);
-  uint32_t prev;
-  if (q > tb.pi[i]) {
-    prev = load_px<C>(c, q - 1);
-  } else {
-    const int nxt = i + 1 == L.n ? 0 : i + 1;
-    const long long sp = tb.pi[nxt + 1] - 1;
-    const uint32_t bs = load_px<C>(b, sp);
-    prev = vsub4(bs ^ load_px<C>(c, sp) ^ load_px<C>(c, sp - 1), bs);
-  }
-  store_px<C>(X + f * os, p, vsub4(bb ^ cc ^ prev, bb));
-}
-
-template <int C>
-cudaError_t pc_round_c(bool enc, const Layout& L, Tables tb, const uint8_t* in, long long in_stride, uint8_t* out,
-                       long long out_stride, const uint8_t* ks_round, long long ks_stride, const int* kmod,
-                       int nframes, cudaStream_t st) {
-  if (enc)
-    k_pc_enc_round<C><<<dim3((unsigned)((L.n + 3) / 4), (unsigned)nframes), 128, 0, st>>>(
-        L, tb, in, in_stride, ks_round, ks_stride, kmod, out, out_stride);
-  else
-    k_pc_dec_round<C><<<dim3((unsigned)((L.P + 255) / 256), (unsigned)nframes), 256, 0, st>>>(
-        L, tb, in, in_stride, ks_round, ks_stride, kmod, out, out_stride);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pc_round(bool encrypt, const Layout& L, Tables tb, const uint8_t* in, long long in_stride,
-                            uint8_t* out, long long out_stride, const uint8_t* ks_round, long long ks_stride,
-                            const int* kmod, int nframes, cudaStream_t st) {
-  if (nframes <= 0) return cudaSuccess;
-  switch (L.C) {
-    case 1: return pc_round_c<1>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
-    case 3: return pc_round_c<3>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
-    case 4: return pc_round_c<4>(encrypt, L, tb, in, in_stride, out, out_stride, ks_round, ks_stride, kmod, nframes, st);
+    case 1: return dec_round_c<1, false>(A, nframes, st);
+    case 3: return pc ? dec_round_c<3, true>(A, nframes, st) : dec_round_c<3, false>(A, nframes, st);
+    case 4: return pc ? dec_round_c<4, true>(A, nframes, st) : dec_round_c<4, false>(A, nframes, st);
   }
   return cudaErrorInvalidValue;
 }

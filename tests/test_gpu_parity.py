@@ -266,12 +266,28 @@ def test_odd_shapes(B, orc, kind, H, W, C, n, r):
     (64, 64, 1, 2048, 3),  # 2-pixel subframes (the minimum)
     (70, 70, 3, 2450, 5),  # 2-pixel subframes, 3 channels
     (33, 65, 3, 7, 1),     # one round, in place below
+    # W a multiple of 16 with whole 16-byte rows: the 16-pixel chunk path
+    (64, 64, 3, 2048, 3),  # 2-pixel subframes: up to 8 starts in a chunk
+    (96, 160, 4, 77, 5),   # 4 channels, subframes across sub-tiles
+    (128, 96, 3, 5, 5),    # long subframes across many tiles (carries between tiles)
+    (48, 32, 3, 1, 5),     # n = 1
+    (40, 48, 4, 3, 1),     # one round, in place below
 ])
 def test_per_channel_diffusion(B, orc, kind, H, W, C, n, r):
     """The per-channel diffusion variant (VC_OPT_DIFFUSION = 1) against the
     oracle's per-channel reading, encrypt and decrypt, in place for one round."""
     X = synth.uniform_frames(2, H, W, C, seed=H * W + n)
     _check_enc_dec(B, orc, kind, synth.key_for_seed(kind, 400 + n), X, n, r, per_channel=True, inplace=(r == 1))
+
+
+@pytest.mark.parametrize("tile_rows", [1, 2, 4, 8, 32])
+@pytest.mark.parametrize("H,W,C,n", [(64, 96, 3, 40), (72, 48, 4, 9), (50, 70, 3, 33)])
+def test_per_channel_diffusion_tile_rows(B, orc, tile_rows, H, W, C, n):
+    """Per-channel chains under every tile height (tiles of 1 and 2 rows
+    gather pixel by pixel; sub-tiles of 1 to 4 rows), chunked and general
+    paths, against the oracle."""
+    X = synth.uniform_frames(2, H, W, C, seed=H + W + n + tile_rows)
+    _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 450 + n), X, n, 5, tile_rows=tile_rows, per_channel=True)
 
 
 def test_per_channel_diffusion_clip_in_passes(B, orc):
