@@ -218,6 +218,11 @@ struct vc_ctx {
   int ks_sm_warps = -1;
   int num_sms = 0;
   cudaStream_t ks_stream = nullptr;
+  // the frame schedule (s_c, shift tables) of a pass runs here, beside the
+  // pass's keystream kernel; ev_sc_in / ev_sc_out order it after what the
+  // keystream side held before and the keystream side after it
+  cudaStream_t sc_stream = nullptr;
+  cudaEvent_t ev_sc_in = nullptr, ev_sc_out = nullptr;
   cudaEvent_t ev_ks[2] = {};   // keystream buffer b written
   cudaEvent_t ev_rd[2] = {};   // rounds reading buffer b done
   cudaEvent_t ev_entry = nullptr;
@@ -289,6 +294,7 @@ void sync_all(vc_ctx* c) {
   if (c->last) cudaStreamSynchronize(c->last);
   if (c->ks_stream) cudaStreamSynchronize(c->ks_stream);
   if (c->prod_stream) cudaStreamSynchronize(c->prod_stream);
+  if (c->sc_stream) cudaStreamSynchronize(c->sc_stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
 }
@@ -312,7 +318,7 @@ cudaStream_t ctx_join(vc_ctx* c) {
     sync_all(c);
     return nullptr;
   }
-  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream, c->prod_stream})
+  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream, c->prod_stream, c->sc_stream})
     if (o && o != ks && cudaEventRecord(c->ev_free, o) == cudaSuccess) cudaStreamWaitEvent(ks, c->ev_free, 0);
   return ks;
 }
@@ -456,10 +462,19 @@ int ks_warps_in_use(const vc_ctx* c) {
 int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
   vc::NvtxRange range("vc.keystream");
   const Layout& L = c->L;
+  // s_c and the shift tables (which need only PRBG_m) on their own stream,
+  // beside the keystream kernel (which needs only the subframe chains): after
+  // what `ks` holds so far (buffer reuse, state snapshots), and `ks` waits for
+  // them at the end of the stage, so whoever waits for the stage sees both
+  // and the next pass's keystream never queues behind a schedule
+  cudaStream_t sc = c->sc_stream;
+  VC_CUDA(cudaEventRecord(c->ev_sc_in, ks));
+  VC_CUDA(cudaStreamWaitEvent(sc, c->ev_sc_in, 0));
   {
-    StageMark m(c, ks, 0, 2);
-    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc[b], c->d_kmod[b], ks));
+    StageMark m(c, sc, 0, 2);
+    VC_CUDA(vc::launch_frame_schedule(L, c->d_main, nf, c->d_sc[b], c->d_kmod[b], sc));
   }
+  VC_CUDA(cudaEventRecord(c->ev_sc_out, sc));
   {
     StageMark m(c, ks, 1, 1);
     VC_CUDA(c->ks_lanes == 2
@@ -467,6 +482,7 @@ int keystream_stage(vc_ctx* c, int b, int nf, cudaStream_t ks) {
                                        ks_warps_in_use(c))
                 : vc::launch_keystream_thread(c->kind, L, c->tables(), c->chains(), nf, c->d_ks[b], c->plcm_int, ks));
   }
+  VC_CUDA(cudaStreamWaitEvent(ks, c->ev_sc_out, 0));
   return VC_OK;
 }
 
@@ -803,6 +819,9 @@ int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out) {
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
   if (cudaStreamCreateWithPriority(&c->ks_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->sc_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sc_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sc_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ks[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ks[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rd[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -1024,6 +1043,7 @@ int enc_sync_status(vc_ctx* c) {
   if (e == cudaSuccess && c->d2h_stream) e = cudaStreamSynchronize(c->d2h_stream);
   if (e == cudaSuccess && c->ks_stream) e = cudaStreamSynchronize(c->ks_stream);
   if (e == cudaSuccess && c->prod_stream) e = cudaStreamSynchronize(c->prod_stream);
+  if (e == cudaSuccess && c->sc_stream) e = cudaStreamSynchronize(c->sc_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_err("asynchronous CUDA error: %s", cudaGetErrorString(e));
@@ -1035,7 +1055,7 @@ int enc_sync_status(vc_ctx* c) {
 int enc_join(vc_ctx* c, void* stream) {
   if (!c) return VC_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  for (cudaStream_t o : {c->ks_stream, c->prod_stream, c->copy_stream, c->d2h_stream})
+  for (cudaStream_t o : {c->ks_stream, c->prod_stream, c->sc_stream, c->copy_stream, c->d2h_stream})
     if (o && o != st) {
       VC_CUDA(cudaEventRecord(c->ev_free, o));
       VC_CUDA(cudaStreamWaitEvent(st, c->ev_free, 0));
@@ -1210,11 +1230,12 @@ void destroy_ctx(vc_ctx* c, bool wait) {
   if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
   if (c->ks_stream) cudaStreamDestroy(c->ks_stream);
   if (c->prod_stream) cudaStreamDestroy(c->prod_stream);
+  if (c->sc_stream) cudaStreamDestroy(c->sc_stream);
   for (int b = 0; b < 2; b++) {
     if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
     if (c->ev_rd[b]) cudaEventDestroy(c->ev_rd[b]);
   }
-  for (cudaEvent_t e : {c->ev_entry, c->ev_batch, c->ev_free})
+  for (cudaEvent_t e : {c->ev_entry, c->ev_batch, c->ev_free, c->ev_sc_in, c->ev_sc_out})
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_slot) cudaEventDestroy(e);
   for (int i = 0; i < vc_ctx::kProdEv; i++)
