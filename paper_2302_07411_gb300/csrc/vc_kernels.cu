@@ -2539,6 +2539,217 @@ __device__ __forceinline__ void dec_round_tile(const RoundArgs& A, const int f, 
   }
 }
 
+// Decryption round in scatter form (C = 3 or 4, W a multiple of 16, rows of
+// whole 16-byte pieces, 16-byte aligned frames): one CTA per band of rows of
+// the round's INPUT, the ciphertext C.  Eq. 4 is elementwise (each byte needs
+// c_q, c_{q-1} or, per channel, c_{q-C}, and b_q), so the band is read
+// contiguously, 16 pixels per lane and step (C 16-byte loads of ciphertext and
+// of keystream plus the word before), decrypted with byte-wise SWAR into the
+// band's pixel slots in shared memory, and then written through Eq. 2:
+// Y[alpha][beta] goes to X[a][o] with o = (beta - k(alpha)) mod W and
+// a = (alpha - o) mod H, so output row a receives the T consecutive columns
+// o = alpha - a (mod H, + m H) from the band's T rows.  Four lanes write one
+// output row's run (4 pixels each), realigned by a shuffle so that every
+// 32-bit store is aligned and inside the run; the run's first and last partial
+// words go byte by byte (their other bytes belong to neighbouring bands).
+// Subframe starts use the decrypted seed at the end of the next subframe.
+template <int C, bool PC>
+__device__ __forceinline__ void dec_scatter_tile(const RoundArgs& A, const int f, const int t, uint8_t* smem) {
+  constexpr int NW = 4 * C;       // words per 16-pixel unit
+  constexpr int CS = PC ? C : 1;  // the chain's step in bytes
+  const Layout& L = A.L;
+  const int a0 = t * L.T;
+  const int Te = min(L.T, L.H - a0);
+  uint32_t* Yw = reinterpret_cast<uint32_t*>(smem);
+  int* s_kmod = reinterpret_cast<int*>(smem + (((long long)L.T * tile_row_bytes(L.W, C) + 15) & ~15LL));
+  const uint8_t* Cin = A.in + f * A.in_stride;
+  uint8_t* Out = A.out + f * A.out_stride;
+  const uint8_t* KS = A.ks + f * A.ks_stride;
+  const int* kmod = A.kmod + (long long)f * L.H;
+  if (threadIdx.x < Te) s_kmod[threadIdx.x] = __ldg(&kmod[a0 + threadIdx.x]);
+  auto cpx = [&](const uint8_t* base, int pp) -> uint32_t {  // the C bytes of pixel pp
+    uint32_t v = 0;
+#pragma unroll
+    for (int c = 0; c < C; c++) v |= (uint32_t)__ldg(base + pp * C + c) << (8 * c);
+    return v;
+  };
+  const uint32_t pmask = C == 4 ? 0xFFFFFFFFu : 0xFFFFFFu;
+
+  // ---- Eq. 4 over the band, 16 pixels per lane and step ---------------------
+  const int upr = L.W >> 4;  // units per row
+  const int nunits = Te * upr;
+  for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+    const int rl = u / upr;
+    const int beta0 = (u - rl * upr) << 4;
+    const int p0 = (a0 + rl) * L.W + beta0;
+    const int q0 = p0 * C;  // a multiple of 16
+    uint32_t c[NW + 1], b[NW];  // c[0]: the ciphertext word before the unit
+    c[0] = q0 > 0 ? __ldg(reinterpret_cast<const uint32_t*>(Cin + q0) - 1) : 0u;
+#pragma unroll
+    for (int i = 0; i < C; i++) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(Cin + q0) + i);
+      const uint4 y = __ldg(reinterpret_cast<const uint4*>(KS + q0) + i);
+      c[1 + 4 * i] = x.x;
+      c[2 + 4 * i] = x.y;
+      c[3 + 4 * i] = x.z;
+      c[4 + 4 * i] = x.w;
+      b[4 * i] = y.x;
+      b[4 * i + 1] = y.y;
+      b[4 * i + 2] = y.z;
+      b[4 * i + 3] = y.w;
+    }
+    uint32_t yv[NW];
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+      // ciphertext bytes q - CS of the word's bytes q
+      const uint32_t prev = CS == 4 ? c[i] : __funnelshift_r(c[i], c[i + 1], 32 - 8 * CS);
+      yv[i] = vsub4(b[i] ^ c[i + 1] ^ prev, b[i]);
+    }
+    const uint32_t sw = (__ldg(&A.tb.sbits[p0 >> 5]) >> (p0 & 16)) & 0xFFFFu;
+    if (sw != 0u) {
+      // pixels that start a subframe: their first byte (per channel: all C
+      // bytes) follows the decrypted seed at the end of the next subframe
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        if ((sw >> j) & 1u) {
+          const int pix = p0 + j;
+          const int s = __ldg(&A.tb.srank[pix >> 5]) +
+                        __popc(__ldg(&A.tb.sbits[pix >> 5]) & ((1u << (pix & 31)) - 1u));
+          const int nx = (s + 1 == L.n) ? 0 : s + 1;
+          const int sp = __ldg(&A.tb.pi[nx + 1]) - 1;  // never a start: every subframe has 2 bytes or more
+          if constexpr (PC) {
+            const uint32_t bs = cpx(KS, sp);
+            const uint32_t seed = vsub4(bs ^ cpx(Cin, sp) ^ cpx(Cin, sp - 1), bs) & pmask;
+            const uint32_t bb = cpx(KS, pix), cc = cpx(Cin, pix);
+            const uint32_t v = vsub4(bb ^ cc ^ seed, bb) & pmask;
+#pragma unroll
+            for (int ch = 0; ch < C; ch++) {
+              const int k = j * C + ch;  // byte of the unit (compile-time)
+              const uint32_t sh = 8u * (uint32_t)(k & 3);
+              yv[k >> 2] = (yv[k >> 2] & ~(0xFFu << sh)) | (((v >> (8 * ch)) & 0xFFu) << sh);
+            }
+          } else {
+            const int sb = sp * C + C - 1;  // the last byte of subframe nx
+            const uint8_t bs = __ldg(KS + sb);
+            const uint8_t seed = (uint8_t)((uint8_t)(bs ^ __ldg(Cin + sb) ^ __ldg(Cin + sb - 1)) - bs);
+            const int k = j * C;
+            const uint32_t sh = 8u * (uint32_t)(k & 3);
+            const uint8_t bb = (uint8_t)(b[k >> 2] >> sh), cc = (uint8_t)(c[1 + (k >> 2)] >> sh);
+            const uint8_t v = (uint8_t)((uint8_t)(bb ^ cc ^ seed) - bb);
+            yv[k >> 2] = (yv[k >> 2] & ~(0xFFu << sh)) | ((uint32_t)v << sh);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) Yw[zslot<C>(L, rl, beta0 + j)] = C == 4 ? yv[j] : chunk_px<C>(yv, j);
+  }
+  __syncthreads();
+
+  // ---- Eq. 2: runs of the band's columns into the output rows ---------------
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int MC = (L.W + L.H - 1) / L.H;
+  const bool full = Te == L.T && L.T >= 4;
+  if (full) {
+    const int LS = L.T / 4;  // lanes per output row (4 pixels each)
+    const int rpw = 32 / LS;
+    const int tt0 = (lane % LS) * 4;
+    const int k = lane % LS;  // the lane's segment in its row's run
+    const int sub = lane / LS;
+    for (int m = 0; m < MC; m++) {
+      const int mo = m * L.H;
+      for (int abase = warp * rpw; abase < L.H; abase += nw * rpw) {  // warp-uniform trips
+        const int a = abase + sub;
+        int os = a0 - a;  // column of band row 0 in output row a (mod H)
+        if (os < 0) os += L.H;
+        // the row's run is contiguous, inside the frame's columns: aligned stores
+        const bool fast = a < L.H && os + L.T <= L.H && os + mo + L.T <= L.W;
+        uint32_t px[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const int tt = tt0 + j;
+          int o = os + tt;
+          if (o >= L.H) o -= L.H;
+          o += mo;
+          int beta = o + s_kmod[tt];
+          if (beta >= L.W) beta -= L.W;
+          px[j] = (a < L.H && o < L.W) ? Yw[tt * L.ZS + beta + (beta >> 5)] : 0u;
+        }
+        if (C == 4) {
+          if (fast) {
+            uint32_t* dst = reinterpret_cast<uint32_t*>(Out + ((long long)a * L.W + os + mo + tt0) * 4);
+#pragma unroll
+            for (int j = 0; j < 4; j++) dst[j] = px[j];
+            continue;
+          }
+        } else {
+          // the lane's 12 bytes as three words, and the next lane's first word
+          const uint32_t w0 = px[0] | (px[1] << 24), w1 = (px[1] >> 8) | (px[2] << 16);
+          const uint32_t w2 = (px[2] >> 16) | (px[3] << 8);
+          const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, w0, 1);
+          if (fast) {
+            const long long S = ((long long)a * L.W + os + mo + tt0) * 3;  // the segment's first byte
+            const int r = (int)(S & 3);
+            const int sh = (4 - r) & 3;  // bytes up to the first aligned word
+            uint32_t* dst = reinterpret_cast<uint32_t*>(Out + S + sh);
+            const uint32_t v0 = __funnelshift_r(w0, w1, 8 * sh), v1 = __funnelshift_r(w1, w2, 8 * sh);
+            const uint32_t v2 = __funnelshift_r(w2, n0, 8 * sh);
+            if (k == 0) {  // the run's head bytes
+              for (int i = 0; i < sh; i++) Out[S + i] = (uint8_t)(w0 >> (8 * i));
+            }
+            dst[0] = v0;
+            dst[1] = v1;
+            if (k < LS - 1 || r == 0) {
+              dst[2] = v2;
+            } else {  // the run's tail: r bytes of the last word are ours
+              for (int i = 0; i < r; i++) Out[S + sh + 8 + i] = (uint8_t)(v2 >> (8 * i));
+            }
+            continue;
+          }
+        }
+        // pixel by pixel (the run wraps at H or leaves the frame's columns)
+        if (a < L.H) {
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const int tt = tt0 + j;
+            int o = os + tt;
+            if (o >= L.H) o -= L.H;
+            o += mo;
+            if (o >= L.W) continue;
+            uint8_t* d = Out + ((long long)a * L.W + o) * C;
+#pragma unroll
+            for (int c2 = 0; c2 < C; c2++) d[c2] = (uint8_t)(px[j] >> (8 * c2));
+          }
+        }
+      }
+    }
+  } else {
+    // a partial band or fewer than 4 rows: pixel by pixel, one band row per lane
+    for (int m = 0; m < MC; m++) {
+      const int mo = m * L.H;
+      for (int idx = threadIdx.x; idx < L.H * Te; idx += blockDim.x) {
+        const int a = idx / Te, tt = idx - a * Te;
+        int o = a0 + tt - a;
+        if (o < 0) o += L.H;
+        o += mo;
+        if (o >= L.W) continue;
+        int beta = o + s_kmod[tt];
+        if (beta >= L.W) beta -= L.W;
+        const uint32_t v = Yw[tt * L.ZS + beta + (beta >> 5)];
+        uint8_t* d = Out + ((long long)a * L.W + o) * C;
+#pragma unroll
+        for (int c2 = 0; c2 < C; c2++) d[c2] = (uint8_t)(v >> (8 * c2));
+      }
+    }
+  }
+}
+
+template <int C, bool PC>
+__global__ void __launch_bounds__(kRoundThreads, 4) k_dec_scatter(RoundArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  dec_scatter_tile<C, PC>(A, blockIdx.y, blockIdx.x, smem);
+}
+
 template <int C, bool PC>
 __global__ void __launch_bounds__(kRoundThreads, 4) k_dec_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -2547,10 +2758,27 @@ __global__ void __launch_bounds__(kRoundThreads, 4) k_dec_round(RoundArgs A) {
 
 template <int C, bool PC>
 static cudaError_t dec_round_c(const RoundArgs& A, int nframes, cudaStream_t st) {
-  const size_t smem = dec_smem_bytes(A.L);
+  const Layout& L = A.L;
+  dim3 grid(L.NT, nframes);
+  // the scatter form when the band can be read as whole 16-byte pieces and the
+  // output rows written as aligned words (and input and output are apart)
+  const uintptr_t al = reinterpret_cast<uintptr_t>(A.in) | reinterpret_cast<uintptr_t>(A.ks) |
+                       reinterpret_cast<uintptr_t>(A.out) | (uintptr_t)A.in_stride | (uintptr_t)A.ks_stride |
+                       (uintptr_t)A.out_stride;
+  const bool apart = A.in + (long long)(nframes - 1) * A.in_stride + L.N <= A.out ||
+                     A.out + (long long)(nframes - 1) * A.out_stride + L.N <= A.in;
+  if constexpr (C > 1) {
+    if ((L.W & 15) == 0 && (al & 15) == 0 && apart) {
+      const size_t smem = dec_smem_bytes(L) + 32 * sizeof(int);
+      cudaError_t e = allow_smem(k_dec_scatter<C, PC>, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_dec_scatter<C, PC><<<grid, kRoundThreads, smem, st>>>(A);
+      return cudaGetLastError();
+    }
+  }
+  const size_t smem = dec_smem_bytes(L);
   cudaError_t e = allow_smem(k_dec_round<C, PC>, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(A.L.NT, nframes);
   k_dec_round<C, PC><<<grid, kRoundThreads, smem, st>>>(A);
   return cudaGetLastError();
 }
