@@ -297,9 +297,15 @@ int32_t vc_server_inflight(const vc_server* s);
  * cannot be set), or VC_SOPT_QUEUED_TICKS: q > 0 submits a tick only while
  * fewer than q earlier ticks wait for the device to start them (a tick that
  * would queue deeper submits nothing, and its frames join the next, larger
- * batch); 0 (default) submits every tick.  Errors: VC_ERR_ARG (mode 1,
- * VC_BOPT_RUNAHEAD, bad option or value). */
+ * batch); 0 (default) submits every tick.  VC_SOPT_LANES: k in 1..8 batching
+ * lanes, set before the first stream and after the batcher options: tick i
+ * goes to lane i mod k, each lane with its own batcher and a stream of the
+ * server stream's priority (lane 0 is the server's stream), so that a tick
+ * whose kernels wait for SMs does not hold up the next ticks; 1 (default).
+ * Errors: VC_ERR_ARG (mode 1, VC_BOPT_RUNAHEAD, bad option or value, options
+ * in the wrong order), VC_ERR_CUDA. */
 #define VC_SOPT_QUEUED_TICKS 100
+#define VC_SOPT_LANES 101
 int vc_server_set_option(vc_server* s, int32_t option, int64_t value);
 void vc_server_destroy(vc_server* s);
 

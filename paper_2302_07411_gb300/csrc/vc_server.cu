@@ -89,6 +89,13 @@ struct vc_server {
   // skipped tick go into the next, larger batch
   int max_queued = 0;
   int64_t skipped = 0;
+  // batching lanes: tick i goes to lane i mod lanes (lane 0: b on st), each
+  // with its own batcher (scratch, staging, graphs) and stream, so that a tick
+  // whose kernels wait for SMs does not hold up the ticks of the other lanes
+  std::vector<vc_batcher*> lane_b;
+  std::vector<cudaStream_t> lane_st;
+  int64_t next_lane = 0;
+  std::vector<std::pair<int32_t, int64_t>> bopts;  // batcher options set so far (replayed on new lanes)
 };
 
 namespace {
@@ -242,12 +249,22 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
   if (s->jobs.empty()) return VC_OK;
   t_start = std::chrono::steady_clock::now();
   tick.ev0 = srv_event(s);
-  if (!tick.ev0 || cudaEventRecord(tick.ev0, s->st) != cudaSuccess) {
+  // the tick's lane
+  vc_batcher* lb = s->b;
+  cudaStream_t lst = s->st;
+  if (s->mode == 0 && !s->lane_b.empty()) {
+    const int k = (int)(s->next_lane++ % (int64_t)(s->lane_b.size() + 1));
+    if (k > 0) {
+      lb = s->lane_b[k - 1];
+      lst = s->lane_st[k - 1];
+    }
+  }
+  if (!tick.ev0 || cudaEventRecord(tick.ev0, lst) != cudaSuccess) {
     cudaGetLastError();
     return VC_ERR_CUDA;
   }
   if (s->mode == 0) {
-    int rc = vc_batch_submit(s->b, s->jobs.data(), (int32_t)s->jobs.size(), s->st);
+    int rc = vc_batch_submit(lb, s->jobs.data(), (int32_t)s->jobs.size(), lst);
     if (rc) return rc;
   } else {
     // each stream's calls on its own CUDA stream (after the tick's start),
@@ -280,7 +297,7 @@ int vc_server_tick(vc_server* s, double now, int32_t* frames_submitted) {
   s->host_ms[2] += ms_since(t_start);
   t_start = std::chrono::steady_clock::now();
   tick.ev = srv_event(s);
-  if (!tick.ev || cudaEventRecord(tick.ev, s->st) != cudaSuccess) {
+  if (!tick.ev || cudaEventRecord(tick.ev, lst) != cudaSuccess) {
     cudaGetLastError();
     return VC_ERR_CUDA;
   }
@@ -380,7 +397,38 @@ int vc_server_set_option(vc_server* s, int32_t option, int64_t value) {
     s->max_queued = (int)value;
     return VC_OK;
   }
-  return vc_batcher_set_option(s->b, option, value);
+  if (option == VC_SOPT_LANES) {
+    if (value < 1 || value > 8 || !s->streams.empty() || !s->lane_b.empty()) return VC_ERR_ARG;
+    int least = 0, greatest = 0, prio = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamGetPriority(s->st, &prio) != cudaSuccess) {
+      cudaGetLastError();
+      return VC_ERR_CUDA;
+    }
+    for (int k = 1; k < (int)value; k++) {
+      vc_batcher* b = nullptr;
+      cudaStream_t st = nullptr;
+      int rc = vc_batcher_create(&b);
+      if (rc == VC_OK) rc = vc_batcher_set_option(b, VC_BOPT_RUNAHEAD, s->maxf);
+      for (const auto& o : s->bopts)
+        if (rc == VC_OK) rc = vc_batcher_set_option(b, o.first, o.second);
+      if (rc == VC_OK && cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess) {
+        cudaGetLastError();
+        rc = VC_ERR_CUDA;
+      }
+      if (rc != VC_OK) {
+        if (b) vc_batcher_destroy(b);
+        return rc;
+      }
+      s->lane_b.push_back(b);
+      s->lane_st.push_back(st);
+    }
+    return VC_OK;
+  }
+  if (!s->lane_b.empty()) return VC_ERR_ARG;  // batcher options come before the lanes
+  const int rc = vc_batcher_set_option(s->b, option, value);
+  if (rc == VC_OK) s->bopts.emplace_back(option, value);
+  return rc;
 }
 
 int vc_dbg_server_stats(vc_server* s, double* ms6, int64_t* ticks) {
@@ -421,6 +469,7 @@ int vc_dbg_server_take(vc_server* s, int32_t which, int32_t cap, double* out, in
 void vc_server_destroy(vc_server* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
+  for (cudaStream_t st : s->lane_st) cudaStreamSynchronize(st);
   for (SrvTick& tk : s->inflight) {
     if (tk.ev) cudaEventDestroy(tk.ev);
     if (tk.ev0) cudaEventDestroy(tk.ev0);
@@ -436,6 +485,8 @@ void vc_server_destroy(vc_server* s) {
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->t0) cudaEventDestroy(s->t0);
   if (s->b) vc_batcher_destroy(s->b);
+  for (vc_batcher* b : s->lane_b) vc_batcher_destroy(b);
+  for (cudaStream_t st : s->lane_st) cudaStreamDestroy(st);
   delete s;
 }
 

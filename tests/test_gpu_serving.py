@@ -30,13 +30,16 @@ def _requests():
     return reqs
 
 
-@pytest.mark.parametrize("mode", ["batch", "perframe"])
-def test_served_streams_equal_solo_runs(B, mode):
+@pytest.mark.parametrize("mode,lanes", [("batch", 1), ("batch", 2), ("batch", 4), ("perframe", None)])
+def test_served_streams_equal_solo_runs(B, mode, lanes):
+    """lanes: batching tick lanes (consecutive ticks on different batchers and
+    CUDA streams, so a stream's frames of consecutive ticks run concurrently)."""
     from paper_2302_07411_gb300 import serve
 
     reqs = _requests()
+    opts = {B.VC_SOPT_LANES: lanes} if lanes else None
     srv = serve.Server(hbm_budget_bytes=1 << 30, tick_ms=3.0, mode=mode, max_frames_per_tick=4, ring=64,
-                       keep_outputs=True)
+                       keep_outputs=True, server_options=opts)
     res = srv.run(reqs)
     summ = res.summary()
     assert summ["admitted"] == len(reqs) and summ["rejected"] == 0
