@@ -280,6 +280,9 @@ void vc_batcher_destroy(vc_batcher* b);
  *   completed, 0 otherwise, -VC_ERR_ARG for a bad handle.
  * vc_server_remove: unregisters a stream (waits for its frames in flight);
  *   the caller may then destroy its context.  Errors: VC_ERR_ARG.
+ * vc_server_destroy: waits for the server's work; the contexts of streams
+ *   still registered must still exist (the server detaches its internal
+ *   streams from them), so remove a stream before destroying its context.
  * vc_server_inflight: ticks submitted and not yet drained. */
 typedef struct vc_server vc_server;
 int vc_server_create(int32_t mode, int32_t max_frames_per_tick, void* stream, vc_server** out);

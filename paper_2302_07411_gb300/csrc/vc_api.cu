@@ -326,12 +326,17 @@ cudaStream_t ctx_join(vc_ctx* c) {
 }  // namespace
 
 void vc::ctx_release_stream(vc_ctx* c, cudaStream_t s) {
-  if (!c || !s) return;
-  cudaStreamSynchronize(s);
-  if (c->last == s) {
-    // later calls order themselves after the internal streams, not after s
+  if (!c || !s || c->last != s) return;
+  // later work orders itself after the internal keystream stream, which now
+  // waits (on the device) for what was enqueued on s
+  if (c->ks_stream && c->ev_free && cudaEventRecord(c->ev_free, s) == cudaSuccess &&
+      cudaStreamWaitEvent(c->ks_stream, c->ev_free, 0) == cudaSuccess) {
     c->last = nullptr;
+    return;
   }
+  cudaGetLastError();
+  cudaStreamSynchronize(s);
+  c->last = nullptr;
 }
 
 namespace {

@@ -128,8 +128,9 @@ struct vc_ctx;
 namespace vc {
 
 // For a caller inside the library that is about to destroy CUDA stream `s`:
-// waits for the context's work on `s` and makes the context forget `s` as
-// the stream of its last call (vc_api.cu).
+// if `s` is the stream of the context's last work, the context's internal
+// keystream stream waits (on the device, the host does not block) for what
+// was enqueued on `s`, and the context forgets `s` (vc_api.cu).
 void ctx_release_stream(vc_ctx* c, cudaStream_t s);
 
 // Launchers (vc_kernels.cu).  All enqueue on `st` and return the launch error.

@@ -374,8 +374,11 @@ int vc_server_remove(vc_server* s, int32_t id) {
           break;
         }
   }
+  // the context must not keep a stream of this server as the one of its last
+  // work (the server destroys them)
+  for (cudaStream_t ls : s->lane_st) vc::ctx_release_stream(t.ctx, ls);
   if (t.cs) {
-    vc::ctx_release_stream(t.ctx, t.cs);  // the context must not keep the stream as its last one
+    vc::ctx_release_stream(t.ctx, t.cs);
     cudaStreamDestroy(t.cs);
     t.cs = nullptr;
   }
@@ -475,11 +478,12 @@ void vc_server_destroy(vc_server* s) {
     if (tk.ev0) cudaEventDestroy(tk.ev0);
     for (cudaEvent_t e : tk.job_ev) cudaEventDestroy(e);
   }
-  for (SrvStream& t : s->streams) {
-    if (t.cs) {
-      vc::ctx_release_stream(t.ctx, t.cs);
-      cudaStreamDestroy(t.cs);
+  for (SrvStream& t : s->streams) {  // streams still registered: their contexts are alive
+    if (t.active && t.ctx) {
+      for (cudaStream_t ls : s->lane_st) vc::ctx_release_stream(t.ctx, ls);
+      if (t.cs) vc::ctx_release_stream(t.ctx, t.cs);
     }
+    if (t.cs) cudaStreamDestroy(t.cs);
     if (t.join) cudaEventDestroy(t.join);
   }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);

@@ -481,7 +481,8 @@ class Server:
             res.native_ms = srv.host_stats()
             if self.record:
                 res.frame_records, res.tick_records = srv.take_records()
-            for st in active.values():
+            for sid, st in active.items():
+                srv.remove(sid)  # before its context goes: the server forgets it
                 if self.keep:
                     self.finished.append(st)
                 else:
