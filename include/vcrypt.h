@@ -394,9 +394,11 @@ int enc_join(vc_ctx* ctx, void* stream);
  *                  pixel of the next subframe (a variant: a plaintext change
  *                  in one channel then never reaches the others).  1 needs at
  *                  least 2 pixels in every subframe (else VC_ERR_LAYOUT) and
- *                  runs through encrypt_frames, decrypt_frames and
- *                  crypt_frames_host only (vc_batch_submit and
- *                  encrypt_frames_static return VC_ERR_UNSUPPORTED).  The
+ *                  the round kernels' shared memory for word carries (a
+ *                  layout whose needs exceed the device's: VC_ERR_LAYOUT);
+ *                  it runs through encrypt_frames, decrypt_frames,
+ *                  crypt_frames_host and batches (encrypt_frames_static
+ *                  returns VC_ERR_UNSUPPORTED).  The
  *                  decrypting context must use the value the encrypting one
  *                  used; checkpoints do not record it.
  * VC_OPT_CHUNK = 0 selects frames per pass automatically (default). */

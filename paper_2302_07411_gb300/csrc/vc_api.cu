@@ -1577,8 +1577,9 @@ int grow_lane(BatchLane& l, int need, cudaStream_t after) {
   return VC_OK;
 }
 
-size_t job_scratch_bytes(const Layout& L, int nf, bool with_keystream) {
-  size_t b = 2 * round256((size_t)nf * L.Npad) + 2 * round256((size_t)nf * L.NS);
+// aggw: bytes per sub-tile aggregate (4 for per-channel chains)
+size_t job_scratch_bytes(const Layout& L, int nf, bool with_keystream, int aggw = 1) {
+  size_t b = 2 * round256((size_t)nf * L.Npad) + 2 * round256((size_t)nf * L.NS * aggw);
   if (with_keystream)
     b += round256((size_t)nf * L.rounds * L.Npad) + round256((size_t)nf * L.H * sizeof(int)) +
          round256((size_t)nf * sizeof(long long));
@@ -1932,7 +1933,8 @@ void fill_lane(vc_batcher* b, BatchLane& l, const vc_job* jobs, const std::vecto
     vc_ctx* c = J.ctx;
     const Layout& L = c->L;
     const int nf = J.nframes;
-    const int v = vc::batch_variant(J.direction, L.C);
+    const bool pc = c->diff_pc && L.C > 1;
+    const int v = vc::batch_variant(J.direction, L.C, pc);
     if (!(F.variants & (1 << v))) F.vbeg[v] = F.tiles;
     F.variants |= 1 << v;
     F.vend[v] = F.tiles + nf * L.NT;
@@ -1961,10 +1963,11 @@ void fill_lane(vc_batcher* b, BatchLane& l, const vc_job* jobs, const std::vecto
     p += round256((size_t)nf * L.Npad);
     d.buf[1] = p;
     p += round256((size_t)nf * L.Npad);
+    d.pc = pc ? 1 : 0;
     d.agg[0] = p;
-    p += round256((size_t)nf * L.NS);
+    p += round256((size_t)nf * L.NS * (pc ? 4 : 1));
     d.agg[1] = p;
-    p += round256((size_t)nf * L.NS);
+    p += round256((size_t)nf * L.NS * (pc ? 4 : 1));
     d.warp_base = F.warps;
     d.tile_base = F.tiles;
     d.kmod_base = F.kmods;
@@ -1974,7 +1977,7 @@ void fill_lane(vc_batcher* b, BatchLane& l, const vc_job* jobs, const std::vecto
     }
     F.tiles += nf * L.NT;
     if (L.rounds > F.rounds) F.rounds = L.rounds;
-    const size_t sm = vc::round_smem_bytes(L);
+    const size_t sm = vc::round_smem_bytes(L, pc);
     if (sm > F.smem) F.smem = sm;
     hj[F.nj++] = d;
   }
@@ -2020,10 +2023,6 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       return VC_ERR_ARG;
     }
     if (J.nframes == 0) continue;
-    if (J.ctx->diff_pc) {
-      set_err("job %d: per-channel diffusion runs through encrypt_frames / decrypt_frames only", j);
-      return VC_ERR_UNSUPPORTED;
-    }
     if (J.ctx->L.rounds == 1 && J.d_in == J.d_out) {
       set_err("job %d: in-place with one round is not supported in a batch", j);
       return VC_ERR_ARG;
@@ -2037,15 +2036,15 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       return VC_ERR_SEQUENCE;
     }
     live.push_back(j);
-    pool_need += job_scratch_bytes(J.ctx->L, J.nframes, A == 0);
+    pool_need += job_scratch_bytes(J.ctx->L, J.nframes, A == 0, J.ctx->diff_pc ? 4 : 1);
   }
   const int nj = (int)live.size();
   if (nj == 0) return VC_OK;
   // jobs ordered by round-kernel variant (direction, channels): each variant's
   // tiles form one range
   std::stable_sort(live.begin(), live.end(), [&](int x, int y) {
-    return vc::batch_variant(jobs[x].direction, jobs[x].ctx->L.C) <
-           vc::batch_variant(jobs[y].direction, jobs[y].ctx->L.C);
+    return vc::batch_variant(jobs[x].direction, jobs[x].ctx->L.C, jobs[x].ctx->diff_pc) <
+           vc::batch_variant(jobs[y].direction, jobs[y].ctx->L.C, jobs[y].ctx->diff_pc);
   });
   int rc = VC_OK;
   for (int k = 0; k < nj; k++) {  // single-stream calls' keystream generated ahead: undone

@@ -99,12 +99,16 @@ struct JobDesc {
   int warp_base, tile_base, kmod_base;
   int mode;                 // 0: keystream + rounds; 1: rounds on keystream already in the ring; 2: keystream only
   int ring_cap, ring_slot0; // ks / sc / kmod frame slots: ring of ring_cap (0 = frames laid end to end)
-  int pad1, pad2;
+  int pc;                   // per-channel diffusion chains (C > 1): word carries and aggregates
+  int pad2;
 };
 
-// Round-kernel variants: (direction, channels) -> index dir * 3 + {C=1: 0, 3: 1, 4: 2}.
-constexpr int kBatchVariants = 6;
-__host__ __device__ inline int batch_variant(int dir, int C) { return dir * 3 + (C == 1 ? 0 : (C == 3 ? 1 : 2)); }
+// Round-kernel variants: (direction, channels, per-channel chains) -> index
+// dir * 5 + {C=1: 0, C=3: 1, C=4: 2, C=3 per channel: 3, C=4 per channel: 4}.
+constexpr int kBatchVariants = 10;
+__host__ __device__ inline int batch_variant(int dir, int C, bool pc = false) {
+  return dir * 5 + (C == 1 ? 0 : (C == 3 ? 1 : 2)) + (pc && C > 1 ? 2 : 0);
+}
 
 struct BatchHdr {
   int njobs, total_warps, total_tiles, total_kmod;

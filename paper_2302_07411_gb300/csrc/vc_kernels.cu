@@ -2898,22 +2898,24 @@ __device__ __forceinline__ RoundArgs batch_round_args(const JobDesc& d, int step
   A.ks = d.ks + (long long)slot * r * L.Npad + (long long)jr * L.Npad;
   A.ks_stride = 0;
   A.kmod = d.kmod + (long long)slot * L.H;
-  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] + (long long)f * L.NS : nullptr;
-  A.agg_out = d.dir == 0 ? d.agg[step & 1] + (long long)f * L.NS : nullptr;
+  const long long aw = d.pc ? 4 : 1;  // bytes per sub-tile aggregate
+  A.agg_in = (d.dir == 0 && step > 0) ? d.agg[(step - 1) & 1] + (long long)f * L.NS * aw : nullptr;
+  A.agg_out = d.dir == 0 ? d.agg[step & 1] + (long long)f * L.NS * aw : nullptr;
   return A;
 }
 
-// One round of every tile of the batch's jobs of one (direction, channels)
-// variant: their tiles are the contiguous range [vbeg, vend) (jobs ordered by
-// variant), so each variant is a lean kernel like the single-stream ones.
-template <int DIR, int C>
+// One round of every tile of the batch's jobs of one (direction, channels,
+// chains) variant: their tiles are the contiguous range [vbeg, vend) (jobs
+// ordered by variant), so each variant is a lean kernel like the single-stream
+// ones.
+template <int DIR, int C, bool PC = false>
 __global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc* J, const BatchHdr* hdr, int step) {
   extern __shared__ __align__(16) uint8_t smem[];
   // the item's round arguments, built once per CTA and read by every thread as
   // shared-memory broadcasts (a per-thread copy would live in local memory)
   __shared__ RoundArgs sA;
   __shared__ int s_item[2];  // the round applies, tile
-  constexpr int v = DIR * 3 + (C == 1 ? 0 : (C == 3 ? 1 : 2));
+  constexpr int v = DIR * 5 + (C == 1 ? 0 : (C == 3 ? 1 : 2)) + (PC ? 2 : 0);
   const int beg = hdr->vbeg[v], end = hdr->vend[v], nj = hdr->njobs;
   for (int item = beg + blockIdx.x; item < end; item += gridDim.x) {
     if (threadIdx.x == 0) {
@@ -2930,22 +2932,22 @@ __global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc*
     __syncthreads();
     if (s_item[0]) {
       if (DIR == 0)
-        enc_round_tile<C>(sA, 0, s_item[1], smem);
+        enc_round_tile<C, PC>(sA, 0, s_item[1], smem);
       else
-        dec_round_tile<C>(sA, 0, s_item[1], smem);
+        dec_round_tile<C, 4, PC>(sA, 0, s_item[1], smem);
     }
     __syncthreads();  // shared memory (and sA) is reused by the next item
   }
 }
 
-template <int DIR, int C>
+template <int DIR, int C, bool PC = false>
 static cudaError_t batch_round_attr(size_t smem) {
-  return allow_smem(k_batch_round<DIR, C>, (int)smem);
+  return allow_smem(k_batch_round<DIR, C, PC>, (int)smem);
 }
 
-template <int DIR, int C>
+template <int DIR, int C, bool PC = false>
 static cudaError_t batch_round_ctas(size_t smem, int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_batch_round<DIR, C>, kRoundThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_batch_round<DIR, C, PC>, kRoundThreads, smem);
 }
 
 __global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J, const BatchHdr* hdr) {
@@ -2958,7 +2960,10 @@ __global__ void __launch_bounds__(kRoundThreads) k_batch_fixup(const JobDesc* J,
       const int local = item - d.tile_base;
       const int f = local / d.L.NT;
       const int t = local - f * d.L.NT;
-      enc_fixup_tile(d.L, d.tb, d.out, d.L.N, d.agg[(d.L.rounds - 1) & 1], f, t, smem);
+      if (d.pc)
+        enc_fixup_tile_pc(d.L, d.tb, d.out, d.L.N, d.agg[(d.L.rounds - 1) & 1], f, t, smem);
+      else
+        enc_fixup_tile(d.L, d.tb, d.out, d.L.N, d.agg[(d.L.rounds - 1) & 1], f, t, smem);
     }
     __syncthreads();
   }
@@ -2972,21 +2977,30 @@ cudaError_t prepare_batch_kernels(size_t smem) {
   if (e == cudaSuccess) e = batch_round_attr<1, 1>(smem);
   if (e == cudaSuccess) e = batch_round_attr<1, 3>(smem);
   if (e == cudaSuccess) e = batch_round_attr<1, 4>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<0, 3, true>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<0, 4, true>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<1, 3, true>(smem);
+  if (e == cudaSuccess) e = batch_round_attr<1, 4, true>(smem);
   return e;
 }
 
 // CTAs per SM every round-kernel variant reaches with this shared memory.
 cudaError_t batch_ctas_per_sm(size_t smem, int* ctas) {
-  int c[kBatchVariants];
+  constexpr int NV = 10;
+  int c[NV];
   cudaError_t e = batch_round_ctas<0, 1>(smem, &c[0]);
   if (e == cudaSuccess) e = batch_round_ctas<0, 3>(smem, &c[1]);
   if (e == cudaSuccess) e = batch_round_ctas<0, 4>(smem, &c[2]);
   if (e == cudaSuccess) e = batch_round_ctas<1, 1>(smem, &c[3]);
   if (e == cudaSuccess) e = batch_round_ctas<1, 3>(smem, &c[4]);
   if (e == cudaSuccess) e = batch_round_ctas<1, 4>(smem, &c[5]);
+  if (e == cudaSuccess) e = batch_round_ctas<0, 3, true>(smem, &c[6]);
+  if (e == cudaSuccess) e = batch_round_ctas<0, 4, true>(smem, &c[7]);
+  if (e == cudaSuccess) e = batch_round_ctas<1, 3, true>(smem, &c[8]);
+  if (e == cudaSuccess) e = batch_round_ctas<1, 4, true>(smem, &c[9]);
   if (e != cudaSuccess) return e;
   int m = c[0];
-  for (int k = 1; k < kBatchVariants; k++) m = c[k] < m ? c[k] : m;
+  for (int k = 1; k < NV; k++) m = c[k] < m ? c[k] : m;
   *ctas = m;
   return cudaSuccess;
 }
@@ -3004,12 +3018,21 @@ cudaError_t launch_batch(const JobDesc* jobs, const BatchHdr* hdr, const BatchSh
   }
   if (sh.rounds > 0) {
     for (int step = 0; step < sh.rounds; step++) {
+      // variant v = dir * 5 + {C=1, C=3, C=4, C=3 per channel, C=4 per channel}
       if (sh.variants & (1 << 0)) k_batch_round<0, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
       if (sh.variants & (1 << 1)) k_batch_round<0, 3><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
       if (sh.variants & (1 << 2)) k_batch_round<0, 4><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
-      if (sh.variants & (1 << 3)) k_batch_round<1, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
-      if (sh.variants & (1 << 4)) k_batch_round<1, 3><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
-      if (sh.variants & (1 << 5)) k_batch_round<1, 4><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 3))
+        k_batch_round<0, 3, true><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 4))
+        k_batch_round<0, 4, true><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 5)) k_batch_round<1, 1><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 6)) k_batch_round<1, 3><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 7)) k_batch_round<1, 4><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 8))
+        k_batch_round<1, 3, true><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
+      if (sh.variants & (1 << 9))
+        k_batch_round<1, 4, true><<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr, step);
     }
     k_batch_fixup<<<sh.grid, kRoundThreads, sh.smem, st>>>(jobs, hdr);
   }

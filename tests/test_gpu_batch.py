@@ -160,6 +160,45 @@ def test_batch_of_alike_jobs_equals_solo_runs(B, split):
     batcher.close()
 
 
+@pytest.mark.parametrize("runahead", [0, 2])
+def test_batch_with_per_channel_streams_equals_solo_runs(B, orc, runahead):
+    """Streams with per-channel diffusion chains (VC_OPT_DIFFUSION = 1) in the
+    same ragged batches as byte-chain streams, both directions, 3 and 4
+    channels, over consecutive batches: every output equals the stream run
+    alone, and one per-channel stream's first batch equals the oracle's
+    per-channel reading."""
+    shapes = [(0, 48, 64, 3, 12, 1, 0), (1, 40, 48, 4, 5, 1, 1), (0, 64, 64, 3, 33, 0, 0), (2, 32, 80, 3, 7, 1, 0),
+              (0, 72, 48, 4, 9, 1, 1), (0, 30, 50, 3, 6, 1, 0)]  # (kind, H, W, C, n, per channel, direction)
+    batcher = B.Batcher(graph=True, runahead=runahead)
+    mixed, solo = [], []
+    for i, (k, H, W, C, n, pc, d) in enumerate(shapes):
+        for lst in (mixed, solo):
+            c = B.Cipher(k, synth.key_for_seed(k, 860 + i), H, W, C, n)
+            if pc:
+                c.set_option(B.VC_OPT_DIFFUSION, 1)
+            lst.append(c)
+    for tick in range(3):
+        jobs, outs, refs, xs = [], [], [], []
+        for i, (k, H, W, C, n, pc, d) in enumerate(shapes):
+            x = torch.from_numpy(synth.uniform_frames(2, H, W, C, seed=870 + 10 * tick + i)).cuda()
+            y = torch.empty_like(x)
+            jobs.append((mixed[i], d, x, y, 2))
+            outs.append(y)
+            xs.append(x)
+            refs.append(solo[i].encrypt(x) if d == 0 else solo[i].decrypt(x))
+        batcher.submit(jobs)
+        torch.cuda.synchronize()
+        for i in range(len(shapes)):
+            assert torch.equal(outs[i], refs[i]), f"tick {tick}, stream {i}"
+        if tick == 0:
+            k, H, W, C, n, pc, d = shapes[0]
+            o = orc.OracleCipher(k, synth.key_for_seed(k, 860), H, W, C, n, 5, per_channel=True)
+            assert np.array_equal(outs[0].cpu().numpy(), o.encrypt(xs[0].cpu().numpy()))
+    for c in mixed + solo:
+        c.close()
+    batcher.close()
+
+
 def test_batch_round_trip_and_mixing_with_single_calls(B, orc):
     """Encrypt in a batch, continue the same contexts with single-stream calls,
     then decrypt everything in a batch; the oracle agrees on the ciphertext."""

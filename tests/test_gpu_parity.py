@@ -307,11 +307,10 @@ def test_per_channel_diffusion_limits(B):
     d.set_option(B.VC_OPT_DIFFUSION, 1)
     assert d.get_option(B.VC_OPT_DIFFUSION) == 1
     x = torch.zeros((1, 8, 8, 3), dtype=torch.uint8, device="cuda")
-    batcher = B.Batcher()
-    with pytest.raises(B.VcError) as e:
-        batcher.submit([(d, 0, x, torch.empty_like(x), 1)])
+    y = torch.empty_like(x)
+    with pytest.raises(B.VcError) as e:  # the scratch-free entry point keeps the byte chains only
+        B.encrypt_frames_static(d.ctx, x, y, 1)
     assert e.value.code == 9  # VC_ERR_UNSUPPORTED
-    batcher.close()
     c.close()
     d.close()
 
