@@ -86,3 +86,25 @@ def test_result_summary_without_gpu():
     assert s["frames"] == 4 and s["fps"] == 2.0 and s["admitted"] == 2 and s["rejected_chain"] == 1
     assert s["steady_frames"] == 3 and s["steady_p50_ms"] == 3.0
     assert s["first_frame_p99_ms"] == 1.0
+
+
+def test_latency_split_of_recorded_frames():
+    """The split of each frame's latency at its submission (host arithmetic
+    over the native server's records): wait = submission - arrival, device =
+    completion - submission, frames before the steady window left out; per
+    tick, device time and the queue before the device starts it."""
+    import numpy as np
+
+    fr = np.array([[0, 0.5, 0.502, 0.510],   # before the window
+                   [1, 2.0, 2.004, 2.014],
+                   [2, 2.1, 2.101, 2.141],
+                   [1, 2.2, 2.210, 2.215]])
+    tk = np.array([[0.502, 0.503, 0.509, 1], [2.004, 2.005, 2.013, 2], [2.210, 2.230, 2.240, 1]])
+    r = serve.ServeResult("batch", frame_records=fr, tick_records=tk)
+    s = r.latency_split(steady_after_s=1.0)
+    assert s["frames"] == 3 and s["ticks"] == 2
+    assert s["wait_p50_ms"] == pytest.approx(4.0) and s["wait_p99_ms"] == pytest.approx(9.9, abs=0.05)
+    assert s["device_p50_ms"] == pytest.approx(10.0) and s["device_p99_ms"] == pytest.approx(39.4, abs=0.05)
+    assert s["tick_device_p99_ms"] == pytest.approx(10.0, abs=0.1)
+    assert s["tick_queue_p99_ms"] == pytest.approx(19.8, abs=0.05)
+    assert serve.ServeResult("batch").latency_split() == {}
