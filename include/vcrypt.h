@@ -76,8 +76,12 @@ typedef struct vc_ctx vc_ctx;
  * keyed by K -> the parameters P_m of every PRBG_a^i) on the device
  * (synchronously).  Limits: H, W <= 16384, N = H*W*C < 2^31, n <= H*W, every
  * subframe >= 2 bytes.  *out receives the context (owned by the caller; free
- * with enc_destroy).  Errors: VC_ERR_ARG, VC_ERR_KEY_RANGE, VC_ERR_LAYOUT,
- * VC_ERR_OOM, VC_ERR_CUDA. */
+ * with enc_destroy).  The device memory of contexts and batchers comes from a
+ * stream-ordered pool of the library's own on each device: memory given back
+ * is kept for reuse by later contexts until the process exits, and neither
+ * allocation nor release waits for other work on the device.
+ * Errors: VC_ERR_ARG, VC_ERR_KEY_RANGE, VC_ERR_LAYOUT, VC_ERR_OOM,
+ * VC_ERR_CUDA. */
 int enc_init(const vc_key* key, const vc_layout* layout, vc_ctx** out);
 
 /* Encrypt nframes >= 0 consecutive frames of the stream (Alg. 1: per frame

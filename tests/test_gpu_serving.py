@@ -103,3 +103,28 @@ def test_failed_stream_setup_leaves_the_others_served(B, mode):
         solo.close()
         st.cipher.close()
     srv.close()
+
+
+def test_server_options_are_checked(B):
+    """Batching-server options: tick lanes 1..8, set before the first stream
+    and after the batcher options; the queued-tick limit 0..64; none of them
+    on a per-frame server."""
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    srv = B.NativeServer(0, 2, st)
+    for bad in ((B.VC_SOPT_LANES, 0), (B.VC_SOPT_LANES, 9), (B.VC_SOPT_QUEUED_TICKS, -1),
+                (B.VC_SOPT_QUEUED_TICKS, 65), (B.VC_BOPT_RUNAHEAD, 3)):
+        with pytest.raises(B.VcError):
+            srv.set_option(*bad)
+    srv.set_option(B.VC_BOPT_KS_PRIORITY, 1)
+    srv.set_option(B.VC_SOPT_QUEUED_TICKS, 2)
+    srv.set_option(B.VC_SOPT_LANES, 3)
+    with pytest.raises(B.VcError):  # the lanes copied the batcher options: no more of those
+        srv.set_option(B.VC_BOPT_SPLIT, 0)
+    with pytest.raises(B.VcError):  # lanes only once
+        srv.set_option(B.VC_SOPT_LANES, 2)
+    srv.close()
+    per_frame = B.NativeServer(1, 2, st)
+    with pytest.raises(B.VcError):
+        per_frame.set_option(B.VC_SOPT_LANES, 2)
+    per_frame.close()
