@@ -236,10 +236,13 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next
  * A frames now (e.g. right after a stream is admitted), on the context's
- * internal keystream stream: the next frame alone first, the rest queued
- * behind it.  A call for a context whose production is still in flight adds
- * nothing.  Errors: VC_ERR_ARG (run-ahead off, null or repeated
- * context), VC_ERR_OOM, VC_ERR_CUDA. */
+ * production stream: the next frame alone first, the rest queued behind it.
+ * A call for a context whose production is still in flight adds nothing.
+ * Productions after a submit are queued behind the ones still running (at
+ * most four in flight per context); a production overwriting a ring slot
+ * waits, on the device, for the batch that read the slot.
+ * Errors: VC_ERR_ARG (run-ahead off, null or repeated context), VC_ERR_OOM,
+ * VC_ERR_CUDA. */
 int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n);
 
 /* 1 if the keystream of the context's next nframes frames has been produced
