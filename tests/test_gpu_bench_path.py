@@ -38,15 +38,16 @@ def B():
     return binding
 
 
-def _bench_options(B, g):
-    """The options bench.py sets for its default run (all defaults)."""
+def _bench_options(B, g, pc=0):
+    """The options bench.py sets for its default run (all defaults; pc: its
+    --diffusion per-channel variant)."""
     g.set_option(B.VC_OPT_CHUNK, 0)
     g.set_option(B.VC_OPT_OVERLAP, 1)
     g.set_option(B.VC_OPT_TILE_ROWS, 0)
     g.set_option(B.VC_OPT_PLCM_INT, 1)
     g.set_option(B.VC_OPT_KS_LANES, 2)
     g.set_option(B.VC_OPT_KS_SM_WARPS, -1)
-    g.set_option(B.VC_OPT_DIFFUSION, 0)
+    g.set_option(B.VC_OPT_DIFFUSION, pc)
 
 
 def _sample(passes, f0, rng):
@@ -61,8 +62,8 @@ def _sample(passes, f0, rng):
     return out
 
 
-@pytest.mark.parametrize("kind", [0])
-def test_bench_sequence_768_n4096_two_calls(B, orc, kind):
+@pytest.mark.parametrize("kind,pc", [(0, 0), (0, 1)])
+def test_bench_sequence_768_n4096_two_calls(B, orc, kind, pc):
     H = W = 768
     C, n, r = 3, 4096, 5
     calls = (240, 64)
@@ -71,7 +72,7 @@ def test_bench_sequence_768_n4096_two_calls(B, orc, kind):
     X = np.ascontiguousarray(np.concatenate([clip] * ((total + 15) // 16))[:total])
     key = synth.key_for_seed(kind, 100)
     g = B.Cipher(kind, key, H, W, C, n, r)
-    _bench_options(B, g)
+    _bench_options(B, g, pc)
     d_in = torch.from_numpy(X).cuda()
     d_out = torch.empty_like(d_in)
     rng = np.random.default_rng(5)
@@ -92,7 +93,7 @@ def test_bench_sequence_768_n4096_two_calls(B, orc, kind):
     assert plans[1]["first_runahead"] and plans[1]["passes"][0] == plans[0]["runahead_next"]
     assert plans[0]["ks_sm_warps"] > 0
     Y = d_out.cpu().numpy()
-    ref = orc.OracleCipher(kind, key, H, W, C, n, r)
+    ref = orc.OracleCipher(kind, key, H, W, C, n, r, per_channel=bool(pc))
     for f in range(total):
         if f in sample:
             exp = ref.encrypt(X[f])
@@ -102,7 +103,7 @@ def test_bench_sequence_768_n4096_two_calls(B, orc, kind):
     assert calls[0] in sample  # the first frame of call 2
     # decryption with the same options returns every frame of both calls
     dd = B.Cipher(kind, key, H, W, C, n, r)
-    _bench_options(B, dd)
+    _bench_options(B, dd, pc)
     back = torch.empty_like(d_out)
     f0 = 0
     for nf in calls:
