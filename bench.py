@@ -254,7 +254,7 @@ def serving_capacity() -> dict:
     from paper_2302_07411_gb300 import serve
 
     out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
-    b = serve.capacity("batch", 768, 768, counts=(192, 256, 320, 352, 384, 448), seconds=3.0)
+    b = serve.capacity("batch", 768, 768, counts=(256, 320, 384, 448, 512), seconds=3.0)
     p = serve.capacity("perframe", 768, 768, counts=(64, 96, 128, 160, 192, 256), seconds=2.5)
     # the same with PLCM streams only (2DLASM keystream is binary64-bound and
     # about eight times the work of PLCM per frame)

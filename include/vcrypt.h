@@ -224,6 +224,11 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
  *                      batches' round kernels, on a stream of higher priority,
  *                      take the SMs that free up first).  It applies to the
  *                      streams whose first production comes after it is set.
+ * VC_BOPT_KS_URGENT:   1: a production for a stream that has no frame
+ *                      produced ahead of its next one (it fell behind, or it
+ *                      was just admitted) runs on a second production stream
+ *                      of the device's highest priority, still after the
+ *                      stream's earlier productions; 0 (default): all on one.
  * Errors: VC_ERR_ARG. */
 #define VC_BOPT_GRAPH 1
 #define VC_BOPT_CTAS_PER_SM 2
@@ -232,6 +237,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
 #define VC_BOPT_SPLIT 5
 #define VC_BOPT_KS_PLACE 6
 #define VC_BOPT_KS_PRIORITY 7
+#define VC_BOPT_KS_URGENT 8
 int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value);
 
 /* With run-ahead on: start producing the keystream of each context's next

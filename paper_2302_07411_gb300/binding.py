@@ -21,7 +21,7 @@ VC_PLCM, VC_2DLASM, VC_LOGISTIC = 0, 1, 2
 VC_OPT_CHUNK, VC_OPT_PLCM_INT, VC_OPT_KS_LANES, VC_OPT_OVERLAP, VC_OPT_TILE_ROWS, VC_OPT_KS_SM_WARPS = 1, 2, 3, 4, 5, 6
 VC_OPT_RUNAHEAD_CALLS, VC_OPT_DIFFUSION = 7, 8
 VC_BOPT_GRAPH, VC_BOPT_CTAS_PER_SM, VC_BOPT_RUNAHEAD, VC_BOPT_SINE, VC_BOPT_SPLIT, VC_BOPT_KS_PLACE = 1, 2, 3, 4, 5, 6
-VC_BOPT_KS_PRIORITY = 7
+VC_BOPT_KS_PRIORITY, VC_BOPT_KS_URGENT = 7, 8
 VC_SOPT_QUEUED_TICKS, VC_SOPT_LANES = 100, 101
 ERRORS = {1: "VC_ERR_ARG", 2: "VC_ERR_KEY_RANGE", 3: "VC_ERR_LAYOUT", 4: "VC_ERR_CUDA", 5: "VC_ERR_OOM",
           6: "VC_ERR_TIMEOUT", 7: "VC_ERR_SEQUENCE", 8: "VC_ERR_STATE", 9: "VC_ERR_UNSUPPORTED"}

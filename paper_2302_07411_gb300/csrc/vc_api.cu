@@ -242,6 +242,11 @@ struct vc_ctx {
   // the productions' stream (created with the ring, at the priority the
   // batcher asks for: VC_BOPT_KS_PRIORITY)
   cudaStream_t prod_stream = nullptr;
+  // a second production stream of the device's highest priority, for the
+  // productions of a stream with no frame produced ahead (VC_BOPT_KS_URGENT);
+  // last_prod: the stream of the last production (chain order across the two)
+  cudaStream_t prod_urgent = nullptr;
+  cudaStream_t last_prod = nullptr;
   int64_t produced = 0;
   // productions of the ring run on ks_stream; the last eight are tracked so
   // that readiness can be polled without blocking
@@ -294,6 +299,7 @@ void sync_all(vc_ctx* c) {
   if (c->last) cudaStreamSynchronize(c->last);
   if (c->ks_stream) cudaStreamSynchronize(c->ks_stream);
   if (c->prod_stream) cudaStreamSynchronize(c->prod_stream);
+  if (c->prod_urgent) cudaStreamSynchronize(c->prod_urgent);
   if (c->sc_stream) cudaStreamSynchronize(c->sc_stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   if (c->d2h_stream) cudaStreamSynchronize(c->d2h_stream);
@@ -318,7 +324,7 @@ cudaStream_t ctx_join(vc_ctx* c) {
     sync_all(c);
     return nullptr;
   }
-  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream, c->prod_stream, c->sc_stream})
+  for (cudaStream_t o : {c->last, c->copy_stream, c->d2h_stream, c->prod_stream, c->prod_urgent, c->sc_stream})
     if (o && o != ks && cudaEventRecord(c->ev_free, o) == cudaSuccess) cudaStreamWaitEvent(ks, c->ev_free, 0);
   return ks;
 }
@@ -1048,6 +1054,7 @@ int enc_sync_status(vc_ctx* c) {
   if (e == cudaSuccess && c->d2h_stream) e = cudaStreamSynchronize(c->d2h_stream);
   if (e == cudaSuccess && c->ks_stream) e = cudaStreamSynchronize(c->ks_stream);
   if (e == cudaSuccess && c->prod_stream) e = cudaStreamSynchronize(c->prod_stream);
+  if (e == cudaSuccess && c->prod_urgent) e = cudaStreamSynchronize(c->prod_urgent);
   if (e == cudaSuccess && c->sc_stream) e = cudaStreamSynchronize(c->sc_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1060,7 +1067,7 @@ int enc_sync_status(vc_ctx* c) {
 int enc_join(vc_ctx* c, void* stream) {
   if (!c) return VC_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  for (cudaStream_t o : {c->ks_stream, c->prod_stream, c->sc_stream, c->copy_stream, c->d2h_stream})
+  for (cudaStream_t o : {c->ks_stream, c->prod_stream, c->prod_urgent, c->sc_stream, c->copy_stream, c->d2h_stream})
     if (o && o != st) {
       VC_CUDA(cudaEventRecord(c->ev_free, o));
       VC_CUDA(cudaStreamWaitEvent(st, c->ev_free, 0));
@@ -1235,6 +1242,7 @@ void destroy_ctx(vc_ctx* c, bool wait) {
   if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
   if (c->ks_stream) cudaStreamDestroy(c->ks_stream);
   if (c->prod_stream) cudaStreamDestroy(c->prod_stream);
+  if (c->prod_urgent) cudaStreamDestroy(c->prod_urgent);
   if (c->sc_stream) cudaStreamDestroy(c->sc_stream);
   for (int b = 0; b < 2; b++) {
     if (c->ev_ks[b]) cudaEventDestroy(c->ev_ks[b]);
@@ -1509,6 +1517,7 @@ struct vc_batcher {
   int split = -1;    // long-chain lane: -1 automatic, 0 never, 1 whenever the jobs differ
   int last_split = 0;  // jobs the last batch ran in the long-chain lane
   int ks_place = 0;    // run-ahead productions: 0 shared SMs, 1 as the context's own calls place them
+  bool ks_urgent = false;  // productions for a stream with no frame produced ahead go to its urgent stream
   bool ks_low = false;  // run-ahead productions at the device's lowest stream priority (else its highest)
   BatchLane cons_long;  // the long-chain lane (its own staging and graphs)
   cudaStream_t side = nullptr;  // the long-chain lane's stream
@@ -1593,6 +1602,7 @@ int ensure_ring(vc_ctx* c, int cap, bool low_priority) {
     int least = 0, greatest = 0;
     VC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     VC_CUDA(cudaStreamCreateWithPriority(&c->prod_stream, cudaStreamNonBlocking, low_priority ? least : greatest));
+    VC_CUDA(cudaStreamCreateWithPriority(&c->prod_urgent, cudaStreamNonBlocking, greatest));
   }
   if (c->ring_cap >= cap) return VC_OK;
   if (c->ring_cap > 0 && c->produced != c->frame) {
@@ -1663,10 +1673,15 @@ int productions_in_flight(vc_ctx* c) {
 // place: 0 one-warp CTAs sharing the SMs, 1 the placement of the context's own
 // calls (VC_OPT_KS_SM_WARPS); an explicit VC_OPT_KS_SM_WARPS > 0 holds SMs in
 // both.
-int produce(vc_ctx* c, int64_t target, int place) {
+// urgent: on the high-priority production stream (the stream has no frame
+// produced ahead of its next one), after the last production wherever it ran.
+int produce(vc_ctx* c, int64_t target, int place, bool urgent = false) {
   if (c->produced >= target) return VC_OK;
   vc::NvtxRange range("vc.keystream");
-  cudaStream_t ks = c->prod_stream;
+  cudaStream_t ks = (urgent && c->prod_urgent) ? c->prod_urgent : c->prod_stream;
+  if (c->last_prod && c->last_prod != ks && c->nprod > 0)  // the chains continue from the last production
+    VC_CUDA(cudaStreamWaitEvent(ks, c->ev_prod[(c->nprod - 1) % vc_ctx::kProdEv], 0));
+  c->last_prod = ks;
   if (c->produced == c->frame && !c->batch_pending) {  // single-stream work on this context first
     for (cudaStream_t o : {c->last, c->ks_stream})
       if (o) {
@@ -1854,6 +1869,10 @@ int vc_batcher_set_option(vc_batcher* b, int32_t option, int64_t value) {
     case VC_BOPT_KS_PRIORITY:
       if (value != 0 && value != 1) return VC_ERR_ARG;
       b->ks_low = value == 1;
+      return VC_OK;
+    case VC_BOPT_KS_URGENT:
+      if (value != 0 && value != 1) return VC_ERR_ARG;
+      b->ks_urgent = value == 1;
       return VC_OK;
   }
   return VC_ERR_ARG;
@@ -2084,7 +2103,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
       rc = ensure_ring(c, 2 * A + 1, b->ks_low);
       if (rc) return rc;
       if (c->produced < c->frame + J.nframes) {
-        rc = produce(c, c->frame + J.nframes + A, b->ks_place);
+        rc = produce(c, c->frame + J.nframes + A, b->ks_place, b->ks_urgent);
         if (rc) return rc;
       }
       rc = poll_production(c);
@@ -2147,7 +2166,7 @@ int vc_batch_submit(vc_batcher* b, const vc_job* jobs, int32_t njobs, void* stre
     for (int k = 0; k < nj; k++) {
       vc_ctx* c = jobs[live[k]].ctx;
       if (c->produced >= c->frame + A || productions_in_flight(c) >= vc_ctx::kProdEv / 2) continue;
-      rc = produce(c, c->frame + A, b->ks_place);
+      rc = produce(c, c->frame + A, b->ks_place, b->ks_urgent && c->produced <= c->frame);
       if (rc) return rc;
     }
   }
@@ -2177,7 +2196,7 @@ int vc_batch_prefetch(vc_batcher* b, vc_ctx* const* ctxs, int32_t n) {
     // nothing (coalesced, like the top-ups)
     bool issued = false;
     if (c->produced < c->frame + 1) {
-      rc = produce(c, c->frame + 1, b->ks_place);
+      rc = produce(c, c->frame + 1, b->ks_place, b->ks_urgent);
       if (rc) return rc;
       issued = true;
     }

@@ -312,7 +312,12 @@ class Server:
         (VC_SOPT_LANES 2): consecutive ticks on two batchers and streams, so
         that a tick whose round kernels wait for SMs does not hold up the
         next one (320 streams of 768x768 at p99 12 ms with two lanes, 392 ms
-        with one, in the same run)."""
+        with one, in the same run).  Urgent productions (VC_BOPT_KS_URGENT
+        1: a stream with no frame produced ahead gets its next production on
+        a stream of the highest priority) are left off: in an A/B of three
+        repeats both held 320 streams of 768x768 at p99 12 ms, and past the
+        capacity (384) the urgent form collapsed further (p99 1.2-1.4 s
+        against 0.4-0.9 s)."""
         import torch
 
         self.torch = torch
