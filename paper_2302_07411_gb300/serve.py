@@ -513,10 +513,12 @@ def capacity(mode: str, H: int, W: int, fps: int = 24, budget_ms: float = 1000.0
 
     best, runs = 0, []
     steady_from = ramp_s + warm_s
-    # one short untimed run first: one-time costs (module loading, first
-    # allocations, shared-memory configuration) stay out of the search
-    warm = synth.serving_workload(1, seed=seed, rate_per_s=1.0 / ramp_s, resolutions=((H, W),),
-                                  fps_choices=(fps,), duration_s=(0.5, 0.5))
+    # one short untimed run first, as large as the first count: one-time
+    # costs (module loading, the memory pool's growth, shared-memory
+    # configuration) stay out of the search
+    nw = counts[0] if counts else 1
+    warm = synth.serving_workload(nw, seed=seed + 1, rate_per_s=nw / ramp_s, resolutions=((H, W),),
+                                  fps_choices=(fps,), duration_s=(1.0, 1.0))
     srv = Server(hbm_budget_bytes=hbm_budget_bytes, tick_ms=tick_ms, mode=mode, cipher_options=cipher_options)
     srv.run(warm)
     srv.close()
