@@ -323,6 +323,30 @@ def test_tile_shapes_do_not_change_the_ciphertext(B, orc, tile_rows):
     _check_enc_dec(B, orc, 0, synth.key_for_seed(0, 17), X, 9, 5, tile_rows=tile_rows)
 
 
+@pytest.mark.parametrize("tile_rows", [4, 8, 16, 32])
+@pytest.mark.parametrize("H,W,C,per_channel", [(50, 64, 3, False), (100, 160, 3, False), (36, 64, 3, True),
+                                               (200, 48, 3, False), (72, 48, 4, False), (66, 96, 4, True)])
+def test_decrypt_band_heights(B, orc, tile_rows, H, W, C, per_channel):
+    """Decryption of the oracle's ciphertext in bands of 4 to 32 rows (the
+    scatter form: rows of whole 16-byte pieces), with heights that leave a
+    partial last band, widths above and below the height, and words of the
+    output shared between the runs of neighbouring bands."""
+    n, r = 11, 3
+    X = synth.uniform_frames(2, H, W, C, seed=H * W + tile_rows)
+    key = synth.key_for_seed(0, 470 + tile_rows)
+    ref = orc.OracleCipher(0, key, H, W, C, n, r, per_channel=per_channel)
+    Y = ref.encrypt(X)
+    g = B.Cipher(0, key, H, W, C, n, r)
+    if per_channel:
+        g.set_option(B.VC_OPT_DIFFUSION, 1)
+    g.set_option(B.VC_OPT_TILE_ROWS, tile_rows)
+    Xg = g.decrypt(dev(Y))
+    g.sync()
+    got = host(Xg)
+    assert np.array_equal(got, X), f"{(got != X).sum()} bytes differ"
+    g.close()
+
+
 @pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("warps", [1, 2, 4])
 def test_keystream_on_reserved_sms(B, orc, kind, warps):
