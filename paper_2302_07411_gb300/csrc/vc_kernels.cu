@@ -2566,6 +2566,14 @@ __device__ __forceinline__ void dec_scatter_tile(const RoundArgs& A, const int f
   uint8_t* Out = A.out + f * A.out_stride;
   const uint8_t* KS = A.ks + f * A.ks_stride;
   const int* kmod = A.kmod + (long long)f * L.H;
+  if (threadIdx.x == 0) {
+    // the band's ciphertext and keystream towards L2 ahead of the unit loads
+    // (band starts and sizes are multiples of 16 bytes)
+    const long long qb = (long long)a0 * L.W * C;
+    const uint32_t nb = (uint32_t)(Te * L.W * C);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(Cin + qb), "r"(nb) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(KS + qb), "r"(nb) : "memory");
+  }
   if (threadIdx.x < Te) s_kmod[threadIdx.x] = __ldg(&kmod[a0 + threadIdx.x]);
   auto cpx = [&](const uint8_t* base, int pp) -> uint32_t {  // the C bytes of pixel pp
     uint32_t v = 0;
