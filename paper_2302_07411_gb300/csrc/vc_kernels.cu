@@ -2922,7 +2922,7 @@ __global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc*
   // the item's round arguments, built once per CTA and read by every thread as
   // shared-memory broadcasts (a per-thread copy would live in local memory)
   __shared__ RoundArgs sA;
-  __shared__ int s_item[2];  // the round applies, tile
+  __shared__ int s_item[3];  // the round applies, tile, decryption in scatter form
   constexpr int v = DIR * 5 + (C == 1 ? 0 : (C == 3 ? 1 : 2)) + (PC ? 2 : 0);
   const int beg = hdr->vbeg[v], end = hdr->vend[v], nj = hdr->njobs;
   for (int item = beg + blockIdx.x; item < end; item += gridDim.x) {
@@ -2935,14 +2935,28 @@ __global__ void __launch_bounds__(kRoundThreads, 3) k_batch_round(const JobDesc*
         const int f = local / d.L.NT;
         s_item[1] = local - f * d.L.NT;
         sA = batch_round_args(d, step, f);
+        // the scatter form (as for a single stream): rows of whole 16-byte
+        // pieces, 16-byte aligned frames, input and output apart
+        const uintptr_t al = reinterpret_cast<uintptr_t>(sA.in) | reinterpret_cast<uintptr_t>(sA.ks) |
+                             reinterpret_cast<uintptr_t>(sA.out);
+        s_item[2] = DIR == 1 && C > 1 && (d.L.W & 15) == 0 && (al & 15) == 0 &&
+                    (sA.in + d.L.N <= sA.out || sA.out + d.L.N <= sA.in);
       }
     }
     __syncthreads();
     if (s_item[0]) {
-      if (DIR == 0)
+      if (DIR == 0) {
         enc_round_tile<C, PC>(sA, 0, s_item[1], smem);
-      else
-        dec_round_tile<C, 4, PC>(sA, 0, s_item[1], smem);
+      } else {
+        if constexpr (C > 1) {
+          if (s_item[2])
+            dec_scatter_tile<C, PC>(sA, 0, s_item[1], smem);
+          else
+            dec_round_tile<C, 4, PC>(sA, 0, s_item[1], smem);
+        } else {
+          dec_round_tile<C, 4, PC>(sA, 0, s_item[1], smem);
+        }
+      }
     }
     __syncthreads();  // shared memory (and sA) is reused by the next item
   }
