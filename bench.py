@@ -254,11 +254,11 @@ def serving_capacity() -> dict:
     from paper_2302_07411_gb300 import serve
 
     out = {"resolution": "768x768x3", "fps": 24, "p99_budget_ms": round(1000 / 24, 2)}
-    b = serve.capacity("batch", 768, 768, counts=(256, 320, 384, 448, 512), seconds=3.0)
+    b = serve.capacity("batch", 768, 768, counts=(256, 288, 320, 384, 448, 512), seconds=3.0)
     p = serve.capacity("perframe", 768, 768, counts=(64, 96, 128, 160, 192, 256), seconds=2.5)
     # the same with PLCM streams only (2DLASM keystream is binary64-bound and
     # about eight times the work of PLCM per frame)
-    bp = serve.capacity("batch", 768, 768, counts=(640, 768, 896, 1024), seconds=3.0, kinds=(0,))
+    bp = serve.capacity("batch", 768, 768, counts=(640, 768, 896, 1024, 1152, 1280, 1408), seconds=3.0, kinds=(0,))
     out["batched_streams"] = b["max_streams"]
     out["per_frame_streams"] = p["max_streams"]
     out["batched_streams_plcm_only"] = bp["max_streams"]
