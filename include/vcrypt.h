@@ -118,6 +118,23 @@ int decrypt_frames_pitched(vc_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int
 int crypt_frames_host(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
                       void* stream);
 
+/* crypt_frames_host without waiting for the result: enqueues the uploads, the
+ * passes (on `stream`) and the downloads, and returns.  done_event, if not
+ * null, is a cudaEvent_t of the caller, recorded after the call's last
+ * download: once it has completed, h_out holds the result.  Until then h_in
+ * must stay unchanged and h_out unread (pinned host memory, so the copies run
+ * asynchronously; pageable memory makes the copies wait on the host).
+ * enc_sync_status also waits for every download issued.  Consecutive calls on
+ * one context pipeline: a call's first uploads and keystream start while the
+ * previous call's last passes and downloads run (three staging buffers in
+ * turn, each uploaded again after its previous download).  `stream` is not
+ * ordered after the downloads.  As for encrypt_frames, the calls on one
+ * context follow one another in the order of the stream they are given; a
+ * caller that changes streams orders them itself.  Errors as
+ * crypt_frames_host. */
+int crypt_frames_host_async(vc_ctx* ctx, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
+                            void* stream, void* done_event);
+
 /* ---- encryption without allocation ----
  * The paper has no counterpart of this entry point.  It serves callers that
  * must not allocate device memory while they work: programs whose GPU memory

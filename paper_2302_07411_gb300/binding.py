@@ -61,6 +61,7 @@ def lib():
             "encrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "decrypt_frames": (C.c_int, [p, p, p, i32, p]),
             "crypt_frames_host": (C.c_int, [p, i32, p, p, i32, p]),
+            "crypt_frames_host_async": (C.c_int, [p, i32, p, p, i32, p, p]),
             "encrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
             "decrypt_frames_pitched": (C.c_int, [p, p, p, i32, sz, p]),
             "vc_dbg_call_plan": (C.c_int, [p, i32, p, i32, p]),
@@ -200,6 +201,13 @@ def encrypt_frames_static(ctx, d_in, d_out, nframes: int, stream=None) -> None:
 def crypt_frames_host(ctx, direction: int, h_in, h_out, nframes: int, stream=None) -> None:
     _check(lib().crypt_frames_host(ctx, direction, _hptr(h_in), _hptr(h_out), nframes, _stream(stream)),
            "crypt_frames_host")
+
+
+def crypt_frames_host_async(ctx, direction: int, h_in, h_out, nframes: int, stream=None, done_event=None) -> None:
+    """crypt_frames_host without the wait; done_event: a torch.cuda.Event recorded after the last download."""
+    ev = C.c_void_p(done_event.cuda_event) if done_event is not None else None
+    _check(lib().crypt_frames_host_async(ctx, direction, _hptr(h_in), _hptr(h_out), nframes, _stream(stream), ev),
+           "crypt_frames_host_async")
 
 
 def enc_save_state(ctx) -> bytes:
@@ -343,6 +351,10 @@ class Cipher:
     def crypt_host(self, direction: int, h_in, h_out, stream=None) -> None:
         nframes = (h_in.size if isinstance(h_in, np.ndarray) else h_in.numel()) // self.N
         crypt_frames_host(self.ctx, direction, h_in, h_out, nframes, stream)
+
+    def crypt_host_async(self, direction: int, h_in, h_out, stream=None, done_event=None) -> None:
+        nframes = (h_in.size if isinstance(h_in, np.ndarray) else h_in.numel()) // self.N
+        crypt_frames_host_async(self.ctx, direction, h_in, h_out, nframes, stream, done_event)
 
     def save_state(self) -> bytes:
         return enc_save_state(self.ctx)

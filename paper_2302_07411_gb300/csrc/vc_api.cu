@@ -267,6 +267,7 @@ struct vc_ctx {
   static constexpr int kIoBufs = 3;
   uint8_t* d_io[kIoBufs] = {nullptr, nullptr, nullptr};
   int io_cap = 0;
+  long long io_uses = 0;  // staging passes issued so far (buffer io_uses % kIoBufs is the next one)
   cudaStream_t copy_stream = nullptr;  // uploads (and table builds)
   cudaStream_t d2h_stream = nullptr;   // downloads of host-buffer calls
   cudaEvent_t ev_io[3 * kIoBufs] = {};
@@ -913,8 +914,12 @@ int ensure_io(vc_ctx* c, int frames) {
   return VC_OK;
 }
 
-int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
-                      void* stream) {
+namespace {
+
+// The host-buffer path: wait = the call returns once h_out holds the result;
+// otherwise `done` (if any) is recorded after the call's last download.
+int crypt_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes, void* stream,
+               bool wait, cudaEvent_t done_ev) {
   if (!c || nframes < 0 || (direction != 0 && direction != 1) || (nframes > 0 && (!h_in || !h_out))) {
     set_err("invalid argument");
     return VC_ERR_ARG;
@@ -935,17 +940,20 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   if (rc) return rc;
   // Three streams and three staging buffers: uploads (copy_stream), passes
   // (st, in place in the buffer) and downloads (d2h_stream) of consecutive
-  // passes overlap; a buffer is uploaded again once its download is done.
+  // passes overlap, also across calls; a buffer is uploaded again once its
+  // previous download is done.
   constexpr int kIo = vc_ctx::kIoBufs;
-  cudaEvent_t* up = c->ev_io;             // upload k done
-  cudaEvent_t* done = c->ev_io + kIo;     // pass k done
-  cudaEvent_t* down = c->ev_io + 2 * kIo; // download k done
+  cudaEvent_t* up = c->ev_io;             // upload into buffer b done
+  cudaEvent_t* done = c->ev_io + kIo;     // pass in buffer b done
+  cudaEvent_t* down = c->ev_io + 2 * kIo; // download from buffer b done
   long long f0 = 0;
+  int b = 0;
   for (int k = 0; k < (int)plan.size(); f0 += plan[k], k++) {
     const int nf = plan[k];
-    const int b = k % kIo;
+    b = (int)(c->io_uses % kIo);
     uint8_t* buf = c->d_io[b];
-    if (k >= kIo) VC_CUDA(cudaStreamWaitEvent(c->copy_stream, down[b], 0));
+    if (c->io_uses >= kIo) VC_CUDA(cudaStreamWaitEvent(c->copy_stream, down[b], 0));
+    c->io_uses++;
     VC_CUDA(cudaMemcpyAsync(buf, h_in + (size_t)f0 * N, nf * N, cudaMemcpyHostToDevice, c->copy_stream));
     VC_CUDA(cudaEventRecord(up[b], c->copy_stream));
     VC_CUDA(cudaStreamWaitEvent(st, up[b], 0));
@@ -962,10 +970,26 @@ int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t
   c->produced_done = c->frame;
   rc = spec_issue(c, next_first);
   if (rc) return rc;
+  if (!wait) {
+    if (done_ev) VC_CUDA(cudaEventRecord(done_ev, c->d2h_stream));  // after the call's last download
+    return VC_OK;
+  }
   VC_CUDA(cudaStreamSynchronize(c->d2h_stream));
   VC_CUDA(cudaStreamSynchronize(c->copy_stream));
   VC_CUDA(cudaStreamSynchronize(st));
   return VC_OK;
+}
+
+}  // namespace
+
+int crypt_frames_host(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
+                      void* stream) {
+  return crypt_host(c, direction, h_in, h_out, nframes, stream, true, nullptr);
+}
+
+int crypt_frames_host_async(vc_ctx* c, int32_t direction, const uint8_t* h_in, uint8_t* h_out, int32_t nframes,
+                            void* stream, void* done_event) {
+  return crypt_host(c, direction, h_in, h_out, nframes, stream, false, (cudaEvent_t)done_event);
 }
 
 namespace {

@@ -407,6 +407,40 @@ def test_host_buffer_entry_point(B, direction):
     assert np.array_equal(out, ref)
 
 
+def test_host_async_calls_pipeline(B):
+    """crypt_frames_host_async calls issued back to back (several passes per
+    call, so the staging buffers rotate across calls; each call's done event
+    waited at the end) give the bytes of synchronous calls, call for call, and
+    decrypt back."""
+    key = synth.key_for_seed(0, 91)
+    H, W, C, n = 96, 128, 3, 7
+    X = synth.uniform_frames(24, H, W, C, seed=92)
+    a = B.Cipher(0, key, H, W, C, n, 5)
+    b = B.Cipher(0, key, H, W, C, n, 5)
+    d = B.Cipher(0, key, H, W, C, n, 5)
+    for c in (a, b, d):
+        c.set_chunk(3)
+    h_in = torch.from_numpy(X).pin_memory()
+    outs = [torch.empty((8, H, W, C), dtype=torch.uint8).pin_memory() for _ in range(3)]
+    back = [torch.empty((8, H, W, C), dtype=torch.uint8).pin_memory() for _ in range(3)]
+    evs = [torch.cuda.Event() for _ in range(3)]
+    for k in range(3):
+        a.crypt_host_async(0, h_in[8 * k: 8 * k + 8], outs[k], done_event=evs[k])
+    for k in range(3):
+        evs[k].synchronize()
+        ref = torch.empty_like(outs[k]).pin_memory()
+        b.crypt_host(0, h_in[8 * k: 8 * k + 8], ref)
+        assert torch.equal(outs[k], ref), f"call {k}: {(outs[k] != ref).sum().item()} bytes differ"
+    for k in range(3):
+        d.crypt_host_async(1, outs[k], back[k])
+    d.sync()
+    for k in range(3):
+        assert np.array_equal(back[k].numpy(), X[8 * k: 8 * k + 8]), f"call {k} does not decrypt back"
+    assert a.frame_index == b.frame_index == d.frame_index == 24
+    for c in (a, b, d):
+        c.close()
+
+
 def test_invalid_arguments_are_errors(B):
     with pytest.raises(B.VcError) as e:
         B.Cipher(0, [0.3, 0.6, 0.5, 0.2], 16, 16)
