@@ -2200,7 +2200,7 @@ __device__ __forceinline__ void enc_round_tile(const RoundArgs& A, const int f, 
 }
 
 template <int C, bool PC>
-__global__ void __launch_bounds__(kRoundThreads, 4) k_enc_round(RoundArgs A) {
+__global__ void __launch_bounds__(kRoundThreads, 3) k_enc_round(RoundArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   enc_round_tile<C, PC>(A, blockIdx.y, blockIdx.x, smem);
 }
