@@ -197,7 +197,7 @@ def run_reference(a) -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u8",
             "data": "synthetic", "config": config(a, 1),
             "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{tot_frames} consecutive frames of the workload ({per_step:.0f} s per step)"},
+                             "sample": f"{tot_frames} consecutive frames of the workload (at most {per_step:.0f} s per step)"},
             "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
